@@ -1,0 +1,151 @@
+/*
+ * hz.h -- C ABI of the GB300 sweeping-preconditioner Helmholtz solver.
+ *
+ * Method: C. C. Stolk, "An improved sweeping domain decomposition
+ * preconditioner for the Helmholtz equation" (arXiv 1412.0464).  The library
+ * solves the discretised Helmholtz equation with PML truncation (Section 2.1,
+ * Eqs. 3-5; discretisation Eq. 40) by restarted GMRES preconditioned by the
+ * double-sweep domain decomposition with PML transmission (Section 2.2,
+ * Tables 2-3), optionally inside the two-grid sweeping preconditioner
+ * (Section 4, Appendix A).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  Along each axis there are n interior cells of size h = 1/n and w_out
+ *   PML cells on each side: n_cells = n + 2 w_out cells, N = n_cells - 1
+ *   unknowns (Dirichlet nodes on the outer boundary, Section 2.2).
+ * Layout.  Fields are dense, contiguous, [rhs][y][x] (2-D), x fastest; x is
+ *   the sweep axis.  Complex values are interleaved (re, im) doubles.
+ * System.  A is Eq. 40 multiplied by h^d (complex symmetric).  The right-hand
+ *   side b of A u = b is h^d f / (alpha_1 alpha_2): a unit point source
+ *   f = h^-d at an interior node is b = 1 there.
+ * Memory.  Every array argument is a DEVICE pointer owned by the caller and
+ *   borrowed only for the duration of the call (work is enqueued on `stream`
+ *   and the call returns after it has completed unless stated otherwise).
+ *   The handle owns every internal buffer (factors, workspaces, Krylov basis).
+ * Streams.  `stream` is a cudaStream_t (passed as void*); 0 is the legacy
+ *   default stream.
+ * Errors.  Calls return an hz_status and never throw or abort; hz_last_error
+ *   gives a one-line message.  A handle is not thread-safe.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } hz_c128;
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_EINVAL = 1,        /* bad argument (sizes, odd J for the X-sweep, n_rhs > max_rhs, ...) */
+  HZ_ENOMEM = 2,        /* device allocation failed */
+  HZ_ECUDA = 3,         /* a CUDA call or kernel failed */
+  HZ_ENOTFACTORED = 4,  /* hz_solve / hz_precond before hz_factor */
+  HZ_ENOTCONV = 5,      /* GMRES hit max_iter; u holds the last iterate, stats are filled */
+  HZ_ETIMEOUT = 6,      /* a bounded device-side wait gave up (no hang, context usable) */
+  HZ_EINACCURATE = 7    /* true residual and GMRES estimate disagree by > 100x */
+} hz_status;
+
+enum { HZ_SWEEP_UD = 0, HZ_SWEEP_X = 1 };        /* SweepingPrecUD / SweepingPrecX (Table 3) */
+enum { HZ_PLAIN_FP64 = 0, HZ_MIXED = 1 };        /* preconditioner in complex128 / complex64 */
+
+typedef struct {
+  int    dim;           /* 2 (3-D is not built yet: HZ_EINVAL) */
+  int    n;             /* interior cells per axis (even when two_grid) */
+  int    w_out;         /* outer PML cells per side */
+  double omega;         /* angular frequency; k = omega / c, k^2 = omega^2 m */
+  double s_pml_out;     /* outer PML strength S_pml (Section 2.1) */
+  double s_pml_dd;      /* DD PML strength (Section 6.1: 15/20/25 for w = 3/4/5) */
+  int    J;             /* slabs along x (even for HZ_SWEEP_X) */
+  int    w_dd;          /* DD PML width in cells (Section 2.1: 3..5) */
+  int    sweep;         /* HZ_SWEEP_UD | HZ_SWEEP_X */
+  int    two_grid;      /* 0: sweep on the fine grid; 1: TGSP (Section 4) */
+  int    nu;            /* omega-Jacobi pre- and post-smoothing steps */
+  double omega_jac;     /* Jacobi relaxation weight */
+  int    precision;     /* HZ_PLAIN_FP64 | HZ_MIXED */
+  int    gmres_m;       /* GMRES restart length */
+  int    max_iter;      /* cap on preconditioned GMRES iterations */
+  double tol;           /* stop at ||b - A u||_2 / ||b||_2 <= tol (per right-hand side) */
+  int    max_rhs;       /* right-hand sides per hz_solve call (buffer capacity) */
+  int    segments;      /* block-row segments per slab solve (0: automatic) */
+} hz_params;
+
+typedef struct {
+  int    n_rhs;
+  int    iters_max;        /* max over right-hand sides of GMRES iterations */
+  double relres_max;       /* max over right-hand sides of the final true relative residual */
+  double t_setup_s;        /* wall time of the last hz_setup / hz_set_medium */
+  double t_factor_s;       /* wall time of the last hz_factor */
+  double t_solve_s;        /* wall time of the last hz_solve */
+  long long precond_applies;
+  long long kernel_launches; /* kernels this library launched in the last hz_solve */
+} hz_stats;
+
+typedef struct hz_handle hz_handle;
+
+/* Create a solver for the grid and parameters in *p.  m_dev: squared slowness
+ * 1/c^2 at the N^d unknowns, FP64, device, copied into the handle.  c_pml
+ * (the "typical velocity" of Section 2.1) is the mean of c over the unknowns.
+ * Builds the PML tables (Eq. 5, alpha below Eq. 40), the slab partition
+ * (Eq. 17) and the slab meshes (Eqs. 9-10).  *out is NULL on failure. */
+hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out);
+
+/* Replace the medium (same grid); invalidates the factors. */
+hz_status hz_set_medium(hz_handle* h, const double* m_dev);
+
+/* Factor every slab operator A^(j) (block-tridiagonal LU along y, Section 2.2
+ * / Section 5: the paper uses a sparse direct solver here) and the segment
+ * products of the parallel-in-y slab solve. */
+hz_status hz_factor(hz_handle* h, void* stream);
+
+/* Solve A u_r = f_r for r < n_rhs by GMRES(m) with the configured
+ * preconditioner, x0 = 0.  f_dev, u_dev: n_rhs * N^d complex128, device.
+ * stats (host, may be NULL) is filled.  Returns HZ_ENOTCONV if any right-hand
+ * side missed tol within max_iter (u holds the last iterate). */
+hz_status hz_solve(hz_handle* h, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,
+                   void* stream, hz_stats* stats);
+
+/* Same as hz_solve with HOST arrays f_host / u_host (n_rhs * N^d complex128):
+ * the host<->device copies are part of the call. */
+hz_status hz_solve_host(hz_handle* h, const hz_c128* f_host, hz_c128* u_host, int n_rhs,
+                        void* stream, hz_stats* stats);
+
+/* Components of the path, exposed for testing and composition. */
+
+/* y = A u (Eq. 40 x h^d), complex128, n_rhs fields. */
+hz_status hz_apply(hz_handle* h, const hz_c128* u_dev, hz_c128* y_dev, int n_rhs, void* stream);
+
+/* z = M r: one application of the configured preconditioner (SweepingPrecX /
+ * SweepingPrecUD of Table 3, or the TGSP of Section 4), complex128 in and out
+ * (computed in the preconditioner precision). */
+hz_status hz_precond(hz_handle* h, const hz_c128* r_dev, hz_c128* z_dev, int n_rhs, void* stream);
+
+/* Geometry of slab j (1..J) on the sweep level: global core columns lo..hi,
+ * added PML columns wl (left) / wr (right), width W = hi-lo+1+wl+wr. */
+hz_status hz_slab_info(const hz_handle* h, int j, int* lo, int* hi, int* wl, int* wr, int* W);
+
+/* u_d = (A^(j))^-1 f_d for slab j (1..J) of the sweep level: f_dev, u_dev are
+ * n_rhs * N_t * W complex128 ([rhs][y][local x]).  Requires hz_factor. */
+hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,
+                        void* stream);
+
+/* Statistics of the last call; fills *out. */
+hz_status hz_get_stats(const hz_handle* h, hz_stats* out);
+
+/* Kernel-level timing of the slab-solve kernels (for roofline reporting):
+ * when enabled, CUDA events bracket every slab-solve launch sequence on its
+ * stream.  hz_slab_solve_timing returns the summed event time (ms), the
+ * number of slab solves, and the algorithmic bytes they moved. */
+hz_status hz_enable_timing(hz_handle* h, int on);
+hz_status hz_slab_solve_timing(hz_handle* h, double* ms, long long* solves, double* bytes);
+
+const char* hz_last_error(const hz_handle* h);
+const char* hz_status_string(hz_status s);
+void hz_destroy(hz_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H */

@@ -1,0 +1,234 @@
+"""GB300 (sm_103a) Helmholtz solver: GMRES with the improved sweeping
+domain-decomposition preconditioner of Stolk (arXiv 1412.0464).
+
+This module is a thin ctypes binding of the C ABI in ``include/hz.h``: it
+marshals torch tensors (device memory) and the current CUDA stream into the
+library's entry points.  All computation runs in the CUDA library
+``_build/libhz.so``; there is no CPU fallback.  Importing the module does not
+load the library; the first call does, and fails loudly if it is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from .build import LIB, build  # noqa: F401
+
+HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_ENOTFACTORED, HZ_ENOTCONV, HZ_ETIMEOUT, HZ_EINACCURATE = range(8)
+HZ_SWEEP_UD, HZ_SWEEP_X = 0, 1
+HZ_PLAIN_FP64, HZ_MIXED = 0, 1
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hz.h")
+
+
+class hz_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n", ctypes.c_int), ("w_out", ctypes.c_int),
+        ("omega", ctypes.c_double), ("s_pml_out", ctypes.c_double), ("s_pml_dd", ctypes.c_double),
+        ("J", ctypes.c_int), ("w_dd", ctypes.c_int), ("sweep", ctypes.c_int),
+        ("two_grid", ctypes.c_int), ("nu", ctypes.c_int), ("omega_jac", ctypes.c_double),
+        ("precision", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_iter", ctypes.c_int),
+        ("tol", ctypes.c_double), ("max_rhs", ctypes.c_int), ("segments", ctypes.c_int),
+    ]
+
+
+class hz_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_rhs", ctypes.c_int), ("iters_max", ctypes.c_int), ("relres_max", ctypes.c_double),
+        ("t_setup_s", ctypes.c_double), ("t_factor_s", ctypes.c_double),
+        ("t_solve_s", ctypes.c_double), ("precond_applies", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_H = ctypes.c_void_p
+_SIGNATURES = {
+    "hz_setup": (ctypes.c_int, [ctypes.POINTER(hz_params), _P, ctypes.POINTER(_H)]),
+    "hz_set_medium": (ctypes.c_int, [_H, _P]),
+    "hz_factor": (ctypes.c_int, [_H, _P]),
+    "hz_solve": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P, ctypes.POINTER(hz_stats)]),
+    "hz_solve_host": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P, ctypes.POINTER(hz_stats)]),
+    "hz_apply": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P]),
+    "hz_precond": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P]),
+    "hz_slab_info": (ctypes.c_int, [_H, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5),
+    "hz_slab_solve": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "hz_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(hz_stats)]),
+    "hz_enable_timing": (ctypes.c_int, [_H, ctypes.c_int]),
+    "hz_slab_solve_timing": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_longlong),
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "hz_last_error": (ctypes.c_char_p, [_H]),
+    "hz_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hz_destroy": (None, [_H]),
+}
+
+_lib = None
+
+
+def declared_symbols(header: str = HEADER):
+    """Function names declared in include/hz.h."""
+    txt = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\*]+\s+)+\**(hz_\w+)\s*\(", txt, re.M)))
+
+
+def lib():
+    """Load libhz.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with `python -m paper_1412_0464_gb300.build`"
+                               " (the CUDA path has no fallback)")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class HzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = lib().hz_status_string(status).decode()
+        super().__init__(f"{name}: {msg}")
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One Helmholtz problem on the device: set-up, factorisation and solves.
+
+    ``m`` is the squared slowness 1/c^2 on the N x N unknowns (torch float64
+    tensor on the GPU, or anything ``torch.as_tensor`` accepts).
+    """
+
+    def __init__(self, m, *, n, w_out, omega, J, w_dd, s_dd, s_out=20.0, sweep="X",
+                 precision="mixed", gmres_m=30, max_iter=500, tol=1e-6, max_rhs=1,
+                 two_grid=False, nu=3, omega_jac=0.8, segments=0):
+        import torch
+        self.N = n + 2 * w_out - 1
+        self.shape = (self.N, self.N)
+        p = hz_params()
+        p.dim, p.n, p.w_out, p.omega = 2, n, w_out, omega
+        p.s_pml_out, p.s_pml_dd, p.J, p.w_dd = s_out, s_dd, J, w_dd
+        p.sweep = HZ_SWEEP_X if sweep == "X" else HZ_SWEEP_UD
+        p.two_grid, p.nu, p.omega_jac = int(two_grid), nu, omega_jac
+        p.precision = HZ_MIXED if precision == "mixed" else HZ_PLAIN_FP64
+        p.gmres_m, p.max_iter, p.tol, p.max_rhs, p.segments = gmres_m, max_iter, tol, max_rhs, segments
+        self.params = p
+        md = torch.as_tensor(m, dtype=torch.float64).to("cuda").contiguous()
+        assert md.shape == self.shape
+        h = _H()
+        st = lib().hz_setup(ctypes.byref(p), _ptr(md), ctypes.byref(h))
+        if st != HZ_OK:
+            raise HzError(st, lib().hz_last_error(None).decode())
+        self.h = h
+        self.factored = False
+
+    @classmethod
+    def from_workload(cls, cfg, m=None, **over):
+        import synth
+        m = synth.medium(cfg) if m is None else m
+        kw = dict(n=cfg.n, w_out=cfg.w_out, omega=cfg.omega, J=cfg.J, w_dd=cfg.w_dd, s_dd=cfg.s_dd,
+                  s_out=cfg.s_out, sweep=cfg.sweep, precision=cfg.precision, gmres_m=cfg.gmres_m,
+                  tol=cfg.tol, max_rhs=cfg.n_src, two_grid=cfg.two_grid, nu=cfg.nu,
+                  omega_jac=cfg.omega_jac)
+        kw.update(over)
+        return cls(m, **kw)
+
+    def _check(self, st):
+        if st != HZ_OK:
+            raise HzError(st, lib().hz_last_error(self.h).decode())
+
+    def factor(self, stream=None):
+        self._check(lib().hz_factor(self.h, _stream(stream)))
+        self.factored = True
+
+    def solve(self, f, stream=None, check=True):
+        """u with A u = f (f: complex128 CUDA tensor [n_rhs, N, N] or [N, N])."""
+        import torch
+        single = f.dim() == 2
+        fb = (f[None] if single else f).contiguous()
+        u = torch.empty_like(fb)
+        st = hz_stats()
+        code = lib().hz_solve(self.h, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream), ctypes.byref(st))
+        if check:
+            self._check(code)
+        return (u[0] if single else u), st.as_dict()
+
+    def solve_host(self, f_host, stream=None):
+        """Same with host (CPU) tensors; the copies are part of the call."""
+        import torch
+        fb = f_host[None] if f_host.dim() == 2 else f_host
+        fb = fb.contiguous()
+        u = torch.empty_like(fb)
+        st = hz_stats()
+        self._check(lib().hz_solve_host(self.h, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream),
+                                        ctypes.byref(st)))
+        return (u[0] if f_host.dim() == 2 else u), st.as_dict()
+
+    def apply(self, u, stream=None):
+        import torch
+        ub = (u[None] if u.dim() == 2 else u).contiguous()
+        y = torch.empty_like(ub)
+        self._check(lib().hz_apply(self.h, _ptr(ub), _ptr(y), ub.shape[0], _stream(stream)))
+        return y[0] if u.dim() == 2 else y
+
+    def precond(self, r, stream=None):
+        import torch
+        rb = (r[None] if r.dim() == 2 else r).contiguous()
+        z = torch.empty_like(rb)
+        self._check(lib().hz_precond(self.h, _ptr(rb), _ptr(z), rb.shape[0], _stream(stream)))
+        return z[0] if r.dim() == 2 else z
+
+    def slab_info(self, j):
+        vals = [ctypes.c_int() for _ in range(5)]
+        self._check(lib().hz_slab_info(self.h, j, *[ctypes.byref(v) for v in vals]))
+        return dict(zip(("lo", "hi", "wl", "wr", "W"), (v.value for v in vals)))
+
+    def slab_solve(self, j, fd, stream=None):
+        import torch
+        fb = (fd[None] if fd.dim() == 2 else fd).contiguous()
+        u = torch.empty_like(fb)
+        self._check(lib().hz_slab_solve(self.h, j, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream)))
+        return u[0] if fd.dim() == 2 else u
+
+    def enable_timing(self, on=True):
+        self._check(lib().hz_enable_timing(self.h, int(on)))
+
+    def slab_solve_timing(self):
+        ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        self._check(lib().hz_slab_solve_timing(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+        return ms.value, n.value, b.value
+
+    def stats(self):
+        st = hz_stats()
+        self._check(lib().hz_get_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,366 @@
+// C ABI entry points (declared in include/hz.h).  Every call catches internal
+// failures and returns an hz_status; nothing throws across the boundary.
+#include "hz_internal.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace hz {
+size_t gmres_red_doubles(int m, int nr);
+}
+
+using namespace hz;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hz_status fail(hz_handle* h, hz_status st, const std::string& msg) {
+  if (h) { h->err.st = st; h->err.msg = msg; }
+  g_last_error = msg;
+  return st;
+}
+
+template <typename F>
+hz_status guarded(hz_handle* h, F&& body) {
+  try {
+    body();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, HZ_ECUDA, cudaGetErrorString(e));
+    if (h) { h->err.st = HZ_OK; h->err.msg.clear(); }
+    return HZ_OK;
+  } catch (const Failure& f) {
+    return fail(h, f.st, f.msg);
+  } catch (const std::exception& e) {
+    return fail(h, HZ_ECUDA, e.what());
+  }
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t prec_size(const hz_params& p) { return p.precision == HZ_MIXED ? sizeof(c64) : sizeof(c128); }
+
+void release_work(hz_handle* h) {
+  for (void** q : {&h->pr_r, &h->pr_u, &h->pr_g, &h->pr_B1, &h->pr_B2, &h->tg_u, &h->tg_r,
+                   &h->tg_t}) {
+    dfree(*q);
+    *q = nullptr;
+  }
+  dfree(h->V); dfree(h->Z); dfree(h->W); dfree(h->R); dfree(h->red); dfree(h->hcol);
+  h->V = h->Z = h->W = h->R = h->hcol = nullptr;
+  h->red = nullptr;
+}
+
+void validate(const hz_params* p) {
+  auto bad = [](const std::string& m) { throw Failure(HZ_EINVAL, m); };
+  if (!p) bad("params is NULL");
+  if (p->dim != 2) bad("only dim = 2 is built");
+  if (p->n < 4) bad("n must be >= 4");
+  if (p->w_out < 0) bad("w_out must be >= 0");
+  if (!(p->omega > 0)) bad("omega must be > 0");
+  if (p->J < 1) bad("J must be >= 1");
+  if (p->sweep != HZ_SWEEP_UD && p->sweep != HZ_SWEEP_X) bad("sweep must be HZ_SWEEP_UD or HZ_SWEEP_X");
+  if (p->sweep == HZ_SWEEP_X && (p->J % 2 != 0)) bad("the X-sweep needs an even J");
+  if (p->w_dd < 1) bad("w_dd must be >= 1");
+  if (p->precision != HZ_PLAIN_FP64 && p->precision != HZ_MIXED) bad("bad precision");
+  if (p->gmres_m < 1 || p->gmres_m > 200) bad("gmres_m must be in 1..200");
+  if (p->max_iter < 1) bad("max_iter must be >= 1");
+  if (!(p->tol > 0)) bad("tol must be > 0");
+  if (p->max_rhs < 1 || p->max_rhs > 8) bad("max_rhs must be in 1..8");
+  if (p->two_grid) bad("the two-grid preconditioner is not built in this version");
+  int N = p->n + 2 * p->w_out - 1;
+  if (N / p->J < 2 * p->w_dd + 2) bad("slabs too thin for the DD PML width");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hz_status_string(hz_status s) {
+  switch (s) {
+    case HZ_OK: return "HZ_OK";
+    case HZ_EINVAL: return "HZ_EINVAL";
+    case HZ_ENOMEM: return "HZ_ENOMEM";
+    case HZ_ECUDA: return "HZ_ECUDA";
+    case HZ_ENOTFACTORED: return "HZ_ENOTFACTORED";
+    case HZ_ENOTCONV: return "HZ_ENOTCONV";
+    case HZ_ETIMEOUT: return "HZ_ETIMEOUT";
+    case HZ_EINACCURATE: return "HZ_EINACCURATE";
+  }
+  return "HZ_UNKNOWN";
+}
+
+const char* hz_last_error(const hz_handle* h) {
+  if (h) return h->err.msg.c_str();
+  return g_last_error.c_str();
+}
+
+hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
+  if (!out) return fail(nullptr, HZ_EINVAL, "out is NULL");
+  *out = nullptr;
+  hz_handle* h = new hz_handle();
+  hz_status st = guarded(h, [&] {
+    validate(p);
+    if (!m_dev) throw Failure(HZ_EINVAL, "m_dev is NULL");
+    h->p = *p;
+    double t0 = now_s();
+    HZ_CU(cudaGetDevice(&h->dev));
+    HZ_CU(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+    HZ_CU(cudaEventCreateWithFlags(&h->evA, cudaEventDisableTiming));
+    HZ_CU(cudaEventCreateWithFlags(&h->evB, cudaEventDisableTiming));
+    h->dev_flag = (int*)dmalloc(sizeof(int));
+    HZ_CU(cudaMemsetAsync(h->dev_flag, 0, sizeof(int), h->s2));
+    const int N = p->n + 2 * p->w_out - 1;
+    const double hh = 1.0 / p->n;
+    h->c_pml = mean_velocity(m_dev, (size_t)N * N, h->s2);
+    build_level_fd(h, h->fine, p->n, p->w_out, hh, m_dev, h->s2);
+    h->fine.J = p->J;
+    h->fine.w = p->w_dd;
+    h->sweep = &h->fine;
+    build_slabs(h, h->fine, h->s2);
+    const size_t n = (size_t)N * N;
+    const size_t ps = prec_size(*p);
+    const int R = p->max_rhs, m = p->gmres_m;
+    Level& L = *h->sweep;
+    const size_t nl = (size_t)L.nx * L.ny;
+    h->pr_r = dmalloc(ps * nl * R);
+    h->pr_u = dmalloc(ps * nl * R);
+    h->pr_g = dmalloc(ps * nl * R);
+    h->pr_B1 = dmalloc(ps * 2 * R * L.ny);
+    h->pr_B2 = dmalloc(ps * 2 * R * L.ny);
+    HZ_CU(cudaMemsetAsync(h->pr_B1, 0, ps * 2 * R * L.ny, h->s2));
+    HZ_CU(cudaMemsetAsync(h->pr_B2, 0, ps * 2 * R * L.ny, h->s2));
+    h->V = (c128*)dmalloc(sizeof(c128) * n * R * (m + 1));
+    h->Z = (c128*)dmalloc(sizeof(c128) * n * R * m);
+    h->W = (c128*)dmalloc(sizeof(c128) * n * R);
+    h->R = (c128*)dmalloc(sizeof(c128) * n * R);
+    h->red = (double*)dmalloc(sizeof(double) * gmres_red_doubles(m, R));
+    h->hcol = (c128*)dmalloc(sizeof(c128) * 2 * R * (m + 2));
+    HZ_CU(cudaStreamSynchronize(h->s2));
+    h->stats.t_setup_s = now_s() - t0;
+  });
+  if (st != HZ_OK) {
+    hz_destroy(h);
+    return st;
+  }
+  *out = h;
+  return HZ_OK;
+}
+
+hz_status hz_set_medium(hz_handle* h, const double* m_dev) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  return guarded(h, [&] {
+    if (!m_dev) throw Failure(HZ_EINVAL, "m_dev is NULL");
+    // rebuild the level from scratch for the new medium (same grid)
+    double t0 = now_s();
+    const hz_params p = h->p;
+    free_level(h->fine);
+    h->fine = Level{};
+    const int N = p.n + 2 * p.w_out - 1;
+    h->c_pml = mean_velocity(m_dev, (size_t)N * N, h->s2);
+    build_level_fd(h, h->fine, p.n, p.w_out, 1.0 / p.n, m_dev, h->s2);
+    h->fine.J = p.J;
+    h->fine.w = p.w_dd;
+    h->sweep = &h->fine;
+    build_slabs(h, h->fine, h->s2);
+    h->factored = false;
+    h->stats.t_setup_s = now_s() - t0;
+  });
+}
+
+hz_status hz_factor(hz_handle* h, void* stream) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  return guarded(h, [&] {
+    double t0 = now_s();
+    if (h->p.precision == HZ_MIXED)
+      factor_level<float>(h, *h->sweep, s);
+    else
+      factor_level<double>(h, *h->sweep, s);
+    check_dev_flag(h, s);
+    h->factored = true;
+    h->stats.t_factor_s = now_s() - t0;
+  });
+}
+
+hz_status hz_solve(hz_handle* h, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs, void* stream,
+                   hz_stats* stats) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  hz_status st = guarded(h, [&] {
+    if (!h->factored) throw Failure(HZ_ENOTFACTORED, "hz_solve before hz_factor");
+    if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
+    if (!f_dev || !u_dev) throw Failure(HZ_EINVAL, "NULL field pointer");
+    double t0 = now_s();
+    h->launches = 0;
+    h->stats.precond_applies = 0;
+    try {
+      gmres_solve(h, (const c128*)f_dev, (c128*)u_dev, n_rhs, s);
+    } catch (const Failure& f) {
+      HZ_CU(cudaStreamSynchronize(s));
+      h->stats.t_solve_s = now_s() - t0;
+      h->stats.kernel_launches = h->launches;
+      throw;
+    }
+    HZ_CU(cudaStreamSynchronize(s));
+    h->stats.t_solve_s = now_s() - t0;
+    h->stats.kernel_launches = h->launches;
+  });
+  if (stats) *stats = h->stats;
+  return st;
+}
+
+hz_status hz_solve_host(hz_handle* h, const hz_c128* f_host, hz_c128* u_host, int n_rhs,
+                        void* stream, hz_stats* stats) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  c128* fd = nullptr;
+  c128* ud = nullptr;
+  hz_status st = guarded(h, [&] {
+    if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
+    if (!f_host || !u_host) throw Failure(HZ_EINVAL, "NULL field pointer");
+    const size_t n = (size_t)h->fine.nx * h->fine.ny * n_rhs;
+    fd = (c128*)dmalloc(sizeof(c128) * n);
+    ud = (c128*)dmalloc(sizeof(c128) * n);
+    HZ_CU(cudaMemcpyAsync(fd, f_host, sizeof(c128) * n, cudaMemcpyHostToDevice, s));
+  });
+  if (st == HZ_OK) {
+    st = hz_solve(h, (const hz_c128*)fd, (hz_c128*)ud, n_rhs, stream, stats);
+    if (st == HZ_OK || st == HZ_ENOTCONV) {
+      hz_status st2 = guarded(h, [&] {
+        const size_t n = (size_t)h->fine.nx * h->fine.ny * n_rhs;
+        HZ_CU(cudaMemcpyAsync(u_host, ud, sizeof(c128) * n, cudaMemcpyDeviceToHost, s));
+        HZ_CU(cudaStreamSynchronize(s));
+      });
+      if (st2 != HZ_OK) st = st2;
+    }
+  }
+  dfree(fd);
+  dfree(ud);
+  return st;
+}
+
+hz_status hz_apply(hz_handle* h, const hz_c128* u_dev, hz_c128* y_dev, int n_rhs, void* stream) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  return guarded(h, [&] {
+    if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
+    if (!u_dev || !y_dev) throw Failure(HZ_EINVAL, "NULL field pointer");
+    apply_fine64(h, (const c128*)u_dev, (c128*)y_dev, n_rhs, s);
+    HZ_CU(cudaStreamSynchronize(s));
+  });
+}
+
+hz_status hz_precond(hz_handle* h, const hz_c128* r_dev, hz_c128* z_dev, int n_rhs, void* stream) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  return guarded(h, [&] {
+    if (!h->factored) throw Failure(HZ_ENOTFACTORED, "hz_precond before hz_factor");
+    if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
+    if (!r_dev || !z_dev || r_dev == z_dev) throw Failure(HZ_EINVAL, "bad field pointers");
+    precond_apply(h, (const c128*)r_dev, (c128*)z_dev, n_rhs, s);
+    HZ_CU(cudaStreamSynchronize(s));
+    check_dev_flag(h, s);
+  });
+}
+
+hz_status hz_slab_info(const hz_handle* h, int j, int* lo, int* hi, int* wl, int* wr, int* W) {
+  if (!h || !h->sweep) return HZ_EINVAL;
+  const Level& L = *h->sweep;
+  if (j < 1 || j > L.J) return HZ_EINVAL;
+  const Slab& S = L.slabs[j];
+  if (lo) *lo = S.lo;
+  if (hi) *hi = S.hi;
+  if (wl) *wl = S.wl;
+  if (wr) *wr = S.wr;
+  if (W) *W = S.W;
+  return HZ_OK;
+}
+
+hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,
+                        void* stream) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  void* tf = nullptr;
+  void* tu = nullptr;
+  hz_status st = guarded(h, [&] {
+    if (!h->factored) throw Failure(HZ_ENOTFACTORED, "hz_slab_solve before hz_factor");
+    Level& L = *h->sweep;
+    if (j < 1 || j > L.J) throw Failure(HZ_EINVAL, "slab index out of range");
+    if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
+    if (!f_dev || !u_dev) throw Failure(HZ_EINVAL, "NULL field pointer");
+    const size_t n = (size_t)n_rhs * L.ny * L.slabs[j].W;
+    if (h->p.precision == HZ_MIXED) {
+      tf = dmalloc(sizeof(c64) * n);
+      tu = dmalloc(sizeof(c64) * n);
+      cast_copy<float, double>((const c128*)f_dev, (c64*)tf, n, s);
+      slab_solve_raw<float>(h, L, j, (const c64*)tf, (c64*)tu, n_rhs, s);
+      cast_copy<double, float>((const c64*)tu, (c128*)u_dev, n, s);
+    } else {
+      slab_solve_raw<double>(h, L, j, (const c128*)f_dev, (c128*)u_dev, n_rhs, s);
+    }
+    HZ_CU(cudaStreamSynchronize(s));
+    check_dev_flag(h, s);
+  });
+  dfree(tf);
+  dfree(tu);
+  return st;
+}
+
+hz_status hz_get_stats(const hz_handle* h, hz_stats* out) {
+  if (!h || !out) return HZ_EINVAL;
+  *out = h->stats;
+  return HZ_OK;
+}
+
+hz_status hz_enable_timing(hz_handle* h, int on) {
+  if (!h) return HZ_EINVAL;
+  h->timing.on = on != 0;
+  h->timing.used = 0;
+  h->timing.ms = 0;
+  h->timing.solves = 0;
+  h->timing.bytes = 0;
+  return HZ_OK;
+}
+
+hz_status hz_slab_solve_timing(hz_handle* h, double* ms, long long* solves, double* bytes) {
+  if (!h) return HZ_EINVAL;
+  return guarded(h, [&] {
+    Timing& t = h->timing;
+    double acc = 0;
+    for (size_t i = 0; i < t.used; ++i) {
+      HZ_CU(cudaEventSynchronize(t.ev[i].second));
+      float x = 0;
+      HZ_CU(cudaEventElapsedTime(&x, t.ev[i].first, t.ev[i].second));
+      acc += x;
+    }
+    t.ms += acc;
+    t.used = 0;
+    if (ms) *ms = t.ms;
+    if (solves) *solves = t.solves;
+    if (bytes) *bytes = t.bytes;
+  });
+}
+
+void hz_destroy(hz_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_level(h->fine);
+  free_level(h->coarse);
+  release_work(h);
+  dfree(h->dev_flag);
+  if (h->s2) cudaStreamDestroy(h->s2);
+  if (h->evA) cudaEventDestroy(h->evA);
+  if (h->evB) cudaEventDestroy(h->evB);
+  for (auto& e : h->timing.ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  cudaGetLastError();
+  delete h;
+}
+
+}  // extern "C"

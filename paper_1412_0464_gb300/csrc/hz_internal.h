@@ -1,0 +1,226 @@
+// Internal declarations of the GB300 Helmholtz sweeping solver (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hz.h"
+
+namespace hz {
+
+// ------------------------------------------------------------------ complex
+template <typename R>
+struct alignas(2 * sizeof(R)) cplx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> mk(R a, R b) { cplx<R> z; z.re = a; z.im = b; return z; }
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator+(cplx<R> a, cplx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator-(cplx<R> a, cplx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator-(cplx<R> a) { return mk(-a.re, -a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator*(cplx<R> a, cplx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> operator*(R s, cplx<R> a) { return mk(s * a.re, s * a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> cconj(cplx<R> a) { return mk(a.re, -a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ R cabs2(cplx<R> a) { return a.re * a.re + a.im * a.im; }
+// acc += a * b
+template <typename R>
+__host__ __device__ __forceinline__ void cfma(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im); acc.im = fma(a.im, b.re, acc.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> cinv(cplx<R> a) {
+  R d = R(1) / (a.re * a.re + a.im * a.im);
+  return mk(a.re * d, -a.im * d);
+}
+template <typename To, typename From>
+__host__ __device__ __forceinline__ cplx<To> ccast(cplx<From> a) { return mk((To)a.re, (To)a.im); }
+
+using c64 = cplx<float>;
+using c128 = cplx<double>;
+
+// ------------------------------------------------------------------ errors
+struct Err {
+  hz_status st = HZ_OK;
+  std::string msg;
+};
+
+#define HZ_CU(call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      throw ::hz::Failure(HZ_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                  \
+  } while (0)
+
+struct Failure {
+  hz_status st;
+  std::string msg;
+  Failure(hz_status s, std::string m) : st(s), msg(std::move(m)) {}
+};
+
+// Device error flag codes (written by kernels, read by the host after a call).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADSIZE = 2 };
+
+// ------------------------------------------------------------------ geometry
+// One 1-D axis of unknowns: PML factors at the unknowns (node) and at the
+// cell midpoints (cell c lies between unknowns c-1 and c), cell sizes.
+struct AxisTables {
+  int N = 0;                 // unknowns
+  c128* a_node = nullptr;    // [N]   alpha at unknowns (device)
+  c128* a_cell = nullptr;    // [N+1] alpha at cell midpoints (device)
+  double* h_cell = nullptr;  // [N+1] cell sizes (device)
+  c64* a_node32 = nullptr;
+  c64* a_cell32 = nullptr;
+};
+
+// Slab j: core columns lo..hi, wl/wr added PML columns, W = width.
+struct Slab {
+  int j = 0, lo = 0, hi = 0, wl = 0, wr = 0, W = 0;
+  AxisTables ax;             // slab x axis (DD PML in the added columns)
+  void* st = nullptr;        // slab stencil [ny][9][W] in the preconditioner precision
+  void* G = nullptr;         // inverse Schur complements [ny][gstride]
+  size_t gstride = 0;        // elements per block (W*W rounded up to 16 bytes)
+  void* Phi = nullptr;       // forward segment products [P][gstride]
+  void* Psi = nullptr;       // backward segment products [P][gstride]
+  void* inj = nullptr;       // injection coefficients [4][ny][3] (T row0, T row1, T~ row0, T~ row1)
+  void* Y = nullptr;         // forward solution work [max_rhs][ny][W]
+  void* carry_f = nullptr;   // [P][max_rhs][W]
+  void* carry_b = nullptr;   // [P][max_rhs][W]
+};
+
+// A grid level on which the sweeping preconditioner (and possibly GMRES) runs.
+struct Level {
+  int nx = 0, ny = 0;        // unknowns along x (sweep) and y
+  double h = 0;              // uniform spacing (finite differences)
+  bool fe = false;           // stored 9-point operator (coarse FE level)
+  AxisTables ax, ay;
+  double* m = nullptr;       // squared slowness at unknowns (FD level), FP64
+  float* m32 = nullptr;      // FP32 copy
+  c128* st128 = nullptr;     // FE level: 9 coefficient planes [9][ny][nx]
+  c64* st64 = nullptr;
+  int J = 0, w = 0;
+  std::vector<int> beta, beta_t;  // Eq. 17, size J+1
+  std::vector<Slab> slabs;        // index 1..J (0 unused)
+  int P = 1;                       // segments per slab solve
+  std::vector<int> seg;            // P+1 segment bounds over block rows
+  int* seg_dev = nullptr;
+};
+
+struct Timing {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t used = 0;
+  double ms = 0;
+  long long solves = 0;
+  double bytes = 0;
+};
+
+}  // namespace hz
+
+struct hz_handle {
+  hz_params p{};
+  hz::Err err;
+  int dev = 0;
+  double c_pml = 0;
+  hz::Level fine;            // the PDE grid (GMRES level)
+  hz::Level coarse;          // two-grid coarse level (sweeps), if p.two_grid
+  hz::Level* sweep = nullptr;  // level carrying the DD (fine or coarse)
+  bool factored = false;
+  int* dev_flag = nullptr;   // device error flag
+  // preconditioner work (precision of the preconditioner), per level
+  void* pr_r = nullptr;      // input residual on the sweep level [max_rhs][n]
+  void* pr_u = nullptr;      // output on the sweep level
+  void* pr_g = nullptr;      // mid-sweep residual g = f - A u
+  void* pr_B1 = nullptr;     // transmission buffers [2][max_rhs][ny]
+  void* pr_B2 = nullptr;
+  void* tg_u = nullptr;      // two-grid fine work (preconditioner precision)
+  void* tg_r = nullptr;
+  void* tg_t = nullptr;
+  // GMRES (FP64)
+  hz::c128* V = nullptr;     // [(m+1)][max_rhs][n]
+  hz::c128* Z = nullptr;     // [m][max_rhs][n]
+  hz::c128* W = nullptr;     // [max_rhs][n] work
+  hz::c128* R = nullptr;     // [max_rhs][n] residual
+  double* red = nullptr;     // reduction scratch
+  hz::c128* hcol = nullptr;  // [max_rhs][m+1] Hessenberg column on device
+  cudaStream_t s2 = nullptr; // second stream for the concurrent chain of the X-sweep
+  cudaEvent_t evA = nullptr, evB = nullptr;
+  hz::Timing timing;
+  hz_stats stats{};
+  long long launches = 0;
+};
+
+namespace hz {
+
+// setup.cu
+void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const double* m_dev,
+                    cudaStream_t s);
+void build_level_fe(hz_handle* h, Level& L, const Level& fine, int n, int w_out, double hh,
+                    cudaStream_t s);
+void build_slabs(hz_handle* h, Level& L, cudaStream_t s);
+void free_level(Level& L);
+double mean_velocity(const double* m_dev, size_t n, cudaStream_t s);
+
+// stencil.cu: fine 5-point operator (on the fly) or stored 9-point operator.
+template <typename R>
+void level_residual(hz_handle* h, const Level& L, const cplx<R>* f, const cplx<R>* u,
+                    cplx<R>* r, int n_rhs, cudaStream_t s);  // r = f - A u (f may be null: r = -A u)
+template <typename R>
+void level_apply(hz_handle* h, const Level& L, const cplx<R>* u, cplx<R>* y, int n_rhs,
+                 cudaStream_t s);
+template <typename R>
+void jacobi_steps(hz_handle* h, const Level& L, const cplx<R>* f, cplx<R>* u, cplx<R>* t,
+                  int nu, double omega_jac, int n_rhs, cudaStream_t s);
+template <typename R>
+void restrict_residual(hz_handle* h, const Level& F, const Level& C, const cplx<R>* rf,
+                       cplx<R>* rc, int n_rhs, cudaStream_t s);
+template <typename R>
+void prolong_add(hz_handle* h, const Level& F, const Level& C, const cplx<R>* ec, cplx<R>* uf,
+                 int n_rhs, cudaStream_t s);
+
+// slab.cu
+template <typename R>
+void factor_level(hz_handle* h, Level& L, cudaStream_t s);
+struct SolveSpec;  // defined in slab.cu
+template <typename R>
+void subdom_solve(hz_handle* h, Level& L, int j, const cplx<R>* f, int a, int b, int at, int bt,
+                  bool tau1, const cplx<R>* B1, bool tau2, cplx<R>* B2, bool tau3,
+                  const cplx<R>* B3, bool tau4, cplx<R>* B4, cplx<R>* u, int n_rhs,
+                  cudaStream_t s);
+template <typename R>
+void slab_solve_raw(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud, int n_rhs,
+                    cudaStream_t s);
+
+// sweep.cu
+template <typename R>
+void sweep_apply(hz_handle* h, Level& L, const cplx<R>* f, cplx<R>* u, int n_rhs,
+                 cudaStream_t s);  // u = P f (P_X or P_UD)
+void precond_apply(hz_handle* h, const c128* r, c128* z, int n_rhs, cudaStream_t s);
+
+// gmres.cu
+void gmres_solve(hz_handle* h, const c128* f, c128* u, int n_rhs, cudaStream_t s);
+void apply_fine64(hz_handle* h, const c128* u, c128* y, int n_rhs, cudaStream_t s);
+
+// util
+template <typename To, typename From>
+void cast_copy(const cplx<From>* a, cplx<To>* b, size_t n, cudaStream_t s);
+void check_dev_flag(hz_handle* h, cudaStream_t s);
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+void* dmalloc(size_t bytes);
+void dfree(void* p);
+
+}  // namespace hz

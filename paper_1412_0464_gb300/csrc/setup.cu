@@ -1,0 +1,350 @@
+// Set-up of a grid level: PML tables, medium copies, slab partition, slab meshes
+// with the added DD PML and frozen k, slab stencils and transmission
+// coefficients.  Everything is computed by kernels on the device.
+#include "hz_internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace hz {
+
+void* dmalloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Failure(HZ_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + ") failed: " +
+                                 cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+// alpha = 1 / (1 + i sigma / omega)  (definition below Eq. 40)
+__device__ __forceinline__ c128 pml_alpha(double sigma, double omega) {
+  double a = sigma / omega;
+  double d = 1.0 / (1.0 + a * a);
+  return mk(d, -a * d);
+}
+
+// Uniform axis of n_cells cells, w_out PML cells per side (Eq. 5):
+// sigma = C d^2, d = distance beyond the interior box [w_out h, (n_cells-w_out) h].
+__global__ void fine_axis_kernel(int N, int n_cells, int w_out, double h, double C,
+                                 double omega, c128* a_node, c128* a_cell, double* h_cell,
+                                 c64* a_node32, c64* a_cell32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > N) return;
+  double lo = w_out * h, hi = (n_cells - w_out) * h;
+  if (i < N) {
+    double x = (i + 1) * h;
+    double d = fmax(0.0, fmax(lo - x, x - hi));
+    c128 a = pml_alpha(C * d * d, omega);
+    a_node[i] = a;
+    a_node32[i] = ccast<float>(a);
+  }
+  double x = (i + 0.5) * h;
+  double d = fmax(0.0, fmax(lo - x, x - hi));
+  c128 a = pml_alpha(C * d * d, omega);
+  a_cell[i] = a;
+  a_cell32[i] = ccast<float>(a);
+  h_cell[i] = h;
+}
+
+// Slab x axis (Eqs. 9-10 with the reading that the added PML starts at the
+// interface half point): core unknowns/cells copy the global tables; the
+// m-th added unknown is at distance (m - 1/2) h_I, added cells at (m - 1) h_I.
+__global__ void slab_axis_kernel(int W, int lo, int hi, int wl, const c128* g_anode,
+                                 const c128* g_acell, const double* g_hcell, double s_dd,
+                                 double c_pml, int w, double omega, c128* a_node, c128* a_cell,
+                                 double* h_cell, c64* a_node32, c64* a_cell32) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e > W) return;
+  double hIl = g_hcell[lo], hIr = g_hcell[hi + 1];
+  double Cl = s_dd * c_pml / ((w * hIl) * (w * hIl) * (w * hIl));
+  double Cr = s_dd * c_pml / ((w * hIr) * (w * hIr) * (w * hIr));
+  if (e < W) {
+    int g = e - wl + lo;
+    c128 a;
+    if (g < lo) {
+      double d = (lo - g - 0.5) * hIl;
+      a = pml_alpha(Cl * d * d, omega);
+    } else if (g > hi) {
+      double d = (g - hi - 0.5) * hIr;
+      a = pml_alpha(Cr * d * d, omega);
+    } else {
+      a = g_anode[g];
+    }
+    a_node[e] = a;
+    a_node32[e] = ccast<float>(a);
+  }
+  int gc = e - wl + lo;
+  c128 a;
+  double hc;
+  if (gc < lo) {
+    double d = (lo - gc) * hIl;
+    a = pml_alpha(Cl * d * d, omega);
+    hc = hIl;
+  } else if (gc > hi + 1) {
+    double d = (gc - hi - 1) * hIr;
+    a = pml_alpha(Cr * d * d, omega);
+    hc = hIr;
+  } else {
+    a = g_acell[gc];
+    hc = g_hcell[gc];
+  }
+  a_cell[e] = a;
+  a_cell32[e] = ccast<float>(a);
+  h_cell[e] = hc;
+}
+
+// Slab stencil of the 5-point operator (Eq. 40 x h^2) on the extended slab
+// mesh, k frozen to the adjacent core column in the added PML (Eq. 10).
+// Layout st[k][9][W], plane (dy+1)*3+(dx+1); couplings to Dirichlet nodes
+// are zero.
+template <typename R>
+__global__ void slab_stencil_fd_kernel(int W, int ny, int lo, int hi, int wl, int nx,
+                                       double h2w2, const double* m, const c128* sa_node,
+                                       const c128* sa_cell, const c128* ay_node,
+                                       const c128* ay_cell, cplx<R>* st) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  if (e >= W || k >= ny) return;
+  int g = min(max(e - wl + lo, lo), hi);
+  double mm = m[(size_t)k * nx + g];
+  c128 inv_a2 = cinv(ay_node[k]);
+  c128 inv_a1 = cinv(sa_node[e]);
+  c128 a1l = sa_cell[e], a1r = sa_cell[e + 1];
+  c128 a2d = ay_cell[k], a2u = ay_cell[k + 1];
+  c128 diag = inv_a2 * (a1l + a1r) + inv_a1 * (a2d + a2u) - (h2w2 * mm) * (inv_a1 * inv_a2);
+  c128 z = mk(0.0, 0.0);
+  c128 v[9];
+  for (int q = 0; q < 9; ++q) v[q] = z;
+  v[4] = diag;
+  v[3] = (e > 0) ? -(inv_a2 * a1l) : z;
+  v[5] = (e < W - 1) ? -(inv_a2 * a1r) : z;
+  v[1] = (k > 0) ? -(inv_a1 * a2d) : z;
+  v[7] = (k < ny - 1) ? -(inv_a1 * a2u) : z;
+  cplx<R>* out = st + (size_t)k * 9 * W;
+  for (int q = 0; q < 9; ++q) out[q * W + e] = ccast<R>(v[q]);
+}
+
+// Transmission coefficients of Eqs. 19-20 for the 5-point operator (only the
+// dy = 0 coupling is non-zero): the global coupling between columns x and
+// x+1 at row k is A_{(k,x),(k,x+1)} = -alpha_{1,x+1/2} / alpha_{2,k}.
+//   inj[0][k] = +A_{beta,beta+1}      (row beta   of T B, multiplies B[1])
+//   inj[1][k] = -A_{beta+1,beta}      (row beta+1 of T B, multiplies B[0])
+//   inj[2][k] = -A_{bt,bt+1}          (row bt     of T~ B, multiplies B[1])
+//   inj[3][k] = +A_{bt+1,bt}          (row bt+1   of T~ B, multiplies B[0])
+// with beta = beta_{j-1}, bt = tilde-beta_j.  Stored [4][ny][3] (dy = -1,0,1).
+template <typename R>
+__global__ void inj_fd_kernel(int ny, int beta, int bt, const c128* ax_cell,
+                              const c128* ay_node, cplx<R>* inj) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ny) return;
+  c128 inv_a2 = cinv(ay_node[k]);
+  c128 z = mk(0.0, 0.0);
+  c128 af = (beta >= 0) ? -(inv_a2 * ax_cell[beta + 1]) : z;
+  c128 ab = (bt >= 0) ? -(inv_a2 * ax_cell[bt + 1]) : z;
+  c128 vals[4] = {af, -af, -ab, ab};
+  for (int q = 0; q < 4; ++q) {
+    cplx<R>* o = inj + ((size_t)q * ny + k) * 3;
+    o[0] = ccast<R>(z);
+    o[1] = ccast<R>(vals[q]);
+    o[2] = ccast<R>(z);
+  }
+}
+
+// Same for a stored 9-point operator (planes st[(dy+1)*3+(dx+1)][y][x]).
+template <typename R>
+__global__ void inj_fe_kernel(int ny, int nx, int beta, int bt, const c128* st, cplx<R>* inj) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ny) return;
+  size_t plane = (size_t)ny * nx;
+  for (int d = 0; d < 3; ++d) {
+    int dy = d - 1;
+    c128 z = mk(0.0, 0.0);
+    c128 f0 = z, f1 = z, b0 = z, b1 = z;
+    if (beta >= 0) {
+      f0 = st[(size_t)(d * 3 + 2) * plane + (size_t)k * nx + beta];         // A_{(k,b),(k+dy,b+1)}
+      f1 = -st[(size_t)(d * 3 + 0) * plane + (size_t)k * nx + beta + 1];    // -A_{(k,b+1),(k+dy,b)}
+    }
+    if (bt >= 0) {
+      b0 = -st[(size_t)(d * 3 + 2) * plane + (size_t)k * nx + bt];
+      b1 = st[(size_t)(d * 3 + 0) * plane + (size_t)k * nx + bt + 1];
+    }
+    c128 vals[4] = {f0, f1, b0, b1};
+    for (int q = 0; q < 4; ++q) inj[((size_t)q * ny + k) * 3 + d] = ccast<R>(vals[q]);
+  }
+}
+
+// Slab stencil copied from a stored 9-point operator; k frozen is built into
+// the coarse-level slab operator by the FE assembly kernel (fe.cu).
+__global__ void mean_inv_sqrt_kernel(const double* m, size_t n, double* partial) {
+  __shared__ double sh[256];
+  double acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    acc += 1.0 / sqrt(m[i]);
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+double mean_velocity(const double* m_dev, size_t n, cudaStream_t s) {
+  const int blocks = 304;
+  double* part = (double*)dmalloc(blocks * sizeof(double));
+  mean_inv_sqrt_kernel<<<blocks, 256, 0, s>>>(m_dev, n, part);
+  std::vector<double> hp(blocks);
+  cudaError_t e = cudaMemcpyAsync(hp.data(), part, blocks * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(part);
+  if (e != cudaSuccess) throw Failure(HZ_ECUDA, std::string("mean velocity: ") + cudaGetErrorString(e));
+  double acc = 0;
+  for (double v : hp) acc += v;
+  return acc / (double)n;
+}
+
+static void alloc_axis(AxisTables& a, int N) {
+  a.N = N;
+  a.a_node = (c128*)dmalloc(sizeof(c128) * N);
+  a.a_cell = (c128*)dmalloc(sizeof(c128) * (N + 1));
+  a.h_cell = (double*)dmalloc(sizeof(double) * (N + 1));
+  a.a_node32 = (c64*)dmalloc(sizeof(c64) * N);
+  a.a_cell32 = (c64*)dmalloc(sizeof(c64) * (N + 1));
+}
+
+static void free_axis(AxisTables& a) {
+  dfree(a.a_node); dfree(a.a_cell); dfree(a.h_cell); dfree(a.a_node32); dfree(a.a_cell32);
+  a = AxisTables{};
+}
+
+__global__ void to_float_kernel(const double* a, float* b, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const double* m_dev,
+                    cudaStream_t s) {
+  int n_cells = n + 2 * w_out;
+  L.nx = L.ny = n_cells - 1;
+  L.h = hh;
+  L.fe = false;
+  double C = (w_out > 0) ? h->p.s_pml_out * h->c_pml / std::pow(w_out * hh, 3) : 0.0;
+  for (AxisTables* a : {&L.ax, &L.ay}) {
+    alloc_axis(*a, L.nx);
+    fine_axis_kernel<<<cdiv(L.nx + 1, 256), 256, 0, s>>>(L.nx, n_cells, w_out, hh, C,
+                                                         h->p.omega, a->a_node, a->a_cell,
+                                                         a->h_cell, a->a_node32, a->a_cell32);
+  }
+  size_t nn = (size_t)L.nx * L.ny;
+  if (!L.m) L.m = (double*)dmalloc(sizeof(double) * nn);
+  if (!L.m32) L.m32 = (float*)dmalloc(sizeof(float) * nn);
+  HZ_CU(cudaMemcpyAsync(L.m, m_dev, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  to_float_kernel<<<cdiv(nn, 256), 256, 0, s>>>(L.m, L.m32, nn);
+  HZ_CU(cudaGetLastError());
+}
+
+// Partition (Eq. 17): beta_0 = -1, beta_J = N-1, first N mod J slabs one wider.
+static void partition(Level& L) {
+  int N = L.nx, J = L.J;
+  L.beta.assign(J + 1, 0);
+  L.beta[0] = -1;
+  for (int j = 0; j < J; ++j) L.beta[j + 1] = L.beta[j] + N / J + (j < N % J ? 1 : 0);
+  L.beta_t = L.beta;
+  for (int j = 1; j < J; ++j) L.beta_t[j] = L.beta[j] - 1;
+}
+
+template <typename R>
+static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
+  partition(L);
+  L.slabs.assign(L.J + 1, Slab{});
+  int maxW = 0;
+  for (int j = 1; j <= L.J; ++j) {
+    Slab& S = L.slabs[j];
+    S.j = j;
+    S.lo = L.beta_t[j - 1] + 1;
+    S.hi = L.beta[j];
+    S.wl = (j > 1) ? L.w : 0;
+    S.wr = (j < L.J) ? L.w : 0;
+    S.W = S.hi - S.lo + 1 + S.wl + S.wr;
+    maxW = std::max(maxW, S.W);
+    alloc_axis(S.ax, S.W);
+    slab_axis_kernel<<<cdiv(S.W + 1, 128), 128, 0, s>>>(
+        S.W, S.lo, S.hi, S.wl, L.ax.a_node, L.ax.a_cell, L.ax.h_cell, h->p.s_pml_dd, h->c_pml,
+        L.w, h->p.omega, S.ax.a_node, S.ax.a_cell, S.ax.h_cell, S.ax.a_node32, S.ax.a_cell32);
+    S.st = dmalloc(sizeof(cplx<R>) * (size_t)L.ny * 9 * S.W);
+    S.inj = dmalloc(sizeof(cplx<R>) * 4 * (size_t)L.ny * 3);
+    int beta = (j > 1) ? L.beta[j - 1] : -1;
+    int bt = (j < L.J) ? L.beta_t[j] : -1;
+    if (!L.fe) {
+      dim3 grid(cdiv(S.W, 128), L.ny);
+      double h2w2 = L.h * L.h * h->p.omega * h->p.omega;
+      slab_stencil_fd_kernel<R><<<grid, 128, 0, s>>>(S.W, L.ny, S.lo, S.hi, S.wl, L.nx, h2w2,
+                                                     L.m, S.ax.a_node, S.ax.a_cell, L.ay.a_node,
+                                                     L.ay.a_cell, (cplx<R>*)S.st);
+      inj_fd_kernel<R><<<cdiv(L.ny, 128), 128, 0, s>>>(L.ny, beta, bt, L.ax.a_cell, L.ay.a_node,
+                                                       (cplx<R>*)S.inj);
+    } else {
+      inj_fe_kernel<R><<<cdiv(L.ny, 128), 128, 0, s>>>(L.ny, L.nx, beta, bt, L.st128,
+                                                       (cplx<R>*)S.inj);
+    }
+    HZ_CU(cudaGetLastError());
+    // factor storage: W*W elements rounded up to a 16-byte multiple per block row
+    size_t per = (size_t)S.W * S.W;
+    size_t elems16 = 16 / sizeof(cplx<R>);
+    if (elems16 < 1) elems16 = 1;
+    S.gstride = (per + elems16 - 1) / elems16 * elems16;
+    S.G = dmalloc(sizeof(cplx<R>) * S.gstride * L.ny);
+    S.Y = dmalloc(sizeof(cplx<R>) * (size_t)h->p.max_rhs * L.ny * S.W);
+  }
+  // segments over block rows for the parallel-in-y slab solve
+  int P = h->p.segments;
+  if (P <= 0) P = std::max(1, (int)std::lround(std::sqrt(L.ny / 2.0)));
+  P = std::min(P, L.ny);
+  L.P = P;
+  L.seg.assign(P + 1, 0);
+  for (int q = 0; q <= P; ++q) L.seg[q] = (int)((long long)L.ny * q / P);
+  L.seg_dev = (int*)dmalloc(sizeof(int) * (P + 1));
+  HZ_CU(cudaMemcpyAsync(L.seg_dev, L.seg.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
+  for (int j = 1; j <= L.J; ++j) {
+    Slab& S = L.slabs[j];
+    if (P > 1) {
+      S.Phi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
+      S.Psi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
+    }
+    S.carry_f = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.W);
+    S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.W);
+  }
+  HZ_CU(cudaStreamSynchronize(s));
+}
+
+void build_slabs(hz_handle* h, Level& L, cudaStream_t s) {
+  if (h->p.precision == HZ_MIXED)
+    build_slabs_t<float>(h, L, s);
+  else
+    build_slabs_t<double>(h, L, s);
+}
+
+void free_level(Level& L) {
+  for (Slab& S : L.slabs) {
+    free_axis(S.ax);
+    dfree(S.st); dfree(S.G); dfree(S.Phi); dfree(S.Psi); dfree(S.inj); dfree(S.Y);
+    dfree(S.carry_f); dfree(S.carry_b);
+  }
+  L.slabs.clear();
+  free_axis(L.ax);
+  free_axis(L.ay);
+  dfree(L.m); dfree(L.m32); dfree(L.st128); dfree(L.st64); dfree(L.seg_dev);
+  L.m = nullptr; L.m32 = nullptr; L.st128 = nullptr; L.st64 = nullptr; L.seg_dev = nullptr;
+}
+
+}  // namespace hz

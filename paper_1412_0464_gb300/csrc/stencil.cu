@@ -1,0 +1,202 @@
+// Matrix-free Helmholtz operator kernels.
+//
+// Fine level: Eq. 40 multiplied by h^2, coefficients recomputed on the fly
+// from m and the 1-D PML tables (alpha at unknowns and at cell midpoints):
+//   (A u)_{k,x} = (1/a2_k)(-a1_{x-1/2} u_{k,x-1} + (a1_{x-1/2}+a1_{x+1/2}) u_{k,x} - a1_{x+1/2} u_{k,x+1})
+//               + (1/a1_x)(-a2_{k-1/2} u_{k-1,x} + (a2_{k-1/2}+a2_{k+1/2}) u_{k,x} - a2_{k+1/2} u_{k+1,x})
+//               - h^2 omega^2 m_{k,x} / (a1_x a2_k) u_{k,x}
+// with a_{i-1/2} = cell i and a_{i+1/2} = cell i+1, Dirichlet zeros outside.
+// Coarse level: a stored 9-point stencil (9 coefficient planes).
+#include "hz_internal.h"
+
+namespace hz {
+
+template <typename R> struct Tab;
+template <> struct Tab<double> {
+  static const c128* node(const AxisTables& a) { return a.a_node; }
+  static const c128* cell(const AxisTables& a) { return a.a_cell; }
+};
+template <> struct Tab<float> {
+  static const c64* node(const AxisTables& a) { return a.a_node32; }
+  static const c64* cell(const AxisTables& a) { return a.a_cell32; }
+};
+template <typename R> struct Med;
+template <> struct Med<double> { static const double* m(const Level& L) { return L.m; } };
+template <> struct Med<float> { static const float* m(const Level& L) { return L.m32; } };
+template <typename R> struct Planes;
+template <> struct Planes<double> { static const c128* st(const Level& L) { return L.st128; } };
+template <> struct Planes<float> { static const c64* st(const Level& L) { return L.st64; } };
+
+struct FdArgs {
+  int nx, ny;
+  double h2w2;
+};
+
+// Returns (A u)_{k,x} and the diagonal entry of A.
+template <typename R>
+__device__ __forceinline__ cplx<R> fd_row(const cplx<R>* __restrict__ u, int nx, int ny, int k,
+                                          int x, R h2w2, const R* __restrict__ m,
+                                          const cplx<R>* __restrict__ a1n,
+                                          const cplx<R>* __restrict__ a1c,
+                                          const cplx<R>* __restrict__ a2n,
+                                          const cplx<R>* __restrict__ a2c, cplx<R>* diag) {
+  const cplx<R> z = mk<R>(0, 0);
+  cplx<R> uc = u[(size_t)k * nx + x];
+  cplx<R> ul = (x > 0) ? u[(size_t)k * nx + x - 1] : z;
+  cplx<R> ur = (x < nx - 1) ? u[(size_t)k * nx + x + 1] : z;
+  cplx<R> ud = (k > 0) ? u[(size_t)(k - 1) * nx + x] : z;
+  cplx<R> uu = (k < ny - 1) ? u[(size_t)(k + 1) * nx + x] : z;
+  cplx<R> ia2 = cinv(a2n[k]);
+  cplx<R> ia1 = cinv(a1n[x]);
+  cplx<R> l = a1c[x], r = a1c[x + 1], d = a2c[k], up = a2c[k + 1];
+  cplx<R> tx = (l + r) * uc - l * ul - r * ur;
+  cplx<R> ty = (d + up) * uc - d * ud - up * uu;
+  cplx<R> mass = (h2w2 * m[(size_t)k * nx + x]) * (ia1 * ia2);
+  if (diag) *diag = ia2 * (l + r) + ia1 * (d + up) - mass;
+  return ia2 * tx + ia1 * ty - mass * uc;
+}
+
+template <typename R>
+__device__ __forceinline__ cplx<R> st_row(const cplx<R>* __restrict__ u, int nx, int ny, int k,
+                                          int x, const cplx<R>* __restrict__ st,
+                                          cplx<R>* diag) {
+  size_t plane = (size_t)nx * ny;
+  cplx<R> acc = mk<R>(0, 0);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    int kk = k + dy;
+    if (kk < 0 || kk >= ny) continue;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      int xx = x + dx;
+      if (xx < 0 || xx >= nx) continue;
+      cfma(acc, st[(size_t)((dy + 1) * 3 + dx + 1) * plane + (size_t)k * nx + x],
+           u[(size_t)kk * nx + xx]);
+    }
+  }
+  if (diag) *diag = st[4 * plane + (size_t)k * nx + x];
+  return acc;
+}
+
+// mode 0: y = A u;  mode 1: y = f - A u;
+// mode 2 (Jacobi): y = u + omega (f - A u) / diag(A)
+template <typename R, bool STORED>
+__global__ void __launch_bounds__(256) op_kernel(int mode, int nx, int ny, R h2w2,
+                                                 const R* __restrict__ m,
+                                                 const cplx<R>* __restrict__ a1n,
+                                                 const cplx<R>* __restrict__ a1c,
+                                                 const cplx<R>* __restrict__ a2n,
+                                                 const cplx<R>* __restrict__ a2c,
+                                                 const cplx<R>* __restrict__ st,
+                                                 const cplx<R>* __restrict__ f,
+                                                 const cplx<R>* __restrict__ u,
+                                                 cplx<R>* __restrict__ y, R omega_jac) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  int r = blockIdx.z;
+  if (x >= nx) return;
+  size_t off = (size_t)r * nx * ny;
+  const cplx<R>* ur = u + off;
+  cplx<R> dg;
+  cplx<R> au = STORED ? st_row<R>(ur, nx, ny, k, x, st, mode == 2 ? &dg : nullptr)
+                      : fd_row<R>(ur, nx, ny, k, x, h2w2, m, a1n, a1c, a2n, a2c,
+                                  mode == 2 ? &dg : nullptr);
+  size_t i = off + (size_t)k * nx + x;
+  if (mode == 0) {
+    y[i] = au;
+  } else if (mode == 1) {
+    y[i] = f[i] - au;
+  } else {
+    cplx<R> res = f[i] - au;
+    y[i] = ur[(size_t)k * nx + x] + omega_jac * (res * cinv(dg));
+  }
+}
+
+template <typename R>
+static void launch_op(hz_handle* h, const Level& L, int mode, const cplx<R>* f,
+                      const cplx<R>* u, cplx<R>* y, int n_rhs, double omega_jac,
+                      cudaStream_t s) {
+  dim3 block(128);
+  dim3 grid(cdiv(L.nx, 128), L.ny, n_rhs);
+  R h2w2 = (R)(L.h * L.h * h->p.omega * h->p.omega);
+  if (L.fe)
+    op_kernel<R, true><<<grid, block, 0, s>>>(mode, L.nx, L.ny, h2w2, nullptr, nullptr, nullptr,
+                                              nullptr, nullptr, Planes<R>::st(L), f, u, y,
+                                              (R)omega_jac);
+  else
+    op_kernel<R, false><<<grid, block, 0, s>>>(
+        mode, L.nx, L.ny, h2w2, Med<R>::m(L), Tab<R>::node(L.ax), Tab<R>::cell(L.ax),
+        Tab<R>::node(L.ay), Tab<R>::cell(L.ay), nullptr, f, u, y, (R)omega_jac);
+  h->launches++;
+  HZ_CU(cudaGetLastError());
+}
+
+template <typename R>
+void level_apply(hz_handle* h, const Level& L, const cplx<R>* u, cplx<R>* y, int n_rhs,
+                 cudaStream_t s) {
+  launch_op<R>(h, L, 0, nullptr, u, y, n_rhs, 0.0, s);
+}
+
+template <typename R>
+void level_residual(hz_handle* h, const Level& L, const cplx<R>* f, const cplx<R>* u,
+                    cplx<R>* r, int n_rhs, cudaStream_t s) {
+  launch_op<R>(h, L, 1, f, u, r, n_rhs, 0.0, s);
+}
+
+// nu omega-Jacobi steps u <- u + omega D^-1 (f - A u) (Section 4.1), ping-pong
+// between u and t; the result ends in u.
+template <typename R>
+void jacobi_steps(hz_handle* h, const Level& L, const cplx<R>* f, cplx<R>* u, cplx<R>* t,
+                  int nu, double omega_jac, int n_rhs, cudaStream_t s) {
+  for (int i = 0; i < nu; ++i) {
+    launch_op<R>(h, L, 2, f, u, t, n_rhs, omega_jac, s);
+    HZ_CU(cudaMemcpyAsync(u, t, sizeof(cplx<R>) * (size_t)n_rhs * L.nx * L.ny,
+                          cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+void apply_fine64(hz_handle* h, const c128* u, c128* y, int n_rhs, cudaStream_t s) {
+  level_apply<double>(h, h->fine, u, y, n_rhs, s);
+}
+
+template <typename To, typename From>
+__global__ void cast_kernel(const cplx<From>* a, cplx<To>* b, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = ccast<To>(a[i]);
+}
+
+template <typename To, typename From>
+void cast_copy(const cplx<From>* a, cplx<To>* b, size_t n, cudaStream_t s) {
+  cast_kernel<To, From><<<cdiv(n, 256), 256, 0, s>>>(a, b, n);
+  HZ_CU(cudaGetLastError());
+}
+
+void check_dev_flag(hz_handle* h, cudaStream_t s) {
+  int flag = 0;
+  HZ_CU(cudaMemcpyAsync(&flag, h->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HZ_CU(cudaStreamSynchronize(s));
+  if (flag == DEV_TIMEOUT) {
+    HZ_CU(cudaMemsetAsync(h->dev_flag, 0, sizeof(int), s));
+    throw Failure(HZ_ETIMEOUT, "a bounded device-side wait gave up");
+  }
+  if (flag != DEV_OK) {
+    HZ_CU(cudaMemsetAsync(h->dev_flag, 0, sizeof(int), s));
+    throw Failure(HZ_ECUDA, "device error flag " + std::to_string(flag));
+  }
+}
+
+template void level_apply<double>(hz_handle*, const Level&, const c128*, c128*, int, cudaStream_t);
+template void level_apply<float>(hz_handle*, const Level&, const c64*, c64*, int, cudaStream_t);
+template void level_residual<double>(hz_handle*, const Level&, const c128*, const c128*, c128*,
+                                     int, cudaStream_t);
+template void level_residual<float>(hz_handle*, const Level&, const c64*, const c64*, c64*, int,
+                                    cudaStream_t);
+template void jacobi_steps<double>(hz_handle*, const Level&, const c128*, c128*, c128*, int,
+                                   double, int, cudaStream_t);
+template void jacobi_steps<float>(hz_handle*, const Level&, const c64*, c64*, c64*, int, double,
+                                  int, cudaStream_t);
+template void cast_copy<float, double>(const c128*, c64*, size_t, cudaStream_t);
+template void cast_copy<double, float>(const c64*, c128*, size_t, cudaStream_t);
+template void cast_copy<double, double>(const c128*, c128*, size_t, cudaStream_t);
+
+}  // namespace hz

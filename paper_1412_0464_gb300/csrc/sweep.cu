@@ -1,0 +1,103 @@
+// Sweep schedules of Tables 2-3: ForwardSweep, BackwardSweep, MidSolveIn,
+// MidSolveOut, SweepingPrecUD and SweepingPrecX.  In the X-sweep the two
+// chains that the paper runs simultaneously (forward over 1..j_mid-1 and
+// backward over J..j_mid+1, then backward over j_mid-1..1 and forward over
+// j_mid+1..J) run on two CUDA streams joined by events; they touch disjoint
+// columns of u, disjoint slabs and separate transmission buffers.
+#include "hz_internal.h"
+
+namespace hz {
+
+template <typename R>
+static void forward_sweep(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, int j0, int j1,
+                          cplx<R>* B, int nr, cudaStream_t s) {
+  const auto& be = L.beta;
+  for (int j = j0; j <= j1; ++j)
+    subdom_solve<R>(h, L, j, f, be[j - 1], be[j], be[j - 1], be[j], j > 1, B, j < L.J, B, false,
+                    nullptr, false, nullptr, u, nr, s);
+}
+
+template <typename R>
+static void backward_sweep(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, int j0, int j1,
+                           cplx<R>* B, int nr, cudaStream_t s) {
+  const auto& bt = L.beta_t;
+  for (int j = j0; j >= j1; --j)
+    subdom_solve<R>(h, L, j, f, bt[j - 1], bt[j], bt[j - 1], bt[j], false, nullptr, false,
+                    nullptr, j < L.J, B, j > 1, B, u, nr, s);
+}
+
+template <typename R>
+static void mid_solve_in(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, int j, cplx<R>* B1,
+                         cplx<R>* B2, int nr, cudaStream_t s) {
+  subdom_solve<R>(h, L, j, f, L.beta[j - 1], L.beta_t[j], L.beta[j - 1], L.beta_t[j], true, B1,
+                  false, nullptr, true, B2, false, nullptr, u, nr, s);
+}
+
+template <typename R>
+static void mid_solve_out(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, int j, cplx<R>* B1,
+                          cplx<R>* B2, int nr, cudaStream_t s) {
+  subdom_solve<R>(h, L, j, f, L.beta_t[j - 1], L.beta[j], L.beta_t[j - 1], L.beta[j], false,
+                  nullptr, true, B1, false, nullptr, true, B2, u, nr, s);
+}
+
+template <typename R>
+void sweep_apply(hz_handle* h, Level& L, const cplx<R>* f, cplx<R>* u, int nr, cudaStream_t s) {
+  const size_t n = (size_t)L.nx * L.ny;
+  cplx<R>* g = (cplx<R>*)h->pr_g;
+  cplx<R>* B1 = (cplx<R>*)h->pr_B1;
+  cplx<R>* B2 = (cplx<R>*)h->pr_B2;
+  HZ_CU(cudaMemsetAsync(u, 0, sizeof(cplx<R>) * n * nr, s));
+  const int J = L.J;
+  if (h->p.sweep == HZ_SWEEP_UD) {                  // SweepingPrecUD
+    forward_sweep<R>(h, L, u, f, 1, J, B1, nr, s);
+    level_residual<R>(h, L, f, u, g, nr, s);
+    backward_sweep<R>(h, L, u, g, J, 1, B1, nr, s);
+    return;
+  }
+  const int jm = J / 2 + 1;                          // SweepingPrecX
+  cudaStream_t s2 = h->s2;
+  HZ_CU(cudaEventRecord(h->evA, s));
+  HZ_CU(cudaStreamWaitEvent(s2, h->evA, 0));
+  forward_sweep<R>(h, L, u, f, 1, jm - 1, B1, nr, s);
+  backward_sweep<R>(h, L, u, f, J, jm + 1, B2, nr, s2);
+  HZ_CU(cudaEventRecord(h->evB, s2));
+  HZ_CU(cudaStreamWaitEvent(s, h->evB, 0));
+  mid_solve_in<R>(h, L, u, f, jm, B1, B2, nr, s);
+  level_residual<R>(h, L, f, u, g, nr, s);
+  mid_solve_out<R>(h, L, u, g, jm, B2, B1, nr, s);
+  HZ_CU(cudaEventRecord(h->evA, s));
+  HZ_CU(cudaStreamWaitEvent(s2, h->evA, 0));
+  backward_sweep<R>(h, L, u, g, jm - 1, 1, B1, nr, s);
+  forward_sweep<R>(h, L, u, g, jm + 1, J, B2, nr, s2);
+  HZ_CU(cudaEventRecord(h->evB, s2));
+  HZ_CU(cudaStreamWaitEvent(s, h->evB, 0));
+}
+
+template <typename R>
+static void precond_t(hz_handle* h, const c128* r, c128* z, int nr, cudaStream_t s) {
+  Level& F = h->fine;
+  const size_t n = (size_t)F.nx * F.ny;
+  if (!h->p.two_grid) {
+    if (sizeof(R) == 8) {
+      sweep_apply<R>(h, F, (const cplx<R>*)r, (cplx<R>*)z, nr, s);
+    } else {
+      cast_copy<R, double>(r, (cplx<R>*)h->pr_r, n * nr, s);
+      sweep_apply<R>(h, F, (const cplx<R>*)h->pr_r, (cplx<R>*)h->pr_u, nr, s);
+      cast_copy<double, R>((const cplx<R>*)h->pr_u, z, n * nr, s);
+    }
+    return;
+  }
+  throw Failure(HZ_EINVAL, "two-grid preconditioner is not built in this version");
+}
+
+void precond_apply(hz_handle* h, const c128* r, c128* z, int nr, cudaStream_t s) {
+  if (h->p.precision == HZ_MIXED)
+    precond_t<float>(h, r, z, nr, s);
+  else
+    precond_t<double>(h, r, z, nr, s);
+}
+
+template void sweep_apply<float>(hz_handle*, Level&, const c64*, c64*, int, cudaStream_t);
+template void sweep_apply<double>(hz_handle*, Level&, const c128*, c128*, int, cudaStream_t);
+
+}  // namespace hz
