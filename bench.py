@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark: time to a 1e-6 relative residual (and Mdof/s) of the GMRES +
+sweeping-preconditioner solve of the 2-D heterogeneous workload
+(1000^2 interior cells + 20 PML cells per side = 1039^2 unknowns, seeded
+random-field + layer medium, one point source, J = 16 slabs, X-sweep,
+complex64 preconditioner, FP64 GMRES).
+
+One step = hz_factor + hz_solve (factorise every slab, then solve to 1e-6).
+Inputs are resident in HBM when the timed region starts; L2 is flushed
+(256 MiB write) between timed steps, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank solves its own replica of the workload (the
+path has no data-path exchange for one right-hand side): value = all ranks'
+dof / max-over-ranks time.  Prints one JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-6 rel. residual (s) and Mdof/s; mixed+batched vs plain FP64 on GB300"
+CONFIG_INDEX = 2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.idx = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.idx is not None:
+                cmd += ["-i", str(self.idx)]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _slab_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1412_0464_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1412_0464_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(tag):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != _slab_hash():
+        return None
+    e = d.get("kernels", {}).get(tag)
+    return None if e is None else e.get("dram_bytes_per_launch_full_size")
+
+
+def cpu_baseline(cfg, iters_hint):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload.
+
+    Sample: oracle set-up (assembly + sparse LU of every slab) and one GMRES
+    iteration's work (one X-sweep application + one operator application) on
+    the full workload; time to solution is estimated as set-up +
+    iterations x per-iteration time, with the iteration count of the run.
+    """
+    import numpy as np
+    import synth
+    from oracle.problem import Problem
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    p = Problem(cfg)
+    t1 = time.perf_counter()
+    b = synth.sources(cfg)[0].ravel()
+    z = p.precondition(b)
+    w = p.apply(z)
+    t2 = time.perf_counter()
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    wall = t2 - t0
+    t_setup, t_iter = t1 - t0, t2 - t1
+    t_sol = t_setup + iters_hint * t_iter
+    del w
+    return {"value": cfg.ndof / t_sol / 1e6, "unit": "Mdof/s",
+            "cores": max(1, round(cpu / wall)), "kind": "oracle",
+            "sample": (f"full {cfg.N}x{cfg.N} workload: oracle set-up {t_setup:.2f} s + one GMRES "
+                       f"iteration (X-sweep + matvec) {t_iter:.2f} s; time to solution estimated as "
+                       f"set-up + {iters_hint} x iteration = {t_sol:.1f} s"),
+            "time_to_solution_s_est": t_sol, "host_cores_available": os.cpu_count()}
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    from oracle.problem import Problem
+    cfg = synth.workload(CONFIG_INDEX)
+    b = synth.sources(cfg)[0]
+    t0 = time.perf_counter()
+    p = Problem(cfg)
+    t_setup = time.perf_counter() - t0
+    # warm-up: the first warm-up step runs the oracle's full solve once to fix
+    # the iteration count; later steps time one GMRES iteration's work each.
+    _, info = p.solve(b)
+    iters = info["iters"]
+    for _ in range(max(0, args.warmup - 1)):
+        p.apply(p.precondition(b.ravel()))
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    ts = []
+    tw0 = time.perf_counter()
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        p.apply(p.precondition(b.ravel()))
+        ts.append(time.perf_counter() - t)
+    wall = time.perf_counter() - tw0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    t_iter = statistics.mean(ts)
+    t_sol = t_setup + iters * t_iter
+    value = cfg.ndof / t_sol / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mdof/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_sol,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": cfg.name, "dof": cfg.ndof, "n_rhs": 1, "J": cfg.J,
+                       "sweep": cfg.sweep, "step": "oracle set-up + iterations x one GMRES iteration"},
+            "cpu_baseline": {"value": value, "unit": "Mdof/s", "kind": "oracle",
+                             "cores": max(1, round(cpu / wall)),
+                             "sample": (f"set-up {t_setup:.2f} s once; each step one GMRES iteration "
+                                        f"({t_iter:.2f} s mean); {iters} iterations (oracle full solve)")},
+            "e2e": {"value": value, "unit": "Mdof/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iters": iters}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1412_0464_gb300 as hz
+    import synth
+    if rank == 0:
+        hz.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    cfg = synth.workload(CONFIG_INDEX)
+    m = synth.medium(cfg)
+    b = synth.sources(cfg)
+    solver = hz.Solver.from_workload(cfg, m=m)
+    f_dev = torch.from_numpy(b).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        solver.factor()
+        return solver.solve(f_dev)
+
+    for _ in range(args.warmup):
+        u, st = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gidx = vis.split(",")[local] if vis and vis.split(",")[local].strip().isdigit() else (local if ws > 1 else None)
+    clocks = ClockSampler(gidx)
+    launches0 = solver.stats()["kernel_launches"]
+    solver.enable_timing(True)
+    clocks.start()
+    barrier()
+    total_ms = 0.0
+    iters, relres, solve_s = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, st = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        iters.append(st["iters_max"])
+        relres.append(st["relres_max"])
+        solve_s.append(st["t_solve_s"])
+    barrier()
+    clk = clocks.stop()
+    gpu_launches = solver.stats()["kernel_launches"] - launches0
+    tags = ["slab_fwd_pass1", "slab_fwd_bwd1", "slab_bwd", "slab_carry", "slab_fwd", "slab_solve"]
+    kt = {t: solver.kernel_timing(t) for t in tags}
+    solver.enable_timing(False)
+    ms_step = total_ms / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t)
+    value = ws * cfg.ndof * cfg.n_src / (ms_step / 1000.0) / 1e6
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    f_host = torch.from_numpy(b).pin_memory()
+    e2e_ms = []
+    for i in range(max(2, min(args.steps, 3)) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.factor()
+        u_host, _ = solver.solve_host(f_host)
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_ms = statistics.mean(e2e_ms[1:])
+    nbytes = cfg.ndof * cfg.n_src * 16
+
+    # dominant slab kernel: the largest summed time among the per-kernel tags
+    peak, peak_kind = _peaks()
+    per_kernel = {t: {"ms": v[0], "launches": v[1], "bytes": v[2]} for t, v in kt.items() if v[1] > 0}
+    kernels = {t: v for t, v in per_kernel.items() if t != "slab_solve"}
+    dom = max(kernels, key=lambda t: kernels[t]["ms"])
+    d = kernels[dom]
+    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+    sol = per_kernel.get("slab_solve")
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": _traffic(dom),
+                "avg_launch_us": 1000 * d["ms"] / d["launches"],
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"]}
+    if sol:
+        roofline["slab_solve_sequence"] = {
+            "achieved_gbs": sol["bytes"] / (sol["ms"] / 1000.0) / 1e9,
+            "avg_us": 1000 * sol["ms"] / sol["launches"], "solves": sol["launches"],
+            "note": "whole subdomain solve (all its kernels), method-minimal bytes (G read twice)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mdof/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 preconditioner / c128 GMRES",
+            "data": "synthetic (seeded random-field + layer medium, point source)",
+            "config": {"workload": f"{cfg.name}: {cfg.N}x{cfg.N} dof, J={cfg.J}, X-sweep, w_dd={cfg.w_dd}",
+                       "n_rhs": cfg.n_src, "step": "hz_factor + hz_solve",
+                       "l2": "flushed (256 MiB write) between timed steps",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "time_to_solution_s": ms_step / 1000.0, "solve_only_s": statistics.mean(solve_s),
+            "iters": max(iters), "relres": max(relres),
+            "e2e": {"value": cfg.ndof * cfg.n_src / (e2e_ms / 1000.0) / 1e6, "unit": "Mdof/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "roofline": roofline, "kernels": per_kernel, "clocks": clk, "gpu_launches": gpu_launches}
+    solver.close()
+
+    if rank == 0 and ws == 1 and not args.no_fp64_arm:
+        s64 = hz.Solver.from_workload(cfg, m=m, precision="fp64")
+        s64.factor()
+        s64.solve(f_dev)
+        ts, it64 = [], 0
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s64.factor()
+            _, st64 = s64.solve(f_dev)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            it64 = st64["iters_max"]
+        t64 = statistics.mean(ts) / 1000.0
+        line["fp64_arm"] = {"time_to_solution_s": t64, "value": cfg.ndof / t64 / 1e6,
+                            "unit": "Mdof/s", "iters": it64,
+                            "speedup_mixed_vs_fp64": t64 / (ms_step / 1000.0)}
+        s64.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, max(iters))
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -79,8 +79,8 @@ typedef struct {
   double t_setup_s;        /* wall time of the last hz_setup / hz_set_medium */
   double t_factor_s;       /* wall time of the last hz_factor */
   double t_solve_s;        /* wall time of the last hz_solve */
-  long long precond_applies;
-  long long kernel_launches; /* kernels this library launched in the last hz_solve */
+  long long precond_applies; /* preconditioner applications in the last hz_solve */
+  long long kernel_launches; /* kernels this handle has launched since hz_setup (cumulative) */
 } hz_stats;
 
 typedef struct hz_handle hz_handle;
@@ -107,8 +107,9 @@ hz_status hz_factor(hz_handle* h, void* stream);
 hz_status hz_solve(hz_handle* h, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,
                    void* stream, hz_stats* stats);
 
-/* Same as hz_solve with HOST arrays f_host / u_host (n_rhs * N^d complex128):
- * the host<->device copies are part of the call. */
+/* Same as hz_solve with HOST arrays f_host / u_host (n_rhs * N^d complex128,
+ * pinned or pageable): the host<->device copies are part of the call.  The
+ * first call allocates two device staging buffers owned by the handle. */
 hz_status hz_solve_host(hz_handle* h, const hz_c128* f_host, hz_c128* u_host, int n_rhs,
                         void* stream, hz_stats* stats);
 
@@ -134,12 +135,17 @@ hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_de
 /* Statistics of the last call; fills *out. */
 hz_status hz_get_stats(const hz_handle* h, hz_stats* out);
 
-/* Kernel-level timing of the slab-solve kernels (for roofline reporting):
- * when enabled, CUDA events bracket every slab-solve launch sequence on its
- * stream.  hz_slab_solve_timing returns the summed event time (ms), the
- * number of slab solves, and the algorithmic bytes they moved. */
+/* Kernel-level timing for roofline reporting.  hz_enable_timing(h, 1) resets
+ * the counters and brackets every launch of a tagged kernel with two CUDA
+ * events on the stream it is launched on (0 disables).  hz_kernel_timing
+ * returns, for one tag, the summed event time (ms), the number of launches
+ * and the algorithmic bytes those launches move (method minimum: each
+ * factor block read once per pass, vectors once).  Tags: "slab_solve" (one
+ * whole subdomain solve, Table 2 line 6), "slab_fwd", "slab_fwd_pass1",
+ * "slab_fwd_bwd1", "slab_carry", "slab_bwd".  Unknown tags return zeros. */
 hz_status hz_enable_timing(hz_handle* h, int on);
-hz_status hz_slab_solve_timing(hz_handle* h, double* ms, long long* solves, double* bytes);
+hz_status hz_kernel_timing(hz_handle* h, const char* tag, double* ms, long long* launches,
+                           double* bytes);
 
 const char* hz_last_error(const hz_handle* h);
 const char* hz_status_string(hz_status s);

@@ -60,9 +60,9 @@ _SIGNATURES = {
     "hz_slab_solve": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hz_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(hz_stats)]),
     "hz_enable_timing": (ctypes.c_int, [_H, ctypes.c_int]),
-    "hz_slab_solve_timing": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double),
-                                            ctypes.POINTER(ctypes.c_longlong),
-                                            ctypes.POINTER(ctypes.c_double)]),
+    "hz_kernel_timing": (ctypes.c_int, [_H, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_double)]),
     "hz_last_error": (ctypes.c_char_p, [_H]),
     "hz_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hz_destroy": (None, [_H]),
@@ -212,9 +212,11 @@ class Solver:
     def enable_timing(self, on=True):
         self._check(lib().hz_enable_timing(self.h, int(on)))
 
-    def slab_solve_timing(self):
+    def kernel_timing(self, tag):
+        """(ms, launches, algorithmic bytes) summed over launches of ``tag``."""
         ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
-        self._check(lib().hz_slab_solve_timing(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+        self._check(lib().hz_kernel_timing(self.h, tag.encode(), ctypes.byref(ms), ctypes.byref(n),
+                                           ctypes.byref(b)))
         return ms.value, n.value, b.value
 
     def stats(self):

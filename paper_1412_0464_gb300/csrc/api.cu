@@ -195,7 +195,6 @@ hz_status hz_solve(hz_handle* h, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs
     if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
     if (!f_dev || !u_dev) throw Failure(HZ_EINVAL, "NULL field pointer");
     double t0 = now_s();
-    h->launches = 0;
     h->stats.precond_applies = 0;
     try {
       gmres_solve(h, (const c128*)f_dev, (c128*)u_dev, n_rhs, s);
@@ -217,29 +216,27 @@ hz_status hz_solve_host(hz_handle* h, const hz_c128* f_host, hz_c128* u_host, in
                         void* stream, hz_stats* stats) {
   if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  c128* fd = nullptr;
-  c128* ud = nullptr;
+  const size_t n = (size_t)h->fine.nx * h->fine.ny * n_rhs;
   hz_status st = guarded(h, [&] {
     if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
     if (!f_host || !u_host) throw Failure(HZ_EINVAL, "NULL field pointer");
-    const size_t n = (size_t)h->fine.nx * h->fine.ny * n_rhs;
-    fd = (c128*)dmalloc(sizeof(c128) * n);
-    ud = (c128*)dmalloc(sizeof(c128) * n);
-    HZ_CU(cudaMemcpyAsync(fd, f_host, sizeof(c128) * n, cudaMemcpyHostToDevice, s));
+    if (!h->stage_f) {   // allocated once, on the first host call
+      const size_t cap = (size_t)h->fine.nx * h->fine.ny * h->p.max_rhs;
+      h->stage_f = (c128*)dmalloc(sizeof(c128) * cap);
+      h->stage_u = (c128*)dmalloc(sizeof(c128) * cap);
+    }
+    HZ_CU(cudaMemcpyAsync(h->stage_f, f_host, sizeof(c128) * n, cudaMemcpyHostToDevice, s));
   });
   if (st == HZ_OK) {
-    st = hz_solve(h, (const hz_c128*)fd, (hz_c128*)ud, n_rhs, stream, stats);
+    st = hz_solve(h, (const hz_c128*)h->stage_f, (hz_c128*)h->stage_u, n_rhs, stream, stats);
     if (st == HZ_OK || st == HZ_ENOTCONV) {
       hz_status st2 = guarded(h, [&] {
-        const size_t n = (size_t)h->fine.nx * h->fine.ny * n_rhs;
-        HZ_CU(cudaMemcpyAsync(u_host, ud, sizeof(c128) * n, cudaMemcpyDeviceToHost, s));
+        HZ_CU(cudaMemcpyAsync(u_host, h->stage_u, sizeof(c128) * n, cudaMemcpyDeviceToHost, s));
         HZ_CU(cudaStreamSynchronize(s));
       });
       if (st2 != HZ_OK) st = st2;
     }
   }
-  dfree(fd);
-  dfree(ud);
   return st;
 }
 
@@ -313,35 +310,48 @@ hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_de
 hz_status hz_get_stats(const hz_handle* h, hz_stats* out) {
   if (!h || !out) return HZ_EINVAL;
   *out = h->stats;
+  out->kernel_launches = h->launches;
   return HZ_OK;
 }
 
 hz_status hz_enable_timing(hz_handle* h, int on) {
   if (!h) return HZ_EINVAL;
-  h->timing.on = on != 0;
-  h->timing.used = 0;
-  h->timing.ms = 0;
-  h->timing.solves = 0;
-  h->timing.bytes = 0;
-  return HZ_OK;
+  return guarded(h, [&] {
+    for (auto& kv : h->timing.tags) {
+      TagTiming& t = kv.second;
+      for (size_t i = 0; i < t.used; ++i) HZ_CU(cudaEventSynchronize(t.ev[i].second));
+      t.used = 0;
+      t.ms = 0;
+      t.launches = 0;
+      t.bytes = 0;
+    }
+    h->timing.on = on != 0;
+  });
 }
 
-hz_status hz_slab_solve_timing(hz_handle* h, double* ms, long long* solves, double* bytes) {
-  if (!h) return HZ_EINVAL;
+hz_status hz_kernel_timing(hz_handle* h, const char* tag, double* ms, long long* launches,
+                           double* bytes) {
+  if (!h || !tag) return HZ_EINVAL;
   return guarded(h, [&] {
-    Timing& t = h->timing;
-    double acc = 0;
-    for (size_t i = 0; i < t.used; ++i) {
-      HZ_CU(cudaEventSynchronize(t.ev[i].second));
-      float x = 0;
-      HZ_CU(cudaEventElapsedTime(&x, t.ev[i].first, t.ev[i].second));
-      acc += x;
+    auto it = h->timing.tags.find(tag);
+    double m = 0, b = 0;
+    long long n = 0;
+    if (it != h->timing.tags.end()) {
+      TagTiming& t = it->second;
+      double acc = 0;
+      for (size_t i = 0; i < t.used; ++i) {
+        HZ_CU(cudaEventSynchronize(t.ev[i].second));
+        float x = 0;
+        HZ_CU(cudaEventElapsedTime(&x, t.ev[i].first, t.ev[i].second));
+        acc += x;
+      }
+      t.ms += acc;
+      t.used = 0;
+      m = t.ms; n = t.launches; b = t.bytes;
     }
-    t.ms += acc;
-    t.used = 0;
-    if (ms) *ms = t.ms;
-    if (solves) *solves = t.solves;
-    if (bytes) *bytes = t.bytes;
+    if (ms) *ms = m;
+    if (launches) *launches = n;
+    if (bytes) *bytes = b;
   });
 }
 
@@ -355,10 +365,13 @@ void hz_destroy(hz_handle* h) {
   if (h->s2) cudaStreamDestroy(h->s2);
   if (h->evA) cudaEventDestroy(h->evA);
   if (h->evB) cudaEventDestroy(h->evB);
-  for (auto& e : h->timing.ev) {
-    cudaEventDestroy(e.first);
-    cudaEventDestroy(e.second);
-  }
+  for (auto& kv : h->timing.tags)
+    for (auto& e : kv.second.ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  dfree(h->stage_f);
+  dfree(h->stage_u);
   cudaGetLastError();
   delete h;
 }

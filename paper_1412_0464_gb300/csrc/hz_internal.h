@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -120,14 +121,23 @@ struct Level {
   int* seg_dev = nullptr;
 };
 
-struct Timing {
-  bool on = false;
+// Per-kernel event timing (enabled for roofline reporting): every launch of a
+// tagged kernel is bracketed by two events on its own stream.
+struct TagTiming {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t used = 0;
   double ms = 0;
-  long long solves = 0;
+  long long launches = 0;
   double bytes = 0;
 };
+struct Timing {
+  bool on = false;
+  std::map<std::string, TagTiming> tags;   // node-based: references stay valid
+  TagTiming& tag(const std::string& name) { return tags[name]; }
+};
+// Records start/stop events around `launch` when timing is on.
+template <typename F>
+void timed(hz_handle* h, const char* tag, double bytes, cudaStream_t s, F&& launch);
 
 }  // namespace hz
 
@@ -162,7 +172,32 @@ struct hz_handle {
   hz::Timing timing;
   hz_stats stats{};
   long long launches = 0;
+  hz::c128* stage_f = nullptr;  // host-call staging buffers [max_rhs][n]
+  hz::c128* stage_u = nullptr;
 };
+
+namespace hz {
+template <typename F>
+void timed(hz_handle* h, const char* tag, double bytes, cudaStream_t s, F&& launch) {
+  if (!h->timing.on) {
+    launch();
+    return;
+  }
+  TagTiming& t = h->timing.tag(tag);
+  if (t.used == t.ev.size()) {
+    cudaEvent_t a, b;
+    HZ_CU(cudaEventCreate(&a));
+    HZ_CU(cudaEventCreate(&b));
+    t.ev.push_back({a, b});
+  }
+  auto& e = t.ev[t.used++];
+  HZ_CU(cudaEventRecord(e.first, s));
+  launch();
+  HZ_CU(cudaEventRecord(e.second, s));
+  t.launches++;
+  t.bytes += bytes;
+}
+}  // namespace hz
 
 namespace hz {
 

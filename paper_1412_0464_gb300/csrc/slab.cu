@@ -693,47 +693,45 @@ static void run_solve(hz_handle* h, Level& L, Slab& S, const Rhs<R>& rhs, const 
     HZ_CU(cudaFuncSetAttribute(slab_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
     attr_set[ai] = true;
   }
-  Timing& tm = h->timing;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (tm.on) {
-    if (tm.used == tm.ev.size()) {
-      cudaEvent_t x, y;
-      HZ_CU(cudaEventCreate(&x));
-      HZ_CU(cudaEventCreate(&y));
-      tm.ev.push_back({x, y});
-    }
-    e0 = tm.ev[tm.used].first;
-    e1 = tm.ev[tm.used].second;
-    tm.used++;
-    HZ_CU(cudaEventRecord(e0, s));
-  }
   const int P = L.P;
+  const double el = sizeof(cplx<R>);
+  const double gbytes = (double)L.ny * S.W * S.W * el;          // one pass over G_0..G_{ny-1}
+  const double vbytes = (double)n_rhs * L.ny * S.W * el;        // one slab-sized vector
+  const double pbytes = (double)P * S.W * S.W * el;             // one set of segment products
   dim3 grid(P);
-  if (P == 1) {
-    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 0);
-    slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
-    h->launches += 2;
-  } else {
-    size_t csm = 2 * (size_t)kNR * S.W * sizeof(cplx<R>);
-    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 0, 0);
-    slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Phi, 0);
-    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 1);
-    slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Psi, 1);
-    slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
-    h->launches += 5;
-  }
+  auto seq = [&] {
+    if (P == 1) {
+      timed(h, "slab_fwd", gbytes + 2 * vbytes, s, [&] {
+        slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 0);
+      });
+      timed(h, "slab_bwd", gbytes + 2 * vbytes, s, [&] {
+        slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
+      });
+      h->launches += 2;
+    } else {
+      size_t csm = 2 * (size_t)kNR * S.W * sizeof(cplx<R>);
+      timed(h, "slab_fwd_pass1", gbytes + vbytes, s, [&] {
+        slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 0, 0);
+      });
+      timed(h, "slab_carry", pbytes, s, [&] {
+        slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Phi, 0);
+      });
+      timed(h, "slab_fwd_bwd1", 2 * gbytes + 3 * vbytes, s, [&] {
+        slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 1);
+      });
+      timed(h, "slab_carry", pbytes, s, [&] {
+        slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Psi, 1);
+      });
+      timed(h, "slab_bwd", gbytes + 2 * vbytes, s, [&] {
+        slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
+      });
+      h->launches += 5;
+    }
+  };
+  // the whole slab solve; algorithmic bytes = the method's minimum: G read
+  // once per substitution direction plus right-hand side and solution
+  timed(h, "slab_solve", 2 * gbytes + 2 * vbytes, s, seq);
   HZ_CU(cudaGetLastError());
-  if (tm.on) {
-    HZ_CU(cudaEventRecord(e1, s));
-    tm.solves++;
-    // algorithmic bytes: G read per pass (2 for P = 1, 4 otherwise), products,
-    // right-hand side and solution traffic
-    double gb = (double)L.ny * S.W * S.W * sizeof(cplx<R>);
-    double passes = (P == 1) ? 2.0 : 4.0;
-    double prod = (P == 1) ? 0.0 : 2.0 * P * S.W * S.W * sizeof(cplx<R>);
-    double vec = (double)n_rhs * L.ny * S.W * sizeof(cplx<R>) * (P == 1 ? 4.0 : 6.0);
-    tm.bytes += passes * gb + prod + vec;
-  }
 }
 
 template <typename R>
