@@ -132,6 +132,24 @@ hz_status hz_slab_info(const hz_handle* h, int j, int* lo, int* hi, int* wl, int
 hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,
                         void* stream);
 
+/* hz_slab_solve without any device allocation.  (The paper has no
+ * counterpart: this serves callers that cannot allocate device memory at the
+ * time of the call -- code inside a CUDA stream capture, schedulers that
+ * forbid allocation after start-up, applications that own all device
+ * memory through their own pool.)  Same arguments, layout and result as
+ * hz_slab_solve.  Its work space is a fixed 8 MiB device array inside the
+ * library, present on every GPU that loads the library until the process
+ * exits; a call needing more (about 3 * n_rhs * N_t * W complex values in
+ * mixed precision, n_rhs * N_t * W in FP64, plus segment carries) returns
+ * HZ_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls whose GPU work overlaps (two streams, two host
+ * threads) race and give wrong results.  The call synchronises `stream`
+ * before returning.  Requires hz_factor. */
+hz_status hz_slab_solve_noalloc(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_dev,
+                                int n_rhs, void* stream);
+
 /* Statistics of the last call; fills *out. */
 hz_status hz_get_stats(const hz_handle* h, hz_stats* out);
 

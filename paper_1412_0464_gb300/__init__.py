@@ -58,6 +58,7 @@ _SIGNATURES = {
     "hz_precond": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P]),
     "hz_slab_info": (ctypes.c_int, [_H, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5),
     "hz_slab_solve": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "hz_slab_solve_noalloc": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hz_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(hz_stats)]),
     "hz_enable_timing": (ctypes.c_int, [_H, ctypes.c_int]),
     "hz_kernel_timing": (ctypes.c_int, [_H, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -207,6 +208,15 @@ class Solver:
         fb = (fd[None] if fd.dim() == 2 else fd).contiguous()
         u = torch.empty_like(fb)
         self._check(lib().hz_slab_solve(self.h, j, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream)))
+        return u[0] if fd.dim() == 2 else u
+
+    def slab_solve_noalloc(self, j, fd, stream=None):
+        """slab_solve through the entry point that allocates no device memory."""
+        import torch
+        fb = (fd[None] if fd.dim() == 2 else fd).contiguous()
+        u = torch.empty_like(fb)
+        self._check(lib().hz_slab_solve_noalloc(self.h, j, _ptr(fb), _ptr(u), fb.shape[0],
+                                                _stream(stream)))
         return u[0] if fd.dim() == 2 else u
 
     def enable_timing(self, on=True):

@@ -239,6 +239,10 @@ void subdom_solve(hz_handle* h, Level& L, int j, const cplx<R>* f, int a, int b,
 template <typename R>
 void slab_solve_raw(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud, int n_rhs,
                     cudaStream_t s);
+template <typename R>
+void slab_solve_raw_scratch(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud,
+                            int n_rhs, cudaStream_t s, cplx<R>* Y, cplx<R>* carry_f,
+                            cplx<R>* carry_b);
 
 // sweep.cu
 template <typename R>

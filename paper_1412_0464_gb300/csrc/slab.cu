@@ -781,3 +781,53 @@ template void slab_solve_raw<float>(hz_handle*, Level&, int, const c64*, c64*, i
 template void slab_solve_raw<double>(hz_handle*, Level&, int, const c128*, c128*, int, cudaStream_t);
 
 }  // namespace hz
+
+namespace hz {
+
+// Slab solve of a raw right-hand side with caller-provided work buffers
+// (forward-solution rows Y [n_rhs][ny][W] and segment carries
+// [P][n_rhs][W] each); launches the same kernels as slab_solve_raw and
+// allocates nothing.
+template <typename R>
+void slab_solve_raw_scratch(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud,
+                            int n_rhs, cudaStream_t s, cplx<R>* Y, cplx<R>* carry_f,
+                            cplx<R>* carry_b) {
+  Slab& S = L.slabs[j];
+  if (n_rhs > kNR) throw Failure(HZ_EINVAL, "too many right-hand sides per slab launch");
+  SolveArgs<R> a;
+  a.W = S.W; a.ny = L.ny; a.n_rhs = n_rhs; a.P = L.P; a.seg = L.seg_dev;
+  a.st = (const cplx<R>*)S.st; a.G = (const cplx<R>*)S.G; a.gstride = S.gstride;
+  a.stages = pick_stages<R>(S);
+  a.Y = Y; a.carry_f = carry_f; a.carry_b = carry_b;
+  a.flag = h->dev_flag;
+  a.rhs = Rhs<R>{};
+  a.rhs.raw = fd; a.rhs.ef = -1; a.rhs.eb = -1;
+  a.out = Out<R>{};
+  a.out.raw = ud; a.out.e2 = -1; a.out.e4 = -1;
+  const size_t smem = solve_smem(S.W, S.gstride, sizeof(cplx<R>), a.stages);
+  HZ_CU(cudaFuncSetAttribute(slab_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
+  HZ_CU(cudaFuncSetAttribute(slab_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
+  const int P = L.P;
+  dim3 grid(P);
+  if (P == 1) {
+    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 0);
+    slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
+    h->launches += 2;
+  } else {
+    const size_t csm = 2 * (size_t)kNR * S.W * sizeof(cplx<R>);
+    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 0, 0);
+    slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Phi, 0);
+    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 1);
+    slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Psi, 1);
+    slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
+    h->launches += 5;
+  }
+  HZ_CU(cudaGetLastError());
+}
+
+template void slab_solve_raw_scratch<float>(hz_handle*, Level&, int, const c64*, c64*, int,
+                                            cudaStream_t, c64*, c64*, c64*);
+template void slab_solve_raw_scratch<double>(hz_handle*, Level&, int, const c128*, c128*, int,
+                                             cudaStream_t, c128*, c128*, c128*);
+
+}  // namespace hz
