@@ -44,7 +44,7 @@ double now_s() {
 size_t prec_size(const hz_params& p) { return p.precision == HZ_MIXED ? sizeof(c64) : sizeof(c128); }
 
 void release_work(hz_handle* h) {
-  for (void** q : {&h->pr_r, &h->pr_u, &h->pr_g, &h->pr_B1, &h->pr_B2, &h->tg_u, &h->tg_r,
+  for (void** q : {&h->pr_r, &h->pr_u, &h->pr_u2, &h->pr_g, &h->pr_B1, &h->pr_B2, &h->tg_u, &h->tg_r,
                    &h->tg_t}) {
     dfree(*q);
     *q = nullptr;
@@ -128,6 +128,7 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
     const size_t nl = (size_t)L.nx * L.ny;
     h->pr_r = dmalloc(ps * nl * R);
     h->pr_u = dmalloc(ps * nl * R);
+    h->pr_u2 = dmalloc(ps * nl * R);
     h->pr_g = dmalloc(ps * nl * R);
     h->pr_B1 = dmalloc(ps * 2 * R * L.ny);
     h->pr_B2 = dmalloc(ps * 2 * R * L.ny);

@@ -91,16 +91,17 @@ struct AxisTables {
 // Slab j: core columns lo..hi, wl/wr added PML columns, W = width.
 struct Slab {
   int j = 0, lo = 0, hi = 0, wl = 0, wr = 0, W = 0;
+  int wp = 0;                // W padded to a 16-byte row (plane / row stride of st and Y)
   AxisTables ax;             // slab x axis (DD PML in the added columns)
-  void* st = nullptr;        // slab stencil [ny][9][W] in the preconditioner precision
+  void* st = nullptr;        // slab stencil [ny][9][wp] in the preconditioner precision
   void* G = nullptr;         // inverse Schur complements [ny][gstride]
   size_t gstride = 0;        // elements per block (W*W rounded up to 16 bytes)
   void* Phi = nullptr;       // forward segment products [P][gstride]
   void* Psi = nullptr;       // backward segment products [P][gstride]
   void* inj = nullptr;       // injection coefficients [4][ny][3] (T row0, T row1, T~ row0, T~ row1)
-  void* Y = nullptr;         // forward solution work [max_rhs][ny][W]
-  void* carry_f = nullptr;   // [P][max_rhs][W]
-  void* carry_b = nullptr;   // [P][max_rhs][W]
+  void* Y = nullptr;         // right-hand side, then forward solution rows [ny][n_rhs][wp]
+  void* carry_f = nullptr;   // [P][n_rhs][wp]
+  void* carry_b = nullptr;   // [P][n_rhs][wp]
 };
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.
@@ -154,6 +155,7 @@ struct hz_handle {
   // preconditioner work (precision of the preconditioner), per level
   void* pr_r = nullptr;      // input residual on the sweep level [max_rhs][n]
   void* pr_u = nullptr;      // output on the sweep level
+  void* pr_u2 = nullptr;     // second sweep phase output on the sweep level
   void* pr_g = nullptr;      // mid-sweep residual g = f - A u
   void* pr_B1 = nullptr;     // transmission buffers [2][max_rhs][ny]
   void* pr_B2 = nullptr;

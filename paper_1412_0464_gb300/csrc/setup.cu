@@ -106,7 +106,7 @@ __global__ void slab_axis_kernel(int W, int lo, int hi, int wl, const c128* g_an
 // Layout st[k][9][W], plane (dy+1)*3+(dx+1); couplings to Dirichlet nodes
 // are zero.
 template <typename R>
-__global__ void slab_stencil_fd_kernel(int W, int ny, int lo, int hi, int wl, int nx,
+__global__ void slab_stencil_fd_kernel(int W, int wp, int ny, int lo, int hi, int wl, int nx,
                                        double h2w2, const double* m, const c128* sa_node,
                                        const c128* sa_cell, const c128* ay_node,
                                        const c128* ay_cell, cplx<R>* st) {
@@ -128,8 +128,8 @@ __global__ void slab_stencil_fd_kernel(int W, int ny, int lo, int hi, int wl, in
   v[5] = (e < W - 1) ? -(inv_a2 * a1r) : z;
   v[1] = (k > 0) ? -(inv_a1 * a2d) : z;
   v[7] = (k < ny - 1) ? -(inv_a1 * a2u) : z;
-  cplx<R>* out = st + (size_t)k * 9 * W;
-  for (int q = 0; q < 9; ++q) out[q * W + e] = ccast<R>(v[q]);
+  cplx<R>* out = st + (size_t)k * 9 * wp;
+  for (int q = 0; q < 9; ++q) out[q * wp + e] = ccast<R>(v[q]);
 }
 
 // Transmission coefficients of Eqs. 19-20 for the 5-point operator (only the
@@ -281,14 +281,17 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
     slab_axis_kernel<<<cdiv(S.W + 1, 128), 128, 0, s>>>(
         S.W, S.lo, S.hi, S.wl, L.ax.a_node, L.ax.a_cell, L.ax.h_cell, h->p.s_pml_dd, h->c_pml,
         L.w, h->p.omega, S.ax.a_node, S.ax.a_cell, S.ax.h_cell, S.ax.a_node32, S.ax.a_cell32);
-    S.st = dmalloc(sizeof(cplx<R>) * (size_t)L.ny * 9 * S.W);
+    // plane stride padded so that every plane row starts on a 16-byte boundary
+    S.wp = (sizeof(cplx<R>) >= 16) ? S.W : (S.W + 1) / 2 * 2;
+    S.st = dmalloc(sizeof(cplx<R>) * (size_t)L.ny * 9 * S.wp);
+    HZ_CU(cudaMemsetAsync(S.st, 0, sizeof(cplx<R>) * (size_t)L.ny * 9 * S.wp, s));
     S.inj = dmalloc(sizeof(cplx<R>) * 4 * (size_t)L.ny * 3);
     int beta = (j > 1) ? L.beta[j - 1] : -1;
     int bt = (j < L.J) ? L.beta_t[j] : -1;
     if (!L.fe) {
       dim3 grid(cdiv(S.W, 128), L.ny);
       double h2w2 = L.h * L.h * h->p.omega * h->p.omega;
-      slab_stencil_fd_kernel<R><<<grid, 128, 0, s>>>(S.W, L.ny, S.lo, S.hi, S.wl, L.nx, h2w2,
+      slab_stencil_fd_kernel<R><<<grid, 128, 0, s>>>(S.W, S.wp, L.ny, S.lo, S.hi, S.wl, L.nx, h2w2,
                                                      L.m, S.ax.a_node, S.ax.a_cell, L.ay.a_node,
                                                      L.ay.a_cell, (cplx<R>*)S.st);
       inj_fd_kernel<R><<<cdiv(L.ny, 128), 128, 0, s>>>(L.ny, beta, bt, L.ax.a_cell, L.ay.a_node,
@@ -304,7 +307,7 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
     if (elems16 < 1) elems16 = 1;
     S.gstride = (per + elems16 - 1) / elems16 * elems16;
     S.G = dmalloc(sizeof(cplx<R>) * S.gstride * L.ny);
-    S.Y = dmalloc(sizeof(cplx<R>) * (size_t)h->p.max_rhs * L.ny * S.W);
+    S.Y = dmalloc(sizeof(cplx<R>) * (size_t)h->p.max_rhs * L.ny * S.wp);
   }
   // segments over block rows for the parallel-in-y slab solve
   int P = h->p.segments;
@@ -321,8 +324,8 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
       S.Phi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
       S.Psi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
     }
-    S.carry_f = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.W);
-    S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.W);
+    S.carry_f = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.wp);
+    S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.wp);
   }
   HZ_CU(cudaStreamSynchronize(s));
 }

@@ -3,7 +3,8 @@
 //
 // A^(j) is block tridiagonal along y with W x W blocks (one block row per
 // grid row k): D_k couples row k to itself, C_k to row k-1, B_k to row k+1
-// (taken from the slab stencil st[k][9][W]).  Block LU:
+// (taken from the slab stencil st[k][9][wp], plane (dy+1)*3 + (dx+1)).
+// Block LU:
 //   S_0 = D_0,  S_k = D_k - C_k S_{k-1}^{-1} B_{k-1},  G_k = S_k^{-1} (stored).
 // Solve A^(j) x = f:
 //   forward   y_k = G_k (f_k - C_k y_{k-1})
@@ -15,6 +16,12 @@
 // a solve runs each segment from a zero start (all segments in parallel),
 // carries the segment end values through Phi / Psi (P short steps), and
 // re-runs each segment from its true start value.
+//
+// Every block-row step reads its operands -- the factor block G_k, the
+// coupling row C_k or B_k and the right-hand-side / forward row -- through
+// one stage of a shared-memory pipeline filled by TMA bulk copies
+// (cp.async.bulk + mbarrier); the step itself touches only shared memory and
+// registers.
 #include "hz_internal.h"
 
 #include <algorithm>
@@ -37,7 +44,15 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_fence_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// Orders this thread's earlier generic-proxy accesses (shared and global)
+// before later async-proxy (TMA) accesses.
 __device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+// Same for shared memory only: issued before a TMA copy overwrites a stage
+// that the block has just read with ordinary loads (a warp may pass the block
+// barrier with such loads still in flight).
+__device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -76,135 +91,138 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* f
 constexpr int kThreads = 512;
 constexpr int kTPR = 4;                 // threads cooperating on one row of a GEMV
 constexpr int kGroups = kThreads / kTPR;
-constexpr int kNR = 8;                  // right-hand sides per launch
+constexpr int kNRMax = 8;               // right-hand sides per launch
 
 // --------------------------------------------------------------- factorisation
 struct FactorDesc {
-  int W, ny;
+  int W, wp, ny;
   const void* st;
   void* G;
   size_t gstride;
 };
 
+// One CTA per slab, sequential over block rows.  Each S_k is inverted by
+// Gauss-Jordan elimination with partial pivoting done implicitly (pivot rows
+// are marked, not moved); the permutations are applied when G_k is written:
+// G_k[p][piv[q]] = S[piv[p]][q].  Two block barriers per pivot.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc* descs) {
   const FactorDesc d = descs[blockIdx.x];
-  const int W = d.W, ny = d.ny, tid = threadIdx.x;
+  const int W = d.W, wp = d.wp, ny = d.ny, tid = threadIdx.x;
+  const int ty = tid >> 2, tx = tid & 3;
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* S = (cplx<R>*)smem_raw;          // W*W
-  cplx<R>* T = S + W * W;                   // W*W
-  cplx<R>* colp = T + W * W;                // W
-  int* perm = (int*)(colp + W);             // W
+  cplx<R>* bufA = (cplx<R>*)smem_raw;
+  cplx<R>* bufB = bufA + W * W;
+  cplx<R>* rowbuf = bufB + W * W;
+  cplx<R>* colbuf = rowbuf + W;
+  int* piv = (int*)(colbuf + W);
+  int* ipiv = piv + W;
+  int* used = ipiv + W;
   __shared__ int sh_r;
-  __shared__ cplx<R> sh_inv;
   const cplx<R> zero = mk<R>(0, 0);
+  cplx<R>* S = bufA;    // working matrix
+  cplx<R>* Gl = bufB;   // inverse of the previous block row, natural order
   for (int k = 0; k < ny; ++k) {
-    const cplx<R>* stk = st + (size_t)k * 9 * W;
+    const cplx<R>* stk = st + (size_t)k * 9 * wp;
     if (k == 0) {
       for (int i = tid; i < W * W; i += kThreads) S[i] = zero;
-    } else {
-      // T = G_{k-1} B_{k-1}: T[a][b] = sum_dx G[a][b-dx] * B_{k-1}(b-dx, dx)
-      const cplx<R>* stp = st + (size_t)(k - 1) * 9 * W;
-      for (int i = tid; i < W * W; i += kThreads) {
-        int a = i / W, b = i - a * W;
-        cplx<R> acc = zero;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          int e = b - dx;
-          if (e >= 0 && e < W) cfma(acc, S[a * W + e], stp[(6 + dx + 1) * W + e]);
-        }
-        T[i] = acc;
-      }
       __syncthreads();
-      // S = -C_k T: S[a][b] = -sum_dx C_k(a, dx) T[a+dx][b]
-      for (int i = tid; i < W * W; i += kThreads) {
-        int a = i / W, b = i - a * W;
-        cplx<R> acc = zero;
+    } else {
+      const cplx<R>* stp = st + (size_t)(k - 1) * 9 * wp;
+      // S = G_{k-1} B_{k-1}:  S[i][j] = sum_dx G[i][j-dx] B_{k-1}(j-dx, dx)
+      for (int i = ty; i < W; i += kGroups)
+        for (int j = tx; j < W; j += kTPR) {
+          cplx<R> acc = zero;
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          int e = a + dx;
-          if (e >= 0 && e < W) cfma(acc, stk[(0 + dx + 1) * W + a], T[e * W + b]);
+          for (int dx = -1; dx <= 1; ++dx) {
+            int e = j - dx;
+            if (e >= 0 && e < W) cfma(acc, Gl[i * W + e], stp[(6 + dx + 1) * wp + e]);
+          }
+          S[i * W + j] = acc;
         }
-        S[i] = -acc;
-      }
+      __syncthreads();
+      // Gl = -C_k S:  Gl[i][j] = -sum_dx C_k(i, dx) S[i+dx][j]
+      for (int i = ty; i < W; i += kGroups)
+        for (int j = tx; j < W; j += kTPR) {
+          cplx<R> acc = zero;
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            int e = i + dx;
+            if (e >= 0 && e < W) cfma(acc, stk[(dx + 1) * wp + i], S[e * W + j]);
+          }
+          Gl[i * W + j] = -acc;
+        }
+      __syncthreads();
+      cplx<R>* t = S; S = Gl; Gl = t;   // S = -C_k G_{k-1} B_{k-1}
     }
-    __syncthreads();
-    // + D_k
-    for (int a = tid; a < W; a += kThreads) {
+    for (int i = tid; i < W; i += kThreads) {   // + D_k
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
-        int b = a + dx;
-        if (b >= 0 && b < W) S[a * W + b] = S[a * W + b] + stk[(3 + dx + 1) * W + a];
+        int j = i + dx;
+        if (j >= 0 && j < W) S[i * W + j] = S[i * W + j] + stk[(3 + dx + 1) * wp + i];
       }
+      used[i] = 0;
     }
     __syncthreads();
-    // In-place Gauss-Jordan inversion with partial pivoting.
     for (int p = 0; p < W; ++p) {
       if (tid < 32) {
         R best = -1;
-        int bi = p;
-        for (int i = p + tid; i < W; i += 32) {
+        int bi = 1 << 30;
+        for (int i = tid; i < W; i += 32) {
+          if (used[i]) continue;
           R v = cabs2(S[i * W + p]);
-          if (v > best) { best = v; bi = i; }
+          if (v > best || (v == best && i < bi)) { best = v; bi = i; }
         }
+#pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           R ob = __shfl_xor_sync(0xffffffffu, best, o);
           int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (tid == 0) { sh_r = bi; perm[p] = bi; }
+        const int r = bi;
+        const cplx<R> inv = cinv(S[r * W + p]);
+        for (int j = tid; j < W; j += 32) rowbuf[j] = (j == p) ? inv : S[r * W + j] * inv;
+        for (int i = tid; i < W; i += 32) colbuf[i] = S[i * W + p];
+        if (tid == 0) { used[r] = 1; piv[p] = r; sh_r = r; }
       }
       __syncthreads();
       const int r = sh_r;
-      if (r != p) {
-        for (int j = tid; j < W; j += kThreads) {
-          cplx<R> t = S[p * W + j];
-          S[p * W + j] = S[r * W + j];
-          S[r * W + j] = t;
+      for (int i = ty; i < W; i += kGroups) {
+        const cplx<R> c = colbuf[i];
+        for (int j = tx; j < W; j += kTPR) {
+          cplx<R> q = rowbuf[j];
+          if (i == r) {
+            S[i * W + j] = q;
+          } else {
+            cplx<R> v = (j == p) ? zero : S[i * W + j];
+            v.re -= c.re * q.re - c.im * q.im;
+            v.im -= c.re * q.im + c.im * q.re;
+            S[i * W + j] = v;
+          }
         }
-        __syncthreads();
-      }
-      for (int i = tid; i < W; i += kThreads) colp[i] = S[i * W + p];
-      if (tid == 0) sh_inv = cinv(S[p * W + p]);
-      __syncthreads();
-      const cplx<R> inv = sh_inv;
-      for (int j = tid; j < W; j += kThreads) S[p * W + j] = (j == p ? mk<R>(1, 0) : S[p * W + j]) * inv;
-      __syncthreads();
-      for (int i = tid; i < W * W; i += kThreads) {
-        int a = i / W, b = i - a * W;
-        if (a == p) continue;
-        cplx<R> v = (b == p) ? zero : S[i];
-        cplx<R> c = colp[a];
-        cplx<R> q = S[p * W + b];
-        v.re -= c.re * q.re - c.im * q.im;
-        v.im -= c.re * q.im + c.im * q.re;
-        S[i] = v;
       }
       __syncthreads();
     }
-    // undo the row interchanges as column interchanges, last first
-    for (int p = W - 1; p >= 0; --p) {
-      int r = perm[p];
-      if (r != p) {
-        for (int i = tid; i < W; i += kThreads) {
-          cplx<R> t = S[i * W + p];
-          S[i * W + p] = S[i * W + r];
-          S[i * W + r] = t;
-        }
-        __syncthreads();
-      }
-    }
+    for (int q = tid; q < W; q += kThreads) ipiv[piv[q]] = q;
+    __syncthreads();
     cplx<R>* Gk = G + (size_t)k * d.gstride;
-    for (int i = tid; i < W * W; i += kThreads) Gk[i] = S[i];
+    for (int i = ty; i < W; i += kGroups) {
+      const int pr = piv[i];
+      for (int c = tx; c < W; c += kTPR) {
+        cplx<R> v = S[pr * W + ipiv[c]];
+        Gk[i * W + c] = v;
+        Gl[i * W + c] = v;
+      }
+    }
     __syncthreads();
   }
 }
 
 // ------------------------------------------------------------ segment products
 struct ProdDesc {
-  int W, k0, k1, backward;
+  int W, wp, k0, k1, backward;
   const void* st;
   const void* G;
   size_t gstride;
@@ -216,38 +234,41 @@ struct ProdDesc {
 template <typename R>
 __global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDesc* descs) {
   const ProdDesc d = descs[blockIdx.x];
-  const int W = d.W, tid = threadIdx.x;
+  const int W = d.W, wp = d.wp, tid = threadIdx.x;
+  const int ty = tid >> 2, tx = tid & 3;
   const cplx<R>* st = (const cplx<R>*)d.st;
   const cplx<R>* G = (const cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* M = (cplx<R>*)smem_raw;
   cplx<R>* T = M + W * W;
   const cplx<R> zero = mk<R>(0, 0);
-  for (int i = tid; i < W * W; i += kThreads) M[i] = (i / W == i % W) ? mk<R>(1, 0) : zero;
+  for (int i = tid; i < W * W; i += kThreads) M[i] = zero;
+  __syncthreads();
+  for (int i = tid; i < W; i += kThreads) M[i * W + i] = mk<R>(1, 0);
   __syncthreads();
   const int n = d.k1 - d.k0;
   const int plane = d.backward ? 6 : 0;   // B_k (dy=+1) or C_k (dy=-1)
   for (int s = 0; s < n; ++s) {
     const int k = d.backward ? d.k1 - 1 - s : d.k0 + s;
-    const cplx<R>* stk = st + (size_t)k * 9 * W;
-    for (int i = tid; i < W * W; i += kThreads) {      // T = coupling_k M
-      int a = i / W, c = i - a * W;
-      cplx<R> acc = zero;
+    const cplx<R>* stk = st + (size_t)k * 9 * wp;
+    for (int i = ty; i < W; i += kGroups)          // T = coupling_k M
+      for (int c = tx; c < W; c += kTPR) {
+        cplx<R> acc = zero;
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        int e = a + dx;
-        if (e >= 0 && e < W) cfma(acc, stk[(plane + dx + 1) * W + a], M[e * W + c]);
+        for (int dx = -1; dx <= 1; ++dx) {
+          int e = i + dx;
+          if (e >= 0 && e < W) cfma(acc, stk[(plane + dx + 1) * wp + i], M[e * W + c]);
+        }
+        T[i * W + c] = acc;
       }
-      T[i] = acc;
-    }
     __syncthreads();
     const cplx<R>* Gk = G + (size_t)k * d.gstride;
-    for (int i = tid; i < W * W; i += kThreads) {      // M = -G_k T
-      int a = i / W, c = i - a * W;
-      cplx<R> acc = zero;
-      for (int j = 0; j < W; ++j) cfma(acc, Gk[a * W + j], T[j * W + c]);
-      M[i] = -acc;
-    }
+    for (int i = ty; i < W; i += kGroups)          // M = -G_k T
+      for (int c = tx; c < W; c += kTPR) {
+        cplx<R> acc = zero;
+        for (int j = 0; j < W; ++j) cfma(acc, Gk[i * W + j], T[j * W + c]);
+        M[i * W + c] = -acc;
+      }
     __syncthreads();
   }
   cplx<R>* out = (cplx<R>*)d.out;
@@ -274,8 +295,8 @@ struct Rhs {
 template <typename R>
 struct Out {
   cplx<R>* raw;               // [n_rhs][ny][W] or null
-  cplx<R>* u;                 // global field [n_rhs][ny][nx]
-  int nx, lo, wl, ua, ub;     // scatter global columns (ua, ub]
+  cplx<R>* u;                 // global field [n_rhs][ny][nx]: columns (ua, ub] are stored
+  int nx, lo, wl, ua, ub;     // (each sweep phase writes every column exactly once)
   cplx<R>* B2;                // [2][n_rhs][ny]: layers at local e2, e2+1 (tau2)
   int e2;
   cplx<R>* B4;                // layers at local e4, e4+1 (tau4)
@@ -284,14 +305,14 @@ struct Out {
 
 template <typename R>
 struct SolveArgs {
-  int W, ny, n_rhs, P;
+  int W, wp, ny, nr, P;
   const int* seg;
-  const cplx<R>* st;
-  const cplx<R>* G;
+  const cplx<R>* st;          // [ny][9][wp]
+  const cplx<R>* G;           // [ny][gstride]
   size_t gstride;
   int stages;
-  cplx<R>* Y;                 // [n_rhs][ny][W]
-  cplx<R>* carry_f;           // [P][n_rhs][W]
+  cplx<R>* Y;                 // [ny][nr][wp]: gathered right-hand side, then forward rows
+  cplx<R>* carry_f;           // [P][nr][wp]
   cplx<R>* carry_b;
   int* flag;
   Rhs<R> rhs;
@@ -299,7 +320,8 @@ struct SolveArgs {
 };
 
 template <typename R>
-__device__ __forceinline__ cplx<R> rhs_at(const Rhs<R>& q, int ny, int W, int nr, int r, int k, int e) {
+__device__ __forceinline__ cplx<R> rhs_at(const Rhs<R>& q, int ny, int W, int nr, int r, int k,
+                                          int e) {
   const cplx<R> zero = mk<R>(0, 0);
   if (q.raw) return q.raw[((size_t)r * ny + k) * W + e];
   cplx<R> v = zero;
@@ -308,7 +330,7 @@ __device__ __forceinline__ cplx<R> rhs_at(const Rhs<R>& q, int ny, int W, int nr
   if (q.ef >= 0 && (e == q.ef || e == q.ef + 1)) {
     int s = e - q.ef;                          // 0: row beta uses B[1]; 1: row beta+1 uses B[0]
     const cplx<R>* c = q.inj + ((size_t)s * ny + k) * 3;
-    const cplx<R>* B = q.B1 + ((size_t)(1 - s) * nr + r) * ny;  // layer 1-s
+    const cplx<R>* B = q.B1 + ((size_t)(1 - s) * nr + r) * ny;
     for (int dy = -1; dy <= 1; ++dy) {
       int kk = k + dy;
       if (kk >= 0 && kk < ny) cfma(v, c[dy + 1], B[kk]);
@@ -326,244 +348,311 @@ __device__ __forceinline__ cplx<R> rhs_at(const Rhs<R>& q, int ny, int W, int nr
   return v;
 }
 
-// Shared-memory pipeline of G blocks (one TMA bulk copy per block row).
+// Pipeline stage: [G_k (gstride) | coupling row (3 wp) | vector row (nr wp)].
 template <typename R>
-struct GPipe {
+struct Pipe {
   uint64_t* bar;
   cplx<R>* buf;
   int stages;
-  uint32_t bytes;
-  const cplx<R>* G;
-  size_t gstride;
-  __device__ cplx<R>* slot(int i) { return buf + (size_t)i * gstride; }
-  __device__ void issue(int i, int k) {     // thread 0 only
-    fence_proxy_async();
-    mbar_expect_tx(&bar[i], bytes);
-    tma_load_1d(slot(i), G + (size_t)k * gstride, bytes, &bar[i]);
+  size_t stage_elems, gstride;
+  int wp, nr;
+  __device__ cplx<R>* slot(int i) const { return buf + (size_t)i * stage_elems; }
+  // thread 0 only: fetch block row k (coupling plane 0 = C_k or 6 = B_k)
+  __device__ void issue(int i, int k, const cplx<R>* G, const cplx<R>* st, int plane,
+                        const cplx<R>* rows) const {
+    const uint32_t gb = (uint32_t)(gstride * sizeof(cplx<R>));
+    const uint32_t cb = (uint32_t)(3 * wp * sizeof(cplx<R>));
+    const uint32_t vb = (uint32_t)((size_t)nr * wp * sizeof(cplx<R>));
+    cplx<R>* dst = slot(i);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[i], gb + cb + vb);
+    tma_load_1d(dst, G + (size_t)k * gstride, gb, &bar[i]);
+    tma_load_1d(dst + gstride, st + (size_t)k * 9 * wp + plane * wp, cb, &bar[i]);
+    tma_load_1d(dst + gstride + 3 * wp, rows + (size_t)k * nr * wp, vb, &bar[i]);
   }
 };
 
-// y = M v for NR right-hand sides, M row-major W x W in shared memory; the
-// TPR threads of a group split the columns and reduce with shuffles.
-// Called by every thread of the block with the same trip count; rows >= W
-// contribute zeros so that the shuffles stay warp-uniform.
-template <typename R>
-__device__ __forceinline__ void gemv_rows(const cplx<R>* M, const cplx<R>* v, int W, int nr,
-                                          int row, int lane, cplx<R>* acc) {
-  for (int r = 0; r < kNR; ++r) acc[r] = mk<R>(0, 0);
-  const cplx<R>* Mr = M + (size_t)row * W;
-  const int jend = row < W ? W : 0;
-  for (int j = lane; j < jend; j += kTPR) {
-    cplx<R> m = Mr[j];
+// acc[r] = sum_j M[row][j] v[r][j] for r < nr; every thread of the block calls
+// this with the same trip count (rows >= W contribute zeros) so that the
+// shuffles stay warp-uniform.  Two partial sums shorten the FMA chain.
+template <typename R, int NR>
+__device__ __forceinline__ void gemv_rows(const cplx<R>* M, int ldm, const cplx<R>* v, int ldv,
+                                          int W, int nr, int row, int lane, cplx<R> (&acc)[NR]) {
+  cplx<R> a0[NR], a1[NR];
 #pragma unroll
-    for (int r = 0; r < kNR; ++r)
-      if (r < nr) cfma(acc[r], m, v[r * W + j]);
+  for (int r = 0; r < NR; ++r) { a0[r] = mk<R>(0, 0); a1[r] = mk<R>(0, 0); }
+  const cplx<R>* Mr = M + (size_t)row * ldm;
+  const int jend = row < W ? W : 0;
+  int j = lane;
+  for (; j + kTPR < jend; j += 2 * kTPR) {
+    const cplx<R> m0 = Mr[j], m1 = Mr[j + kTPR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nr) {
+        cfma(a0[r], m0, v[r * ldv + j]);
+        cfma(a1[r], m1, v[r * ldv + j + kTPR]);
+      }
+  }
+  if (j < jend) {
+    const cplx<R> m0 = Mr[j];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nr) cfma(a0[r], m0, v[r * ldv + j]);
   }
 #pragma unroll
-  for (int r = 0; r < kNR; ++r) {
-    if (r < nr) {
+  for (int r = 0; r < NR; ++r) {
+    acc[r] = a0[r] + a1[r];
 #pragma unroll
-      for (int o = kTPR / 2; o > 0; o >>= 1) {
-        acc[r].re += __shfl_xor_sync(0xffffffffu, acc[r].re, o);
-        acc[r].im += __shfl_xor_sync(0xffffffffu, acc[r].im, o);
-      }
+    for (int o = kTPR / 2; o > 0; o >>= 1) {
+      acc[r].re += __shfl_xor_sync(0xffffffffu, acc[r].re, o);
+      acc[r].im += __shfl_xor_sync(0xffffffffu, acc[r].im, o);
     }
   }
+}
+
+template <typename R>
+__device__ __forceinline__ void init_pipe(Pipe<R>& pipe, unsigned char* smem, const SolveArgs<R>& a,
+                                          int NR, cplx<R>** vbuf, cplx<R>** ybuf) {
+  pipe.bar = (uint64_t*)smem;
+  *vbuf = (cplx<R>*)(smem + 128);
+  *ybuf = *vbuf + NR * a.wp;
+  cplx<R>* b = *ybuf + NR * a.wp;
+  pipe.buf = (cplx<R>*)(((uintptr_t)b + 127) & ~(uintptr_t)127);
+  pipe.stages = a.stages;
+  pipe.gstride = a.gstride;
+  pipe.wp = a.wp;
+  pipe.nr = a.nr;
+  pipe.stage_elems = a.gstride + 3 * (size_t)a.wp + (size_t)a.nr * a.wp;
+}
+
+// SubdomSolve lines 1-5: the slab right-hand side (gather + transmission
+// injection) into the rows Y[k][r][0..wp).  A kernel of its own, so that the
+// TMA reads of these rows in the next launch see them.
+template <typename R>
+__global__ void slab_gather_kernel(SolveArgs<R> a) {
+  const int rowlen = a.nr * a.wp;
+  const size_t total = (size_t)a.ny * rowlen;
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx / rowlen), rem = (int)(idx - (size_t)k * rowlen);
+  const int r = rem / a.wp, e = rem - r * a.wp;
+  a.Y[idx] = (e < a.W) ? rhs_at<R>(a.rhs, a.ny, a.W, a.nr, r, k, e) : mk<R>(0, 0);
 }
 
 // Forward recurrence over one segment.
 //   mode 0: zero start, store only the segment's last y into carry_f[p];
-//   mode 1: start from carry_f[p-1] (segment 0: zero), store every y_k into Y;
-//           if bwd1, then run the backward recurrence over the segment from a
-//           zero start and store its first x into carry_b[p].
-template <typename R>
+//   mode 1: start from carry_f[p-1] (segment 0: zero), store every y_k into
+//           Y (over the right-hand side); if bwd1, then run the backward
+//           recurrence over the segment from a zero start and store its first
+//           x into carry_b[p].
+template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int mode, int bwd1) {
-  const int p = blockIdx.x, tid = threadIdx.x, W = a.W, ny = a.ny, nr = a.n_rhs;
+  const int p = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
   const int k0 = a.seg[p], k1 = a.seg[p + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
-  GPipe<R> pipe;
-  pipe.bar = (uint64_t*)smem_raw;
-  cplx<R>* vbuf = (cplx<R>*)(smem_raw + 128);
-  cplx<R>* ybuf = vbuf + kNR * W;
-  pipe.buf = ybuf + kNR * W;
-  pipe.buf = (cplx<R>*)(((uintptr_t)pipe.buf + 127) & ~(uintptr_t)127);
-  pipe.stages = a.stages;
-  pipe.bytes = (uint32_t)(a.gstride * sizeof(cplx<R>));
-  pipe.G = a.G;
-  pipe.gstride = a.gstride;
+  Pipe<R> pipe;
+  cplx<R>* vbuf;
+  cplx<R>* ybuf;
+  init_pipe<R>(pipe, smem_raw, a, NR, &vbuf, &ybuf);
   const cplx<R> zero = mk<R>(0, 0);
   if (tid == 0) {
     sh_abort = 0;
     for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
     mbar_fence_init();
   }
-  // initial y_{k0-1}
-  for (int i = tid; i < nr * W; i += kThreads) {
-    int r = i / W, e = i - r * W;
-    ybuf[i] = (mode == 1 && p > 0) ? a.carry_f[((size_t)(p - 1) * nr + r) * W + e] : zero;
+  for (int i = tid; i < NR * wp; i += kThreads) {
+    const int r = i / wp, e = i - r * wp;
+    ybuf[i] = (mode == 1 && p > 0 && r < nr) ? a.carry_f[((size_t)(p - 1) * nr + r) * wp + e] : zero;
   }
   __syncthreads();
   const int n = k1 - k0;
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + i);
-  uint32_t phase_bits = 0;   // parity per stage
+    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + i, a.G, a.st, 0, a.Y);
+  uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
-  cplx<R> acc[kNR];
+  cplx<R> acc[NR];
   for (int s = 0; s < n; ++s) {
     const int k = k0 + s;
-    const cplx<R>* stk = a.st + (size_t)k * 9 * W;
-    // v_k = f_k - C_k y_{k-1}
-    for (int i = tid; i < nr * W; i += kThreads) {
-      int r = i / W, e = i - r * W;
-      cplx<R> v = rhs_at<R>(a.rhs, ny, W, nr, r, k, e);
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        int ee = e + dx;
-        if (ee >= 0 && ee < W) {
-          cplx<R> c = stk[(0 + dx + 1) * W + e];
-          cplx<R> y = ybuf[r * W + ee];
-          v.re -= c.re * y.re - c.im * y.im;
-          v.im -= c.re * y.im + c.im * y.re;
-        }
-      }
-      vbuf[i] = v;
-    }
     const int slot = s % pipe.stages;
-    __syncthreads();
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Gk = pipe.slot(slot);
+    const cplx<R>* Ck = Gk + pipe.gstride;
+    const cplx<R>* Fk = Ck + 3 * wp;
+    if (tid < W) {                       // v_k = f_k - C_k y_{k-1}
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r >= nr) break;
+        cplx<R> v = Fk[r * wp + tid];
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ee = tid + dx;
+          if (ee >= 0 && ee < W) {
+            const cplx<R> c = Ck[(dx + 1) * wp + tid];
+            const cplx<R> y = ybuf[r * wp + ee];
+            v.re -= c.re * y.re - c.im * y.im;
+            v.im -= c.re * y.im + c.im * y.re;
+          }
+        }
+        vbuf[r * wp + tid] = v;
+      }
+    }
+    __syncthreads();
     for (int rb = 0; rb < W; rb += kGroups) {
       const int row = rb + grp;
-      gemv_rows<R>(Gk, vbuf, W, nr, row, lane, acc);
+      gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
-        for (int r = 0; r < nr; ++r) {
-          ybuf[r * W + row] = acc[r];
-          if (mode == 1) a.Y[((size_t)r * ny + k) * W + row] = acc[r];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r >= nr) break;
+          ybuf[r * wp + row] = acc[r];
+          if (mode == 1) a.Y[((size_t)k * nr + r) * wp + row] = acc[r];
         }
       }
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k + pipe.stages);
+    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k + pipe.stages, a.G, a.st, 0, a.Y);
   }
   if (mode == 0) {
-    for (int i = tid; i < nr * W; i += kThreads) {
-      int r = i / W, e = i - r * W;
-      a.carry_f[((size_t)p * nr + r) * W + e] = ybuf[i];
-    }
+    for (int i = tid; i < nr * wp; i += kThreads) a.carry_f[(size_t)p * nr * wp + i] = ybuf[i];
     return;
   }
   if (!bwd1) return;
-  // backward recurrence from a zero start: x_k = y_k - G_k (B_k x_{k+1})
-  for (int i = tid; i < nr * W; i += kThreads) ybuf[i] = zero;  // x_{k1}
+  // Backward recurrence from a zero start: x_k = y_k - G_k (B_k x_{k+1}).
+  // The y rows were written above by this CTA (generic stores); they are read
+  // with ordinary loads, one step ahead, never through TMA.  The pipeline
+  // still brings G_k and B_k (its vector part, Y row k, is not used here).
+  for (int i = tid; i < NR * wp; i += kThreads) ybuf[i] = zero;   // x_{k1}
   __syncthreads();
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k1 - 1 - i);
-  // stage parities continue from the forward pass: each stage was used a
-  // known number of times; phase_bits already tracks them.
+    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k1 - 1 - i, a.G, a.st, 6, a.Y);
+  cplx<R> ynext[NR];
+  {
+    const int row0 = grp;   // rows handled by this group in the first pass over rb
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      ynext[r] = (lane == 0 && row0 < W && r < nr) ? a.Y[((size_t)(k1 - 1) * nr + r) * wp + row0] : zero;
+  }
   for (int s = 0; s < n; ++s) {
     const int k = k1 - 1 - s;
-    const cplx<R>* stk = a.st + (size_t)k * 9 * W;
-    for (int i = tid; i < nr * W; i += kThreads) {      // w = B_k x_{k+1}
-      int r = i / W, e = i - r * W;
-      cplx<R> v = zero;
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        int ee = e + dx;
-        if (ee >= 0 && ee < W) cfma(v, stk[(6 + dx + 1) * W + e], ybuf[r * W + ee]);
-      }
-      vbuf[i] = v;
-    }
     const int slot = s % pipe.stages;
-    __syncthreads();
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Gk = pipe.slot(slot);
+    const cplx<R>* Bk = Gk + pipe.gstride;
+    if (tid < W) {                       // w = B_k x_{k+1}
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r >= nr) break;
+        cplx<R> v = zero;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ee = tid + dx;
+          if (ee >= 0 && ee < W) cfma(v, Bk[(dx + 1) * wp + tid], ybuf[r * wp + ee]);
+        }
+        vbuf[r * wp + tid] = v;
+      }
+    }
+    __syncthreads();
     for (int rb = 0; rb < W; rb += kGroups) {
       const int row = rb + grp;
-      gemv_rows<R>(Gk, vbuf, W, nr, row, lane, acc);
-      if (lane == 0 && row < W)
-        for (int r = 0; r < nr; ++r) ybuf[r * W + row] = a.Y[((size_t)r * ny + k) * W + row] - acc[r];
+      cplx<R> ycur[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) ycur[r] = ynext[r];
+      if (rb + kGroups >= W) {           // last pass over rows: prefetch row k-1
+        const int rowp = grp;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          ynext[r] = (lane == 0 && rowp < W && r < nr && k > k0)
+                         ? a.Y[((size_t)(k - 1) * nr + r) * wp + rowp] : zero;
+      }
+      if (rb > 0) {                      // rows beyond the first pass: plain load now
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          ycur[r] = (lane == 0 && row < W && r < nr) ? a.Y[((size_t)k * nr + r) * wp + row] : zero;
+      }
+      gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
+      if (lane == 0 && row < W) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r >= nr) break;
+          ybuf[r * wp + row] = ycur[r] - acc[r];
+        }
+      }
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k - pipe.stages);
+    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k - pipe.stages, a.G, a.st, 6, a.Y);
   }
-  for (int i = tid; i < nr * W; i += kThreads) {
-    int r = i / W, e = i - r * W;
-    a.carry_b[((size_t)p * nr + r) * W + e] = ybuf[i];
-  }
+  for (int i = tid; i < nr * wp; i += kThreads) a.carry_b[(size_t)p * nr * wp + i] = ybuf[i];
 }
 
 // Final backward recurrence over one segment from x_{k1} = carry_b[p+1]
 // (last segment: zero), with the epilogue of Table 2.
-template <typename R>
+template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
-  const int p = blockIdx.x, tid = threadIdx.x, W = a.W, ny = a.ny, nr = a.n_rhs;
+  const int p = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
   const int k0 = a.seg[p], k1 = a.seg[p + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
-  GPipe<R> pipe;
-  pipe.bar = (uint64_t*)smem_raw;
-  cplx<R>* vbuf = (cplx<R>*)(smem_raw + 128);
-  cplx<R>* xbuf = vbuf + kNR * W;
-  pipe.buf = xbuf + kNR * W;
-  pipe.buf = (cplx<R>*)(((uintptr_t)pipe.buf + 127) & ~(uintptr_t)127);
-  pipe.stages = a.stages;
-  pipe.bytes = (uint32_t)(a.gstride * sizeof(cplx<R>));
-  pipe.G = a.G;
-  pipe.gstride = a.gstride;
+  Pipe<R> pipe;
+  cplx<R>* vbuf;
+  cplx<R>* xbuf;
+  init_pipe<R>(pipe, smem_raw, a, NR, &vbuf, &xbuf);
   const cplx<R> zero = mk<R>(0, 0);
   if (tid == 0) {
     sh_abort = 0;
     for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
     mbar_fence_init();
   }
-  for (int i = tid; i < nr * W; i += kThreads) {
-    int r = i / W, e = i - r * W;
-    xbuf[i] = (p + 1 < a.P) ? a.carry_b[((size_t)(p + 1) * nr + r) * W + e] : zero;
+  for (int i = tid; i < NR * wp; i += kThreads) {
+    const int r = i / wp, e = i - r * wp;
+    xbuf[i] = (p + 1 < a.P && r < nr) ? a.carry_b[((size_t)(p + 1) * nr + r) * wp + e] : zero;
   }
   __syncthreads();
   const int n = k1 - k0;
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k1 - 1 - i);
+    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k1 - 1 - i, a.G, a.st, 6, a.Y);
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
-  cplx<R> acc[kNR];
+  cplx<R> acc[NR];
   const Out<R>& o = a.out;
   for (int s = 0; s < n; ++s) {
     const int k = k1 - 1 - s;
-    const cplx<R>* stk = a.st + (size_t)k * 9 * W;
-    for (int i = tid; i < nr * W; i += kThreads) {
-      int r = i / W, e = i - r * W;
-      cplx<R> v = zero;
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        int ee = e + dx;
-        if (ee >= 0 && ee < W) cfma(v, stk[(6 + dx + 1) * W + e], xbuf[r * W + ee]);
-      }
-      vbuf[i] = v;
-    }
     const int slot = s % pipe.stages;
-    __syncthreads();
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Gk = pipe.slot(slot);
+    const cplx<R>* Bk = Gk + pipe.gstride;
+    const cplx<R>* Yk = Bk + 3 * wp;
+    if (tid < W) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r >= nr) break;
+        cplx<R> v = zero;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ee = tid + dx;
+          if (ee >= 0 && ee < W) cfma(v, Bk[(dx + 1) * wp + tid], xbuf[r * wp + ee]);
+        }
+        vbuf[r * wp + tid] = v;
+      }
+    }
+    __syncthreads();
     for (int rb = 0; rb < W; rb += kGroups) {
       const int row = rb + grp;
-      gemv_rows<R>(Gk, vbuf, W, nr, row, lane, acc);
+      gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
         const int g = row - o.wl + o.lo;
-        for (int r = 0; r < nr; ++r) {
-          cplx<R> x = a.Y[((size_t)r * ny + k) * W + row] - acc[r];
-          xbuf[r * W + row] = x;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r >= nr) break;
+          const cplx<R> x = Yk[r * wp + row] - acc[r];
+          xbuf[r * wp + row] = x;
           if (o.raw) o.raw[((size_t)r * ny + k) * W + row] = x;
-          if (o.u && g > o.ua && g <= o.ub) {
-            cplx<R>* uu = o.u + ((size_t)r * ny + k) * o.nx + g;
-            *uu = *uu + x;
-          }
+          if (o.u && g > o.ua && g <= o.ub) o.u[((size_t)r * ny + k) * o.nx + g] = x;
           if (o.B2 && (row == o.e2 || row == o.e2 + 1))
             o.B2[((size_t)(row - o.e2) * nr + r) * ny + k] = x;
           if (o.B4 && (row == o.e4 || row == o.e4 + 1))
@@ -573,58 +662,116 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k - pipe.stages);
+    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k - pipe.stages, a.G, a.st, 6, a.Y);
   }
 }
 
-// Segment carries: forward Y_p = yhat_p + Phi_p Y_{p-1}; backward
-// X_p = xhat_p + Psi_p X_{p+1}.
-template <typename R>
+// Segment carries: forward Y_p = yhat_p + Phi_p Y_{p-1} (p = 1..P-1);
+// backward X_p = xhat_p + Psi_p X_{p+1} (p = P-2..0).  The products and the
+// segment values come through a TMA pipeline: stage = [M_p | carry row p].
+template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, const cplx<R>* prod,
                                                               int backward) {
-  const int tid = threadIdx.x, W = a.W, nr = a.n_rhs, P = a.P;
+  const int tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr, P = a.P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* prev = (cplx<R>*)smem_raw;  // [nr][W]
-  cplx<R>* nxt = prev + kNR * W;       // [nr][W]
+  __shared__ int sh_abort;
+  uint64_t* bar = (uint64_t*)smem_raw;
+  cplx<R>* prev = (cplx<R>*)(smem_raw + 128);
+  cplx<R>* buf = (cplx<R>*)(((uintptr_t)(prev + NR * wp) + 127) & ~(uintptr_t)127);
+  const size_t se = a.gstride + (size_t)nr * wp;
+  const int stages = a.stages;
   cplx<R>* carry = backward ? a.carry_b : a.carry_f;
-  const int grp = tid / kTPR, lane = tid % kTPR;
-  cplx<R> acc[kNR];
-  const int pstart = backward ? P - 1 : 0;
-  for (int i = tid; i < nr * W; i += kThreads) prev[i] = carry[(size_t)pstart * nr * W + i];
+  const uint32_t mb = (uint32_t)(a.gstride * sizeof(cplx<R>));
+  const uint32_t vb = (uint32_t)((size_t)nr * wp * sizeof(cplx<R>));
+  auto seg_of = [&](int q) { return backward ? P - 1 - q : q; };
+  auto issue = [&](int i, int q) {
+    const int p = seg_of(q);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[i], mb + vb);
+    tma_load_1d(buf + (size_t)i * se, prod + (size_t)p * a.gstride, mb, &bar[i]);
+    tma_load_1d(buf + (size_t)i * se + a.gstride, carry + (size_t)p * nr * wp, vb, &bar[i]);
+  };
+  if (tid == 0) {
+    sh_abort = 0;
+    for (int i = 0; i < stages; ++i) mbar_init(&bar[i], 1);
+    mbar_fence_init();
+  }
+  const int pstart = seg_of(0);
+  for (int i = tid; i < NR * wp; i += kThreads)
+    prev[i] = (i < nr * wp) ? carry[(size_t)pstart * nr * wp + i] : mk<R>(0, 0);
   __syncthreads();
-  for (int q = 1; q < P; ++q) {
-    const int p = backward ? P - 1 - q : q;
-    const cplx<R>* M = prod + (size_t)p * a.gstride;
-    cplx<R>* cp = carry + (size_t)p * nr * W;
+  const int n = P - 1;
+  if (tid == 0)
+    for (int i = 0; i < stages && i < n; ++i) issue(i, i + 1);
+  uint32_t phase_bits = 0;
+  const int grp = tid / kTPR, lane = tid % kTPR;
+  cplx<R> acc[NR];
+  for (int s = 0; s < n; ++s) {
+    const int q = s + 1;
+    const int p = seg_of(q);
+    const int slot = s % stages;
+    if (!mbar_wait(&bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
+    phase_bits ^= 1u << slot;
+    __syncthreads();
+    if (sh_abort) return;
+    const cplx<R>* M = buf + (size_t)slot * se;
+    const cplx<R>* hat = M + a.gstride;
+    cplx<R> res[NR];
+    int myrow = -1;
     for (int rb = 0; rb < W; rb += kGroups) {
       const int row = rb + grp;
-      gemv_rows<R>(M, prev, W, nr, row, lane, acc);
-      if (lane == 0 && row < W)
-        for (int r = 0; r < nr; ++r) nxt[r * W + row] = cp[r * W + row] + acc[r];
+      gemv_rows<R, NR>(M, W, prev, wp, W, nr, row, lane, acc);
+      if (lane == 0 && row < W) {
+        myrow = row;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) res[r] = (r < nr) ? hat[r * wp + row] + acc[r] : mk<R>(0, 0);
+      }
+    }
+    __syncthreads();   // everyone has read prev
+    if (myrow >= 0) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r >= nr) break;
+        prev[r * wp + myrow] = res[r];
+        carry[((size_t)p * nr + r) * wp + myrow] = res[r];
+      }
     }
     __syncthreads();
-    for (int i = tid; i < nr * W; i += kThreads) {
-      cp[i] = nxt[i];
-      prev[i] = nxt[i];
-    }
-    __syncthreads();
+    if (tid == 0 && s + stages < n) issue(slot, q + stages);
   }
 }
 
 // ------------------------------------------------------------------ host side
-static size_t solve_smem(int W, size_t gstride, size_t elem, int stages) {
-  size_t fixed = 128 + 2 * kNR * (size_t)W * elem + 128;
-  return fixed + (size_t)stages * gstride * elem;
+template <typename R>
+static size_t solve_smem(const Slab& S, int nr, int NR, int stages) {
+  const size_t el = sizeof(cplx<R>);
+  size_t fixed = 128 + 2 * (size_t)NR * S.wp * el + 128;
+  size_t stage = (S.gstride + 3 * (size_t)S.wp + (size_t)nr * S.wp) * el;
+  return fixed + (size_t)stages * stage;
 }
 
 template <typename R>
-static int pick_stages(const Slab& S) {
-  const size_t limit = 225 * 1024;
+static size_t carry_smem(const Slab& S, int nr, int NR, int stages) {
+  const size_t el = sizeof(cplx<R>);
+  return 128 + (size_t)NR * S.wp * el + 128 + (size_t)stages * (S.gstride + (size_t)nr * S.wp) * el;
+}
+
+constexpr size_t kSmemLimit = 225 * 1024;
+
+template <typename R>
+static int pick_stages(const Slab& S, int nr, int NR) {
   int st = 4;
-  while (st > 1 && solve_smem(S.W, S.gstride, sizeof(cplx<R>), st) > limit) --st;
-  if (solve_smem(S.W, S.gstride, sizeof(cplx<R>), st) > limit)
+  while (st > 1 && solve_smem<R>(S, nr, NR, st) > kSmemLimit) --st;
+  if (solve_smem<R>(S, nr, NR, st) > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the shared-memory slab solve (W=" +
                                  std::to_string(S.W) + ")");
+  return st;
+}
+
+template <typename R>
+static int pick_carry_stages(const Slab& S, int nr, int NR) {
+  int st = 4;
+  while (st > 1 && carry_smem<R>(S, nr, NR, st) > kSmemLimit) --st;
   return st;
 }
 
@@ -633,20 +780,21 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   const int J = L.J;
   int maxW = 0;
   for (int j = 1; j <= J; ++j) maxW = std::max(maxW, L.slabs[j].W);
-  size_t smem = 2 * (size_t)maxW * maxW * sizeof(cplx<R>) + maxW * (sizeof(cplx<R>) + sizeof(int)) + 64;
-  if (smem > 225 * 1024)
+  size_t smem = 2 * (size_t)maxW * maxW * sizeof(cplx<R>) + 2 * maxW * sizeof(cplx<R>) +
+                3 * maxW * sizeof(int) + 64;
+  if (smem > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the shared-memory factorisation (W=" +
                                  std::to_string(maxW) + ")");
   std::vector<FactorDesc> fd(J);
   for (int j = 1; j <= J; ++j) {
     const Slab& S = L.slabs[j];
-    fd[j - 1] = FactorDesc{S.W, L.ny, S.st, S.G, S.gstride};
+    fd[j - 1] = FactorDesc{S.W, S.wp, L.ny, S.st, S.G, S.gstride};
   }
   FactorDesc* d_fd = (FactorDesc*)dmalloc(sizeof(FactorDesc) * J);
   HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), sizeof(FactorDesc) * J, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaFuncSetAttribute(slab_factor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem));
-  slab_factor_kernel<R><<<J, kThreads, smem, s>>>(d_fd);
+  timed(h, "slab_factor", 0.0, s, [&] { slab_factor_kernel<R><<<J, kThreads, smem, s>>>(d_fd); });
   h->launches++;
   HZ_CU(cudaGetLastError());
   ProdDesc* d_pd = nullptr;
@@ -656,7 +804,7 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
       const Slab& S = L.slabs[j];
       for (int p = 0; p < L.P; ++p)
         for (int bw = 0; bw < 2; ++bw)
-          pd.push_back(ProdDesc{S.W, L.seg[p], L.seg[p + 1], bw, S.st, S.G, S.gstride,
+          pd.push_back(ProdDesc{S.W, S.wp, L.seg[p], L.seg[p + 1], bw, S.st, S.G, S.gstride,
                                 (cplx<R>*)(bw ? S.Psi : S.Phi) + (size_t)p * S.gstride});
     }
     d_pd = (ProdDesc*)dmalloc(sizeof(ProdDesc) * pd.size());
@@ -664,7 +812,9 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
     size_t psm = 2 * (size_t)maxW * maxW * sizeof(cplx<R>);
     HZ_CU(cudaFuncSetAttribute(segment_product_kernel<R>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-    segment_product_kernel<R><<<(unsigned)pd.size(), kThreads, psm, s>>>(d_pd);
+    timed(h, "segment_product", 0.0, s, [&] {
+      segment_product_kernel<R><<<(unsigned)pd.size(), kThreads, psm, s>>>(d_pd);
+    });
     h->launches++;
     HZ_CU(cudaGetLastError());
   }
@@ -673,65 +823,96 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   dfree(d_pd);
 }
 
+template <typename R, int NR>
+static void set_solve_attrs() {
+  static bool done = false;
+  if (done) return;
+  HZ_CU(cudaFuncSetAttribute(slab_fwd_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  HZ_CU(cudaFuncSetAttribute(slab_bwd_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  HZ_CU(cudaFuncSetAttribute(slab_carry_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  done = true;
+}
+
+// Launch sequence of one slab solve; `tagged` brackets the kernels with
+// timing events (when timing is on).
+template <typename R, int NR>
+static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaStream_t s,
+                         bool tagged) {
+  set_solve_attrs<R, NR>();
+  const int P = L.P, nr = a.nr;
+  a.stages = pick_stages<R>(S, nr, NR);
+  const size_t smem = solve_smem<R>(S, nr, NR, a.stages);
+  const double el = sizeof(cplx<R>);
+  const double gbytes = (double)L.ny * S.W * S.W * el;          // one pass over G_0..G_{ny-1}
+  const double cbytes = (double)L.ny * 3 * S.W * el;            // one pass over the couplings
+  const double vbytes = (double)nr * L.ny * S.W * el;           // one slab-sized vector
+  const double pbytes = (double)P * S.W * S.W * el;             // one set of segment products
+  auto T = [&](const char* tag, double bytes, auto&& fn) {
+    if (tagged) timed(h, tag, bytes, s, fn); else fn();
+  };
+  dim3 grid(P);
+  const size_t gtotal = (size_t)L.ny * nr * S.wp;
+  T("slab_gather", 2 * vbytes, [&] {
+    slab_gather_kernel<R><<<cdiv(gtotal, 256), 256, 0, s>>>(a);
+  });
+  h->launches++;
+  if (P == 1) {
+    T("slab_fwd", gbytes + cbytes + 3 * vbytes, [&] {
+      slab_fwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a, 1, 0);
+    });
+    T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
+      slab_bwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a);
+    });
+    h->launches += 2;
+  } else {
+    SolveArgs<R> ac = a;
+    ac.stages = pick_carry_stages<R>(S, nr, NR);
+    const size_t csm = carry_smem<R>(S, nr, NR, ac.stages);
+    T("slab_fwd_pass1", gbytes + cbytes + 3 * vbytes, [&] {
+      slab_fwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a, 0, 0);
+    });
+    T("slab_carry", pbytes, [&] {
+      slab_carry_kernel<R, NR><<<1, kThreads, csm, s>>>(ac, (const cplx<R>*)S.Phi, 0);
+    });
+    T("slab_fwd_bwd1", 2 * gbytes + 2 * cbytes + 4 * vbytes, [&] {
+      slab_fwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a, 1, 1);
+    });
+    T("slab_carry", pbytes, [&] {
+      slab_carry_kernel<R, NR><<<1, kThreads, csm, s>>>(ac, (const cplx<R>*)S.Psi, 1);
+    });
+    T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
+      slab_bwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a);
+    });
+    h->launches += 5;
+  }
+  HZ_CU(cudaGetLastError());
+}
+
 template <typename R>
 static void run_solve(hz_handle* h, Level& L, Slab& S, const Rhs<R>& rhs, const Out<R>& out,
-                      int n_rhs, cudaStream_t s) {
-  if (n_rhs > kNR) throw Failure(HZ_EINVAL, "too many right-hand sides per slab launch");
+                      int n_rhs, cudaStream_t s, cplx<R>* Y, cplx<R>* cf, cplx<R>* cb,
+                      bool tagged) {
+  if (n_rhs < 1 || n_rhs > kNRMax) throw Failure(HZ_EINVAL, "right-hand sides per slab launch must be 1..8");
   SolveArgs<R> a;
-  a.W = S.W; a.ny = L.ny; a.n_rhs = n_rhs; a.P = L.P; a.seg = L.seg_dev;
+  a.W = S.W; a.wp = S.wp; a.ny = L.ny; a.nr = n_rhs; a.P = L.P; a.seg = L.seg_dev;
   a.st = (const cplx<R>*)S.st; a.G = (const cplx<R>*)S.G; a.gstride = S.gstride;
-  a.stages = pick_stages<R>(S);
-  a.Y = (cplx<R>*)S.Y; a.carry_f = (cplx<R>*)S.carry_f; a.carry_b = (cplx<R>*)S.carry_b;
+  a.stages = 1;
+  a.Y = Y; a.carry_f = cf; a.carry_b = cb;
   a.flag = h->dev_flag;
   a.rhs = rhs;
   a.out = out;
-  size_t smem = solve_smem(S.W, S.gstride, sizeof(cplx<R>), a.stages);
-  static bool attr_set[2] = {false, false};
-  int ai = sizeof(R) == 8 ? 1 : 0;
-  if (!attr_set[ai]) {
-    HZ_CU(cudaFuncSetAttribute(slab_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
-    HZ_CU(cudaFuncSetAttribute(slab_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
-    attr_set[ai] = true;
-  }
-  const int P = L.P;
   const double el = sizeof(cplx<R>);
-  const double gbytes = (double)L.ny * S.W * S.W * el;          // one pass over G_0..G_{ny-1}
-  const double vbytes = (double)n_rhs * L.ny * S.W * el;        // one slab-sized vector
-  const double pbytes = (double)P * S.W * S.W * el;             // one set of segment products
-  dim3 grid(P);
   auto seq = [&] {
-    if (P == 1) {
-      timed(h, "slab_fwd", gbytes + 2 * vbytes, s, [&] {
-        slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 0);
-      });
-      timed(h, "slab_bwd", gbytes + 2 * vbytes, s, [&] {
-        slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
-      });
-      h->launches += 2;
-    } else {
-      size_t csm = 2 * (size_t)kNR * S.W * sizeof(cplx<R>);
-      timed(h, "slab_fwd_pass1", gbytes + vbytes, s, [&] {
-        slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 0, 0);
-      });
-      timed(h, "slab_carry", pbytes, s, [&] {
-        slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Phi, 0);
-      });
-      timed(h, "slab_fwd_bwd1", 2 * gbytes + 3 * vbytes, s, [&] {
-        slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 1);
-      });
-      timed(h, "slab_carry", pbytes, s, [&] {
-        slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Psi, 1);
-      });
-      timed(h, "slab_bwd", gbytes + 2 * vbytes, s, [&] {
-        slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
-      });
-      h->launches += 5;
-    }
+    if (n_rhs == 1) launch_solve<R, 1>(h, L, S, a, s, tagged);
+    else if (n_rhs == 2) launch_solve<R, 2>(h, L, S, a, s, tagged);
+    else if (n_rhs <= 4) launch_solve<R, 4>(h, L, S, a, s, tagged);
+    else launch_solve<R, 8>(h, L, S, a, s, tagged);
   };
-  // the whole slab solve; algorithmic bytes = the method's minimum: G read
-  // once per substitution direction plus right-hand side and solution
-  timed(h, "slab_solve", 2 * gbytes + 2 * vbytes, s, seq);
-  HZ_CU(cudaGetLastError());
+  // whole subdomain solve; algorithmic bytes = the method's minimum: G and
+  // the couplings read once per substitution direction, right-hand side and
+  // solution once
+  const double minimal = 2.0 * L.ny * S.W * (S.W + 3.0) * el + 2.0 * n_rhs * L.ny * S.W * el;
+  if (tagged) timed(h, "slab_solve", minimal, s, seq); else seq();
 }
 
 template <typename R>
@@ -755,7 +936,8 @@ void subdom_solve(hz_handle* h, Level& L, int j, const cplx<R>* f, int a, int b,
   o.raw = nullptr; o.u = u; o.nx = L.nx; o.lo = S.lo; o.wl = S.wl; o.ua = at; o.ub = bt;
   o.B2 = tau2 ? B2 : nullptr; o.e2 = tau2 ? loc(L.beta[j]) : -1;
   o.B4 = tau4 ? B4 : nullptr; o.e4 = tau4 ? loc(L.beta_t[j - 1]) : -1;
-  run_solve<R>(h, L, S, q, o, n_rhs, s);
+  run_solve<R>(h, L, S, q, o, n_rhs, s, (cplx<R>*)S.Y, (cplx<R>*)S.carry_f, (cplx<R>*)S.carry_b,
+               true);
 }
 
 template <typename R>
@@ -766,7 +948,23 @@ void slab_solve_raw(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* u
   q.raw = fd; q.ef = -1; q.eb = -1;
   Out<R> o{};
   o.raw = ud; o.e2 = -1; o.e4 = -1;
-  run_solve<R>(h, L, S, q, o, n_rhs, s);
+  run_solve<R>(h, L, S, q, o, n_rhs, s, (cplx<R>*)S.Y, (cplx<R>*)S.carry_f, (cplx<R>*)S.carry_b,
+               true);
+}
+
+// Slab solve of a raw right-hand side with caller-provided work buffers
+// (Y [ny][n_rhs][wp], segment carries [P][n_rhs][wp] each); the same kernels
+// as slab_solve_raw, no allocation, no timing events.
+template <typename R>
+void slab_solve_raw_scratch(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud,
+                            int n_rhs, cudaStream_t s, cplx<R>* Y, cplx<R>* carry_f,
+                            cplx<R>* carry_b) {
+  Slab& S = L.slabs[j];
+  Rhs<R> q{};
+  q.raw = fd; q.ef = -1; q.eb = -1;
+  Out<R> o{};
+  o.raw = ud; o.e2 = -1; o.e4 = -1;
+  run_solve<R>(h, L, S, q, o, n_rhs, s, Y, carry_f, carry_b, false);
 }
 
 template void factor_level<float>(hz_handle*, Level&, cudaStream_t);
@@ -779,52 +977,6 @@ template void subdom_solve<double>(hz_handle*, Level&, int, const c128*, int, in
                                    int, cudaStream_t);
 template void slab_solve_raw<float>(hz_handle*, Level&, int, const c64*, c64*, int, cudaStream_t);
 template void slab_solve_raw<double>(hz_handle*, Level&, int, const c128*, c128*, int, cudaStream_t);
-
-}  // namespace hz
-
-namespace hz {
-
-// Slab solve of a raw right-hand side with caller-provided work buffers
-// (forward-solution rows Y [n_rhs][ny][W] and segment carries
-// [P][n_rhs][W] each); launches the same kernels as slab_solve_raw and
-// allocates nothing.
-template <typename R>
-void slab_solve_raw_scratch(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud,
-                            int n_rhs, cudaStream_t s, cplx<R>* Y, cplx<R>* carry_f,
-                            cplx<R>* carry_b) {
-  Slab& S = L.slabs[j];
-  if (n_rhs > kNR) throw Failure(HZ_EINVAL, "too many right-hand sides per slab launch");
-  SolveArgs<R> a;
-  a.W = S.W; a.ny = L.ny; a.n_rhs = n_rhs; a.P = L.P; a.seg = L.seg_dev;
-  a.st = (const cplx<R>*)S.st; a.G = (const cplx<R>*)S.G; a.gstride = S.gstride;
-  a.stages = pick_stages<R>(S);
-  a.Y = Y; a.carry_f = carry_f; a.carry_b = carry_b;
-  a.flag = h->dev_flag;
-  a.rhs = Rhs<R>{};
-  a.rhs.raw = fd; a.rhs.ef = -1; a.rhs.eb = -1;
-  a.out = Out<R>{};
-  a.out.raw = ud; a.out.e2 = -1; a.out.e4 = -1;
-  const size_t smem = solve_smem(S.W, S.gstride, sizeof(cplx<R>), a.stages);
-  HZ_CU(cudaFuncSetAttribute(slab_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
-  HZ_CU(cudaFuncSetAttribute(slab_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
-  const int P = L.P;
-  dim3 grid(P);
-  if (P == 1) {
-    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 0);
-    slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
-    h->launches += 2;
-  } else {
-    const size_t csm = 2 * (size_t)kNR * S.W * sizeof(cplx<R>);
-    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 0, 0);
-    slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Phi, 0);
-    slab_fwd_kernel<R><<<grid, kThreads, smem, s>>>(a, 1, 1);
-    slab_carry_kernel<R><<<1, kThreads, csm, s>>>(a, (const cplx<R>*)S.Psi, 1);
-    slab_bwd_kernel<R><<<grid, kThreads, smem, s>>>(a);
-    h->launches += 5;
-  }
-  HZ_CU(cudaGetLastError());
-}
-
 template void slab_solve_raw_scratch<float>(hz_handle*, Level&, int, const c64*, c64*, int,
                                             cudaStream_t, c64*, c64*, c64*);
 template void slab_solve_raw_scratch<double>(hz_handle*, Level&, int, const c128*, c128*, int,

@@ -41,36 +41,49 @@ static void mid_solve_out(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, 
 }
 
 template <typename R>
+__global__ void add_kernel(cplx<R>* u, const cplx<R>* v, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) u[i] = u[i] + v[i];
+}
+
+// u = P f.  SubdomSolve adds J^T u_d into u; every column receives exactly one
+// contribution in each of the two phases of a sweep (the forward phase up to
+// g = f - A u, and the phase after it), so each phase stores into its own
+// buffer (u, then u2) and u += u2 at the end.
+template <typename R>
 void sweep_apply(hz_handle* h, Level& L, const cplx<R>* f, cplx<R>* u, int nr, cudaStream_t s) {
   const size_t n = (size_t)L.nx * L.ny;
   cplx<R>* g = (cplx<R>*)h->pr_g;
+  cplx<R>* u2 = (cplx<R>*)h->pr_u2;
   cplx<R>* B1 = (cplx<R>*)h->pr_B1;
   cplx<R>* B2 = (cplx<R>*)h->pr_B2;
-  HZ_CU(cudaMemsetAsync(u, 0, sizeof(cplx<R>) * n * nr, s));
   const int J = L.J;
   if (h->p.sweep == HZ_SWEEP_UD) {                  // SweepingPrecUD
     forward_sweep<R>(h, L, u, f, 1, J, B1, nr, s);
     level_residual<R>(h, L, f, u, g, nr, s);
-    backward_sweep<R>(h, L, u, g, J, 1, B1, nr, s);
-    return;
+    backward_sweep<R>(h, L, u2, g, J, 1, B1, nr, s);
+  } else {
+    const int jm = J / 2 + 1;                        // SweepingPrecX
+    cudaStream_t s2 = h->s2;
+    HZ_CU(cudaEventRecord(h->evA, s));
+    HZ_CU(cudaStreamWaitEvent(s2, h->evA, 0));
+    forward_sweep<R>(h, L, u, f, 1, jm - 1, B1, nr, s);
+    backward_sweep<R>(h, L, u, f, J, jm + 1, B2, nr, s2);
+    HZ_CU(cudaEventRecord(h->evB, s2));
+    HZ_CU(cudaStreamWaitEvent(s, h->evB, 0));
+    mid_solve_in<R>(h, L, u, f, jm, B1, B2, nr, s);
+    level_residual<R>(h, L, f, u, g, nr, s);
+    mid_solve_out<R>(h, L, u2, g, jm, B2, B1, nr, s);
+    HZ_CU(cudaEventRecord(h->evA, s));
+    HZ_CU(cudaStreamWaitEvent(s2, h->evA, 0));
+    backward_sweep<R>(h, L, u2, g, jm - 1, 1, B1, nr, s);
+    forward_sweep<R>(h, L, u2, g, jm + 1, J, B2, nr, s2);
+    HZ_CU(cudaEventRecord(h->evB, s2));
+    HZ_CU(cudaStreamWaitEvent(s, h->evB, 0));
   }
-  const int jm = J / 2 + 1;                          // SweepingPrecX
-  cudaStream_t s2 = h->s2;
-  HZ_CU(cudaEventRecord(h->evA, s));
-  HZ_CU(cudaStreamWaitEvent(s2, h->evA, 0));
-  forward_sweep<R>(h, L, u, f, 1, jm - 1, B1, nr, s);
-  backward_sweep<R>(h, L, u, f, J, jm + 1, B2, nr, s2);
-  HZ_CU(cudaEventRecord(h->evB, s2));
-  HZ_CU(cudaStreamWaitEvent(s, h->evB, 0));
-  mid_solve_in<R>(h, L, u, f, jm, B1, B2, nr, s);
-  level_residual<R>(h, L, f, u, g, nr, s);
-  mid_solve_out<R>(h, L, u, g, jm, B2, B1, nr, s);
-  HZ_CU(cudaEventRecord(h->evA, s));
-  HZ_CU(cudaStreamWaitEvent(s2, h->evA, 0));
-  backward_sweep<R>(h, L, u, g, jm - 1, 1, B1, nr, s);
-  forward_sweep<R>(h, L, u, g, jm + 1, J, B2, nr, s2);
-  HZ_CU(cudaEventRecord(h->evB, s2));
-  HZ_CU(cudaStreamWaitEvent(s, h->evB, 0));
+  add_kernel<R><<<cdiv(n * nr, 256), 256, 0, s>>>(u, u2, n * nr);
+  h->launches++;
+  HZ_CU(cudaGetLastError());
 }
 
 template <typename R>
