@@ -102,119 +102,186 @@ struct FactorDesc {
 };
 
 // One CTA per slab, sequential over block rows.  Each S_k is inverted by
-// Gauss-Jordan elimination with partial pivoting done implicitly (pivot rows
-// are marked, not moved); the permutations are applied when G_k is written:
-// G_k[p][piv[q]] = S[piv[p]][q].  Two block barriers per pivot.
+// Gauss-Jordan elimination with partial pivoting; pivot rows are marked, not
+// moved, and the permutations are applied when G_k is written:
+// G_k[p][piv[q]] = S[piv[p]][q].  With colmod = column p of S except
+// colmod[r] = S[r][p] - 1, and rowmod = row r of S scaled by inv = 1/S[r][p]
+// except rowmod[p] = inv + 1, one elimination step (pivot row included) is the
+// rank-1 update S -= colmod rowmod^T.
+// Layout: thread t < nph * W owns column j = t % W and rows
+// i = t / W + nph * m (m < M) of S, in registers; nph = blockDim / W.  The
+// owners of the next pivot column publish it with their best candidate; every
+// thread then picks the pivot from the nph candidates itself.  Two barriers
+// per pivot.
 template <typename R>
+struct FactorRegs { static constexpr int M = 32; };
+template <>
+struct FactorRegs<double> { static constexpr int M = 20; };
+
+// Rows per thread MM (compile time); nph = ceil(W / MM) phases, nph * W <= blockDim.
+template <typename R, int MM>
 __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc* descs) {
   const FactorDesc d = descs[blockIdx.x];
   const int W = d.W, wp = d.wp, ny = d.ny, tid = threadIdx.x;
-  const int ty = tid >> 2, tx = tid & 3;
+  const int WW = W * W;
+  const int nph = (W + MM - 1) / MM;             // row phases
+  const int M = MM;
+  const bool owner = tid < nph * W;
+  const int jt = owner ? tid % W : 0;            // my column
+  const int ph = owner ? tid / W : 0;            // my row phase
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* bufA = (cplx<R>*)smem_raw;
-  cplx<R>* bufB = bufA + W * W;
-  cplx<R>* rowbuf = bufB + W * W;
-  cplx<R>* colbuf = rowbuf + W;
-  int* piv = (int*)(colbuf + W);
+  cplx<R>* S = (cplx<R>*)smem_raw;               // W*W (Schur complement / result)
+  cplx<R>* Gl = S + WW;                          // W*W: G_{k-1}, natural order
+  cplx<R>* rowm = Gl + WW;                       // W
+  cplx<R>* const col0 = rowm + W;                // pivot column, double-buffered
+  cplx<R>* const col1 = rowm + 2 * W;
+  cplx<R>* cC = rowm + 3 * W;                    // C_k (3 x W)
+  cplx<R>* cD = cC + 3 * W;                      // D_k (3 x W)
+  cplx<R>* cB = cD + 3 * W;                      // B_{k-1} (3 x W)
+  R* const cval0 = (R*)(cB + 3 * W);            // candidates per phase, double-buffered
+  R* const cval1 = cval0 + 32;
+  int* const crow0 = (int*)(cval1 + 32);
+  int* const crow1 = crow0 + 32;
+  int* piv = crow1 + 32;
   int* ipiv = piv + W;
-  int* used = ipiv + W;
-  __shared__ int sh_r;
   const cplx<R> zero = mk<R>(0, 0);
-  cplx<R>* S = bufA;    // working matrix
-  cplx<R>* Gl = bufB;   // inverse of the previous block row, natural order
+  cplx<R> a[MM];
+
   for (int k = 0; k < ny; ++k) {
     const cplx<R>* stk = st + (size_t)k * 9 * wp;
-    if (k == 0) {
-      for (int i = tid; i < W * W; i += kThreads) S[i] = zero;
-      __syncthreads();
-    } else {
-      const cplx<R>* stp = st + (size_t)(k - 1) * 9 * wp;
-      // S = G_{k-1} B_{k-1}:  S[i][j] = sum_dx G[i][j-dx] B_{k-1}(j-dx, dx)
-      for (int i = ty; i < W; i += kGroups)
-        for (int j = tx; j < W; j += kTPR) {
-          cplx<R> acc = zero;
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            int e = j - dx;
-            if (e >= 0 && e < W) cfma(acc, Gl[i * W + e], stp[(6 + dx + 1) * wp + e]);
-          }
-          S[i * W + j] = acc;
-        }
-      __syncthreads();
-      // Gl = -C_k S:  Gl[i][j] = -sum_dx C_k(i, dx) S[i+dx][j]
-      for (int i = ty; i < W; i += kGroups)
-        for (int j = tx; j < W; j += kTPR) {
-          cplx<R> acc = zero;
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            int e = i + dx;
-            if (e >= 0 && e < W) cfma(acc, stk[(dx + 1) * wp + i], S[e * W + j]);
-          }
-          Gl[i * W + j] = -acc;
-        }
-      __syncthreads();
-      cplx<R>* t = S; S = Gl; Gl = t;   // S = -C_k G_{k-1} B_{k-1}
+    for (int t = tid; t < 3 * W; t += kThreads) {     // stage the couplings
+      const int q = t / W, e = t - q * W;
+      cC[t] = stk[q * wp + e];
+      cD[t] = stk[(3 + q) * wp + e];
+      cB[t] = (k > 0) ? st[(size_t)(k - 1) * 9 * wp + (6 + q) * wp + e] : zero;
     }
-    for (int i = tid; i < W; i += kThreads) {   // + D_k
+    __syncthreads();
+    // Schur complement S_k = D_k - C_k G_{k-1} B_{k-1}, into registers:
+    // first X = G_{k-1} B_{k-1} into S (shared), then a = D_k - C_k X.
+    if (k > 0) {
+      for (int e = tid; e < WW; e += kThreads) {
+        const int i = e / W, j = e - i * W;
+        cplx<R> acc = zero;
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        int j = i + dx;
-        if (j >= 0 && j < W) S[i * W + j] = S[i * W + j] + stk[(3 + dx + 1) * wp + i];
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int c = j - dx;
+          if (c >= 0 && c < W) cfma(acc, Gl[i * W + c], cB[(dx + 1) * W + c]);
+        }
+        S[e] = acc;
       }
-      used[i] = 0;
+      __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      const int i = ph + nph * m;
+      cplx<R> v = zero;
+      if (owner && m < M && i < W) {
+        if (k > 0) {
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int rr = i + dx;
+            if (rr >= 0 && rr < W) cfma(v, cC[(dx + 1) * W + i], S[rr * W + jt]);
+          }
+          v = -v;
+        }
+        const int dd = jt - i;
+        if (dd >= -1 && dd <= 1) v = v + cD[(dd + 1) * W + i];
+      }
+      a[m] = v;
+    }
+    uint32_t usedmask = 0;     // my rows already used as pivots (bit m)
+    // publish column 0 and the candidates for the first pivot
+    if (owner && jt == 0) {
+      R bv = -1;
+      int bi = 1 << 30;
+#pragma unroll
+      for (int m = 0; m < MM; ++m) {
+        const int i = ph + nph * m;
+        if (m < M && i < W) {
+          col0[i] = a[m];
+          const R v = cabs2(a[m]);
+          if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        }
+      }
+      cval0[ph] = bv;
+      crow0[ph] = bi;
     }
     __syncthreads();
     for (int p = 0; p < W; ++p) {
-      if (tid < 32) {
-        R best = -1;
-        int bi = 1 << 30;
-        for (int i = tid; i < W; i += 32) {
-          if (used[i]) continue;
-          R v = cabs2(S[i * W + p]);
-          if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          R ob = __shfl_xor_sync(0xffffffffu, best, o);
-          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        const int r = bi;
-        const cplx<R> inv = cinv(S[r * W + p]);
-        for (int j = tid; j < W; j += 32) rowbuf[j] = (j == p) ? inv : S[r * W + j] * inv;
-        for (int i = tid; i < W; i += 32) colbuf[i] = S[i * W + p];
-        if (tid == 0) { used[r] = 1; piv[p] = r; sh_r = r; }
+      const bool odd = p & 1;
+      const cplx<R>* col = odd ? col1 : col0;
+      cplx<R>* ncol = odd ? col0 : col1;
+      const R* cv = odd ? cval1 : cval0;
+      const int* cr = odd ? crow1 : crow0;
+      R* ncv = odd ? cval0 : cval1;
+      int* ncr = odd ? crow0 : crow1;
+      // pivot: best of the nph candidates (ties to the lower row)
+      R bv = -1;
+      int r = 1 << 30;
+      for (int q = 0; q < nph; ++q) {
+        const R v = cv[q];
+        const int ri = cr[q];
+        if (v > bv || (v == bv && ri < r)) { bv = v; r = ri; }
       }
+      const cplx<R> inv = cinv(col[r]);
+      const int rph = r % nph, rm = r / nph;
+      if (owner && ph == rph) {          // my element of the pivot row
+        cplx<R> x = zero;
+#pragma unroll
+        for (int m = 0; m < MM; ++m)
+          if (m == rm) x = a[m];
+        rowm[jt] = (jt == p) ? mk<R>(inv.re + (R)1, inv.im) : x * inv;
+        usedmask |= 1u << rm;
+      }
+      if (tid == 0) piv[p] = r;
       __syncthreads();
-      const int r = sh_r;
-      for (int i = ty; i < W; i += kGroups) {
-        const cplx<R> c = colbuf[i];
-        for (int j = tx; j < W; j += kTPR) {
-          cplx<R> q = rowbuf[j];
-          if (i == r) {
-            S[i * W + j] = q;
-          } else {
-            cplx<R> v = (j == p) ? zero : S[i * W + j];
-            v.re -= c.re * q.re - c.im * q.im;
-            v.im -= c.re * q.im + c.im * q.re;
-            S[i * W + j] = v;
+      if (owner) {
+        const cplx<R> q = rowm[jt];
+        const bool pub = (jt == p + 1);
+        R nbv = -1;
+        int nbi = 1 << 30;
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+          const int i = ph + nph * m;
+          if (m < M && i < W) {
+            cplx<R> c = col[i];
+            if (i == r) c.re -= (R)1;
+            a[m].re -= c.re * q.re - c.im * q.im;
+            a[m].im -= c.re * q.im + c.im * q.re;
+            if (pub) {
+              ncol[i] = a[m];
+              if (!((usedmask >> m) & 1u)) {
+                const R v = cabs2(a[m]);
+                if (v > nbv || (v == nbv && i < nbi)) { nbv = v; nbi = i; }
+              }
+            }
           }
         }
+        if (pub) {
+          ncv[ph] = nbv;
+          ncr[ph] = nbi;
+        }
       }
       __syncthreads();
+    }
+    // write back, then apply the permutations into G_k (global) and Gl (next row)
+    if (owner) {
+#pragma unroll
+      for (int m = 0; m < MM; ++m) {
+        const int i = ph + nph * m;
+        if (m < M && i < W) S[i * W + jt] = a[m];
+      }
     }
     for (int q = tid; q < W; q += kThreads) ipiv[piv[q]] = q;
     __syncthreads();
     cplx<R>* Gk = G + (size_t)k * d.gstride;
-    for (int i = ty; i < W; i += kGroups) {
-      const int pr = piv[i];
-      for (int c = tx; c < W; c += kTPR) {
-        cplx<R> v = S[pr * W + ipiv[c]];
-        Gk[i * W + c] = v;
-        Gl[i * W + c] = v;
-      }
+    for (int e = tid; e < WW; e += kThreads) {
+      const int i = e / W, j = e - i * W;
+      const cplx<R> v = S[piv[i] * W + ipiv[j]];
+      Gk[e] = v;
+      Gl[e] = v;
     }
     __syncthreads();
   }
@@ -448,6 +515,7 @@ __global__ void slab_gather_kernel(SolveArgs<R> a) {
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int mode, int bwd1) {
   const int p = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
+  const int nthr = blockDim.x, ngroups = nthr / kTPR;
   const int k0 = a.seg[p], k1 = a.seg[p + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
@@ -461,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
     for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
     mbar_fence_init();
   }
-  for (int i = tid; i < NR * wp; i += kThreads) {
+  for (int i = tid; i < NR * wp; i += nthr) {
     const int r = i / wp, e = i - r * wp;
     ybuf[i] = (mode == 1 && p > 0 && r < nr) ? a.carry_f[((size_t)(p - 1) * nr + r) * wp + e] : zero;
   }
@@ -499,7 +567,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
       }
     }
     __syncthreads();
-    for (int rb = 0; rb < W; rb += kGroups) {
+    for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
       gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
@@ -516,7 +584,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
     if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k + pipe.stages, a.G, a.st, 0, a.Y);
   }
   if (mode == 0) {
-    for (int i = tid; i < nr * wp; i += kThreads) a.carry_f[(size_t)p * nr * wp + i] = ybuf[i];
+    for (int i = tid; i < nr * wp; i += nthr) a.carry_f[(size_t)p * nr * wp + i] = ybuf[i];
     return;
   }
   if (!bwd1) return;
@@ -524,7 +592,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
   // The y rows were written above by this CTA (generic stores); they are read
   // with ordinary loads, one step ahead, never through TMA.  The pipeline
   // still brings G_k and B_k (its vector part, Y row k, is not used here).
-  for (int i = tid; i < NR * wp; i += kThreads) ybuf[i] = zero;   // x_{k1}
+  for (int i = tid; i < NR * wp; i += nthr) ybuf[i] = zero;   // x_{k1}
   __syncthreads();
   if (tid == 0)
     for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k1 - 1 - i, a.G, a.st, 6, a.Y);
@@ -556,12 +624,12 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
       }
     }
     __syncthreads();
-    for (int rb = 0; rb < W; rb += kGroups) {
+    for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
       cplx<R> ycur[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) ycur[r] = ynext[r];
-      if (rb + kGroups >= W) {           // last pass over rows: prefetch row k-1
+      if (rb + ngroups >= W) {           // last pass over rows: prefetch row k-1
         const int rowp = grp;
 #pragma unroll
         for (int r = 0; r < NR; ++r)
@@ -586,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
     if (sh_abort) return;
     if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k - pipe.stages, a.G, a.st, 6, a.Y);
   }
-  for (int i = tid; i < nr * wp; i += kThreads) a.carry_b[(size_t)p * nr * wp + i] = ybuf[i];
+  for (int i = tid; i < nr * wp; i += nthr) a.carry_b[(size_t)p * nr * wp + i] = ybuf[i];
 }
 
 // Final backward recurrence over one segment from x_{k1} = carry_b[p+1]
@@ -594,6 +662,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
   const int p = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
+  const int nthr = blockDim.x, ngroups = nthr / kTPR;
   const int k0 = a.seg[p], k1 = a.seg[p + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
@@ -607,7 +676,7 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
     for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
     mbar_fence_init();
   }
-  for (int i = tid; i < NR * wp; i += kThreads) {
+  for (int i = tid; i < NR * wp; i += nthr) {
     const int r = i / wp, e = i - r * wp;
     xbuf[i] = (p + 1 < a.P && r < nr) ? a.carry_b[((size_t)(p + 1) * nr + r) * wp + e] : zero;
   }
@@ -641,7 +710,7 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
       }
     }
     __syncthreads();
-    for (int rb = 0; rb < W; rb += kGroups) {
+    for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
       gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
@@ -673,6 +742,7 @@ template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, const cplx<R>* prod,
                                                               int backward) {
   const int tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr, P = a.P;
+  const int nthr = blockDim.x, ngroups = nthr / kTPR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   uint64_t* bar = (uint64_t*)smem_raw;
@@ -697,7 +767,7 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
     mbar_fence_init();
   }
   const int pstart = seg_of(0);
-  for (int i = tid; i < NR * wp; i += kThreads)
+  for (int i = tid; i < NR * wp; i += nthr)
     prev[i] = (i < nr * wp) ? carry[(size_t)pstart * nr * wp + i] : mk<R>(0, 0);
   __syncthreads();
   const int n = P - 1;
@@ -718,7 +788,7 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
     const cplx<R>* hat = M + a.gstride;
     cplx<R> res[NR];
     int myrow = -1;
-    for (int rb = 0; rb < W; rb += kGroups) {
+    for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
       gemv_rows<R, NR>(M, W, prev, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
@@ -780,10 +850,18 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   const int J = L.J;
   int maxW = 0;
   for (int j = 1; j <= J; ++j) maxW = std::max(maxW, L.slabs[j].W);
-  size_t smem = 2 * (size_t)maxW * maxW * sizeof(cplx<R>) + 2 * maxW * sizeof(cplx<R>) +
-                3 * maxW * sizeof(int) + 64;
-  if (smem > kSmemLimit)
-    throw Failure(HZ_EINVAL, "slab too wide for the shared-memory factorisation (W=" +
+  size_t smem = 2 * (size_t)maxW * maxW * sizeof(cplx<R>) + 12 * maxW * sizeof(cplx<R>) +
+                64 * (sizeof(R) + sizeof(int)) + 2 * maxW * sizeof(int) + 64;
+  // rows per thread: the smallest compile-time size that fits the block
+  int MM = 0;
+  for (int cand : {8, 16, 24, 32}) {
+    if (cand > FactorRegs<R>::M) break;
+    if ((maxW + cand - 1) / cand * maxW <= kThreads) { MM = cand; break; }
+  }
+  if (MM == 0 && (maxW + FactorRegs<R>::M - 1) / FactorRegs<R>::M * maxW <= kThreads)
+    MM = FactorRegs<R>::M;
+  if (MM == 0)
+    throw Failure(HZ_EINVAL, "slab too wide for the register-resident factorisation (W=" +
                                  std::to_string(maxW) + ")");
   std::vector<FactorDesc> fd(J);
   for (int j = 1; j <= J; ++j) {
@@ -792,9 +870,15 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   }
   FactorDesc* d_fd = (FactorDesc*)dmalloc(sizeof(FactorDesc) * J);
   HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), sizeof(FactorDesc) * J, cudaMemcpyHostToDevice, s));
-  HZ_CU(cudaFuncSetAttribute(slab_factor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem));
-  timed(h, "slab_factor", 0.0, s, [&] { slab_factor_kernel<R><<<J, kThreads, smem, s>>>(d_fd); });
+  auto launch = [&](auto kern) {
+    HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    timed(h, "slab_factor", 0.0, s, [&] { kern<<<J, kThreads, smem, s>>>(d_fd); });
+  };
+  if (MM == 8) launch(slab_factor_kernel<R, 8>);
+  else if (MM == 16) launch(slab_factor_kernel<R, 16>);
+  else if (MM == 20) launch(slab_factor_kernel<R, 20>);
+  else if (MM == 24) launch(slab_factor_kernel<R, 24>);
+  else launch(slab_factor_kernel<R, 32>);
   h->launches++;
   HZ_CU(cudaGetLastError());
   ProdDesc* d_pd = nullptr;
@@ -851,6 +935,8 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
     if (tagged) timed(h, tag, bytes, s, fn); else fn();
   };
   dim3 grid(P);
+  // one 4-thread group per row of G: round W * kTPR up to whole warps
+  const int nthr = std::min(kThreads, std::max(128, (S.W * kTPR + 31) / 32 * 32));
   const size_t gtotal = (size_t)L.ny * nr * S.wp;
   T("slab_gather", 2 * vbytes, [&] {
     slab_gather_kernel<R><<<cdiv(gtotal, 256), 256, 0, s>>>(a);
@@ -858,10 +944,10 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   h->launches++;
   if (P == 1) {
     T("slab_fwd", gbytes + cbytes + 3 * vbytes, [&] {
-      slab_fwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a, 1, 0);
+      slab_fwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a, 1, 0);
     });
     T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
-      slab_bwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a);
+      slab_bwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a);
     });
     h->launches += 2;
   } else {
@@ -869,19 +955,19 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
     ac.stages = pick_carry_stages<R>(S, nr, NR);
     const size_t csm = carry_smem<R>(S, nr, NR, ac.stages);
     T("slab_fwd_pass1", gbytes + cbytes + 3 * vbytes, [&] {
-      slab_fwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a, 0, 0);
+      slab_fwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a, 0, 0);
     });
     T("slab_carry", pbytes, [&] {
-      slab_carry_kernel<R, NR><<<1, kThreads, csm, s>>>(ac, (const cplx<R>*)S.Phi, 0);
+      slab_carry_kernel<R, NR><<<1, nthr, csm, s>>>(ac, (const cplx<R>*)S.Phi, 0);
     });
     T("slab_fwd_bwd1", 2 * gbytes + 2 * cbytes + 4 * vbytes, [&] {
-      slab_fwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a, 1, 1);
+      slab_fwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a, 1, 1);
     });
     T("slab_carry", pbytes, [&] {
-      slab_carry_kernel<R, NR><<<1, kThreads, csm, s>>>(ac, (const cplx<R>*)S.Psi, 1);
+      slab_carry_kernel<R, NR><<<1, nthr, csm, s>>>(ac, (const cplx<R>*)S.Psi, 1);
     });
     T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
-      slab_bwd_kernel<R, NR><<<grid, kThreads, smem, s>>>(a);
+      slab_bwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a);
     });
     h->launches += 5;
   }
