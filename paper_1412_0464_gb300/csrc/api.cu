@@ -16,6 +16,23 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Fine level (finite differences, Eq. 40) and, for two-grid, the coarse FE
+// level that carries the domain decomposition; then the slabs.
+void build_levels(hz_handle* h, const double* m_dev) {
+  const hz_params& p = h->p;
+  const double hh = 1.0 / p.n;
+  build_level_fd(h, h->fine, p.n, p.w_out, hh, m_dev, h->s2);
+  if (p.two_grid) {
+    build_level_fe(h, h->coarse, h->fine, p.n, p.w_out, hh, h->s2);
+    h->sweep = &h->coarse;
+  } else {
+    h->sweep = &h->fine;
+  }
+  h->sweep->J = p.J;
+  h->sweep->w = p.w_dd;
+  build_slabs(h, *h->sweep, h->s2);
+}
+
 hz_status fail(hz_handle* h, hz_status st, const std::string& msg) {
   if (h) { h->err.st = st; h->err.msg = msg; }
   g_last_error = msg;
@@ -70,9 +87,10 @@ void validate(const hz_params* p) {
   if (p->max_iter < 1) bad("max_iter must be >= 1");
   if (!(p->tol > 0)) bad("tol must be > 0");
   if (p->max_rhs < 1 || p->max_rhs > 8) bad("max_rhs must be in 1..8");
-  if (p->two_grid) bad("the two-grid preconditioner is not built in this version");
-  int N = p->n + 2 * p->w_out - 1;
-  if (N / p->J < 2 * p->w_dd + 2) bad("slabs too thin for the DD PML width");
+  if (p->two_grid && (p->n % 2 != 0)) bad("two_grid needs an even number of interior cells");
+  if (p->two_grid && (p->nu < 0 || !(p->omega_jac > 0))) bad("bad smoother parameters");
+  int N = p->two_grid ? 2 * p->w_out + p->n / 2 - 1 : p->n + 2 * p->w_out - 1;
+  if (N / p->J < 4) bad("slabs too thin: fewer than 4 columns per slab");
 }
 
 }  // namespace
@@ -116,11 +134,7 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
     const int N = p->n + 2 * p->w_out - 1;
     const double hh = 1.0 / p->n;
     h->c_pml = mean_velocity(m_dev, (size_t)N * N, h->s2);
-    build_level_fd(h, h->fine, p->n, p->w_out, hh, m_dev, h->s2);
-    h->fine.J = p->J;
-    h->fine.w = p->w_dd;
-    h->sweep = &h->fine;
-    build_slabs(h, h->fine, h->s2);
+    build_levels(h, m_dev);
     const size_t n = (size_t)N * N;
     const size_t ps = prec_size(*p);
     const int R = p->max_rhs, m = p->gmres_m;
@@ -134,6 +148,11 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
     h->pr_B2 = dmalloc(ps * 2 * R * L.ny);
     HZ_CU(cudaMemsetAsync(h->pr_B1, 0, ps * 2 * R * L.ny, h->s2));
     HZ_CU(cudaMemsetAsync(h->pr_B2, 0, ps * 2 * R * L.ny, h->s2));
+    if (p->two_grid) {
+      h->tg_u = dmalloc(ps * n * R);
+      h->tg_r = dmalloc(ps * n * R);
+      h->tg_t = dmalloc(ps * n * R);
+    }
     h->V = (c128*)dmalloc(sizeof(c128) * n * R * (m + 1));
     h->Z = (c128*)dmalloc(sizeof(c128) * n * R * m);
     h->W = (c128*)dmalloc(sizeof(c128) * n * R);
@@ -159,14 +178,10 @@ hz_status hz_set_medium(hz_handle* h, const double* m_dev) {
     double t0 = now_s();
     const hz_params p = h->p;
     free_level(h->fine);
-    h->fine = Level{};
+    free_level(h->coarse);
     const int N = p.n + 2 * p.w_out - 1;
     h->c_pml = mean_velocity(m_dev, (size_t)N * N, h->s2);
-    build_level_fd(h, h->fine, p.n, p.w_out, 1.0 / p.n, m_dev, h->s2);
-    h->fine.J = p.J;
-    h->fine.w = p.w_dd;
-    h->sweep = &h->fine;
-    build_slabs(h, h->fine, h->s2);
+    build_levels(h, m_dev);
     h->factored = false;
     h->stats.t_setup_s = now_s() - t0;
   });

@@ -114,6 +114,11 @@ struct Level {
   float* m32 = nullptr;      // FP32 copy
   c128* st128 = nullptr;     // FE level: 9 coefficient planes [9][ny][nx]
   c64* st64 = nullptr;
+  double* k2c = nullptr;     // FE level: cell k^2 [(ny+1)][(nx+1)]
+  int* ifp = nullptr;        // FE level: coarse node -> fine node (per axis, both axes equal)
+  int* refined = nullptr;    // FE level: coarse cell refined flags
+  int* q0 = nullptr;         // FE level: prolongation sources per fine node
+  int* q1 = nullptr;
   int J = 0, w = 0;
   std::vector<int> beta, beta_t;  // Eq. 17, size J+1
   std::vector<Slab> slabs;        // index 1..J (0 unused)
@@ -228,6 +233,9 @@ void restrict_residual(hz_handle* h, const Level& F, const Level& C, const cplx<
 template <typename R>
 void prolong_add(hz_handle* h, const Level& F, const Level& C, const cplx<R>* ec, cplx<R>* uf,
                  int n_rhs, cudaStream_t s);
+
+template <typename R>
+void slab_stencil_fe(hz_handle* h, const Level& L, const Slab& S, cudaStream_t s);
 
 // slab.cu
 template <typename R>

@@ -181,8 +181,6 @@ __global__ void inj_fe_kernel(int ny, int nx, int beta, int bt, const c128* st, 
   }
 }
 
-// Slab stencil copied from a stored 9-point operator; k frozen is built into
-// the coarse-level slab operator by the FE assembly kernel (fe.cu).
 __global__ void mean_inv_sqrt_kernel(const double* m, size_t n, double* partial) {
   __shared__ double sh[256];
   double acc = 0;
@@ -297,6 +295,7 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
       inj_fd_kernel<R><<<cdiv(L.ny, 128), 128, 0, s>>>(L.ny, beta, bt, L.ax.a_cell, L.ay.a_node,
                                                        (cplx<R>*)S.inj);
     } else {
+      slab_stencil_fe<R>(h, L, S, s);
       inj_fe_kernel<R><<<cdiv(L.ny, 128), 128, 0, s>>>(L.ny, L.nx, beta, bt, L.st128,
                                                        (cplx<R>*)S.inj);
     }
@@ -347,7 +346,8 @@ void free_level(Level& L) {
   free_axis(L.ax);
   free_axis(L.ay);
   dfree(L.m); dfree(L.m32); dfree(L.st128); dfree(L.st64); dfree(L.seg_dev);
-  L.m = nullptr; L.m32 = nullptr; L.st128 = nullptr; L.st64 = nullptr; L.seg_dev = nullptr;
+  dfree(L.k2c); dfree(L.ifp); dfree(L.refined); dfree(L.q0); dfree(L.q1);
+  L = Level{};
 }
 
 }  // namespace hz

@@ -86,6 +86,24 @@ void sweep_apply(hz_handle* h, Level& L, const cplx<R>* f, cplx<R>* u, int nr, c
   HZ_CU(cudaGetLastError());
 }
 
+// Two-grid sweeping preconditioner (Section 4): u = 0; nu omega-Jacobi steps;
+// r_c = R (f - A u); e_c = P_X r_c (or P_UD) on the coarse operator; u += P e_c;
+// nu omega-Jacobi steps.
+template <typename R>
+static void tgsp(hz_handle* h, const cplx<R>* f, cplx<R>* u, int nr, cudaStream_t s) {
+  Level& F = h->fine;
+  Level& C = h->coarse;
+  const size_t nf = (size_t)F.nx * F.ny;
+  cplx<R>* t = (cplx<R>*)h->tg_t;
+  HZ_CU(cudaMemsetAsync(u, 0, sizeof(cplx<R>) * nf * nr, s));
+  jacobi_steps<R>(h, F, f, u, t, h->p.nu, h->p.omega_jac, nr, s);
+  level_residual<R>(h, F, f, u, t, nr, s);
+  restrict_residual<R>(h, F, C, t, (cplx<R>*)h->pr_r, nr, s);
+  sweep_apply<R>(h, C, (const cplx<R>*)h->pr_r, (cplx<R>*)h->pr_u, nr, s);
+  prolong_add<R>(h, F, C, (const cplx<R>*)h->pr_u, u, nr, s);
+  jacobi_steps<R>(h, F, f, u, t, h->p.nu, h->p.omega_jac, nr, s);
+}
+
 template <typename R>
 static void precond_t(hz_handle* h, const c128* r, c128* z, int nr, cudaStream_t s) {
   Level& F = h->fine;
@@ -100,7 +118,13 @@ static void precond_t(hz_handle* h, const c128* r, c128* z, int nr, cudaStream_t
     }
     return;
   }
-  throw Failure(HZ_EINVAL, "two-grid preconditioner is not built in this version");
+  if (sizeof(R) == 8) {
+    tgsp<R>(h, (const cplx<R>*)r, (cplx<R>*)z, nr, s);
+  } else {
+    cast_copy<R, double>(r, (cplx<R>*)h->tg_r, n * nr, s);
+    tgsp<R>(h, (const cplx<R>*)h->tg_r, (cplx<R>*)h->tg_u, nr, s);
+    cast_copy<double, R>((const cplx<R>*)h->tg_u, z, n * nr, s);
+  }
 }
 
 void precond_apply(hz_handle* h, const c128* r, c128* z, int nr, cudaStream_t s) {

@@ -34,7 +34,7 @@ def _params(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(dim=3), dict(J=3), dict(n=2), dict(max_rhs=0),
-                                 dict(max_rhs=99), dict(tol=0.0), dict(w_dd=0), dict(J=40),
+                                 dict(max_rhs=99), dict(tol=0.0), dict(w_dd=0), dict(J=60),
                                  dict(precision=7), dict(sweep=5)])
 def test_setup_rejects_bad_parameters(L, bad):
     h = ctypes.c_void_p()

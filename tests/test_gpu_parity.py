@@ -155,3 +155,60 @@ def test_error_paths():
     assert e.value.status == hz.HZ_EINVAL
     u, st = s.solve(b)                      # zero right-hand side: zero solution
     assert float(u.abs().max()) == 0.0
+
+
+# ------------------------------------------------------------------ two-grid
+TG_CASES = [(3, 120, 10, 4), (3, 96, 6, 6)]    # (config, n even, w_out, J on the coarse grid)
+
+
+@pytest.mark.parametrize("idx,n,w_out,J", TG_CASES)
+def test_two_grid_coarse_slabs_match_oracle(idx, n, w_out, J):
+    hz = _hz()
+    cfg = synth.scaled_workload(idx, n, w_out=w_out, J=J)
+    p = Problem(cfg)
+    s = hz.Solver.from_workload(cfg, precision="fp64")
+    s.factor()
+    for j in range(1, J + 1):
+        sl = p.dd.slabs[j]
+        info = s.slab_info(j)
+        assert (info["lo"], info["hi"], info["wl"], info["wr"], info["W"]) == \
+            (sl.lo, sl.hi, sl.wl, sl.wr, sl.W)
+        fd = _rand((sl.A.shape[0] // sl.W, sl.W), 40 + j)
+        ud = s.slab_solve(j, torch.from_numpy(fd).cuda()).cpu().numpy()
+        ref = sl.lu.solve(fd.ravel()).reshape(fd.shape)
+        assert _rel(ud, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("sweep", ["X", "UD"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 3e-4)])
+@pytest.mark.parametrize("idx,n,w_out,J", TG_CASES)
+def test_two_grid_preconditioner_matches_oracle(idx, n, w_out, J, sweep, precision, tol):
+    hz = _hz()
+    cfg = synth.scaled_workload(idx, n, w_out=w_out, J=J)
+    p = Problem(cfg, sweep=sweep)
+    s = hz.Solver.from_workload(cfg, precision=precision, sweep=sweep, max_rhs=2)
+    s.factor()
+    f = _rand((2,) + cfg.shape, 5)
+    z = s.precond(torch.from_numpy(f).cuda()).cpu().numpy()
+    for r in range(2):
+        ref = p.precondition(f[r]).reshape(cfg.shape)
+        assert _rel(z[r], ref) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_grid_solve_matches_oracle(precision):
+    hz = _hz()
+    cfg = synth.scaled_workload(3, 200, w_out=16, J=8)
+    p = Problem(cfg)
+    b = synth.sources(cfg)[0]
+    _, info = p.solve(b)
+    exact = spla.spsolve(p.A.tocsc(), b.ravel()).reshape(cfg.shape)
+    s = hz.Solver.from_workload(cfg, precision=precision)
+    s.factor()
+    u, st = s.solve(torch.from_numpy(b).cuda())
+    u = u.cpu().numpy()
+    relres = np.linalg.norm(p.A @ u.ravel() - b.ravel()) / np.linalg.norm(b)
+    assert relres <= 1.05 * cfg.tol
+    assert _rel(u, exact) <= 1e-5
+    if precision == "fp64":
+        assert abs(st["iters_max"] - info["iters"]) <= 1
