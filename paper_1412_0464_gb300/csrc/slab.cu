@@ -107,47 +107,132 @@ struct FactorDesc {
 // G_k[p][piv[q]] = S[piv[p]][q].  With colmod = column p of S except
 // colmod[r] = S[r][p] - 1, and rowmod = row r of S scaled by inv = 1/S[r][p]
 // except rowmod[p] = inv + 1, one elimination step (pivot row included) is the
-// rank-1 update S -= colmod rowmod^T.
-// Layout: thread t < nph * W owns column j = t % W and rows
-// i = t / W + nph * m (m < M) of S, in registers; nph = blockDim / W.  The
-// owners of the next pivot column publish it with their best candidate; every
-// thread then picks the pivot from the nph candidates itself.  Two barriers
-// per pivot.
-template <typename R>
-struct FactorRegs { static constexpr int M = 32; };
-template <>
-struct FactorRegs<double> { static constexpr int M = 20; };
+// rank-1 update S -= colmod rowmod^T.  The steps are blocked by panels of BW
+// columns: one warp eliminates the panel's BW pivots on the panel columns only
+// (shuffles, no block barrier), the pivot rows' other columns follow from the
+// short recurrence rowmod_t = (S[r_t] - sum_{s<t} colmod_s[r_t] rowmod_s) inv_t,
+// and all threads apply the delayed rank-BW update S -= Cm^T R in 4 x TC
+// register tiles.  Three block barriers per panel.
+__device__ __forceinline__ cplx<float> crcp(cplx<float> a) {
+  const float d = __frcp_rn(a.re * a.re + a.im * a.im);
+  return mk(a.re * d, -a.im * d);
+}
+__device__ __forceinline__ cplx<double> crcp(cplx<double> a) {
+  const double d = __drcp_rn(a.re * a.re + a.im * a.im);
+  return mk(a.re * d, -a.im * d);
+}
 
-// Rows per thread MM (compile time); nph = ceil(W / MM) phases, nph * W <= blockDim.
-template <typename R, int MM>
+template <typename R>
+struct FactorPanel { static constexpr int BW = 8; };
+template <>
+struct FactorPanel<double> { static constexpr int BW = 4; };
+
+// One warp eliminates pivots p0 .. p0+bw-1 on the panel columns p0 .. p0+bw-1
+// (rows lane + 32 m, m < MR, in registers) and records colmod (Cm), the pivot
+// inverses and rows.
+template <typename R, int BW, int MR>
+__device__ __forceinline__ void panel_elim(cplx<R>* S, cplx<R>* Cm, cplx<R>* pinv, int* prow,
+                                           int* piv, int* used, int W, int p0, int bw, int lane) {
+  const cplx<R> zero = mk<R>(0, 0);
+  cplx<R> P[MR][BW];
+  bool usd[MR];
+#pragma unroll
+  for (int m = 0; m < MR; ++m) {
+    const int i = lane + 32 * m;
+    usd[m] = (i < W) ? (used[i] != 0) : true;
+#pragma unroll
+    for (int c = 0; c < BW; ++c) P[m][c] = (i < W && c < bw) ? S[i * W + p0 + c] : zero;
+  }
+#pragma unroll
+  for (int t = 0; t < BW; ++t) {
+    if (t < bw) {
+      float lbv = -1.0f;
+      int lbi = 1 << 30;
+#pragma unroll
+      for (int m = 0; m < MR; ++m) {
+        if (!usd[m]) {
+          const float v = (float)cabs2(P[m][t]);
+          if (v > lbv) { lbv = v; lbi = lane + 32 * m; }
+        }
+      }
+      const unsigned key = lbv >= 0.0f ? __float_as_uint(lbv) : 0u;
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+      const unsigned win = __ballot_sync(0xffffffffu, key == kmax && lbi < (1 << 30));
+      const int r = __shfl_sync(0xffffffffu, lbi, __ffs(win) - 1);
+      const int rl = r & 31, rm = r >> 5;
+      cplx<R> prw[BW];
+#pragma unroll
+      for (int c = 0; c < BW; ++c) {
+        cplx<R> x = P[0][c];
+#pragma unroll
+        for (int m = 1; m < MR; ++m)
+          if (rm == m) x = P[m][c];
+        prw[c].re = __shfl_sync(0xffffffffu, x.re, rl);
+        prw[c].im = __shfl_sync(0xffffffffu, x.im, rl);
+      }
+      const cplx<R> inv = crcp(prw[t]);
+      cplx<R> rowm[BW];
+#pragma unroll
+      for (int c = 0; c < BW; ++c)
+        rowm[c] = (c == t) ? mk<R>(inv.re + (R)1, inv.im) : prw[c] * inv;
+#pragma unroll
+      for (int m = 0; m < MR; ++m) {
+        const int i = lane + 32 * m;
+        cplx<R> cm = P[m][t];
+        if (i == r) { cm.re -= (R)1; usd[m] = true; }
+        if (i < W) Cm[t * W + i] = cm;
+#pragma unroll
+        for (int c = 0; c < BW; ++c) {
+          P[m][c].re -= cm.re * rowm[c].re - cm.im * rowm[c].im;
+          P[m][c].im -= cm.re * rowm[c].im + cm.im * rowm[c].re;
+        }
+      }
+      if (lane == 0) {
+        pinv[t] = inv;
+        prow[t] = r;
+        piv[p0 + t] = r;
+        used[r] = 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MR; ++m) {
+    const int i = lane + 32 * m;
+#pragma unroll
+    for (int c = 0; c < BW; ++c)
+      if (i < W && c < bw) S[i * W + p0 + c] = P[m][c];
+  }
+}
+
+template <typename R, int TC>
 __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc* descs) {
+  constexpr int BW = FactorPanel<R>::BW;
+  constexpr int TR = 4;
   const FactorDesc d = descs[blockIdx.x];
   const int W = d.W, wp = d.wp, ny = d.ny, tid = threadIdx.x;
   const int WW = W * W;
-  const int nph = (W + MM - 1) / MM;             // row phases
-  const int M = MM;
-  const bool owner = tid < nph * W;
-  const int jt = owner ? tid % W : 0;            // my column
-  const int ph = owner ? tid / W : 0;            // my row phase
+  const int lane = tid & 31, warp = tid >> 5;
+  const int ntc = (W + TC - 1) / TC;             // tiles per row of S
+  const int ntr = (W + TR - 1) / TR;
+  const bool tile_owner = tid < ntr * ntc;
+  const int ti0 = tile_owner ? (tid / ntc) * TR : 0;
+  const int tj0 = tile_owner ? (tid % ntc) * TC : 0;
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* S = (cplx<R>*)smem_raw;               // W*W (Schur complement / result)
+  cplx<R>* S = (cplx<R>*)smem_raw;               // W*W
   cplx<R>* Gl = S + WW;                          // W*W: G_{k-1}, natural order
-  cplx<R>* rowm = Gl + WW;                       // W
-  cplx<R>* const col0 = rowm + W;                // pivot column, double-buffered
-  cplx<R>* const col1 = rowm + 2 * W;
-  cplx<R>* cC = rowm + 3 * W;                    // C_k (3 x W)
+  cplx<R>* Cm = Gl + WW;                         // BW x W  (colmod of the panel's pivots)
+  cplx<R>* Rm = Cm + BW * W;                     // BW x W  (rowmod on the other columns)
+  cplx<R>* cC = Rm + BW * W;                     // C_k (3 x W)
   cplx<R>* cD = cC + 3 * W;                      // D_k (3 x W)
   cplx<R>* cB = cD + 3 * W;                      // B_{k-1} (3 x W)
-  R* const cval0 = (R*)(cB + 3 * W);            // candidates per phase, double-buffered
-  R* const cval1 = cval0 + 32;
-  int* const crow0 = (int*)(cval1 + 32);
-  int* const crow1 = crow0 + 32;
-  int* piv = crow1 + 32;
-  int* ipiv = piv + W;
+  cplx<R>* pinv = cB + 3 * W;                    // BW
+  int* prow = (int*)(pinv + BW);                 // BW
+  int* piv = prow + BW;                          // W
+  int* ipiv = piv + W;                           // W
+  int* used = ipiv + W;                          // W
   const cplx<R> zero = mk<R>(0, 0);
-  cplx<R> a[MM];
 
   for (int k = 0; k < ny; ++k) {
     const cplx<R>* stk = st + (size_t)k * 9 * wp;
@@ -157,11 +242,11 @@ __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc*
       cD[t] = stk[(3 + q) * wp + e];
       cB[t] = (k > 0) ? st[(size_t)(k - 1) * 9 * wp + (6 + q) * wp + e] : zero;
     }
+    for (int t = tid; t < W; t += kThreads) used[t] = 0;
     __syncthreads();
-    // Schur complement S_k = D_k - C_k G_{k-1} B_{k-1}, into registers:
-    // first X = G_{k-1} B_{k-1} into S (shared), then a = D_k - C_k X.
+    // S_k = D_k - C_k G_{k-1} B_{k-1} (natural order, shared memory)
     if (k > 0) {
-      for (int e = tid; e < WW; e += kThreads) {
+      for (int e = tid; e < WW; e += kThreads) {      // Cm-area is free: X = G B into S
         const int i = e / W, j = e - i * W;
         cplx<R> acc = zero;
 #pragma unroll
@@ -172,107 +257,103 @@ __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc*
         S[e] = acc;
       }
       __syncthreads();
-    }
+      for (int e = tid; e < WW; e += kThreads) {      // Gl = D - C X
+        const int i = e / W, j = e - i * W;
+        cplx<R> acc = zero;
 #pragma unroll
-    for (int m = 0; m < MM; ++m) {
-      const int i = ph + nph * m;
-      cplx<R> v = zero;
-      if (owner && m < M && i < W) {
-        if (k > 0) {
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int rr = i + dx;
-            if (rr >= 0 && rr < W) cfma(v, cC[(dx + 1) * W + i], S[rr * W + jt]);
-          }
-          v = -v;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int rr = i + dx;
+          if (rr >= 0 && rr < W) cfma(acc, cC[(dx + 1) * W + i], S[rr * W + j]);
         }
-        const int dd = jt - i;
+        cplx<R> v = -acc;
+        const int dd = j - i;
         if (dd >= -1 && dd <= 1) v = v + cD[(dd + 1) * W + i];
+        Gl[e] = v;
       }
-      a[m] = v;
-    }
-    uint32_t usedmask = 0;     // my rows already used as pivots (bit m)
-    // publish column 0 and the candidates for the first pivot
-    if (owner && jt == 0) {
-      R bv = -1;
-      int bi = 1 << 30;
-#pragma unroll
-      for (int m = 0; m < MM; ++m) {
-        const int i = ph + nph * m;
-        if (m < M && i < W) {
-          col0[i] = a[m];
-          const R v = cabs2(a[m]);
-          if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
-        }
+      __syncthreads();
+      for (int e = tid; e < WW; e += kThreads) S[e] = Gl[e];
+    } else {
+      for (int e = tid; e < WW; e += kThreads) {
+        const int i = e / W, j = e - i * W;
+        const int dd = j - i;
+        S[e] = (dd >= -1 && dd <= 1) ? cD[(dd + 1) * W + i] : zero;
       }
-      cval0[ph] = bv;
-      crow0[ph] = bi;
     }
     __syncthreads();
-    for (int p = 0; p < W; ++p) {
-      const bool odd = p & 1;
-      const cplx<R>* col = odd ? col1 : col0;
-      cplx<R>* ncol = odd ? col0 : col1;
-      const R* cv = odd ? cval1 : cval0;
-      const int* cr = odd ? crow1 : crow0;
-      R* ncv = odd ? cval0 : cval1;
-      int* ncr = odd ? crow0 : crow1;
-      // pivot: best of the nph candidates (ties to the lower row)
-      R bv = -1;
-      int r = 1 << 30;
-      for (int q = 0; q < nph; ++q) {
-        const R v = cv[q];
-        const int ri = cr[q];
-        if (v > bv || (v == bv && ri < r)) { bv = v; r = ri; }
+
+    for (int p0 = 0; p0 < W; p0 += BW) {
+      const int bw = min(BW, W - p0);
+      // (1) one warp eliminates the panel's pivots on the panel columns
+      if (warp == 0) {
+        const int MR = (W + 31) >> 5;
+        if (bw == BW) {
+          if (MR == 1) panel_elim<R, BW, 1>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
+          else if (MR == 2) panel_elim<R, BW, 2>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
+          else if (MR == 3) panel_elim<R, BW, 3>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
+          else panel_elim<R, BW, 4>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
+        } else {
+          panel_elim<R, BW, 4>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
+        }
       }
-      const cplx<R> inv = cinv(col[r]);
-      const int rph = r % nph, rm = r / nph;
-      if (owner && ph == rph) {          // my element of the pivot row
-        cplx<R> x = zero;
-#pragma unroll
-        for (int m = 0; m < MM; ++m)
-          if (m == rm) x = a[m];
-        rowm[jt] = (jt == p) ? mk<R>(inv.re + (R)1, inv.im) : x * inv;
-        usedmask |= 1u << rm;
-      }
-      if (tid == 0) piv[p] = r;
       __syncthreads();
-      if (owner) {
-        const cplx<R> q = rowm[jt];
-        const bool pub = (jt == p + 1);
-        R nbv = -1;
-        int nbi = 1 << 30;
+      // (2) rowmod of the panel's pivots on the other columns
+      for (int j = tid; j < W; j += kThreads) {
+        if (j >= p0 && j < p0 + bw) continue;
+        cplx<R> rw[BW];
 #pragma unroll
-        for (int m = 0; m < MM; ++m) {
-          const int i = ph + nph * m;
-          if (m < M && i < W) {
-            cplx<R> c = col[i];
-            if (i == r) c.re -= (R)1;
-            a[m].re -= c.re * q.re - c.im * q.im;
-            a[m].im -= c.re * q.im + c.im * q.re;
-            if (pub) {
-              ncol[i] = a[m];
-              if (!((usedmask >> m) & 1u)) {
-                const R v = cabs2(a[m]);
-                if (v > nbv || (v == nbv && i < nbi)) { nbv = v; nbi = i; }
-              }
-            }
+        for (int t = 0; t < BW; ++t) {
+          if (t >= bw) break;
+          const int r = prow[t];
+          cplx<R> acc = S[r * W + j];
+#pragma unroll
+          for (int q = 0; q < t; ++q) {
+            const cplx<R> c = Cm[q * W + r];
+            acc.re -= c.re * rw[q].re - c.im * rw[q].im;
+            acc.im -= c.re * rw[q].im + c.im * rw[q].re;
           }
-        }
-        if (pub) {
-          ncv[ph] = nbv;
-          ncr[ph] = nbi;
+          rw[t] = acc * pinv[t];
+          Rm[t * W + j] = rw[t];
         }
       }
       __syncthreads();
-    }
-    // write back, then apply the permutations into G_k (global) and Gl (next row)
-    if (owner) {
+      // (3) delayed rank-bw update of the other columns, 4 x TC tiles
+      if (tile_owner) {
+        cplx<R> acc[TR][TC];
 #pragma unroll
-      for (int m = 0; m < MM; ++m) {
-        const int i = ph + nph * m;
-        if (m < M && i < W) S[i * W + jt] = a[m];
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+          for (int b = 0; b < TC; ++b) {
+            const int i = ti0 + a, j = tj0 + b;
+            acc[a][b] = (i < W && j < W) ? S[i * W + j] : zero;
+          }
+#pragma unroll
+        for (int t = 0; t < BW; ++t) {
+          if (t >= bw) break;
+          cplx<R> cv[TR], rv[TC];
+#pragma unroll
+          for (int a = 0; a < TR; ++a) cv[a] = (ti0 + a < W) ? Cm[t * W + ti0 + a] : zero;
+#pragma unroll
+          for (int b = 0; b < TC; ++b) {
+            const int j = tj0 + b;
+            rv[b] = (j < W && (j < p0 || j >= p0 + bw)) ? Rm[t * W + j] : zero;
+          }
+#pragma unroll
+          for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) {
+              acc[a][b].re -= cv[a].re * rv[b].re - cv[a].im * rv[b].im;
+              acc[a][b].im -= cv[a].re * rv[b].im + cv[a].im * rv[b].re;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+          for (int b = 0; b < TC; ++b) {
+            const int i = ti0 + a, j = tj0 + b;
+            if (i < W && j < W && (j < p0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
+          }
       }
+      __syncthreads();
     }
     for (int q = tid; q < W; q += kThreads) ipiv[piv[q]] = q;
     __syncthreads();
@@ -850,18 +931,13 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   const int J = L.J;
   int maxW = 0;
   for (int j = 1; j <= J; ++j) maxW = std::max(maxW, L.slabs[j].W);
-  size_t smem = 2 * (size_t)maxW * maxW * sizeof(cplx<R>) + 12 * maxW * sizeof(cplx<R>) +
-                64 * (sizeof(R) + sizeof(int)) + 2 * maxW * sizeof(int) + 64;
-  // rows per thread: the smallest compile-time size that fits the block
-  int MM = 0;
-  for (int cand : {8, 16, 24, 32}) {
-    if (cand > FactorRegs<R>::M) break;
-    if ((maxW + cand - 1) / cand * maxW <= kThreads) { MM = cand; break; }
-  }
-  if (MM == 0 && (maxW + FactorRegs<R>::M - 1) / FactorRegs<R>::M * maxW <= kThreads)
-    MM = FactorRegs<R>::M;
-  if (MM == 0)
-    throw Failure(HZ_EINVAL, "slab too wide for the register-resident factorisation (W=" +
+  size_t smem = 2 * (size_t)maxW * maxW * sizeof(cplx<R>) +
+                (2 * FactorPanel<R>::BW + 9) * maxW * sizeof(cplx<R>) +
+                FactorPanel<R>::BW * (sizeof(cplx<R>) + sizeof(int)) + 3 * maxW * sizeof(int) + 64;
+  // register tiles of the delayed update: 4 x 4 while ceil(W/4)^2 <= block, else 4 x 8
+  const int TC = ((maxW + 3) / 4) * ((maxW + 3) / 4) <= kThreads ? 4 : 8;
+  if (((maxW + 3) / 4) * ((maxW + TC - 1) / TC) > kThreads || maxW > 128)
+    throw Failure(HZ_EINVAL, "slab too wide for the blocked factorisation (W=" +
                                  std::to_string(maxW) + ")");
   std::vector<FactorDesc> fd(J);
   for (int j = 1; j <= J; ++j) {
@@ -874,11 +950,8 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
     HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     timed(h, "slab_factor", 0.0, s, [&] { kern<<<J, kThreads, smem, s>>>(d_fd); });
   };
-  if (MM == 8) launch(slab_factor_kernel<R, 8>);
-  else if (MM == 16) launch(slab_factor_kernel<R, 16>);
-  else if (MM == 20) launch(slab_factor_kernel<R, 20>);
-  else if (MM == 24) launch(slab_factor_kernel<R, 24>);
-  else launch(slab_factor_kernel<R, 32>);
+  if (TC == 4) launch(slab_factor_kernel<R, 4>);
+  else launch(slab_factor_kernel<R, 8>);
   h->launches++;
   HZ_CU(cudaGetLastError());
   ProdDesc* d_pd = nullptr;
