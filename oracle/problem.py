@@ -19,7 +19,7 @@ class Problem:
     def __init__(self, cfg, m: np.ndarray | None = None, *, sweep: str | None = None,
                  J: int | None = None, w_dd: int | None = None, s_dd: float | None = None,
                  two_grid: bool | None = None, nu: int | None = None,
-                 omega_jac: float | None = None):
+                 omega_jac: float | None = None, c_pml: float | None = None):
         import synth
         self.cfg = cfg
         self.m = synth.medium(cfg) if m is None else np.asarray(m, dtype=np.float64)
@@ -32,7 +32,8 @@ class Problem:
         self.omega_jac = cfg.omega_jac if omega_jac is None else omega_jac
         self.omega = cfg.omega
         h = cfg.h
-        self.c_pml = float(np.mean(1.0 / np.sqrt(self.m)))
+        # "typical velocity" of the PML (Section 2.1): mean wave speed unless fixed
+        self.c_pml = float(np.mean(1.0 / np.sqrt(self.m))) if c_pml is None else float(c_pml)
         self.axes = [mesh.fine_axis(cfg.n_cells, cfg.w_out, h, cfg.s_out, self.c_pml)
                      for _ in range(cfg.dim)]
         self.k2 = self.omega ** 2 * self.m

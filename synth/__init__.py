@@ -7,5 +7,5 @@ decomposition.  Both ``oracle/`` and the product package import it; it
 imports neither.
 """
 
-from .configs import CONFIGS, Workload, workload, scaled_workload  # noqa: F401
+from .configs import CONFIGS, Workload, workload, scaled_workload, adjoint_workload_2d  # noqa: F401
 from .media import medium, velocity, sources, source_nodes, receivers, fd_directions  # noqa: F401

@@ -124,3 +124,13 @@ def scaled_workload(idx: int, n: int, w_out: Optional[int] = None, J: Optional[i
         kw["corr"] = w.corr * n / w.n
     kw.update(over)
     return Workload(**kw)
+
+
+def adjoint_workload_2d(n: int = 128) -> Workload:
+    """2-D analogue of configuration 5 (adjoint gradient): smooth random true
+    model in [1.5, 4.5] (correlation 20 cells at n = 256), blurred start model,
+    8 sources and 16 receivers on a row two cells into the interior, two-grid
+    preconditioner, J = 4."""
+    return _cfg(name=f"adj2d_{n}+8", dim=2, n=n, w_out=8, medium="grf3d", corr=20.0 * n / 256,
+                J=4, w_dd=4, s_dd=20.0, two_grid=True, nu=3, omega_jac=0.8, n_src=8, n_rec=16,
+                gmres_m=30, seed=1412105)

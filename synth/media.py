@@ -95,6 +95,10 @@ def source_nodes(cfg: Workload) -> np.ndarray:
     if cfg.medium == "const" and cfg.n_src == 1:
         return np.full((1, cfg.dim), cfg.n_cells // 2 - 1)
     rng = _rng(cfg, _STREAM_SOURCES)
+    if cfg.dim == 2 and cfg.n_rec > 0:
+        # sources on the row two cells into the interior, distinct columns
+        xs = rng.choice(np.arange(w, w + n - 1), size=cfg.n_src, replace=False)
+        return np.stack([np.full(cfg.n_src, w + 2), np.sort(xs)], axis=1)
     if cfg.dim == 2:
         lo, hi = w + n // 4, w + (3 * n) // 4
         return rng.integers(lo, hi, size=(cfg.n_src, 2))
@@ -122,14 +126,19 @@ def sources(cfg: Workload) -> np.ndarray:
 
 
 def receivers(cfg: Workload) -> np.ndarray:
-    """Flat unknown indices of the receivers: a square lattice on the source plane."""
+    """Flat unknown indices of the receivers: a square lattice on the source
+    plane (3-D) or an evenly spaced line on the source row (2-D)."""
     if cfg.n_rec == 0:
         return np.zeros(0, dtype=np.int64)
+    N = cfg.N
+    if cfg.dim == 2:
+        # a line of receivers on the source row, evenly spaced across the interior
+        pos = cfg.w_out - 1 + np.round((np.arange(cfg.n_rec) + 0.5) * cfg.n / cfg.n_rec).astype(np.int64)
+        return (cfg.w_out + 2) * N + pos
     side = int(round(cfg.n_rec ** 0.5))
     assert side * side == cfg.n_rec
     zplane = cfg.w_out + 2
     pos = cfg.w_out - 1 + np.round((np.arange(side) + 0.5) * cfg.n / side).astype(np.int64)
-    N = cfg.N
     return (zplane * N * N + pos[:, None] * N + pos[None, :]).reshape(-1)
 
 
