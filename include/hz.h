@@ -70,6 +70,8 @@ typedef struct {
   double tol;           /* stop at ||b - A u||_2 / ||b||_2 <= tol (per right-hand side) */
   int    max_rhs;       /* right-hand sides per hz_solve call (buffer capacity) */
   int    segments;      /* block-row segments per slab solve (0: automatic) */
+  double c_pml;         /* PML "typical velocity" (Section 2.1); 0: mean of c over the
+                         * unknowns, recomputed by hz_setup / hz_set_medium */
 } hz_params;
 
 typedef struct {
@@ -87,7 +89,8 @@ typedef struct hz_handle hz_handle;
 
 /* Create a solver for the grid and parameters in *p.  m_dev: squared slowness
  * 1/c^2 at the N^d unknowns, FP64, device, copied into the handle.  c_pml
- * (the "typical velocity" of Section 2.1) is the mean of c over the unknowns.
+ * (the "typical velocity" of Section 2.1) is p->c_pml, or the mean of c over
+ * the unknowns when p->c_pml is 0.
  * Builds the PML tables (Eq. 5, alpha below Eq. 40), the slab partition
  * (Eq. 17) and the slab meshes (Eqs. 9-10).  *out is NULL on failure. */
 hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out);
@@ -122,6 +125,26 @@ hz_status hz_apply(hz_handle* h, const hz_c128* u_dev, hz_c128* y_dev, int n_rhs
  * SweepingPrecUD of Table 3, or the TGSP of Section 4), complex128 in and out
  * (computed in the preconditioner precision). */
 hz_status hz_precond(hz_handle* h, const hz_c128* r_dev, hz_c128* z_dev, int n_rhs, void* stream);
+
+/* Receiver misfit and its gradient with respect to the squared slowness m
+ * (the adjoint-state method; the paper supplies the solver, Eq. 40 the
+ * derivative of A):
+ *   Phi = 1/2 sum_s sum_q |u_s[rec_q] - d[s][q]|^2,  A u_s = e_{src_s} (b = 1),
+ *   grad[i] = dPhi/dm_i = omega^2 Re( h^2 / (alpha_x alpha_y)_i sum_s mu_{s,i} u_{s,i} ),
+ * with A mu_s = conj(sum_q (u_s[rec_q] - d[s][q]) e_{rec_q}) (A is complex
+ * symmetric, so the adjoint solve reuses the preconditioner) and the PML held
+ * fixed (set p->c_pml to keep it fixed across hz_set_medium calls).
+ * src_dev: n_src flat unknown indices (int32, device); rec_dev: n_rec flat
+ * indices (int32, device; repeats add up); d_dev: observed data [n_src][n_rec]
+ * complex128 (device); grad_dev: N^d doubles (device, overwritten); *phi
+ * (host) receives Phi.  Sources are solved max_rhs at a time (one forward and
+ * one adjoint GMRES solve per batch).  Indices outside the grid give
+ * HZ_EINVAL before any work; HZ_ENOTCONV if a solve missed tol (results are
+ * still written).  Requires hz_factor.  The first call allocates
+ * 3 * max_rhs * N^d complex128 of work space owned by the handle. */
+hz_status hz_misfit_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_dev,
+                         int n_rec, const hz_c128* d_dev, double* grad_dev, double* phi,
+                         void* stream, hz_stats* stats);
 
 /* Geometry of slab j (1..J) on the sweep level: global core columns lo..hi,
  * added PML columns wl (left) / wr (right), width W = hi-lo+1+wl+wr. */

@@ -31,6 +31,7 @@ class hz_params(ctypes.Structure):
         ("two_grid", ctypes.c_int), ("nu", ctypes.c_int), ("omega_jac", ctypes.c_double),
         ("precision", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_iter", ctypes.c_int),
         ("tol", ctypes.c_double), ("max_rhs", ctypes.c_int), ("segments", ctypes.c_int),
+        ("c_pml", ctypes.c_double),
     ]
 
 
@@ -56,6 +57,8 @@ _SIGNATURES = {
     "hz_solve_host": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P, ctypes.POINTER(hz_stats)]),
     "hz_apply": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P]),
     "hz_precond": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P]),
+    "hz_misfit_grad": (ctypes.c_int, [_H, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P,
+                                      ctypes.POINTER(ctypes.c_double), _P, ctypes.POINTER(hz_stats)]),
     "hz_slab_info": (ctypes.c_int, [_H, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5),
     "hz_slab_solve": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hz_slab_solve_noalloc": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
@@ -121,7 +124,7 @@ class Solver:
 
     def __init__(self, m, *, n, w_out, omega, J, w_dd, s_dd, s_out=20.0, sweep="X",
                  precision="mixed", gmres_m=30, max_iter=500, tol=1e-6, max_rhs=1,
-                 two_grid=False, nu=3, omega_jac=0.8, segments=0):
+                 two_grid=False, nu=3, omega_jac=0.8, segments=0, c_pml=0.0):
         import torch
         self.N = n + 2 * w_out - 1
         self.shape = (self.N, self.N)
@@ -132,6 +135,7 @@ class Solver:
         p.two_grid, p.nu, p.omega_jac = int(two_grid), nu, omega_jac
         p.precision = HZ_MIXED if precision == "mixed" else HZ_PLAIN_FP64
         p.gmres_m, p.max_iter, p.tol, p.max_rhs, p.segments = gmres_m, max_iter, tol, max_rhs, segments
+        p.c_pml = c_pml
         self.params = p
         md = torch.as_tensor(m, dtype=torch.float64).to("cuda").contiguous()
         assert md.shape == self.shape
@@ -156,6 +160,14 @@ class Solver:
     def _check(self, st):
         if st != HZ_OK:
             raise HzError(st, lib().hz_last_error(self.h).decode())
+
+    def set_medium(self, m):
+        """New squared slowness on the same grid (factors must be rebuilt)."""
+        import torch
+        md = torch.as_tensor(m, dtype=torch.float64).to("cuda").contiguous()
+        assert md.shape == self.shape
+        self._check(lib().hz_set_medium(self.h, _ptr(md)))
+        self.factored = False
 
     def factor(self, stream=None):
         self._check(lib().hz_factor(self.h, _stream(stream)))
@@ -197,6 +209,24 @@ class Solver:
         z = torch.empty_like(rb)
         self._check(lib().hz_precond(self.h, _ptr(rb), _ptr(z), rb.shape[0], _stream(stream)))
         return z[0] if r.dim() == 2 else z
+
+    def misfit_grad(self, src, rec, d, stream=None, check=True):
+        """(Phi, dPhi/dm, stats) for point sources at flat indices ``src``,
+        receivers at flat indices ``rec`` and observed data ``d``
+        ([n_src, n_rec] complex128); see hz_misfit_grad."""
+        import torch
+        src = torch.as_tensor(src).to(device="cuda", dtype=torch.int32).contiguous()
+        rec = torch.as_tensor(rec).to(device="cuda", dtype=torch.int32).contiguous()
+        d = torch.as_tensor(d).to(device="cuda", dtype=torch.complex128).contiguous()
+        assert d.shape == (src.numel(), rec.numel())
+        grad = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        phi = ctypes.c_double()
+        st = hz_stats()
+        code = lib().hz_misfit_grad(self.h, _ptr(src), src.numel(), _ptr(rec), rec.numel(), _ptr(d),
+                                    _ptr(grad), ctypes.byref(phi), _stream(stream), ctypes.byref(st))
+        if check:
+            self._check(code)
+        return phi.value, grad, st.as_dict()
 
     def slab_info(self, j):
         vals = [ctypes.c_int() for _ in range(5)]

@@ -86,6 +86,7 @@ void validate(const hz_params* p) {
   if (p->gmres_m < 1 || p->gmres_m > 200) bad("gmres_m must be in 1..200");
   if (p->max_iter < 1) bad("max_iter must be >= 1");
   if (!(p->tol > 0)) bad("tol must be > 0");
+  if (!(p->c_pml >= 0)) bad("c_pml must be >= 0 (0: mean wave speed)");
   if (p->max_rhs < 1 || p->max_rhs > 8) bad("max_rhs must be in 1..8");
   if (p->two_grid && (p->n % 2 != 0)) bad("two_grid needs an even number of interior cells");
   if (p->two_grid && (p->nu < 0 || !(p->omega_jac > 0))) bad("bad smoother parameters");
@@ -133,7 +134,7 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
     HZ_CU(cudaMemsetAsync(h->dev_flag, 0, sizeof(int), h->s2));
     const int N = p->n + 2 * p->w_out - 1;
     const double hh = 1.0 / p->n;
-    h->c_pml = mean_velocity(m_dev, (size_t)N * N, h->s2);
+    h->c_pml = p->c_pml > 0 ? p->c_pml : mean_velocity(m_dev, (size_t)N * N, h->s2);
     build_levels(h, m_dev);
     const size_t n = (size_t)N * N;
     const size_t ps = prec_size(*p);
@@ -180,7 +181,7 @@ hz_status hz_set_medium(hz_handle* h, const double* m_dev) {
     free_level(h->fine);
     free_level(h->coarse);
     const int N = p.n + 2 * p.w_out - 1;
-    h->c_pml = mean_velocity(m_dev, (size_t)N * N, h->s2);
+    h->c_pml = p.c_pml > 0 ? p.c_pml : mean_velocity(m_dev, (size_t)N * N, h->s2);
     build_levels(h, m_dev);
     h->factored = false;
     h->stats.t_setup_s = now_s() - t0;
@@ -278,6 +279,32 @@ hz_status hz_precond(hz_handle* h, const hz_c128* r_dev, hz_c128* z_dev, int n_r
     HZ_CU(cudaStreamSynchronize(s));
     check_dev_flag(h, s);
   });
+}
+
+hz_status hz_misfit_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_dev,
+                         int n_rec, const hz_c128* d_dev, double* grad_dev, double* phi,
+                         void* stream, hz_stats* stats) {
+  if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  hz_status st = guarded(h, [&] {
+    if (!h->factored) throw Failure(HZ_ENOTFACTORED, "hz_misfit_grad before hz_factor");
+    if (n_src < 1 || n_rec < 0) throw Failure(HZ_EINVAL, "need n_src >= 1 and n_rec >= 0");
+    if (!src_dev || !grad_dev || !phi || (n_rec > 0 && (!rec_dev || !d_dev)))
+      throw Failure(HZ_EINVAL, "NULL argument");
+    double t0 = now_s();
+    try {
+      misfit_grad(h, src_dev, n_src, rec_dev, n_rec, (const c128*)d_dev, grad_dev, phi, s);
+    } catch (const Failure& f) {
+      cudaStreamSynchronize(s);
+      h->stats.t_solve_s = now_s() - t0;
+      h->stats.kernel_launches = h->launches;
+      throw;
+    }
+    h->stats.t_solve_s = now_s() - t0;
+    h->stats.kernel_launches = h->launches;
+  });
+  if (stats) *stats = h->stats;
+  return st;
 }
 
 hz_status hz_slab_info(const hz_handle* h, int j, int* lo, int* hi, int* wl, int* wr, int* W) {
@@ -388,6 +415,10 @@ void hz_destroy(hz_handle* h) {
     }
   dfree(h->stage_f);
   dfree(h->stage_u);
+  dfree(h->gr_b);
+  dfree(h->gr_u);
+  dfree(h->gr_mu);
+  dfree(h->gr_phi);
   cudaGetLastError();
   delete h;
 }

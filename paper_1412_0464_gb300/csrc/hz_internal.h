@@ -181,6 +181,10 @@ struct hz_handle {
   long long launches = 0;
   hz::c128* stage_f = nullptr;  // host-call staging buffers [max_rhs][n]
   hz::c128* stage_u = nullptr;
+  hz::c128* gr_b = nullptr;     // gradient work [max_rhs][n]: right-hand sides,
+  hz::c128* gr_u = nullptr;     //   forward fields,
+  hz::c128* gr_mu = nullptr;    //   adjoint fields
+  double* gr_phi = nullptr;     //   per right-hand-side misfit [max_rhs]
 };
 
 namespace hz {
@@ -262,6 +266,8 @@ void precond_apply(hz_handle* h, const c128* r, c128* z, int n_rhs, cudaStream_t
 
 // gmres.cu
 void gmres_solve(hz_handle* h, const c128* f, c128* u, int n_rhs, cudaStream_t s);
+void misfit_grad(hz_handle* h, const int* src, int n_src, const int* rec, int n_rec,
+                 const c128* d, double* grad, double* phi_out, cudaStream_t s);
 void apply_fine64(hz_handle* h, const c128* u, c128* y, int n_rhs, cudaStream_t s);
 
 // util
