@@ -276,8 +276,8 @@ def main():
     barrier()
     clk = clocks.stop()
     gpu_launches = solver.stats()["kernel_launches"] - launches0
-    tags = ["slab_fwd_pass1", "slab_fwd_bwd1", "slab_bwd", "slab_carry", "slab_fwd", "slab_solve",
-            "slab_factor", "segment_product"]
+    tags = ["slab_gather", "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", "slab_solve",
+            "slab_factor", "slab_middle", "segment_product"]
     kt = {t: solver.kernel_timing(t) for t in tags}
     solver.enable_timing(False)
     ms_step = total_ms / args.steps
@@ -303,8 +303,8 @@ def main():
     # dominant slab kernel: the largest summed time among the per-kernel tags
     peak, peak_kind = _peaks()
     per_kernel = {t: {"ms": v[0], "launches": v[1], "bytes": v[2]} for t, v in kt.items() if v[1] > 0}
-    kernels = {t: v for t, v in per_kernel.items() if t not in ("slab_solve", "slab_factor",
-                                                                 "segment_product")}
+    kernels = {t: v for t, v in per_kernel.items()
+               if t not in ("slab_solve", "slab_factor", "slab_middle", "segment_product")}
     dom = max(kernels, key=lambda t: kernels[t]["ms"])
     d = kernels[dom]
     achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9

@@ -69,7 +69,8 @@ typedef struct {
   int    max_iter;      /* cap on preconditioned GMRES iterations */
   double tol;           /* stop at ||b - A u||_2 / ||b||_2 <= tol (per right-hand side) */
   int    max_rhs;       /* right-hand sides per hz_solve call (buffer capacity) */
-  int    segments;      /* block-row segments per slab solve (0: automatic) */
+  int    segments;      /* block-row segments per slab solve, over both elimination
+                         * chains (0: automatic, about 2 sqrt(N_y); at least 2) */
   double c_pml;         /* PML "typical velocity" (Section 2.1); 0: mean of c over the
                          * unknowns, recomputed by hz_setup / hz_set_medium */
 } hz_params;
@@ -98,9 +99,10 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out);
 /* Replace the medium (same grid); invalidates the factors. */
 hz_status hz_set_medium(hz_handle* h, const double* m_dev);
 
-/* Factor every slab operator A^(j) (block-tridiagonal LU along y, Section 2.2
- * / Section 5: the paper uses a sparse direct solver here) and the segment
- * products of the parallel-in-y slab solve. */
+/* Factor every slab operator A^(j) (Section 2.2; Section 5: the paper uses a
+ * sparse direct solver here): a twisted block LU along y whose two
+ * elimination chains start at the outer PML rows and meet in the middle row,
+ * plus the segment transfer products of the parallel-in-y slab solve. */
 hz_status hz_factor(hz_handle* h, void* stream);
 
 /* Solve A u_r = f_r for r < n_rhs by GMRES(m) with the configured
@@ -182,8 +184,10 @@ hz_status hz_get_stats(const hz_handle* h, hz_stats* out);
  * returns, for one tag, the summed event time (ms), the number of launches
  * and the algorithmic bytes those launches move (method minimum: each
  * factor block read once per pass, vectors once).  Tags: "slab_solve" (one
- * whole subdomain solve, Table 2 line 6), "slab_fwd", "slab_fwd_pass1",
- * "slab_fwd_bwd1", "slab_carry", "slab_bwd".  Unknown tags return zeros. */
+ * whole subdomain solve of SubdomSolve, Table 2), its kernels "slab_gather",
+ * "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", and the
+ * factorisation kernels "slab_factor", "slab_middle", "segment_product"
+ * (bytes 0).  Unknown tags return zeros. */
 hz_status hz_enable_timing(hz_handle* h, int on);
 hz_status hz_kernel_timing(hz_handle* h, const char* tag, double* ms, long long* launches,
                            double* bytes);

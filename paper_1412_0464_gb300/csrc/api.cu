@@ -127,6 +127,7 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
     h->p = *p;
     double t0 = now_s();
     HZ_CU(cudaGetDevice(&h->dev));
+    HZ_CU(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev));
     HZ_CU(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
     HZ_CU(cudaEventCreateWithFlags(&h->evA, cudaEventDisableTiming));
     HZ_CU(cudaEventCreateWithFlags(&h->evB, cudaEventDisableTiming));

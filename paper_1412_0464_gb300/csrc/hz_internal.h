@@ -96,12 +96,12 @@ struct Slab {
   void* st = nullptr;        // slab stencil [ny][9][wp] in the preconditioner precision
   void* G = nullptr;         // inverse Schur complements [ny][gstride]
   size_t gstride = 0;        // elements per block (W*W rounded up to 16 bytes)
-  void* Phi = nullptr;       // forward segment products [P][gstride]
-  void* Psi = nullptr;       // backward segment products [P][gstride]
+  void* Phi = nullptr;       // forward segment transfer products [P][gstride]
+  void* Psi = nullptr;       // backward segment transfer products [P][gstride]
   void* inj = nullptr;       // injection coefficients [4][ny][3] (T row0, T row1, T~ row0, T~ row1)
   void* Y = nullptr;         // right-hand side, then forward solution rows [ny][n_rhs][wp]
-  void* carry_f = nullptr;   // [P][n_rhs][wp]
-  void* carry_b = nullptr;   // [P][n_rhs][wp]
+  void* carry_f = nullptr;   // forward segment end values [P][n_rhs][wp]
+  void* carry_b = nullptr;   // backward segment start values [P+1][n_rhs][wp] ([P]: meeting row)
 };
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.
@@ -122,9 +122,10 @@ struct Level {
   int J = 0, w = 0;
   std::vector<int> beta, beta_t;  // Eq. 17, size J+1
   std::vector<Slab> slabs;        // index 1..J (0 unused)
-  int P = 1;                       // segments per slab solve
-  std::vector<int> seg;            // P+1 segment bounds over block rows
-  int* seg_dev = nullptr;
+  int mid = 0;                     // meeting row of the two elimination chains
+  int P = 2, S0 = 1;               // segments per slab solve; the first S0 on the top chain
+  std::vector<int4> seg;           // per segment: first row, rows, direction (+1 / -1)
+  int4* seg_dev = nullptr;
 };
 
 // Per-kernel event timing (enabled for roofline reporting): every launch of a
@@ -151,6 +152,7 @@ struct hz_handle {
   hz_params p{};
   hz::Err err;
   int dev = 0;
+  int sms = 1;               // multiprocessors of the device
   double c_pml = 0;
   hz::Level fine;            // the PDE grid (GMRES level)
   hz::Level coarse;          // two-grid coarse level (sweeps), if p.two_grid

@@ -70,9 +70,10 @@ extern "C" hz_status hz_slab_solve_noalloc(hz_handle* h, int j, const hz_c128* f
     const size_t W = L.slabs[j].W, wp = L.slabs[j].wp;
     const size_t field = (size_t)n_rhs * L.ny * W;           // one slab-sized field
     const size_t rows = (size_t)n_rhs * L.ny * wp;           // forward rows (padded)
-    const size_t carry = (size_t)L.P * n_rhs * wp;           // one set of segment carries
+    const size_t carry_f = (size_t)L.P * n_rhs * wp;         // forward segment carries
+    const size_t carry_b = (size_t)(L.P + 1) * n_rhs * wp;   // backward ones and the meeting row
     const size_t need = (mixed ? 2 * align256(field * el) : 0) + align256(rows * el) +
-                        2 * align256(carry * el);
+                        align256(carry_f * el) + align256(carry_b * el);
     if (need > kScratchBytes)
       throw Failure(HZ_EINVAL, "slab solve needs " + std::to_string(need) +
                                    " bytes of work space; the no-allocation entry point holds " +
@@ -87,15 +88,15 @@ extern "C" hz_status hz_slab_solve_noalloc(hz_handle* h, int j, const hz_c128* f
       c64* fd = (c64*)take(field * el);
       c64* ud = (c64*)take(field * el);
       c64* Y = (c64*)take(rows * el);
-      c64* cf = (c64*)take(carry * el);
-      c64* cb = (c64*)take(carry * el);
+      c64* cf = (c64*)take(carry_f * el);
+      c64* cb = (c64*)take(carry_b * el);
       cast_copy<float, double>((const c128*)f_dev, fd, field, s);
       slab_solve_raw_scratch<float>(h, L, j, fd, ud, n_rhs, s, Y, cf, cb);
       cast_copy<double, float>(ud, (c128*)u_dev, field, s);
     } else {
       c128* Y = (c128*)take(rows * el);
-      c128* cf = (c128*)take(carry * el);
-      c128* cb = (c128*)take(carry * el);
+      c128* cf = (c128*)take(carry_f * el);
+      c128* cb = (c128*)take(carry_b * el);
       slab_solve_raw_scratch<double>(h, L, j, (const c128*)f_dev, (c128*)u_dev, n_rhs, s, Y, cf,
                                      cb);
     }

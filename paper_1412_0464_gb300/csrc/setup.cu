@@ -308,23 +308,39 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
     S.G = dmalloc(sizeof(cplx<R>) * S.gstride * L.ny);
     S.Y = dmalloc(sizeof(cplx<R>) * (size_t)h->p.max_rhs * L.ny * S.wp);
   }
-  // segments over block rows for the parallel-in-y slab solve
+  // Twisted elimination: chains from rows 0 and ny-1 meet at row mid.  Each
+  // chain is cut into segments for the parallel substitution; automatic
+  // count P ~ 2 sqrt(ny) (balances the segment runs, ~4 ny / P steps, against
+  // the two carry chains, ~P / 2 steps each and run side by side).
+  if (L.ny < 3) throw Failure(HZ_EINVAL, "a slab needs at least 3 rows");
+  L.mid = (L.ny - 1) / 2;
+  const int ntop = L.mid, nbot = L.ny - 1 - L.mid;
   int P = h->p.segments;
-  if (P <= 0) P = std::max(1, (int)std::lround(std::sqrt(L.ny / 2.0)));
-  P = std::min(P, L.ny);
+  if (P <= 0) P = (int)std::lround(2.0 * std::sqrt((double)L.ny));
+  P = std::max(2, std::min(P, L.ny - 1));
+  int S0 = (P * ntop + L.ny / 2) / (L.ny - 1);      // segments in proportion to the chain lengths
+  S0 = std::max(1, std::min(S0, std::min(P - 1, ntop)));
+  int S1 = std::min(P - S0, nbot);
+  P = S0 + S1;
   L.P = P;
-  L.seg.assign(P + 1, 0);
-  for (int q = 0; q <= P; ++q) L.seg[q] = (int)((long long)L.ny * q / P);
-  L.seg_dev = (int*)dmalloc(sizeof(int) * (P + 1));
-  HZ_CU(cudaMemcpyAsync(L.seg_dev, L.seg.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, s));
+  L.S0 = S0;
+  L.seg.assign(P, int4{0, 0, 0, 0});
+  for (int q = 0; q < S0; ++q) {
+    const int a0 = (int)((long long)ntop * q / S0), a1 = (int)((long long)ntop * (q + 1) / S0);
+    L.seg[q] = int4{a0, a1 - a0, +1, 0};
+  }
+  for (int q = 0; q < S1; ++q) {
+    const int a0 = (int)((long long)nbot * q / S1), a1 = (int)((long long)nbot * (q + 1) / S1);
+    L.seg[S0 + q] = int4{L.ny - 1 - a0, a1 - a0, -1, 0};
+  }
+  L.seg_dev = (int4*)dmalloc(sizeof(int4) * P);
+  HZ_CU(cudaMemcpyAsync(L.seg_dev, L.seg.data(), sizeof(int4) * P, cudaMemcpyHostToDevice, s));
   for (int j = 1; j <= L.J; ++j) {
     Slab& S = L.slabs[j];
-    if (P > 1) {
-      S.Phi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
-      S.Psi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
-    }
+    S.Phi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
+    S.Psi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
     S.carry_f = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.wp);
-    S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.wp);
+    S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)(P + 1) * h->p.max_rhs * S.wp);
   }
   HZ_CU(cudaStreamSynchronize(s));
 }

@@ -4,24 +4,33 @@
 // A^(j) is block tridiagonal along y with W x W blocks (one block row per
 // grid row k): D_k couples row k to itself, C_k to row k-1, B_k to row k+1
 // (taken from the slab stencil st[k][9][wp], plane (dy+1)*3 + (dx+1)).
-// Block LU:
-//   S_0 = D_0,  S_k = D_k - C_k S_{k-1}^{-1} B_{k-1},  G_k = S_k^{-1} (stored).
-// Solve A^(j) x = f:
-//   forward   y_k = G_k (f_k - C_k y_{k-1})
-//   backward  x_k = y_k - G_k (B_k x_{k+1})
-// Parallel in y: the block rows are cut into P segments.  Both recurrences
-// are affine, y_k = G_k f_k + F_k y_{k-1} with F_k = -G_k C_k and
-// x_k = y_k + E_k x_{k+1} with E_k = -G_k B_k.  Per segment [a, b] the
-// products Phi = F_b ... F_a and Psi = E_a ... E_b are formed at factor time;
-// a solve runs each segment from a zero start (all segments in parallel),
-// carries the segment end values through Phi / Psi (P short steps), and
-// re-runs each segment from its true start value.
 //
-// Every block-row step reads its operands -- the factor block G_k, the
-// coupling row C_k or B_k and the right-hand-side / forward row -- through
-// one stage of a shared-memory pipeline filled by TMA bulk copies
-// (cp.async.bulk + mbarrier); the step itself touches only shared memory and
-// registers.
+// Twisted block LU.  Two elimination chains start at the two outer PML
+// boundaries of the slab (rows 0 and ny-1) and meet at the row m = mid:
+//   top     S_0 = D_0,         S_k = D_k - C_k G_{k-1} B_{k-1}   (k < m)
+//   bottom  S_{ny-1} = D_{ny-1}, S_k = D_k - B_k G_{k+1} C_{k+1}   (k > m)
+//   meeting S_m = D_m - C_m G_{m-1} B_{m-1} - B_m G_{m+1} C_{m+1},
+// G_k = S_k^-1 (stored).  Every Schur complement of a chain belongs to a
+// part of the slab that contains an absorbing layer, so no block inverse is
+// that of a closed (possibly resonant) cavity, and the two chains run in
+// parallel.
+// Solve A^(j) x = f: along each chain (t = position, L_t / R_t the couplings
+// to the previous / next row of the chain)
+//   forward   y_t = G_t (f_t - L_t y_{t-1})
+//   meeting   x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1})
+//   backward  x_t = y_t - G_t R_t x_{t+1}   (x after the last row: x_m).
+// Parallel in y: each chain is cut into segments.  Both recurrences are
+// affine, y_t = G_t f_t + F_t y_{t-1} (F_t = -G_t L_t) and
+// x_t = y_t + E_t x_{t+1} (E_t = -G_t R_t).  Per segment the products
+// Phi = F_last ... F_first and Psi = E_first ... E_last are formed at factor
+// time; a solve runs each segment from a zero start (all segments of both
+// chains in parallel), carries the segment end values through Phi / Psi (the
+// two chains in parallel), and re-runs each segment from its true start.
+//
+// Every substitution step reads its operands -- the factor block G_k, the
+// coupling row and the right-hand-side row -- through one stage of a
+// shared-memory pipeline filled by TMA bulk copies (cp.async.bulk +
+// mbarrier); the step itself touches only shared memory and registers.
 #include "hz_internal.h"
 
 #include <algorithm>
@@ -94,25 +103,18 @@ constexpr int kGroups = kThreads / kTPR;
 constexpr int kNRMax = 8;               // right-hand sides per launch
 
 // --------------------------------------------------------------- factorisation
-struct FactorDesc {
-  int W, wp, ny;
-  const void* st;
-  void* G;
-  size_t gstride;
-};
-
-// One CTA per slab, sequential over block rows.  Each S_k is inverted by
-// Gauss-Jordan elimination with partial pivoting; pivot rows are marked, not
-// moved, and the permutations are applied when G_k is written:
-// G_k[p][piv[q]] = S[piv[p]][q].  With colmod = column p of S except
-// colmod[r] = S[r][p] - 1, and rowmod = row r of S scaled by inv = 1/S[r][p]
-// except rowmod[p] = inv + 1, one elimination step (pivot row included) is the
-// rank-1 update S -= colmod rowmod^T.  The steps are blocked by panels of BW
-// columns: one warp eliminates the panel's BW pivots on the panel columns only
-// (shuffles, no block barrier), the pivot rows' other columns follow from the
-// short recurrence rowmod_t = (S[r_t] - sum_{s<t} colmod_s[r_t] rowmod_s) inv_t,
-// and all threads apply the delayed rank-BW update S -= Cm^T R in 4 x TC
-// register tiles.  Three block barriers per panel.
+// Each S is inverted by Gauss-Jordan elimination with partial pivoting;
+// pivot rows are marked, not moved, and the permutations are applied when the
+// inverse is written: G[p][piv[q]] = S[piv[p]][q].  With colmod = column p of
+// S except colmod[r] = S[r][p] - 1, and rowmod = row r of S scaled by
+// inv = 1/S[r][p] except rowmod[p] = inv + 1, one elimination step (pivot row
+// included) is the rank-1 update S -= colmod rowmod^T.  The steps are blocked
+// by panels of BW columns: one warp eliminates the panel's BW pivots on the
+// panel columns only (shuffles, no block barrier), the pivot rows' other
+// columns follow from the short recurrence
+// rowmod_t = (S[r_t] - sum_{s<t} colmod_s[r_t] rowmod_s) inv_t, and all
+// threads apply the delayed rank-BW update S -= Cm^T R in 4 x TC register
+// tiles.  Three block barriers per panel.
 __device__ __forceinline__ cplx<float> crcp(cplx<float> a) {
   const float d = __frcp_rn(a.re * a.re + a.im * a.im);
   return mk(a.re * d, -a.im * d);
@@ -126,6 +128,54 @@ template <typename R>
 struct FactorPanel { static constexpr int BW = 8; };
 template <>
 struct FactorPanel<double> { static constexpr int BW = 4; };
+
+// Register tile of one thread in a W x W product or update: rows i0..i0+3,
+// columns j0..j0+TC-1.
+struct Tile {
+  bool own;
+  int i0, j0;
+};
+template <int TC>
+__device__ __forceinline__ Tile tile_of(int W, int tid) {
+  const int ntc = (W + TC - 1) / TC, ntr = (W + 3) / 4;
+  Tile t;
+  t.own = tid < ntr * ntc;
+  t.i0 = t.own ? (tid / ntc) * 4 : 0;
+  t.j0 = t.own ? (tid % ntc) * TC : 0;
+  return t;
+}
+
+// dst = base - A B for W x W row-major operands in shared or global memory;
+// base may be null (zero) or alias dst.  The caller synchronises.
+template <typename R, int TC>
+__device__ __forceinline__ void gemm_sub(const cplx<R>* A, const cplx<R>* B, const cplx<R>* base,
+                                         cplx<R>* dst, int W, const Tile& t) {
+  if (!t.own) return;
+  const cplx<R> zero = mk<R>(0, 0);
+  cplx<R> acc[4][TC];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < TC; ++b) acc[a][b] = zero;
+  for (int l = 0; l < W; ++l) {
+    cplx<R> av[4], bv[TC];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = (t.i0 + a < W) ? A[(t.i0 + a) * W + l] : zero;
+#pragma unroll
+    for (int b = 0; b < TC; ++b) bv[b] = (t.j0 + b < W) ? B[l * W + t.j0 + b] : zero;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < TC; ++b) cfma(acc[a][b], av[a], bv[b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < TC; ++b) {
+      const int i = t.i0 + a, j = t.j0 + b;
+      if (i < W && j < W) dst[i * W + j] = base ? base[i * W + j] - acc[a][b] : -acc[a][b];
+    }
+}
 
 // One warp eliminates pivots p0 .. p0+bw-1 on the panel columns p0 .. p0+bw-1
 // (rows lane + 32 m, m < MR, in registers) and records colmod (Cm), the pivot
@@ -204,66 +254,200 @@ __device__ __forceinline__ void panel_elim(cplx<R>* S, cplx<R>* Cm, cplx<R>* pin
   }
 }
 
+// Shared-memory work areas of the Gauss-Jordan inverse.
+template <typename R>
+struct GJWork {
+  cplx<R>* Cm;     // BW x W
+  cplx<R>* Rm;     // BW x W
+  cplx<R>* pinv;   // BW
+  int* prow;       // BW
+  int* piv;        // W
+  int* ipiv;       // W
+  int* used;       // W
+};
+
+// S^-1 (S: W x W in shared memory, overwritten) into `out` (global) and Gl
+// (shared), both in natural order.  Called by every thread of a kThreads
+// block after a barrier that completes S; ends with a barrier.
+template <typename R, int TC>
+__device__ void gj_inverse(cplx<R>* S, cplx<R>* Gl, const GJWork<R>& w, int W, const Tile& tl,
+                           cplx<R>* out) {
+  constexpr int BW = FactorPanel<R>::BW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int WW = W * W;
+  const cplx<R> zero = mk<R>(0, 0);
+  for (int t = tid; t < W; t += kThreads) w.used[t] = 0;
+  __syncthreads();
+  for (int p0 = 0; p0 < W; p0 += BW) {
+    const int bw = min(BW, W - p0);
+    // (1) one warp eliminates the panel's pivots on the panel columns
+    if (warp == 0) {
+      const int MR = (W + 31) >> 5;
+      if (bw == BW) {
+        if (MR == 1) panel_elim<R, BW, 1>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
+        else if (MR == 2) panel_elim<R, BW, 2>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
+        else if (MR == 3) panel_elim<R, BW, 3>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
+        else panel_elim<R, BW, 4>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
+      } else {
+        panel_elim<R, BW, 4>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
+      }
+    }
+    __syncthreads();
+    // (2) rowmod of the panel's pivots on the other columns
+    for (int j = tid; j < W; j += kThreads) {
+      if (j >= p0 && j < p0 + bw) continue;
+      cplx<R> rw[BW];
+#pragma unroll
+      for (int t = 0; t < BW; ++t) {
+        if (t >= bw) break;
+        const int r = w.prow[t];
+        cplx<R> acc = S[r * W + j];
+#pragma unroll
+        for (int q = 0; q < t; ++q) {
+          const cplx<R> c = w.Cm[q * W + r];
+          acc.re -= c.re * rw[q].re - c.im * rw[q].im;
+          acc.im -= c.re * rw[q].im + c.im * rw[q].re;
+        }
+        rw[t] = acc * w.pinv[t];
+        w.Rm[t * W + j] = rw[t];
+      }
+    }
+    __syncthreads();
+    // (3) delayed rank-bw update of the other columns, 4 x TC tiles
+    if (tl.own) {
+      cplx<R> acc[4][TC];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) {
+          const int i = tl.i0 + a, j = tl.j0 + b;
+          acc[a][b] = (i < W && j < W) ? S[i * W + j] : zero;
+        }
+#pragma unroll
+      for (int t = 0; t < BW; ++t) {
+        if (t >= bw) break;
+        cplx<R> cv[4], rv[TC];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) cv[a] = (tl.i0 + a < W) ? w.Cm[t * W + tl.i0 + a] : zero;
+#pragma unroll
+        for (int b = 0; b < TC; ++b) {
+          const int j = tl.j0 + b;
+          rv[b] = (j < W && (j < p0 || j >= p0 + bw)) ? w.Rm[t * W + j] : zero;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < TC; ++b) {
+            acc[a][b].re -= cv[a].re * rv[b].re - cv[a].im * rv[b].im;
+            acc[a][b].im -= cv[a].re * rv[b].im + cv[a].im * rv[b].re;
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) {
+          const int i = tl.i0 + a, j = tl.j0 + b;
+          if (i < W && j < W && (j < p0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
+        }
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < W; q += kThreads) w.ipiv[w.piv[q]] = q;
+  __syncthreads();
+  for (int e = tid; e < WW; e += kThreads) {
+    const int i = e / W, j = e - i * W;
+    const cplx<R> v = S[w.piv[i] * W + w.ipiv[j]];
+    out[e] = v;
+    Gl[e] = v;
+  }
+  __syncthreads();
+}
+
+// Shared-memory layout of the factor kernels: S, Gl (W x W each), the
+// Gauss-Jordan work, then `ncpl` coupling rows of W.
+template <typename R>
+__device__ __forceinline__ void factor_smem(unsigned char* raw, int W, int ncpl, cplx<R>** S,
+                                            cplx<R>** Gl, GJWork<R>* w, cplx<R>** cpl) {
+  constexpr int BW = FactorPanel<R>::BW;
+  cplx<R>* p = (cplx<R>*)raw;
+  *S = p;
+  *Gl = p + W * W;
+  w->Cm = *Gl + W * W;
+  w->Rm = w->Cm + BW * W;
+  *cpl = w->Rm + BW * W;
+  w->pinv = *cpl + ncpl * W;
+  w->prow = (int*)(w->pinv + BW);
+  w->piv = w->prow + BW;
+  w->ipiv = w->piv + W;
+  w->used = w->ipiv + W;
+}
+static size_t factor_smem_bytes(int W, int ncpl, size_t el, int BW) {
+  return (2 * (size_t)W * W + (2 * (size_t)BW + ncpl) * W + BW) * el + (BW + 3 * (size_t)W) * 4 + 64;
+}
+
+// Interior chains of the twisted factorisation (one CTA per slab and half).
+// The chain visits rows k_t = k0 + dir t, t = 0..n-1, starting at the outer
+// PML row (top half: k0 = 0, dir = +1; bottom half: k0 = ny-1, dir = -1):
+//   S_0 = D_{k_0},  S_t = D_{k_t} - L_t G_{t-1} R_{t-1},  G_t = S_t^-1,
+// with L_t the coupling of row k_t to the previous row of the chain (C_k for
+// dir = +1, B_k for dir = -1) and R_{t-1} that of row k_{t-1} to k_t.
+struct FactorDesc {
+  int W, wp, k0, n, dir;
+  const void* st;
+  void* G;
+  size_t gstride;
+};
+
+__host__ __device__ __forceinline__ int lplane(int dir) { return dir > 0 ? 0 : 6; }
+__host__ __device__ __forceinline__ int rplane(int dir) { return dir > 0 ? 6 : 0; }
+
 template <typename R, int TC>
 __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc* descs) {
-  constexpr int BW = FactorPanel<R>::BW;
-  constexpr int TR = 4;
   const FactorDesc d = descs[blockIdx.x];
-  const int W = d.W, wp = d.wp, ny = d.ny, tid = threadIdx.x;
+  const int W = d.W, wp = d.wp, tid = threadIdx.x, dir = d.dir;
   const int WW = W * W;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int ntc = (W + TC - 1) / TC;             // tiles per row of S
-  const int ntr = (W + TR - 1) / TR;
-  const bool tile_owner = tid < ntr * ntc;
-  const int ti0 = tile_owner ? (tid / ntc) * TR : 0;
-  const int tj0 = tile_owner ? (tid % ntc) * TC : 0;
+  const Tile tl = tile_of<TC>(W, tid);
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* S = (cplx<R>*)smem_raw;               // W*W
-  cplx<R>* Gl = S + WW;                          // W*W: G_{k-1}, natural order
-  cplx<R>* Cm = Gl + WW;                         // BW x W  (colmod of the panel's pivots)
-  cplx<R>* Rm = Cm + BW * W;                     // BW x W  (rowmod on the other columns)
-  cplx<R>* cC = Rm + BW * W;                     // C_k (3 x W)
-  cplx<R>* cD = cC + 3 * W;                      // D_k (3 x W)
-  cplx<R>* cB = cD + 3 * W;                      // B_{k-1} (3 x W)
-  cplx<R>* pinv = cB + 3 * W;                    // BW
-  int* prow = (int*)(pinv + BW);                 // BW
-  int* piv = prow + BW;                          // W
-  int* ipiv = piv + W;                           // W
-  int* used = ipiv + W;                          // W
+  cplx<R>*S, *Gl, *cpl;
+  GJWork<R> w;
+  factor_smem<R>(smem_raw, W, 9, &S, &Gl, &w, &cpl);
+  cplx<R>* cL = cpl;                             // L_t (3 x W)
+  cplx<R>* cD = cL + 3 * W;                      // D (3 x W)
+  cplx<R>* cR = cD + 3 * W;                      // R_{t-1} (3 x W)
   const cplx<R> zero = mk<R>(0, 0);
+  const int pl = lplane(dir), pr = rplane(dir);
 
-  for (int k = 0; k < ny; ++k) {
+  for (int t = 0; t < d.n; ++t) {
+    const int k = d.k0 + dir * t;
     const cplx<R>* stk = st + (size_t)k * 9 * wp;
-    for (int t = tid; t < 3 * W; t += kThreads) {     // stage the couplings
-      const int q = t / W, e = t - q * W;
-      cC[t] = stk[q * wp + e];
-      cD[t] = stk[(3 + q) * wp + e];
-      cB[t] = (k > 0) ? st[(size_t)(k - 1) * 9 * wp + (6 + q) * wp + e] : zero;
+    for (int i = tid; i < 3 * W; i += kThreads) {     // stage the couplings
+      const int q = i / W, e = i - q * W;
+      cL[i] = stk[(pl + q) * wp + e];
+      cD[i] = stk[(3 + q) * wp + e];
+      cR[i] = (t > 0) ? st[(size_t)(k - dir) * 9 * wp + (pr + q) * wp + e] : zero;
     }
-    for (int t = tid; t < W; t += kThreads) used[t] = 0;
     __syncthreads();
-    // S_k = D_k - C_k G_{k-1} B_{k-1} (natural order, shared memory)
-    if (k > 0) {
-      for (int e = tid; e < WW; e += kThreads) {      // Cm-area is free: X = G B into S
+    if (t > 0) {
+      for (int e = tid; e < WW; e += kThreads) {      // X = G_{t-1} R_{t-1} into S
         const int i = e / W, j = e - i * W;
         cplx<R> acc = zero;
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const int c = j - dx;
-          if (c >= 0 && c < W) cfma(acc, Gl[i * W + c], cB[(dx + 1) * W + c]);
+          if (c >= 0 && c < W) cfma(acc, Gl[i * W + c], cR[(dx + 1) * W + c]);
         }
         S[e] = acc;
       }
       __syncthreads();
-      for (int e = tid; e < WW; e += kThreads) {      // Gl = D - C X
+      for (int e = tid; e < WW; e += kThreads) {      // Gl = D - L X
         const int i = e / W, j = e - i * W;
         cplx<R> acc = zero;
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const int rr = i + dx;
-          if (rr >= 0 && rr < W) cfma(acc, cC[(dx + 1) * W + i], S[rr * W + j]);
+          if (rr >= 0 && rr < W) cfma(acc, cL[(dx + 1) * W + i], S[rr * W + j]);
         }
         cplx<R> v = -acc;
         const int dd = j - i;
@@ -280,153 +464,134 @@ __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc*
       }
     }
     __syncthreads();
-
-    for (int p0 = 0; p0 < W; p0 += BW) {
-      const int bw = min(BW, W - p0);
-      // (1) one warp eliminates the panel's pivots on the panel columns
-      if (warp == 0) {
-        const int MR = (W + 31) >> 5;
-        if (bw == BW) {
-          if (MR == 1) panel_elim<R, BW, 1>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
-          else if (MR == 2) panel_elim<R, BW, 2>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
-          else if (MR == 3) panel_elim<R, BW, 3>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
-          else panel_elim<R, BW, 4>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
-        } else {
-          panel_elim<R, BW, 4>(S, Cm, pinv, prow, piv, used, W, p0, bw, lane);
-        }
-      }
-      __syncthreads();
-      // (2) rowmod of the panel's pivots on the other columns
-      for (int j = tid; j < W; j += kThreads) {
-        if (j >= p0 && j < p0 + bw) continue;
-        cplx<R> rw[BW];
-#pragma unroll
-        for (int t = 0; t < BW; ++t) {
-          if (t >= bw) break;
-          const int r = prow[t];
-          cplx<R> acc = S[r * W + j];
-#pragma unroll
-          for (int q = 0; q < t; ++q) {
-            const cplx<R> c = Cm[q * W + r];
-            acc.re -= c.re * rw[q].re - c.im * rw[q].im;
-            acc.im -= c.re * rw[q].im + c.im * rw[q].re;
-          }
-          rw[t] = acc * pinv[t];
-          Rm[t * W + j] = rw[t];
-        }
-      }
-      __syncthreads();
-      // (3) delayed rank-bw update of the other columns, 4 x TC tiles
-      if (tile_owner) {
-        cplx<R> acc[TR][TC];
-#pragma unroll
-        for (int a = 0; a < TR; ++a)
-#pragma unroll
-          for (int b = 0; b < TC; ++b) {
-            const int i = ti0 + a, j = tj0 + b;
-            acc[a][b] = (i < W && j < W) ? S[i * W + j] : zero;
-          }
-#pragma unroll
-        for (int t = 0; t < BW; ++t) {
-          if (t >= bw) break;
-          cplx<R> cv[TR], rv[TC];
-#pragma unroll
-          for (int a = 0; a < TR; ++a) cv[a] = (ti0 + a < W) ? Cm[t * W + ti0 + a] : zero;
-#pragma unroll
-          for (int b = 0; b < TC; ++b) {
-            const int j = tj0 + b;
-            rv[b] = (j < W && (j < p0 || j >= p0 + bw)) ? Rm[t * W + j] : zero;
-          }
-#pragma unroll
-          for (int a = 0; a < TR; ++a)
-#pragma unroll
-            for (int b = 0; b < TC; ++b) {
-              acc[a][b].re -= cv[a].re * rv[b].re - cv[a].im * rv[b].im;
-              acc[a][b].im -= cv[a].re * rv[b].im + cv[a].im * rv[b].re;
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < TR; ++a)
-#pragma unroll
-          for (int b = 0; b < TC; ++b) {
-            const int i = ti0 + a, j = tj0 + b;
-            if (i < W && j < W && (j < p0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
-          }
-      }
-      __syncthreads();
-    }
-    for (int q = tid; q < W; q += kThreads) ipiv[piv[q]] = q;
-    __syncthreads();
-    cplx<R>* Gk = G + (size_t)k * d.gstride;
-    for (int e = tid; e < WW; e += kThreads) {
-      const int i = e / W, j = e - i * W;
-      const cplx<R> v = S[piv[i] * W + ipiv[j]];
-      Gk[e] = v;
-      Gl[e] = v;
-    }
-    __syncthreads();
+    gj_inverse<R, TC>(S, Gl, w, W, tl, G + (size_t)k * d.gstride);
   }
 }
 
-// ------------------------------------------------------------ segment products
+// sum_{dx, dy} Lc[dx][i] X[i+dx][j-dy] Rc[dy][j-dy]: (L X R)[i][j] for
+// tridiagonal L (row i: Lc[(dx+1) W + i] at column i+dx) and R.
+template <typename R>
+__device__ __forceinline__ cplx<R> tri_x_tri(const cplx<R>* Lc, const cplx<R>* X, const cplx<R>* Rc,
+                                             int W, int i, int j) {
+  cplx<R> acc = mk<R>(0, 0);
+#pragma unroll
+  for (int dx = -1; dx <= 1; ++dx) {
+    const int r = i + dx;
+    if (r < 0 || r >= W) continue;
+    cplx<R> xr = mk<R>(0, 0);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int l = j - dy;
+      if (l >= 0 && l < W) cfma(xr, X[r * W + l], Rc[(dy + 1) * W + l]);
+    }
+    cfma(acc, Lc[(dx + 1) * W + i], xr);
+  }
+  return acc;
+}
+
+// The meeting row m of the two chains (one CTA per slab):
+//   S_m = D_m - C_m G_{m-1} B_{m-1} - B_m G_{m+1} C_{m+1},  G_m = S_m^-1.
+struct MidDesc {
+  int W, wp, m;
+  const void* st;
+  void* G;
+  size_t gstride;
+};
+
+template <typename R, int TC>
+__global__ void __launch_bounds__(kThreads) slab_middle_kernel(const MidDesc* descs) {
+  const MidDesc d = descs[blockIdx.x];
+  const int W = d.W, wp = d.wp, m = d.m, tid = threadIdx.x, WW = W * W;
+  const Tile tl = tile_of<TC>(W, tid);
+  const cplx<R>* st = (const cplx<R>*)d.st;
+  cplx<R>* G = (cplx<R>*)d.G;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>*S, *Gl, *cpl;
+  GJWork<R> w;
+  factor_smem<R>(smem_raw, W, 15, &S, &Gl, &w, &cpl);
+  cplx<R>* Cm = cpl;            // C_m, D_m, B_m, B_{m-1}, C_{m+1}: 3 x W each
+  cplx<R>* Dm = Cm + 3 * W;
+  cplx<R>* Bm = Dm + 3 * W;
+  cplx<R>* Bu = Bm + 3 * W;
+  cplx<R>* Cd = Bu + 3 * W;
+  for (int i = tid; i < 3 * W; i += kThreads) {
+    const int q = i / W, e = i - q * W;
+    const cplx<R>* sm = st + (size_t)m * 9 * wp;
+    Cm[i] = sm[q * wp + e];
+    Dm[i] = sm[(3 + q) * wp + e];
+    Bm[i] = sm[(6 + q) * wp + e];
+    Bu[i] = st[(size_t)(m - 1) * 9 * wp + (6 + q) * wp + e];
+    Cd[i] = st[(size_t)(m + 1) * 9 * wp + q * wp + e];
+  }
+  __syncthreads();
+  const cplx<R>* Gu = G + (size_t)(m - 1) * d.gstride;
+  const cplx<R>* Gd = G + (size_t)(m + 1) * d.gstride;
+  for (int e = tid; e < WW; e += kThreads) {
+    const int i = e / W, j = e - i * W;
+    const int dd = j - i;
+    cplx<R> v = (dd >= -1 && dd <= 1) ? Dm[(dd + 1) * W + i] : mk<R>(0, 0);
+    S[e] = v - tri_x_tri<R>(Cm, Gu, Bu, W, i, j) - tri_x_tri<R>(Bm, Gd, Cd, W, i, j);
+  }
+  __syncthreads();
+  gj_inverse<R, TC>(S, Gl, w, W, tl, G + (size_t)m * d.gstride);
+}
+
+// Segment transfer products for the parallel substitution (one CTA per slab,
+// segment and direction).  Along a segment's chain positions t = 0..n-1:
+//   forward  F_t = -G_t L_t,  Phi = F_{n-1} ... F_0
+//   backward E_t = -G_t R_t,  Psi = E_0 ... E_{n-1}
 struct ProdDesc {
-  int W, wp, k0, k1, backward;
+  int W, wp, k0, n, dir, backward;
   const void* st;
   const void* G;
   size_t gstride;
   void* out;
 };
 
-// forward:  M <- F_k M for k = k0..k1-1, F_k = -G_k C_k   (M = F_{k1-1} ... F_{k0})
-// backward: M <- E_k M for k = k1-1..k0, E_k = -G_k B_k   (M = E_{k0} ... E_{k1-1})
-template <typename R>
+template <typename R, int TC>
 __global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDesc* descs) {
   const ProdDesc d = descs[blockIdx.x];
-  const int W = d.W, wp = d.wp, tid = threadIdx.x;
-  const int ty = tid >> 2, tx = tid & 3;
+  const int W = d.W, wp = d.wp, tid = threadIdx.x, WW = W * W;
+  const Tile tl = tile_of<TC>(W, tid);
   const cplx<R>* st = (const cplx<R>*)d.st;
   const cplx<R>* G = (const cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* M = (cplx<R>*)smem_raw;
-  cplx<R>* T = M + W * W;
+  cplx<R>* T = M + WW;
+  cplx<R>* cp = T + WW;         // coupling (3 x W)
   const cplx<R> zero = mk<R>(0, 0);
-  for (int i = tid; i < W * W; i += kThreads) M[i] = zero;
-  __syncthreads();
-  for (int i = tid; i < W; i += kThreads) M[i * W + i] = mk<R>(1, 0);
-  __syncthreads();
-  const int n = d.k1 - d.k0;
-  const int plane = d.backward ? 6 : 0;   // B_k (dy=+1) or C_k (dy=-1)
-  for (int s = 0; s < n; ++s) {
-    const int k = d.backward ? d.k1 - 1 - s : d.k0 + s;
-    const cplx<R>* stk = st + (size_t)k * 9 * wp;
-    for (int i = ty; i < W; i += kGroups)          // T = coupling_k M
-      for (int c = tx; c < W; c += kTPR) {
-        cplx<R> acc = zero;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          int e = i + dx;
-          if (e >= 0 && e < W) cfma(acc, stk[(plane + dx + 1) * wp + i], M[e * W + c]);
-        }
-        T[i * W + c] = acc;
-      }
+  for (int e = tid; e < WW; e += kThreads) M[e] = (e / W == e % W) ? mk<R>(1, 0) : zero;
+  const int plane = d.backward ? rplane(d.dir) : lplane(d.dir);
+  for (int s = 0; s < d.n; ++s) {
+    const int t = d.backward ? d.n - 1 - s : s;
+    const int k = d.k0 + d.dir * t;
+    for (int i = tid; i < 3 * W; i += kThreads) {
+      const int q = i / W, e = i - q * W;
+      cp[i] = st[(size_t)k * 9 * wp + (plane + q) * wp + e];
+    }
     __syncthreads();
-    const cplx<R>* Gk = G + (size_t)k * d.gstride;
-    for (int i = ty; i < W; i += kGroups)          // M = -G_k T
-      for (int c = tx; c < W; c += kTPR) {
-        cplx<R> acc = zero;
-        for (int j = 0; j < W; ++j) cfma(acc, Gk[i * W + j], T[j * W + c]);
-        M[i * W + c] = -acc;
+    for (int e = tid; e < WW; e += kThreads) {        // T = coupling_t M
+      const int i = e / W, j = e - i * W;
+      cplx<R> acc = zero;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int rr = i + dx;
+        if (rr >= 0 && rr < W) cfma(acc, cp[(dx + 1) * W + i], M[rr * W + j]);
       }
+      T[e] = acc;
+    }
+    __syncthreads();
+    gemm_sub<R, TC>(G + (size_t)k * d.gstride, T, nullptr, M, W, tl);   // M = -G_t T
     __syncthreads();
   }
   cplx<R>* out = (cplx<R>*)d.out;
-  for (int i = tid; i < W * W; i += kThreads) out[i] = M[i];
+  for (int e = tid; e < WW; e += kThreads) out[e] = M[e];
 }
 
 // ------------------------------------------------------------------ solves
 // Right-hand side of a slab solve: either a raw slab field, or the gather of
-// global columns (ga, gb] plus the transmission injections of Table 2
-// (lines 2-5) at the local columns ef (tau1, from B1) and eb (tau3, from B3).
+// global columns (ga, gb] plus the transmission injections of SubdomSolve
+// (Table 2) at the local columns ef (tau1, from B1) and eb (tau3, from B3).
 template <typename R>
 struct Rhs {
   const cplx<R>* raw;         // [n_rhs][ny][W] or null
@@ -439,7 +604,8 @@ struct Rhs {
   const cplx<R>* inj;         // [4][ny][3]
 };
 
-// Epilogue of a slab solve (Table 2 lines 6-10).
+// Epilogue of a slab solve (Table 2): the slab solution's core columns into
+// the global field and the two layers passed on by the transmission.
 template <typename R>
 struct Out {
   cplx<R>* raw;               // [n_rhs][ny][W] or null
@@ -453,15 +619,16 @@ struct Out {
 
 template <typename R>
 struct SolveArgs {
-  int W, wp, ny, nr, P;
-  const int* seg;
+  int W, wp, ny, nr;
+  int P, S0, mid;             // segments (the first S0 on the top chain), meeting row
+  const int4* seg;            // per segment: first row, rows, direction (+1 top, -1 bottom)
   const cplx<R>* st;          // [ny][9][wp]
   const cplx<R>* G;           // [ny][gstride]
   size_t gstride;
   int stages;
   cplx<R>* Y;                 // [ny][nr][wp]: gathered right-hand side, then forward rows
-  cplx<R>* carry_f;           // [P][nr][wp]
-  cplx<R>* carry_b;
+  cplx<R>* carry_f;           // [P][nr][wp]: segment end values of the forward recurrence
+  cplx<R>* carry_b;           // [P+1][nr][wp]: segment start values of the backward one; [P]: x_m
   int* flag;
   Rhs<R> rhs;
   Out<R> out;
@@ -506,17 +673,18 @@ struct Pipe {
   int wp, nr;
   __device__ cplx<R>* slot(int i) const { return buf + (size_t)i * stage_elems; }
   // thread 0 only: fetch block row k (coupling plane 0 = C_k or 6 = B_k)
+  // (rows == nullptr: G_k and the coupling row only)
   __device__ void issue(int i, int k, const cplx<R>* G, const cplx<R>* st, int plane,
                         const cplx<R>* rows) const {
     const uint32_t gb = (uint32_t)(gstride * sizeof(cplx<R>));
     const uint32_t cb = (uint32_t)(3 * wp * sizeof(cplx<R>));
-    const uint32_t vb = (uint32_t)((size_t)nr * wp * sizeof(cplx<R>));
+    const uint32_t vb = rows ? (uint32_t)((size_t)nr * wp * sizeof(cplx<R>)) : 0u;
     cplx<R>* dst = slot(i);
     fence_proxy_async_smem();
     mbar_expect_tx(&bar[i], gb + cb + vb);
     tma_load_1d(dst, G + (size_t)k * gstride, gb, &bar[i]);
     tma_load_1d(dst + gstride, st + (size_t)k * 9 * wp + plane * wp, cb, &bar[i]);
-    tma_load_1d(dst + gstride + 3 * wp, rows + (size_t)k * nr * wp, vb, &bar[i]);
+    if (rows) tma_load_1d(dst + gstride + 3 * wp, rows + (size_t)k * nr * wp, vb, &bar[i]);
   }
 };
 
@@ -573,7 +741,7 @@ __device__ __forceinline__ void init_pipe(Pipe<R>& pipe, unsigned char* smem, co
   pipe.stage_elems = a.gstride + 3 * (size_t)a.wp + (size_t)a.nr * a.wp;
 }
 
-// SubdomSolve lines 1-5: the slab right-hand side (gather + transmission
+// SubdomSolve (Table 2): the slab right-hand side (gather + transmission
 // injection) into the rows Y[k][r][0..wp).  A kernel of its own, so that the
 // TMA reads of these rows in the next launch see them.
 template <typename R>
@@ -587,17 +755,20 @@ __global__ void slab_gather_kernel(SolveArgs<R> a) {
   a.Y[idx] = (e < a.W) ? rhs_at<R>(a.rhs, a.ny, a.W, a.nr, r, k, e) : mk<R>(0, 0);
 }
 
-// Forward recurrence over one segment.
-//   mode 0: zero start, store only the segment's last y into carry_f[p];
-//   mode 1: start from carry_f[p-1] (segment 0: zero), store every y_k into
-//           Y (over the right-hand side); if bwd1, then run the backward
-//           recurrence over the segment from a zero start and store its first
-//           x into carry_b[p].
+// Forward recurrence over segment s along its chain, t = 0..n-1, rows
+// k_t = k0 + dir t:  y_t = G_t (f_t - L_t y_{t-1}).
+//   mode 0: zero start, store only the last y into carry_f[s];
+//   mode 1: start from carry_f[s-1] (zero for the first segment of each
+//           half), store every y into Y (over the right-hand side); if bwd1,
+//           then run the backward recurrence x_t = y_t - G_t R_t x_{t+1} over
+//           the segment from a zero start and store x_0 into carry_b[s].
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int mode, int bwd1) {
-  const int p = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
+  const int s = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr;
   const int nthr = blockDim.x, ngroups = nthr / kTPR;
-  const int k0 = a.seg[p], k1 = a.seg[p + 1];
+  const int4 sd = a.seg[s];
+  const int k0 = sd.x, n = sd.y, dir = sd.z;
+  const bool first = (s == 0 || s == a.S0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   Pipe<R> pipe;
@@ -612,24 +783,24 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
   }
   for (int i = tid; i < NR * wp; i += nthr) {
     const int r = i / wp, e = i - r * wp;
-    ybuf[i] = (mode == 1 && p > 0 && r < nr) ? a.carry_f[((size_t)(p - 1) * nr + r) * wp + e] : zero;
+    ybuf[i] = (mode == 1 && !first && r < nr) ? a.carry_f[((size_t)(s - 1) * nr + r) * wp + e] : zero;
   }
   __syncthreads();
-  const int n = k1 - k0;
+  const int pl = lplane(dir), pr = rplane(dir);
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + i, a.G, a.st, 0, a.Y);
+    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + dir * i, a.G, a.st, pl, a.Y);
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
-  for (int s = 0; s < n; ++s) {
-    const int k = k0 + s;
-    const int slot = s % pipe.stages;
+  for (int t = 0; t < n; ++t) {
+    const int k = k0 + dir * t;
+    const int slot = t % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Gk = pipe.slot(slot);
-    const cplx<R>* Ck = Gk + pipe.gstride;
-    const cplx<R>* Fk = Ck + 3 * wp;
-    if (tid < W) {                       // v_k = f_k - C_k y_{k-1}
+    const cplx<R>* Lk = Gk + pipe.gstride;
+    const cplx<R>* Fk = Lk + 3 * wp;
+    if (tid < W) {                       // v = f_t - L_t y_{t-1}
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (r >= nr) break;
@@ -638,7 +809,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
         for (int dx = -1; dx <= 1; ++dx) {
           const int ee = tid + dx;
           if (ee >= 0 && ee < W) {
-            const cplx<R> c = Ck[(dx + 1) * wp + tid];
+            const cplx<R> c = Lk[(dx + 1) * wp + tid];
             const cplx<R> y = ybuf[r * wp + ee];
             v.re -= c.re * y.re - c.im * y.im;
             v.im -= c.re * y.im + c.im * y.re;
@@ -662,36 +833,38 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k + pipe.stages, a.G, a.st, 0, a.Y);
+    if (tid == 0 && t + pipe.stages < n) pipe.issue(slot, k + dir * pipe.stages, a.G, a.st, pl, a.Y);
   }
   if (mode == 0) {
-    for (int i = tid; i < nr * wp; i += nthr) a.carry_f[(size_t)p * nr * wp + i] = ybuf[i];
+    for (int i = tid; i < nr * wp; i += nthr) a.carry_f[(size_t)s * nr * wp + i] = ybuf[i];
     return;
   }
   if (!bwd1) return;
-  // Backward recurrence from a zero start: x_k = y_k - G_k (B_k x_{k+1}).
-  // The y rows were written above by this CTA (generic stores); they are read
-  // with ordinary loads, one step ahead, never through TMA.  The pipeline
-  // still brings G_k and B_k (its vector part, Y row k, is not used here).
-  for (int i = tid; i < NR * wp; i += nthr) ybuf[i] = zero;   // x_{k1}
+  // Backward recurrence from a zero start.  The y rows were written above by
+  // this CTA (generic stores); they are read with ordinary loads, one step
+  // ahead, never through TMA; the pipeline brings only G_t and R_t.
+  for (int i = tid; i < NR * wp; i += nthr) ybuf[i] = zero;   // x_n
   __syncthreads();
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k1 - 1 - i, a.G, a.st, 6, a.Y);
+    for (int i = 0; i < pipe.stages && i < n; ++i)
+      pipe.issue(i, k0 + dir * (n - 1 - i), a.G, a.st, pr, nullptr);
   cplx<R> ynext[NR];
   {
     const int row0 = grp;   // rows handled by this group in the first pass over rb
+    const int kl = k0 + dir * (n - 1);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      ynext[r] = (lane == 0 && row0 < W && r < nr) ? a.Y[((size_t)(k1 - 1) * nr + r) * wp + row0] : zero;
+      ynext[r] = (lane == 0 && row0 < W && r < nr) ? a.Y[((size_t)kl * nr + r) * wp + row0] : zero;
   }
-  for (int s = 0; s < n; ++s) {
-    const int k = k1 - 1 - s;
-    const int slot = s % pipe.stages;
+  for (int q = 0; q < n; ++q) {
+    const int t = n - 1 - q;
+    const int k = k0 + dir * t;
+    const int slot = q % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Gk = pipe.slot(slot);
-    const cplx<R>* Bk = Gk + pipe.gstride;
-    if (tid < W) {                       // w = B_k x_{k+1}
+    const cplx<R>* Rk = Gk + pipe.gstride;
+    if (tid < W) {                       // w = R_t x_{t+1}
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (r >= nr) break;
@@ -699,7 +872,7 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const int ee = tid + dx;
-          if (ee >= 0 && ee < W) cfma(v, Bk[(dx + 1) * wp + tid], ybuf[r * wp + ee]);
+          if (ee >= 0 && ee < W) cfma(v, Rk[(dx + 1) * wp + tid], ybuf[r * wp + ee]);
         }
         vbuf[r * wp + tid] = v;
       }
@@ -710,12 +883,12 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
       cplx<R> ycur[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) ycur[r] = ynext[r];
-      if (rb + ngroups >= W) {           // last pass over rows: prefetch row k-1
+      if (rb + ngroups >= W) {           // last pass over rows: prefetch the next row
         const int rowp = grp;
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-          ynext[r] = (lane == 0 && rowp < W && r < nr && k > k0)
-                         ? a.Y[((size_t)(k - 1) * nr + r) * wp + rowp] : zero;
+          ynext[r] = (lane == 0 && rowp < W && r < nr && t > 0)
+                         ? a.Y[((size_t)(k - dir) * nr + r) * wp + rowp] : zero;
       }
       if (rb > 0) {                      // rows beyond the first pass: plain load now
 #pragma unroll
@@ -733,18 +906,34 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k - pipe.stages, a.G, a.st, 6, a.Y);
+    if (tid == 0 && q + pipe.stages < n)
+      pipe.issue(slot, k - dir * pipe.stages, a.G, a.st, pr, nullptr);
   }
-  for (int i = tid; i < nr * wp; i += nthr) a.carry_b[(size_t)p * nr * wp + i] = ybuf[i];
+  for (int i = tid; i < nr * wp; i += nthr) a.carry_b[(size_t)s * nr * wp + i] = ybuf[i];
 }
 
-// Final backward recurrence over one segment from x_{k1} = carry_b[p+1]
-// (last segment: zero), with the epilogue of Table 2.
+// Epilogue of Table 2 for one solution entry x at block row k, local column row.
+template <typename R>
+__device__ __forceinline__ void store_out(const Out<R>& o, int ny, int W, int nr, int r, int k,
+                                          int row, cplx<R> x) {
+  const int g = row - o.wl + o.lo;
+  if (o.raw) o.raw[((size_t)r * ny + k) * W + row] = x;
+  if (o.u && g > o.ua && g <= o.ub) o.u[((size_t)r * ny + k) * o.nx + g] = x;
+  if (o.B2 && (row == o.e2 || row == o.e2 + 1)) o.B2[((size_t)(row - o.e2) * nr + r) * ny + k] = x;
+  if (o.B4 && (row == o.e4 || row == o.e4 + 1)) o.B4[((size_t)(row - o.e4) * nr + r) * ny + k] = x;
+}
+
+// Final backward recurrence over segment s from x_{n} = the next segment's
+// start value carry_b[s+1] (last segment of a half: the meeting row's
+// x_m = carry_b[P]), with the epilogue of Table 2.
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
-  const int p = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
+  const int s = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
   const int nthr = blockDim.x, ngroups = nthr / kTPR;
-  const int k0 = a.seg[p], k1 = a.seg[p + 1];
+  const int4 sd = a.seg[s];
+  const int k0 = sd.x, n = sd.y, dir = sd.z;
+  const bool last = (s == a.S0 - 1 || s == a.P - 1);
+  const int from = last ? a.P : s + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   Pipe<R> pipe;
@@ -759,24 +948,25 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
   }
   for (int i = tid; i < NR * wp; i += nthr) {
     const int r = i / wp, e = i - r * wp;
-    xbuf[i] = (p + 1 < a.P && r < nr) ? a.carry_b[((size_t)(p + 1) * nr + r) * wp + e] : zero;
+    xbuf[i] = (r < nr) ? a.carry_b[((size_t)from * nr + r) * wp + e] : zero;
   }
   __syncthreads();
-  const int n = k1 - k0;
+  const int pr = rplane(dir);
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k1 - 1 - i, a.G, a.st, 6, a.Y);
+    for (int i = 0; i < pipe.stages && i < n; ++i)
+      pipe.issue(i, k0 + dir * (n - 1 - i), a.G, a.st, pr, a.Y);
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
-  const Out<R>& o = a.out;
-  for (int s = 0; s < n; ++s) {
-    const int k = k1 - 1 - s;
-    const int slot = s % pipe.stages;
+  for (int q = 0; q < n; ++q) {
+    const int t = n - 1 - q;
+    const int k = k0 + dir * t;
+    const int slot = q % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Gk = pipe.slot(slot);
-    const cplx<R>* Bk = Gk + pipe.gstride;
-    const cplx<R>* Yk = Bk + 3 * wp;
+    const cplx<R>* Rk = Gk + pipe.gstride;
+    const cplx<R>* Yk = Rk + 3 * wp;
     if (tid < W) {
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
@@ -785,7 +975,7 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const int ee = tid + dx;
-          if (ee >= 0 && ee < W) cfma(v, Bk[(dx + 1) * wp + tid], xbuf[r * wp + ee]);
+          if (ee >= 0 && ee < W) cfma(v, Rk[(dx + 1) * wp + tid], xbuf[r * wp + ee]);
         }
         vbuf[r * wp + tid] = v;
       }
@@ -795,72 +985,117 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
       const int row = rb + grp;
       gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
-        const int g = row - o.wl + o.lo;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (r >= nr) break;
           const cplx<R> x = Yk[r * wp + row] - acc[r];
           xbuf[r * wp + row] = x;
-          if (o.raw) o.raw[((size_t)r * ny + k) * W + row] = x;
-          if (o.u && g > o.ua && g <= o.ub) o.u[((size_t)r * ny + k) * o.nx + g] = x;
-          if (o.B2 && (row == o.e2 || row == o.e2 + 1))
-            o.B2[((size_t)(row - o.e2) * nr + r) * ny + k] = x;
-          if (o.B4 && (row == o.e4 || row == o.e4 + 1))
-            o.B4[((size_t)(row - o.e4) * nr + r) * ny + k] = x;
+          store_out<R>(a.out, ny, W, nr, r, k, row, x);
         }
       }
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && s + pipe.stages < n) pipe.issue(slot, k - pipe.stages, a.G, a.st, 6, a.Y);
+    if (tid == 0 && q + pipe.stages < n) pipe.issue(slot, k - dir * pipe.stages, a.G, a.st, pr, a.Y);
   }
 }
 
-// Segment carries: forward Y_p = yhat_p + Phi_p Y_{p-1} (p = 1..P-1);
-// backward X_p = xhat_p + Psi_p X_{p+1} (p = P-2..0).  The products and the
-// segment values come through a TMA pipeline: stage = [M_p | carry row p].
+// Segment carries along each half (one CTA per half).
+//   forward:  Y_s = yhat_s + Phi_s Y_{s-1} over the half's segments after the
+//             first (carry_f in place: the true last y of every segment);
+//   backward: first the meeting row x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1})
+//             (stored in carry_b[P] and the output by the first CTA), then
+//             X_s = xhat_s + Psi_s X_{s+1} from the half's last segment
+//             (X_{s+1} = x_m) back to its first (carry_b in place).
+// The products and the segment values come through a TMA pipeline:
+// stage = [M_s | carry row s].
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, const cplx<R>* prod,
                                                               int backward) {
-  const int tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr, P = a.P;
+  const int h = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr, P = a.P;
   const int nthr = blockDim.x, ngroups = nthr / kTPR;
+  const int s_first = h ? a.S0 : 0;
+  const int nh = h ? P - a.S0 : a.S0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   uint64_t* bar = (uint64_t*)smem_raw;
   cplx<R>* prev = (cplx<R>*)(smem_raw + 128);
-  cplx<R>* buf = (cplx<R>*)(((uintptr_t)(prev + NR * wp) + 127) & ~(uintptr_t)127);
+  cplx<R>* vtmp = prev + NR * wp;
+  cplx<R>* buf = (cplx<R>*)(((uintptr_t)(vtmp + NR * wp) + 127) & ~(uintptr_t)127);
   const size_t se = a.gstride + (size_t)nr * wp;
   const int stages = a.stages;
   cplx<R>* carry = backward ? a.carry_b : a.carry_f;
   const uint32_t mb = (uint32_t)(a.gstride * sizeof(cplx<R>));
   const uint32_t vb = (uint32_t)((size_t)nr * wp * sizeof(cplx<R>));
-  auto seg_of = [&](int q) { return backward ? P - 1 - q : q; };
-  auto issue = [&](int i, int q) {
-    const int p = seg_of(q);
+  // step i handles segment seg_of(i)
+  const int nsteps = backward ? nh : nh - 1;
+  auto seg_of = [&](int i) { return backward ? s_first + nh - 1 - i : s_first + 1 + i; };
+  auto issue = [&](int slot, int i) {
+    const int sg = seg_of(i);
     fence_proxy_async_smem();
-    mbar_expect_tx(&bar[i], mb + vb);
-    tma_load_1d(buf + (size_t)i * se, prod + (size_t)p * a.gstride, mb, &bar[i]);
-    tma_load_1d(buf + (size_t)i * se + a.gstride, carry + (size_t)p * nr * wp, vb, &bar[i]);
+    mbar_expect_tx(&bar[slot], mb + vb);
+    tma_load_1d(buf + (size_t)slot * se, prod + (size_t)sg * a.gstride, mb, &bar[slot]);
+    tma_load_1d(buf + (size_t)slot * se + a.gstride, carry + (size_t)sg * nr * wp, vb, &bar[slot]);
   };
+  const cplx<R> zero = mk<R>(0, 0);
   if (tid == 0) {
     sh_abort = 0;
     for (int i = 0; i < stages; ++i) mbar_init(&bar[i], 1);
     mbar_fence_init();
   }
-  const int pstart = seg_of(0);
-  for (int i = tid; i < NR * wp; i += nthr)
-    prev[i] = (i < nr * wp) ? carry[(size_t)pstart * nr * wp + i] : mk<R>(0, 0);
-  __syncthreads();
-  const int n = P - 1;
-  if (tid == 0)
-    for (int i = 0; i < stages && i < n; ++i) issue(i, i + 1);
-  uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
-  for (int s = 0; s < n; ++s) {
-    const int q = s + 1;
-    const int p = seg_of(q);
-    const int slot = s % stages;
+  if (!backward) {
+    for (int i = tid; i < NR * wp; i += nthr)
+      prev[i] = (i < nr * wp) ? a.carry_f[(size_t)s_first * nr * wp + i] : zero;
+  } else {
+    // meeting row: v = f_m - C_m y_{m-1} - B_m y_{m+1}, x_m = G_m v
+    const int m = a.mid;
+    const cplx<R>* stm = a.st + (size_t)m * 9 * wp;
+    const cplx<R>* yu = a.carry_f + (size_t)(a.S0 - 1) * nr * wp;
+    const cplx<R>* yd = a.carry_f + (size_t)(P - 1) * nr * wp;
+    for (int i = tid; i < NR * wp; i += nthr) {
+      const int r = i / wp, e = i - r * wp;
+      cplx<R> v = zero;
+      if (r < nr && e < W) {
+        v = a.Y[((size_t)m * nr + r) * wp + e];
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ee = e + dx;
+          if (ee < 0 || ee >= W) continue;
+          v = v - stm[(dx + 1) * wp + e] * yu[r * wp + ee] - stm[(6 + dx + 1) * wp + e] * yd[r * wp + ee];
+        }
+      }
+      vtmp[i] = v;
+    }
+    __syncthreads();
+    const cplx<R>* Gm = a.G + (size_t)m * a.gstride;
+    for (int rb = 0; rb < W; rb += ngroups) {
+      const int row = rb + grp;
+      gemv_rows<R, NR>(Gm, W, vtmp, wp, W, nr, row, lane, acc);
+      if (lane == 0 && row < W)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (r < nr) {
+            prev[r * wp + row] = acc[r];
+            if (h == 0) {
+              a.carry_b[((size_t)P * nr + r) * wp + row] = acc[r];
+              store_out<R>(a.out, a.ny, W, nr, r, m, row, acc[r]);
+            }
+          }
+    }
+    for (int i = tid; i < NR * wp; i += nthr) {   // padding and unused right-hand sides
+      const int r = i / wp, e = i - r * wp;
+      if (r >= nr || e >= W) prev[i] = zero;
+    }
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int i = 0; i < stages && i < nsteps; ++i) issue(i, i);
+  uint32_t phase_bits = 0;
+  for (int i = 0; i < nsteps; ++i) {
+    const int sg = seg_of(i);
+    const int slot = i % stages;
     if (!mbar_wait(&bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     __syncthreads();
@@ -875,7 +1110,7 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
       if (lane == 0 && row < W) {
         myrow = row;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) res[r] = (r < nr) ? hat[r * wp + row] + acc[r] : mk<R>(0, 0);
+        for (int r = 0; r < NR; ++r) res[r] = (r < nr) ? hat[r * wp + row] + acc[r] : zero;
       }
     }
     __syncthreads();   // everyone has read prev
@@ -884,11 +1119,11 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
       for (int r = 0; r < NR; ++r) {
         if (r >= nr) break;
         prev[r * wp + myrow] = res[r];
-        carry[((size_t)p * nr + r) * wp + myrow] = res[r];
+        carry[((size_t)sg * nr + r) * wp + myrow] = res[r];
       }
     }
     __syncthreads();
-    if (tid == 0 && s + stages < n) issue(slot, q + stages);
+    if (tid == 0 && i + stages < nsteps) issue(slot, i + stages);
   }
 }
 
@@ -904,7 +1139,7 @@ static size_t solve_smem(const Slab& S, int nr, int NR, int stages) {
 template <typename R>
 static size_t carry_smem(const Slab& S, int nr, int NR, int stages) {
   const size_t el = sizeof(cplx<R>);
-  return 128 + (size_t)NR * S.wp * el + 128 + (size_t)stages * (S.gstride + (size_t)nr * S.wp) * el;
+  return 128 + 2 * (size_t)NR * S.wp * el + 128 + (size_t)stages * (S.gstride + (size_t)nr * S.wp) * el;
 }
 
 constexpr size_t kSmemLimit = 225 * 1024;
@@ -928,56 +1163,62 @@ static int pick_carry_stages(const Slab& S, int nr, int NR) {
 
 template <typename R>
 void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
-  const int J = L.J;
+  const int J = L.J, P = L.P, m = L.mid;
+  constexpr int BW = FactorPanel<R>::BW;
+  const size_t el = sizeof(cplx<R>);
   int maxW = 0;
   for (int j = 1; j <= J; ++j) maxW = std::max(maxW, L.slabs[j].W);
-  size_t smem = 2 * (size_t)maxW * maxW * sizeof(cplx<R>) +
-                (2 * FactorPanel<R>::BW + 9) * maxW * sizeof(cplx<R>) +
-                FactorPanel<R>::BW * (sizeof(cplx<R>) + sizeof(int)) + 3 * maxW * sizeof(int) + 64;
-  // register tiles of the delayed update: 4 x 4 while ceil(W/4)^2 <= block, else 4 x 8
+  const size_t smem_f = factor_smem_bytes(maxW, 9, el, BW);
+  const size_t smem_m = factor_smem_bytes(maxW, 15, el, BW);
+  const size_t smem_p = (2 * (size_t)maxW * maxW + 3 * (size_t)maxW) * el;
+  // register tiles: 4 x 4 while ceil(W/4)^2 <= block, else 4 x 8
   const int TC = ((maxW + 3) / 4) * ((maxW + 3) / 4) <= kThreads ? 4 : 8;
-  if (((maxW + 3) / 4) * ((maxW + TC - 1) / TC) > kThreads || maxW > 128)
+  if (((maxW + 3) / 4) * ((maxW + TC - 1) / TC) > kThreads || smem_m > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the blocked factorisation (W=" +
                                  std::to_string(maxW) + ")");
-  std::vector<FactorDesc> fd(J);
+  std::vector<FactorDesc> fd;
+  std::vector<MidDesc> md;
+  std::vector<ProdDesc> pd;
   for (int j = 1; j <= J; ++j) {
     const Slab& S = L.slabs[j];
-    fd[j - 1] = FactorDesc{S.W, S.wp, L.ny, S.st, S.G, S.gstride};
-  }
-  FactorDesc* d_fd = (FactorDesc*)dmalloc(sizeof(FactorDesc) * J);
-  HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), sizeof(FactorDesc) * J, cudaMemcpyHostToDevice, s));
-  auto launch = [&](auto kern) {
-    HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    timed(h, "slab_factor", 0.0, s, [&] { kern<<<J, kThreads, smem, s>>>(d_fd); });
-  };
-  if (TC == 4) launch(slab_factor_kernel<R, 4>);
-  else launch(slab_factor_kernel<R, 8>);
-  h->launches++;
-  HZ_CU(cudaGetLastError());
-  ProdDesc* d_pd = nullptr;
-  if (L.P > 1) {
-    std::vector<ProdDesc> pd;
-    for (int j = 1; j <= J; ++j) {
-      const Slab& S = L.slabs[j];
-      for (int p = 0; p < L.P; ++p)
-        for (int bw = 0; bw < 2; ++bw)
-          pd.push_back(ProdDesc{S.W, S.wp, L.seg[p], L.seg[p + 1], bw, S.st, S.G, S.gstride,
-                                (cplx<R>*)(bw ? S.Psi : S.Phi) + (size_t)p * S.gstride});
+    fd.push_back(FactorDesc{S.W, S.wp, 0, m, +1, S.st, S.G, S.gstride});
+    fd.push_back(FactorDesc{S.W, S.wp, L.ny - 1, L.ny - 1 - m, -1, S.st, S.G, S.gstride});
+    md.push_back(MidDesc{S.W, S.wp, m, S.st, S.G, S.gstride});
+    for (int q = 0; q < P; ++q) {
+      const int4 sg = L.seg[q];
+      if (q != 0 && q != L.S0)      // Phi of the first segment of a half is never used
+        pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 0, S.st, S.G, S.gstride,
+                              (cplx<R>*)S.Phi + (size_t)q * S.gstride});
+      pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 1, S.st, S.G, S.gstride,
+                            (cplx<R>*)S.Psi + (size_t)q * S.gstride});
     }
-    d_pd = (ProdDesc*)dmalloc(sizeof(ProdDesc) * pd.size());
-    HZ_CU(cudaMemcpyAsync(d_pd, pd.data(), sizeof(ProdDesc) * pd.size(), cudaMemcpyHostToDevice, s));
-    size_t psm = 2 * (size_t)maxW * maxW * sizeof(cplx<R>);
-    HZ_CU(cudaFuncSetAttribute(segment_product_kernel<R>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-    timed(h, "segment_product", 0.0, s, [&] {
-      segment_product_kernel<R><<<(unsigned)pd.size(), kThreads, psm, s>>>(d_pd);
-    });
-    h->launches++;
-    HZ_CU(cudaGetLastError());
   }
+  const size_t b_fd = sizeof(FactorDesc) * fd.size(), b_md = sizeof(MidDesc) * md.size();
+  const size_t b_pd = sizeof(ProdDesc) * pd.size();
+  unsigned char* d_desc = (unsigned char*)dmalloc(b_fd + b_md + b_pd);
+  FactorDesc* d_fd = (FactorDesc*)d_desc;
+  MidDesc* d_md = (MidDesc*)(d_desc + b_fd);
+  ProdDesc* d_pd = (ProdDesc*)(d_desc + b_fd + b_md);
+  HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), b_fd, cudaMemcpyHostToDevice, s));
+  HZ_CU(cudaMemcpyAsync(d_md, md.data(), b_md, cudaMemcpyHostToDevice, s));
+  HZ_CU(cudaMemcpyAsync(d_pd, pd.data(), b_pd, cudaMemcpyHostToDevice, s));
+  auto run = [&](auto kf, auto km, auto kp) {
+    HZ_CU(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+    HZ_CU(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m));
+    HZ_CU(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+    timed(h, "slab_factor", 0.0, s, [&] { kf<<<(unsigned)fd.size(), kThreads, smem_f, s>>>(d_fd); });
+    timed(h, "slab_middle", 0.0, s, [&] { km<<<(unsigned)md.size(), kThreads, smem_m, s>>>(d_md); });
+    timed(h, "segment_product", 0.0, s,
+          [&] { kp<<<(unsigned)pd.size(), kThreads, smem_p, s>>>(d_pd); });
+    h->launches += 3;
+  };
+  if (TC == 4)
+    run(slab_factor_kernel<R, 4>, slab_middle_kernel<R, 4>, segment_product_kernel<R, 4>);
+  else
+    run(slab_factor_kernel<R, 8>, slab_middle_kernel<R, 8>, segment_product_kernel<R, 8>);
+  HZ_CU(cudaGetLastError());
   HZ_CU(cudaStreamSynchronize(s));
-  dfree(d_fd);
-  dfree(d_pd);
+  dfree(d_desc);
 }
 
 template <typename R, int NR>
@@ -1007,43 +1248,31 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   auto T = [&](const char* tag, double bytes, auto&& fn) {
     if (tagged) timed(h, tag, bytes, s, fn); else fn();
   };
-  dim3 grid(P);
   // one 4-thread group per row of G: round W * kTPR up to whole warps
   const int nthr = std::min(kThreads, std::max(128, (S.W * kTPR + 31) / 32 * 32));
   const size_t gtotal = (size_t)L.ny * nr * S.wp;
+  SolveArgs<R> ac = a;
+  ac.stages = pick_carry_stages<R>(S, nr, NR);
+  const size_t csm = carry_smem<R>(S, nr, NR, ac.stages);
   T("slab_gather", 2 * vbytes, [&] {
     slab_gather_kernel<R><<<cdiv(gtotal, 256), 256, 0, s>>>(a);
   });
-  h->launches++;
-  if (P == 1) {
-    T("slab_fwd", gbytes + cbytes + 3 * vbytes, [&] {
-      slab_fwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a, 1, 0);
-    });
-    T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
-      slab_bwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a);
-    });
-    h->launches += 2;
-  } else {
-    SolveArgs<R> ac = a;
-    ac.stages = pick_carry_stages<R>(S, nr, NR);
-    const size_t csm = carry_smem<R>(S, nr, NR, ac.stages);
-    T("slab_fwd_pass1", gbytes + cbytes + 3 * vbytes, [&] {
-      slab_fwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a, 0, 0);
-    });
-    T("slab_carry", pbytes, [&] {
-      slab_carry_kernel<R, NR><<<1, nthr, csm, s>>>(ac, (const cplx<R>*)S.Phi, 0);
-    });
-    T("slab_fwd_bwd1", 2 * gbytes + 2 * cbytes + 4 * vbytes, [&] {
-      slab_fwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a, 1, 1);
-    });
-    T("slab_carry", pbytes, [&] {
-      slab_carry_kernel<R, NR><<<1, nthr, csm, s>>>(ac, (const cplx<R>*)S.Psi, 1);
-    });
-    T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
-      slab_bwd_kernel<R, NR><<<grid, nthr, smem, s>>>(a);
-    });
-    h->launches += 5;
-  }
+  T("slab_fwd_pass1", gbytes + cbytes + vbytes, [&] {
+    slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 0, 0);
+  });
+  T("slab_carry", pbytes, [&] {
+    slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, (const cplx<R>*)S.Phi, 0);
+  });
+  T("slab_fwd_bwd1", 2 * gbytes + 2 * cbytes + 3 * vbytes, [&] {
+    slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 1, 1);
+  });
+  T("slab_carry", pbytes, [&] {
+    slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, (const cplx<R>*)S.Psi, 1);
+  });
+  T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
+    slab_bwd_kernel<R, NR><<<P, nthr, smem, s>>>(a);
+  });
+  h->launches += 6;
   HZ_CU(cudaGetLastError());
 }
 
@@ -1053,7 +1282,8 @@ static void run_solve(hz_handle* h, Level& L, Slab& S, const Rhs<R>& rhs, const 
                       bool tagged) {
   if (n_rhs < 1 || n_rhs > kNRMax) throw Failure(HZ_EINVAL, "right-hand sides per slab launch must be 1..8");
   SolveArgs<R> a;
-  a.W = S.W; a.wp = S.wp; a.ny = L.ny; a.nr = n_rhs; a.P = L.P; a.seg = L.seg_dev;
+  a.W = S.W; a.wp = S.wp; a.ny = L.ny; a.nr = n_rhs;
+  a.P = L.P; a.S0 = L.S0; a.mid = L.mid; a.seg = L.seg_dev;
   a.st = (const cplx<R>*)S.st; a.G = (const cplx<R>*)S.G; a.gstride = S.gstride;
   a.stages = 1;
   a.Y = Y; a.carry_f = cf; a.carry_b = cb;
