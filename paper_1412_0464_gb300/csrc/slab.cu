@@ -124,10 +124,10 @@ __device__ __forceinline__ cplx<double> crcp(cplx<double> a) {
   return mk(a.re * d, -a.im * d);
 }
 
+// Panel width of the Gauss-Jordan elimination: 4 pivots per panel (wider
+// fully unrolled panels cost more per pivot on sm_103a, measured).
 template <typename R>
-struct FactorPanel { static constexpr int BW = 8; };
-template <>
-struct FactorPanel<double> { static constexpr int BW = 4; };
+struct FactorPanel { static constexpr int BW = 4; };
 
 // Register tile of one thread in a W x W product or update: rows i0..i0+3,
 // columns j0..j0+TC-1.
@@ -135,13 +135,29 @@ struct Tile {
   bool own;
   int i0, j0;
 };
+// Warps of the delayed Gauss-Jordan updates: those that do not share a
+// scheduler with warp 0 (warp w runs on sub-partition w mod 4), so that the
+// panel warp keeps its issue slots while the update runs beside it.  Each
+// takes a strip of RPW consecutive rows.
+constexpr int kUpdateWarps = kThreads / 32 / 4 * 3;
+struct Strip {
+  int row0;        // first row of this warp's strip, -1: not an update warp
+};
+template <int RPW>
+__device__ __forceinline__ Strip strip_of(int tid) {
+  const int warp = tid >> 5;
+  Strip s;
+  s.row0 = ((warp & 3) == 0) ? -1 : ((warp >> 2) * 3 + (warp & 3) - 1) * RPW;
+  return s;
+}
+
 template <int TC>
-__device__ __forceinline__ Tile tile_of(int W, int tid) {
+__device__ __forceinline__ Tile tile_of(int W, int idx) {
   const int ntc = (W + TC - 1) / TC, ntr = (W + 3) / 4;
   Tile t;
-  t.own = tid < ntr * ntc;
-  t.i0 = t.own ? (tid / ntc) * 4 : 0;
-  t.j0 = t.own ? (tid % ntc) * TC : 0;
+  t.own = idx >= 0 && idx < ntr * ntc;
+  t.i0 = t.own ? (idx / ntc) * 4 : 0;
+  t.j0 = t.own ? (idx % ntc) * TC : 0;
   return t;
 }
 
@@ -179,9 +195,11 @@ __device__ __forceinline__ void gemm_sub(const cplx<R>* A, const cplx<R>* B, con
 
 // One warp eliminates pivots p0 .. p0+bw-1 on the panel columns p0 .. p0+bw-1
 // (rows lane + 32 m, m < MR, in registers) and records colmod (Cm), the pivot
-// inverses and rows.
+// inverses and rows.  The panel columns first receive the pending rank-pbw
+// update of the previous panel, S -= Cp^T Rp (pbw = 0: none).
 template <typename R, int BW, int MR>
-__device__ __forceinline__ void panel_elim(cplx<R>* S, cplx<R>* Cm, cplx<R>* pinv, int* prow,
+__device__ __forceinline__ void panel_elim(cplx<R>* S, cplx<R>* Cm, const cplx<R>* Cp,
+                                           const cplx<R>* Rp, int pbw, cplx<R>* pinv, int* prow,
                                            int* piv, int* used, int W, int p0, int bw, int lane) {
   const cplx<R> zero = mk<R>(0, 0);
   cplx<R> P[MR][BW];
@@ -193,22 +211,38 @@ __device__ __forceinline__ void panel_elim(cplx<R>* S, cplx<R>* Cm, cplx<R>* pin
 #pragma unroll
     for (int c = 0; c < BW; ++c) P[m][c] = (i < W && c < bw) ? S[i * W + p0 + c] : zero;
   }
+  for (int t = 0; t < pbw; ++t) {
+    cplx<R> cv[MR];
+#pragma unroll
+    for (int m = 0; m < MR; ++m) cv[m] = (lane + 32 * m < W) ? Cp[t * W + lane + 32 * m] : zero;
+#pragma unroll
+    for (int c = 0; c < BW; ++c) {
+      const cplx<R> rv = (c < bw) ? Rp[t * W + p0 + c] : zero;
+#pragma unroll
+      for (int m = 0; m < MR; ++m) {
+        P[m][c].re -= cv[m].re * rv.re - cv[m].im * rv.im;
+        P[m][c].im -= cv[m].re * rv.im + cv[m].im * rv.re;
+      }
+    }
+  }
 #pragma unroll
   for (int t = 0; t < BW; ++t) {
     if (t < bw) {
-      float lbv = -1.0f;
-      int lbi = 1 << 30;
+      // pivot row: largest |S[i][p]|^2 over the unused rows, by one max
+      // reduction over keys = float bits of |S|^2 (low 8 bits dropped, a
+      // 2^-15 relative tie width) | 0x80 | row.  Every unused row offers a key
+      // > 0 (NaN or zero entries included), so a valid row always wins.
+      unsigned key = 0u;
 #pragma unroll
       for (int m = 0; m < MR; ++m) {
         if (!usd[m]) {
           const float v = (float)cabs2(P[m][t]);
-          if (v > lbv) { lbv = v; lbi = lane + 32 * m; }
+          const unsigned row = (unsigned)(lane + 32 * m) | 0x80u;
+          const unsigned kv = (v > 0.0f) ? ((__float_as_uint(v) & ~255u) | row) : row;
+          key = max(key, kv);
         }
       }
-      const unsigned key = lbv >= 0.0f ? __float_as_uint(lbv) : 0u;
-      const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-      const unsigned win = __ballot_sync(0xffffffffu, key == kmax && lbi < (1 << 30));
-      const int r = __shfl_sync(0xffffffffu, lbi, __ffs(win) - 1);
+      const int r = (int)(__reduce_max_sync(0xffffffffu, key) & 127u);
       const int rl = r & 31, rm = r >> 5;
       cplx<R> prw[BW];
 #pragma unroll
@@ -254,10 +288,26 @@ __device__ __forceinline__ void panel_elim(cplx<R>* S, cplx<R>* Cm, cplx<R>* pin
   }
 }
 
+template <typename R, int BW>
+__device__ __forceinline__ void panel_dispatch(cplx<R>* S, cplx<R>* Cm, const cplx<R>* Cp,
+                                               const cplx<R>* Rp, int pbw, cplx<R>* pinv,
+                                               int* prow, int* piv, int* used, int W, int p0,
+                                               int bw, int lane) {
+  const int MR = (W + 31) >> 5;
+  if (MR == 1)
+    panel_elim<R, BW, 1>(S, Cm, Cp, Rp, pbw, pinv, prow, piv, used, W, p0, bw, lane);
+  else if (MR == 2)
+    panel_elim<R, BW, 2>(S, Cm, Cp, Rp, pbw, pinv, prow, piv, used, W, p0, bw, lane);
+  else if (MR == 3)
+    panel_elim<R, BW, 3>(S, Cm, Cp, Rp, pbw, pinv, prow, piv, used, W, p0, bw, lane);
+  else
+    panel_elim<R, BW, 4>(S, Cm, Cp, Rp, pbw, pinv, prow, piv, used, W, p0, bw, lane);
+}
+
 // Shared-memory work areas of the Gauss-Jordan inverse.
 template <typename R>
 struct GJWork {
-  cplx<R>* Cm;     // BW x W
+  cplx<R>* Cm;     // 2 x BW x W (colmods of two consecutive panels)
   cplx<R>* Rm;     // BW x W
   cplx<R>* pinv;   // BW
   int* prow;       // BW
@@ -268,32 +318,76 @@ struct GJWork {
 
 // S^-1 (S: W x W in shared memory, overwritten) into `out` (global) and Gl
 // (shared), both in natural order.  Called by every thread of a kThreads
-// block after a barrier that completes S; ends with a barrier.
-template <typename R, int TC>
-__device__ void gj_inverse(cplx<R>* S, cplx<R>* Gl, const GJWork<R>& w, int W, const Tile& tl,
+// block after a barrier that completes S; ends with a barrier.  `su` is this
+// warp's row strip in the delayed updates (update warps only; lane l holds
+// columns l, l + 32, ..., so every shared-memory access of the update is
+// conflict-free or a broadcast).
+//
+// Look-ahead: while warp 0 applies panel q-1's pending update to the columns
+// of panel q and eliminates panel q, the update warps apply the same update to
+// all other columns; then all threads form the pivot rows of panel q (rowmod).
+// Two block barriers per panel.
+template <typename R, int RPW, int CPL>
+__device__ void gj_inverse(cplx<R>* S, cplx<R>* Gl, const GJWork<R>& w, int W, const Strip& su,
                            cplx<R>* out) {
   constexpr int BW = FactorPanel<R>::BW;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int WW = W * W;
+  const int NP = (W + BW - 1) / BW;
   const cplx<R> zero = mk<R>(0, 0);
   for (int t = tid; t < W; t += kThreads) w.used[t] = 0;
   __syncthreads();
-  for (int p0 = 0; p0 < W; p0 += BW) {
-    const int bw = min(BW, W - p0);
-    // (1) one warp eliminates the panel's pivots on the panel columns
+  for (int q = 0; q <= NP; ++q) {
+    const int p0 = q * BW, bw = (q < NP) ? min(BW, W - p0) : 0;       // panel q (to eliminate)
+    const int pp0 = (q - 1) * BW, pbw = (q > 0) ? min(BW, W - pp0) : 0;   // panel q-1 (pending)
+    cplx<R>* Cq = w.Cm + (size_t)(q & 1) * BW * W;
+    const cplx<R>* Cp = w.Cm + (size_t)((q + 1) & 1) * BW * W;
     if (warp == 0) {
-      const int MR = (W + 31) >> 5;
-      if (bw == BW) {
-        if (MR == 1) panel_elim<R, BW, 1>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
-        else if (MR == 2) panel_elim<R, BW, 2>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
-        else if (MR == 3) panel_elim<R, BW, 3>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
-        else panel_elim<R, BW, 4>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
-      } else {
-        panel_elim<R, BW, 4>(S, w.Cm, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
+      if (bw > 0)
+        panel_dispatch<R, BW>(S, Cq, Cp, w.Rm, pbw, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
+    } else if (pbw > 0 && su.row0 >= 0) {
+      // delayed rank-pbw update of panel q-1 on every column outside panels
+      // q-1 and q: this warp's rows row0 .. row0+RPW-1, columns lane + 32 b
+      cplx<R> acc[RPW][CPL];
+#pragma unroll
+      for (int a = 0; a < RPW; ++a)
+#pragma unroll
+        for (int b = 0; b < CPL; ++b) {
+          const int i = su.row0 + a, j = lane + 32 * b;
+          acc[a][b] = (i < W && j < W) ? S[i * W + j] : zero;
+        }
+#pragma unroll
+      for (int t = 0; t < BW; ++t) {
+        if (t >= pbw) break;
+        cplx<R> rv[CPL];
+#pragma unroll
+        for (int b = 0; b < CPL; ++b) {
+          const int j = lane + 32 * b;
+          rv[b] = (j < W && (j < pp0 || j >= p0 + bw)) ? w.Rm[t * W + j] : zero;
+        }
+#pragma unroll
+        for (int a = 0; a < RPW; ++a) {
+          const int i = su.row0 + a;
+          const cplx<R> cv = (i < W) ? Cp[t * W + i] : zero;     // same address across the warp
+#pragma unroll
+          for (int b = 0; b < CPL; ++b) {
+            acc[a][b].re -= cv.re * rv[b].re - cv.im * rv[b].im;
+            acc[a][b].im -= cv.re * rv[b].im + cv.im * rv[b].re;
+          }
+        }
       }
+#pragma unroll
+      for (int a = 0; a < RPW; ++a)
+#pragma unroll
+        for (int b = 0; b < CPL; ++b) {
+          const int i = su.row0 + a, j = lane + 32 * b;
+          if (i < W && j < W && (j < pp0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
+        }
     }
     __syncthreads();
-    // (2) rowmod of the panel's pivots on the other columns
+    if (bw == 0) break;
+    // rowmod of panel q's pivots on the other columns:
+    // R_t = (S[r_t] - sum_{s<t} colmod_s[r_t] R_s) inv_t
     for (int j = tid; j < W; j += kThreads) {
       if (j >= p0 && j < p0 + bw) continue;
       cplx<R> rw[BW];
@@ -303,52 +397,14 @@ __device__ void gj_inverse(cplx<R>* S, cplx<R>* Gl, const GJWork<R>& w, int W, c
         const int r = w.prow[t];
         cplx<R> acc = S[r * W + j];
 #pragma unroll
-        for (int q = 0; q < t; ++q) {
-          const cplx<R> c = w.Cm[q * W + r];
-          acc.re -= c.re * rw[q].re - c.im * rw[q].im;
-          acc.im -= c.re * rw[q].im + c.im * rw[q].re;
+        for (int s2 = 0; s2 < t; ++s2) {
+          const cplx<R> c = Cq[s2 * W + r];
+          acc.re -= c.re * rw[s2].re - c.im * rw[s2].im;
+          acc.im -= c.re * rw[s2].im + c.im * rw[s2].re;
         }
         rw[t] = acc * w.pinv[t];
         w.Rm[t * W + j] = rw[t];
       }
-    }
-    __syncthreads();
-    // (3) delayed rank-bw update of the other columns, 4 x TC tiles
-    if (tl.own) {
-      cplx<R> acc[4][TC];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < TC; ++b) {
-          const int i = tl.i0 + a, j = tl.j0 + b;
-          acc[a][b] = (i < W && j < W) ? S[i * W + j] : zero;
-        }
-#pragma unroll
-      for (int t = 0; t < BW; ++t) {
-        if (t >= bw) break;
-        cplx<R> cv[4], rv[TC];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) cv[a] = (tl.i0 + a < W) ? w.Cm[t * W + tl.i0 + a] : zero;
-#pragma unroll
-        for (int b = 0; b < TC; ++b) {
-          const int j = tl.j0 + b;
-          rv[b] = (j < W && (j < p0 || j >= p0 + bw)) ? w.Rm[t * W + j] : zero;
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < TC; ++b) {
-            acc[a][b].re -= cv[a].re * rv[b].re - cv[a].im * rv[b].im;
-            acc[a][b].im -= cv[a].re * rv[b].im + cv[a].im * rv[b].re;
-          }
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < TC; ++b) {
-          const int i = tl.i0 + a, j = tl.j0 + b;
-          if (i < W && j < W && (j < p0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
-        }
     }
     __syncthreads();
   }
@@ -373,7 +429,7 @@ __device__ __forceinline__ void factor_smem(unsigned char* raw, int W, int ncpl,
   *S = p;
   *Gl = p + W * W;
   w->Cm = *Gl + W * W;
-  w->Rm = w->Cm + BW * W;
+  w->Rm = w->Cm + 2 * BW * W;
   *cpl = w->Rm + BW * W;
   w->pinv = *cpl + ncpl * W;
   w->prow = (int*)(w->pinv + BW);
@@ -382,7 +438,7 @@ __device__ __forceinline__ void factor_smem(unsigned char* raw, int W, int ncpl,
   w->used = w->ipiv + W;
 }
 static size_t factor_smem_bytes(int W, int ncpl, size_t el, int BW) {
-  return (2 * (size_t)W * W + (2 * (size_t)BW + ncpl) * W + BW) * el + (BW + 3 * (size_t)W) * 4 + 64;
+  return (2 * (size_t)W * W + (3 * (size_t)BW + ncpl) * W + BW) * el + (BW + 3 * (size_t)W) * 4 + 64;
 }
 
 // Interior chains of the twisted factorisation (one CTA per slab and half).
@@ -401,12 +457,12 @@ struct FactorDesc {
 __host__ __device__ __forceinline__ int lplane(int dir) { return dir > 0 ? 0 : 6; }
 __host__ __device__ __forceinline__ int rplane(int dir) { return dir > 0 ? 6 : 0; }
 
-template <typename R, int TC>
+template <typename R, int RPW, int CPL>
 __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc* descs) {
   const FactorDesc d = descs[blockIdx.x];
   const int W = d.W, wp = d.wp, tid = threadIdx.x, dir = d.dir;
   const int WW = W * W;
-  const Tile tl = tile_of<TC>(W, tid);
+  const Strip su = strip_of<RPW>(tid);
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -464,7 +520,7 @@ __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc*
       }
     }
     __syncthreads();
-    gj_inverse<R, TC>(S, Gl, w, W, tl, G + (size_t)k * d.gstride);
+    gj_inverse<R, RPW, CPL>(S, Gl, w, W, su, G + (size_t)k * d.gstride);
   }
 }
 
@@ -498,11 +554,11 @@ struct MidDesc {
   size_t gstride;
 };
 
-template <typename R, int TC>
+template <typename R, int RPW, int CPL>
 __global__ void __launch_bounds__(kThreads) slab_middle_kernel(const MidDesc* descs) {
   const MidDesc d = descs[blockIdx.x];
   const int W = d.W, wp = d.wp, m = d.m, tid = threadIdx.x, WW = W * W;
-  const Tile tl = tile_of<TC>(W, tid);
+  const Strip su = strip_of<RPW>(tid);
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -533,7 +589,7 @@ __global__ void __launch_bounds__(kThreads) slab_middle_kernel(const MidDesc* de
     S[e] = v - tri_x_tri<R>(Cm, Gu, Bu, W, i, j) - tri_x_tri<R>(Bm, Gd, Cd, W, i, j);
   }
   __syncthreads();
-  gj_inverse<R, TC>(S, Gl, w, W, tl, G + (size_t)m * d.gstride);
+  gj_inverse<R, RPW, CPL>(S, Gl, w, W, su, G + (size_t)m * d.gstride);
 }
 
 // Segment transfer products for the parallel substitution (one CTA per slab,
@@ -1171,9 +1227,11 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   const size_t smem_f = factor_smem_bytes(maxW, 9, el, BW);
   const size_t smem_m = factor_smem_bytes(maxW, 15, el, BW);
   const size_t smem_p = (2 * (size_t)maxW * maxW + 3 * (size_t)maxW) * el;
-  // register tiles: 4 x 4 while ceil(W/4)^2 <= block, else 4 x 8
+  // delayed updates: rows per update warp (RPW) and columns per lane (CPL);
+  // register tiles of the product GEMMs: 4 x 4 while they fit, else 4 x 8
+  const int rpw = (maxW + kUpdateWarps - 1) / kUpdateWarps;
   const int TC = ((maxW + 3) / 4) * ((maxW + 3) / 4) <= kThreads ? 4 : 8;
-  if (((maxW + 3) / 4) * ((maxW + TC - 1) / TC) > kThreads || smem_m > kSmemLimit)
+  if (maxW > 128 || rpw > 11 || smem_m > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the blocked factorisation (W=" +
                                  std::to_string(maxW) + ")");
   std::vector<FactorDesc> fd;
@@ -1212,10 +1270,19 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
           [&] { kp<<<(unsigned)pd.size(), kThreads, smem_p, s>>>(d_pd); });
     h->launches += 3;
   };
-  if (TC == 4)
-    run(slab_factor_kernel<R, 4>, slab_middle_kernel<R, 4>, segment_product_kernel<R, 4>);
-  else
-    run(slab_factor_kernel<R, 8>, slab_middle_kernel<R, 8>, segment_product_kernel<R, 8>);
+  auto prod = [&](auto kp) {
+    if (maxW <= 64) {
+      if (rpw <= 4) run(slab_factor_kernel<R, 4, 2>, slab_middle_kernel<R, 4, 2>, kp);
+      else run(slab_factor_kernel<R, 6, 2>, slab_middle_kernel<R, 6, 2>, kp);
+    } else if (maxW <= 96) {
+      if (rpw <= 6) run(slab_factor_kernel<R, 6, 3>, slab_middle_kernel<R, 6, 3>, kp);
+      else run(slab_factor_kernel<R, 8, 3>, slab_middle_kernel<R, 8, 3>, kp);
+    } else {
+      run(slab_factor_kernel<R, 11, 4>, slab_middle_kernel<R, 11, 4>, kp);
+    }
+  };
+  if (TC == 4) prod(segment_product_kernel<R, 4>);
+  else prod(segment_product_kernel<R, 8>);
   HZ_CU(cudaGetLastError());
   HZ_CU(cudaStreamSynchronize(s));
   dfree(d_desc);
