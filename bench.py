@@ -276,7 +276,7 @@ def main():
     barrier()
     clk = clocks.stop()
     gpu_launches = solver.stats()["kernel_launches"] - launches0
-    tags = ["slab_gather", "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", "slab_solve",
+    tags = ["slab_rhs", "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", "slab_solve",
             "slab_factor", "slab_middle", "segment_product"]
     kt = {t: solver.kernel_timing(t) for t in tags}
     solver.enable_timing(False)

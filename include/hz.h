@@ -45,7 +45,7 @@ typedef enum {
   HZ_ENOTFACTORED = 4,  /* hz_solve / hz_precond before hz_factor */
   HZ_ENOTCONV = 5,      /* GMRES hit max_iter; u holds the last iterate, stats are filled */
   HZ_ETIMEOUT = 6,      /* a bounded device-side wait gave up (no hang, context usable) */
-  HZ_EINACCURATE = 7    /* true residual and GMRES estimate disagree by > 100x */
+  HZ_EINACCURATE = 7    /* a residual norm is not finite (NaN / Inf in the data or operator) */
 } hz_status;
 
 enum { HZ_SWEEP_UD = 0, HZ_SWEEP_X = 1 };        /* SweepingPrecUD / SweepingPrecX (Table 3) */
@@ -184,7 +184,7 @@ hz_status hz_get_stats(const hz_handle* h, hz_stats* out);
  * returns, for one tag, the summed event time (ms), the number of launches
  * and the algorithmic bytes those launches move (method minimum: each
  * factor block read once per pass, vectors once).  Tags: "slab_solve" (one
- * whole subdomain solve of SubdomSolve, Table 2), its kernels "slab_gather",
+ * whole subdomain solve of SubdomSolve, Table 2), its kernels "slab_rhs",
  * "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", and the
  * factorisation kernels "slab_factor", "slab_middle", "segment_product"
  * (bytes 0).  Unknown tags return zeros. */

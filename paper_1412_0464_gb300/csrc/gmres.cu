@@ -322,6 +322,9 @@ void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
       if (!active[r]) continue;
       iters[r] += kd[r] < 0 ? -kd[r] : kd[r];
       relres[r] = bnorm[r] > 0 ? rnorm[r] / bnorm[r] : 0.0;
+      if (!std::isfinite(relres[r]))
+        throw Failure(HZ_EINACCURATE, "non-finite residual in GMRES (right-hand side " +
+                                          std::to_string(r) + ")");
       if (relres[r] <= tol) active[r] = 0;
     }
     ++cycles;

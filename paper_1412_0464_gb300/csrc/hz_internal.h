@@ -91,13 +91,16 @@ struct AxisTables {
 // Slab j: core columns lo..hi, wl/wr added PML columns, W = width.
 struct Slab {
   int j = 0, lo = 0, hi = 0, wl = 0, wr = 0, W = 0;
-  int wp = 0;                // W padded to a 16-byte row (plane / row stride of st and Y)
+  int wp = 0;                // row stride of st, Y, F, E, Phi, Psi: smallest >= W with wp % 8 == 4
   AxisTables ax;             // slab x axis (DD PML in the added columns)
   void* st = nullptr;        // slab stencil [ny][9][wp] in the preconditioner precision
   void* G = nullptr;         // inverse Schur complements [ny][gstride]
   size_t gstride = 0;        // elements per block (W*W rounded up to 16 bytes)
-  void* Phi = nullptr;       // forward segment transfer products [P][gstride]
-  void* Psi = nullptr;       // backward segment transfer products [P][gstride]
+  size_t mstride = 0;        // elements per block of F, E, Phi, Psi (W rows of stride wp)
+  void* F = nullptr;         // substitution operators F'_k = G_k L_k [ny][mstride]
+  void* E = nullptr;         //   and E'_k = G_k R_k [ny][mstride]
+  void* Phi = nullptr;       // forward segment transfer products [P][mstride]
+  void* Psi = nullptr;       // backward segment transfer products [P][mstride]
   void* inj = nullptr;       // injection coefficients [4][ny][3] (T row0, T row1, T~ row0, T~ row1)
   void* Y = nullptr;         // right-hand side, then forward solution rows [ny][n_rhs][wp]
   void* carry_f = nullptr;   // forward segment end values [P][n_rhs][wp]

@@ -280,7 +280,9 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
         S.W, S.lo, S.hi, S.wl, L.ax.a_node, L.ax.a_cell, L.ax.h_cell, h->p.s_pml_dd, h->c_pml,
         L.w, h->p.omega, S.ax.a_node, S.ax.a_cell, S.ax.h_cell, S.ax.a_node32, S.ax.a_cell32);
     // plane stride padded so that every plane row starts on a 16-byte boundary
-    S.wp = (sizeof(cplx<R>) >= 16) ? S.W : (S.W + 1) / 2 * 2;
+    // row stride = 4 (mod 8): rows start on 16-byte boundaries and the eight
+    // rows a warp reads in one substitution step fall on disjoint bank groups
+    S.wp = S.W + ((4 - S.W % 8) + 8) % 8;
     S.st = dmalloc(sizeof(cplx<R>) * (size_t)L.ny * 9 * S.wp);
     HZ_CU(cudaMemsetAsync(S.st, 0, sizeof(cplx<R>) * (size_t)L.ny * 9 * S.wp, s));
     S.inj = dmalloc(sizeof(cplx<R>) * 4 * (size_t)L.ny * 3);
@@ -306,6 +308,11 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
     if (elems16 < 1) elems16 = 1;
     S.gstride = (per + elems16 - 1) / elems16 * elems16;
     S.G = dmalloc(sizeof(cplx<R>) * S.gstride * L.ny);
+    S.mstride = (size_t)S.W * S.wp;
+    S.F = dmalloc(sizeof(cplx<R>) * S.mstride * L.ny);
+    S.E = dmalloc(sizeof(cplx<R>) * S.mstride * L.ny);
+    HZ_CU(cudaMemsetAsync(S.F, 0, sizeof(cplx<R>) * S.mstride * L.ny, s));   // zero padding
+    HZ_CU(cudaMemsetAsync(S.E, 0, sizeof(cplx<R>) * S.mstride * L.ny, s));
     S.Y = dmalloc(sizeof(cplx<R>) * (size_t)h->p.max_rhs * L.ny * S.wp);
   }
   // Twisted elimination: chains from rows 0 and ny-1 meet at row mid.  Each
@@ -337,10 +344,12 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
   HZ_CU(cudaMemcpyAsync(L.seg_dev, L.seg.data(), sizeof(int4) * P, cudaMemcpyHostToDevice, s));
   for (int j = 1; j <= L.J; ++j) {
     Slab& S = L.slabs[j];
-    S.Phi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
-    S.Psi = dmalloc(sizeof(cplx<R>) * S.gstride * P);
+    S.Phi = dmalloc(sizeof(cplx<R>) * S.mstride * P);
+    S.Psi = dmalloc(sizeof(cplx<R>) * S.mstride * P);
     S.carry_f = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.wp);
     S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)(P + 1) * h->p.max_rhs * S.wp);
+    HZ_CU(cudaMemsetAsync(S.Phi, 0, sizeof(cplx<R>) * S.mstride * P, s));      // zero padding
+    HZ_CU(cudaMemsetAsync(S.Psi, 0, sizeof(cplx<R>) * S.mstride * P, s));
   }
   HZ_CU(cudaStreamSynchronize(s));
 }
@@ -355,7 +364,8 @@ void build_slabs(hz_handle* h, Level& L, cudaStream_t s) {
 void free_level(Level& L) {
   for (Slab& S : L.slabs) {
     free_axis(S.ax);
-    dfree(S.st); dfree(S.G); dfree(S.Phi); dfree(S.Psi); dfree(S.inj); dfree(S.Y);
+    dfree(S.st); dfree(S.G); dfree(S.F); dfree(S.E); dfree(S.Phi); dfree(S.Psi);
+    dfree(S.inj); dfree(S.Y);
     dfree(S.carry_f); dfree(S.carry_b);
   }
   L.slabs.clear();

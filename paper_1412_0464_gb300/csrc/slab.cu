@@ -161,11 +161,13 @@ __device__ __forceinline__ Tile tile_of(int W, int idx) {
   return t;
 }
 
-// dst = base - A B for W x W row-major operands in shared or global memory;
-// base may be null (zero) or alias dst.  The caller synchronises.
+// dst = base - A B for W x W row-major operands in shared or global memory
+// (A with row stride lda, the others W); base may be null (zero) or alias dst.
+// The caller synchronises.
 template <typename R, int TC>
 __device__ __forceinline__ void gemm_sub(const cplx<R>* A, const cplx<R>* B, const cplx<R>* base,
-                                         cplx<R>* dst, int W, const Tile& t) {
+                                         cplx<R>* dst, int W, const Tile& t, int lda = -1) {
+  if (lda < 0) lda = W;
   if (!t.own) return;
   const cplx<R> zero = mk<R>(0, 0);
   cplx<R> acc[4][TC];
@@ -176,7 +178,7 @@ __device__ __forceinline__ void gemm_sub(const cplx<R>* A, const cplx<R>* B, con
   for (int l = 0; l < W; ++l) {
     cplx<R> av[4], bv[TC];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = (t.i0 + a < W) ? A[(t.i0 + a) * W + l] : zero;
+    for (int a = 0; a < 4; ++a) av[a] = (t.i0 + a < W) ? A[(t.i0 + a) * lda + l] : zero;
 #pragma unroll
     for (int b = 0; b < TC; ++b) bv[b] = (t.j0 + b < W) ? B[l * W + t.j0 + b] : zero;
 #pragma unroll
@@ -592,16 +594,22 @@ __global__ void __launch_bounds__(kThreads) slab_middle_kernel(const MidDesc* de
   gj_inverse<R, RPW, CPL>(S, Gl, w, W, su, G + (size_t)m * d.gstride);
 }
 
-// Segment transfer products for the parallel substitution (one CTA per slab,
-// segment and direction).  Along a segment's chain positions t = 0..n-1:
-//   forward  F_t = -G_t L_t,  Phi = F_{n-1} ... F_0
-//   backward E_t = -G_t R_t,  Psi = E_0 ... E_{n-1}
+// Substitution operators and segment transfer products (one CTA per slab,
+// segment and direction; all independent).  Along a segment's chain positions
+// t = 0..n-1 the CTA forms and stores
+//   forward  F'_t = G_t L_t   (y_t = g_t - F'_t y_{t-1})
+//   backward E'_t = G_t R_t   (x_t = y_t - E'_t x_{t+1})
+// (L_t / R_t: the tridiagonal coupling of row k_t to the previous / next row
+// of its chain), and, if `chain`, the segment products
+//   Phi = (-F'_{n-1}) ... (-F'_0),   Psi = (-E'_0) ... (-E'_{n-1}).
 struct ProdDesc {
-  int W, wp, k0, n, dir, backward;
+  int W, wp, k0, n, dir, backward, chain;
+  int stage;                 // 1: A_t also kept in shared memory for the GEMM
   const void* st;
-  const void* G;
-  size_t gstride;
-  void* out;
+  const void* G;             // [ny][gstride], dense W x W
+  void* A;                   // F' (forward) or E' (backward), [ny][mstride], row stride wp
+  size_t gstride, mstride;
+  void* out;                 // Phi or Psi block, row stride wp
 };
 
 template <typename R, int TC>
@@ -614,10 +622,13 @@ __global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDes
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* M = (cplx<R>*)smem_raw;
   cplx<R>* T = M + WW;
-  cplx<R>* cp = T + WW;         // coupling (3 x W)
+  cplx<R>* cp = T + WW;               // coupling (3 x W)
+  cplx<R>* As = cp + 3 * W;           // A_t (if d.stage)
   const cplx<R> zero = mk<R>(0, 0);
-  for (int e = tid; e < WW; e += kThreads) M[e] = (e / W == e % W) ? mk<R>(1, 0) : zero;
   const int plane = d.backward ? rplane(d.dir) : lplane(d.dir);
+  if (d.chain) {
+    for (int e = tid; e < WW; e += kThreads) M[e] = (e / W == e % W) ? mk<R>(1, 0) : zero;
+  }
   for (int s = 0; s < d.n; ++s) {
     const int t = d.backward ? d.n - 1 - s : s;
     const int k = d.k0 + d.dir * t;
@@ -626,22 +637,33 @@ __global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDes
       cp[i] = st[(size_t)k * 9 * wp + (plane + q) * wp + e];
     }
     __syncthreads();
-    for (int e = tid; e < WW; e += kThreads) {        // T = coupling_t M
+    const cplx<R>* Gk = G + (size_t)k * d.gstride;
+    cplx<R>* Ak = (cplx<R>*)d.A + (size_t)k * d.mstride;
+    for (int e = tid; e < WW; e += kThreads) {        // A_t = G_t Cpl_t
       const int i = e / W, j = e - i * W;
       cplx<R> acc = zero;
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
-        const int rr = i + dx;
-        if (rr >= 0 && rr < W) cfma(acc, cp[(dx + 1) * W + i], M[rr * W + j]);
+        const int c = j - dx;
+        if (c >= 0 && c < W) cfma(acc, Gk[i * W + c], cp[(dx + 1) * W + c]);
       }
-      T[e] = acc;
+      if (d.stage) As[e] = acc;
+      Ak[i * wp + j] = acc;
     }
     __syncthreads();
-    gemm_sub<R, TC>(G + (size_t)k * d.gstride, T, nullptr, M, W, tl);   // M = -G_t T
-    __syncthreads();
+    if (d.chain) {                                   // T = -A_t M
+      if (d.stage) gemm_sub<R, TC>(As, M, nullptr, T, W, tl);
+      else gemm_sub<R, TC>(Ak, M, nullptr, T, W, tl, wp);
+      __syncthreads();
+      cplx<R>* x = M;
+      M = T;
+      T = x;
+    }
   }
-  cplx<R>* out = (cplx<R>*)d.out;
-  for (int e = tid; e < WW; e += kThreads) out[e] = M[e];
+  if (d.chain) {
+    cplx<R>* out = (cplx<R>*)d.out;
+    for (int e = tid; e < WW; e += kThreads) out[(e / W) * wp + e % W] = M[e];
+  }
 }
 
 // ------------------------------------------------------------------ solves
@@ -679,10 +701,13 @@ struct SolveArgs {
   int P, S0, mid;             // segments (the first S0 on the top chain), meeting row
   const int4* seg;            // per segment: first row, rows, direction (+1 top, -1 bottom)
   const cplx<R>* st;          // [ny][9][wp]
-  const cplx<R>* G;           // [ny][gstride]
-  size_t gstride;
+  const cplx<R>* G;           // [ny][gstride]: G_k = S_k^-1
+  const cplx<R>* F;           // [ny][mstride]: F'_k = G_k L_k (coupling to the previous chain row)
+  const cplx<R>* E;           // [ny][mstride]: E'_k = G_k R_k (coupling to the next chain row)
+  size_t gstride;             // elements per G block (W x W)
+  size_t mstride;             // elements per F', E', Phi, Psi block (W rows of stride wp)
   int stages;
-  cplx<R>* Y;                 // [ny][nr][wp]: gathered right-hand side, then forward rows
+  cplx<R>* Y;                 // [ny][nr][wp]: G_k f_k, then forward rows y_k
   cplx<R>* carry_f;           // [P][nr][wp]: segment end values of the forward recurrence
   cplx<R>* carry_b;           // [P+1][nr][wp]: segment start values of the backward one; [P]: x_m
   int* flag;
@@ -719,7 +744,7 @@ __device__ __forceinline__ cplx<R> rhs_at(const Rhs<R>& q, int ny, int W, int nr
   return v;
 }
 
-// Pipeline stage: [G_k (gstride) | coupling row (3 wp) | vector row (nr wp)].
+// Pipeline stage: [matrix (gstride) | vector row (nr wp)].
 template <typename R>
 struct Pipe {
   uint64_t* bar;
@@ -728,19 +753,16 @@ struct Pipe {
   size_t stage_elems, gstride;
   int wp, nr;
   __device__ cplx<R>* slot(int i) const { return buf + (size_t)i * stage_elems; }
-  // thread 0 only: fetch block row k (coupling plane 0 = C_k or 6 = B_k)
-  // (rows == nullptr: G_k and the coupling row only)
-  __device__ void issue(int i, int k, const cplx<R>* G, const cplx<R>* st, int plane,
-                        const cplx<R>* rows) const {
-    const uint32_t gb = (uint32_t)(gstride * sizeof(cplx<R>));
-    const uint32_t cb = (uint32_t)(3 * wp * sizeof(cplx<R>));
+  // thread 0 only: fetch the matrix of block row k and, if `rows` is given,
+  // the vector row k of rows
+  __device__ void issue(int i, int k, const cplx<R>* M, const cplx<R>* rows) const {
+    const uint32_t mb = (uint32_t)(gstride * sizeof(cplx<R>));
     const uint32_t vb = rows ? (uint32_t)((size_t)nr * wp * sizeof(cplx<R>)) : 0u;
     cplx<R>* dst = slot(i);
     fence_proxy_async_smem();
-    mbar_expect_tx(&bar[i], gb + cb + vb);
-    tma_load_1d(dst, G + (size_t)k * gstride, gb, &bar[i]);
-    tma_load_1d(dst + gstride, st + (size_t)k * 9 * wp + plane * wp, cb, &bar[i]);
-    if (rows) tma_load_1d(dst + gstride + 3 * wp, rows + (size_t)k * nr * wp, vb, &bar[i]);
+    mbar_expect_tx(&bar[i], mb + vb);
+    tma_load_1d(dst, M + (size_t)k * gstride, mb, &bar[i]);
+    if (rows) tma_load_1d(dst + gstride, rows + (size_t)k * nr * wp, vb, &bar[i]);
   }
 };
 
@@ -782,42 +804,108 @@ __device__ __forceinline__ void gemv_rows(const cplx<R>* M, int ldm, const cplx<
   }
 }
 
+// gemv_rows for matrices and vectors of row stride ldm = ldv = wp (wp = 4 mod
+// 8, zero beyond W): complex64 entries are read in pairs (128-bit loads).
+// With wp = 4 mod 8 the eight rows a warp reads at once fall on disjoint
+// bank groups, so every load takes the minimum number of wavefronts.
+template <typename R, int NR>
+__device__ __forceinline__ void gemv_op(const cplx<R>* M, int ldm, const cplx<R>* v, int ldv,
+                                        int W, int nr, int row, int lane, cplx<R> (&acc)[NR]) {
+  if constexpr (sizeof(R) == 4) {
+    float ar[NR], ai[NR], br[NR], bi[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) { ar[r] = 0.f; ai[r] = 0.f; br[r] = 0.f; bi[r] = 0.f; }
+    if (row < W) {
+      const float4* Mr = reinterpret_cast<const float4*>(M + (size_t)row * ldm);
+      const int npair = ldm >> 1;
+      for (int p = lane; p < npair; p += kTPR) {
+        const float4 m = Mr[p];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r >= nr) break;
+          const float4 x = reinterpret_cast<const float4*>(v + (size_t)r * ldv)[p];
+          ar[r] += m.x * x.x - m.y * x.y;
+          ai[r] += m.x * x.y + m.y * x.x;
+          br[r] += m.z * x.z - m.w * x.w;
+          bi[r] += m.z * x.w + m.w * x.z;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      acc[r] = mk<R>(ar[r] + br[r], ai[r] + bi[r]);
+#pragma unroll
+      for (int o = kTPR / 2; o > 0; o >>= 1) {
+        acc[r].re += __shfl_xor_sync(0xffffffffu, acc[r].re, o);
+        acc[r].im += __shfl_xor_sync(0xffffffffu, acc[r].im, o);
+      }
+    }
+  } else {
+    gemv_rows<R, NR>(M, ldm, v, ldv, W, nr, row, lane, acc);
+  }
+}
+
+// Shared memory of the substitution kernels: barriers, two NR x wp vectors
+// (the recurrence value, double-buffered so that a step needs one block
+// barrier), then the pipeline stages.
 template <typename R>
 __device__ __forceinline__ void init_pipe(Pipe<R>& pipe, unsigned char* smem, const SolveArgs<R>& a,
-                                          int NR, cplx<R>** vbuf, cplx<R>** ybuf) {
+                                          int NR, cplx<R>** vec) {
   pipe.bar = (uint64_t*)smem;
-  *vbuf = (cplx<R>*)(smem + 128);
-  *ybuf = *vbuf + NR * a.wp;
-  cplx<R>* b = *ybuf + NR * a.wp;
+  *vec = (cplx<R>*)(smem + 128);
+  cplx<R>* b = *vec + 2 * NR * a.wp;
   pipe.buf = (cplx<R>*)(((uintptr_t)b + 127) & ~(uintptr_t)127);
   pipe.stages = a.stages;
-  pipe.gstride = a.gstride;
+  pipe.gstride = a.mstride;
   pipe.wp = a.wp;
   pipe.nr = a.nr;
-  pipe.stage_elems = a.gstride + 3 * (size_t)a.wp + (size_t)a.nr * a.wp;
+  pipe.stage_elems = a.mstride + (size_t)a.nr * a.wp;
 }
 
 // SubdomSolve (Table 2): the slab right-hand side (gather + transmission
-// injection) into the rows Y[k][r][0..wp).  A kernel of its own, so that the
-// TMA reads of these rows in the next launch see them.
-template <typename R>
-__global__ void slab_gather_kernel(SolveArgs<R> a) {
-  const int rowlen = a.nr * a.wp;
-  const size_t total = (size_t)a.ny * rowlen;
-  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int k = (int)(idx / rowlen), rem = (int)(idx - (size_t)k * rowlen);
-  const int r = rem / a.wp, e = rem - r * a.wp;
-  a.Y[idx] = (e < a.W) ? rhs_at<R>(a.rhs, a.ny, a.W, a.nr, r, k, e) : mk<R>(0, 0);
+// injection) of block row k, premultiplied by its factor block: Y[k] =
+// G_k f_k (the meeting row keeps f_m).  One CTA per block row; every row is
+// independent.
+template <typename R, int NR>
+__global__ void __launch_bounds__(kThreads) slab_rhs_kernel(SolveArgs<R> a) {
+  const int k = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr;
+  const int nthr = blockDim.x, ngroups = nthr / kTPR;
+  const int grp = tid / kTPR, lane = tid % kTPR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* f = (cplx<R>*)smem_raw;   // NR x wp
+  for (int i = tid; i < NR * wp; i += nthr) {
+    const int r = i / wp, e = i - r * wp;
+    f[i] = (r < nr && e < W) ? rhs_at<R>(a.rhs, a.ny, W, nr, r, k, e) : mk<R>(0, 0);
+  }
+  __syncthreads();
+  cplx<R>* Yk = a.Y + (size_t)k * nr * wp;
+  if (k == a.mid) {
+    for (int i = tid; i < nr * wp; i += nthr) Yk[i] = f[i];
+    return;
+  }
+  cplx<R> acc[NR];
+  const cplx<R>* Gk = a.G + (size_t)k * a.gstride;
+  for (int rb = 0; rb < W; rb += ngroups) {
+    const int row = rb + grp;
+    gemv_rows<R, NR>(Gk, W, f, wp, W, nr, row, lane, acc);
+    if (lane == 0 && row < W)
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < nr) Yk[r * wp + row] = acc[r];
+  }
+  if (tid < nr * (wp - W)) {            // padding columns
+    const int r = tid / (wp - W), e = W + tid % (wp - W);
+    Yk[r * wp + e] = mk<R>(0, 0);
+  }
 }
 
 // Forward recurrence over segment s along its chain, t = 0..n-1, rows
-// k_t = k0 + dir t:  y_t = G_t (f_t - L_t y_{t-1}).
+// k_t = k0 + dir t:  y_t = g_t - F'_t y_{t-1}  (g_t = G_t f_t, F'_t = G_t L_t).
 //   mode 0: zero start, store only the last y into carry_f[s];
 //   mode 1: start from carry_f[s-1] (zero for the first segment of each
-//           half), store every y into Y (over the right-hand side); if bwd1,
-//           then run the backward recurrence x_t = y_t - G_t R_t x_{t+1} over
-//           the segment from a zero start and store x_0 into carry_b[s].
+//           half), store every y into Y (over g); if bwd1, then run the
+//           backward recurrence x_t = y_t - E'_t x_{t+1} (E'_t = G_t R_t)
+//           over the segment from a zero start and store x_0 into carry_b[s].
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int mode, int bwd1) {
   const int s = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr;
@@ -828,82 +916,68 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   Pipe<R> pipe;
-  cplx<R>* vbuf;
-  cplx<R>* ybuf;
-  init_pipe<R>(pipe, smem_raw, a, NR, &vbuf, &ybuf);
+  cplx<R>* vec;
+  init_pipe<R>(pipe, smem_raw, a, NR, &vec);
+  const int VS = NR * wp;
   const cplx<R> zero = mk<R>(0, 0);
   if (tid == 0) {
     sh_abort = 0;
     for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
     mbar_fence_init();
   }
-  for (int i = tid; i < NR * wp; i += nthr) {
+  // both buffers in full: the paired loads of the GEMV also read the padding
+  for (int i = tid; i < 2 * VS; i += nthr) {
     const int r = i / wp, e = i - r * wp;
-    ybuf[i] = (mode == 1 && !first && r < nr) ? a.carry_f[((size_t)(s - 1) * nr + r) * wp + e] : zero;
+    vec[i] = (i < VS && mode == 1 && !first && r < nr) ? a.carry_f[((size_t)(s - 1) * nr + r) * wp + e]
+                                                         : zero;
   }
   __syncthreads();
-  const int pl = lplane(dir), pr = rplane(dir);
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + dir * i, a.G, a.st, pl, a.Y);
+    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + dir * i, a.F, a.Y);
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
+  int cur = 0;
   for (int t = 0; t < n; ++t) {
     const int k = k0 + dir * t;
     const int slot = t % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
-    const cplx<R>* Gk = pipe.slot(slot);
-    const cplx<R>* Lk = Gk + pipe.gstride;
-    const cplx<R>* Fk = Lk + 3 * wp;
-    if (tid < W) {                       // v = f_t - L_t y_{t-1}
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r >= nr) break;
-        cplx<R> v = Fk[r * wp + tid];
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int ee = tid + dx;
-          if (ee >= 0 && ee < W) {
-            const cplx<R> c = Lk[(dx + 1) * wp + tid];
-            const cplx<R> y = ybuf[r * wp + ee];
-            v.re -= c.re * y.re - c.im * y.im;
-            v.im -= c.re * y.im + c.im * y.re;
-          }
-        }
-        vbuf[r * wp + tid] = v;
-      }
-    }
-    __syncthreads();
+    const cplx<R>* Mk = pipe.slot(slot);
+    const cplx<R>* gk = Mk + pipe.gstride;
+    const cplx<R>* yp = vec + cur * VS;
+    cplx<R>* yn = vec + (cur ^ 1) * VS;
     for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
-      gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
+      gemv_op<R, NR>(Mk, wp, yp, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (r >= nr) break;
-          ybuf[r * wp + row] = acc[r];
-          if (mode == 1) a.Y[((size_t)k * nr + r) * wp + row] = acc[r];
+          const cplx<R> y = gk[r * wp + row] - acc[r];
+          yn[r * wp + row] = y;
+          if (mode == 1) a.Y[((size_t)k * nr + r) * wp + row] = y;
         }
       }
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && t + pipe.stages < n) pipe.issue(slot, k + dir * pipe.stages, a.G, a.st, pl, a.Y);
+    cur ^= 1;
+    if (tid == 0 && t + pipe.stages < n) pipe.issue(slot, k + dir * pipe.stages, a.F, a.Y);
   }
   if (mode == 0) {
-    for (int i = tid; i < nr * wp; i += nthr) a.carry_f[(size_t)s * nr * wp + i] = ybuf[i];
+    for (int i = tid; i < nr * wp; i += nthr) a.carry_f[(size_t)s * nr * wp + i] = vec[cur * VS + i];
     return;
   }
   if (!bwd1) return;
   // Backward recurrence from a zero start.  The y rows were written above by
   // this CTA (generic stores); they are read with ordinary loads, one step
-  // ahead, never through TMA; the pipeline brings only G_t and R_t.
-  for (int i = tid; i < NR * wp; i += nthr) ybuf[i] = zero;   // x_n
+  // ahead, never through TMA; the pipeline brings only E'_t.
+  for (int i = tid; i < VS; i += nthr) vec[cur * VS + i] = zero;   // x_n
   __syncthreads();
   if (tid == 0)
     for (int i = 0; i < pipe.stages && i < n; ++i)
-      pipe.issue(i, k0 + dir * (n - 1 - i), a.G, a.st, pr, nullptr);
+      pipe.issue(i, k0 + dir * (n - 1 - i), a.E, nullptr);
   cplx<R> ynext[NR];
   {
     const int row0 = grp;   // rows handled by this group in the first pass over rb
@@ -918,22 +992,9 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
     const int slot = q % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
-    const cplx<R>* Gk = pipe.slot(slot);
-    const cplx<R>* Rk = Gk + pipe.gstride;
-    if (tid < W) {                       // w = R_t x_{t+1}
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r >= nr) break;
-        cplx<R> v = zero;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int ee = tid + dx;
-          if (ee >= 0 && ee < W) cfma(v, Rk[(dx + 1) * wp + tid], ybuf[r * wp + ee]);
-        }
-        vbuf[r * wp + tid] = v;
-      }
-    }
-    __syncthreads();
+    const cplx<R>* Mk = pipe.slot(slot);
+    const cplx<R>* xp = vec + cur * VS;
+    cplx<R>* xn = vec + (cur ^ 1) * VS;
     for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
       cplx<R> ycur[NR];
@@ -951,21 +1012,21 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
         for (int r = 0; r < NR; ++r)
           ycur[r] = (lane == 0 && row < W && r < nr) ? a.Y[((size_t)k * nr + r) * wp + row] : zero;
       }
-      gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
+      gemv_op<R, NR>(Mk, wp, xp, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (r >= nr) break;
-          ybuf[r * wp + row] = ycur[r] - acc[r];
+          xn[r * wp + row] = ycur[r] - acc[r];
         }
       }
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && q + pipe.stages < n)
-      pipe.issue(slot, k - dir * pipe.stages, a.G, a.st, pr, nullptr);
+    cur ^= 1;
+    if (tid == 0 && q + pipe.stages < n) pipe.issue(slot, k - dir * pipe.stages, a.E, nullptr);
   }
-  for (int i = tid; i < nr * wp; i += nthr) a.carry_b[(size_t)s * nr * wp + i] = ybuf[i];
+  for (int i = tid; i < nr * wp; i += nthr) a.carry_b[(size_t)s * nr * wp + i] = vec[cur * VS + i];
 }
 
 // Epilogue of Table 2 for one solution entry x at block row k, local column row.
@@ -993,66 +1054,53 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   Pipe<R> pipe;
-  cplx<R>* vbuf;
-  cplx<R>* xbuf;
-  init_pipe<R>(pipe, smem_raw, a, NR, &vbuf, &xbuf);
+  cplx<R>* vec;
+  init_pipe<R>(pipe, smem_raw, a, NR, &vec);
+  const int VS = NR * wp;
   const cplx<R> zero = mk<R>(0, 0);
   if (tid == 0) {
     sh_abort = 0;
     for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
     mbar_fence_init();
   }
-  for (int i = tid; i < NR * wp; i += nthr) {
+  for (int i = tid; i < 2 * VS; i += nthr) {   // both buffers (padding is read)
     const int r = i / wp, e = i - r * wp;
-    xbuf[i] = (r < nr) ? a.carry_b[((size_t)from * nr + r) * wp + e] : zero;
+    vec[i] = (i < VS && r < nr) ? a.carry_b[((size_t)from * nr + r) * wp + e] : zero;
   }
   __syncthreads();
-  const int pr = rplane(dir);
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i)
-      pipe.issue(i, k0 + dir * (n - 1 - i), a.G, a.st, pr, a.Y);
+    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + dir * (n - 1 - i), a.E, a.Y);
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
+  int cur = 0;
   for (int q = 0; q < n; ++q) {
     const int t = n - 1 - q;
     const int k = k0 + dir * t;
     const int slot = q % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
-    const cplx<R>* Gk = pipe.slot(slot);
-    const cplx<R>* Rk = Gk + pipe.gstride;
-    const cplx<R>* Yk = Rk + 3 * wp;
-    if (tid < W) {
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r >= nr) break;
-        cplx<R> v = zero;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int ee = tid + dx;
-          if (ee >= 0 && ee < W) cfma(v, Rk[(dx + 1) * wp + tid], xbuf[r * wp + ee]);
-        }
-        vbuf[r * wp + tid] = v;
-      }
-    }
-    __syncthreads();
+    const cplx<R>* Mk = pipe.slot(slot);
+    const cplx<R>* yk = Mk + pipe.gstride;
+    const cplx<R>* xp = vec + cur * VS;
+    cplx<R>* xn = vec + (cur ^ 1) * VS;
     for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
-      gemv_rows<R, NR>(Gk, W, vbuf, wp, W, nr, row, lane, acc);
+      gemv_op<R, NR>(Mk, wp, xp, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (r >= nr) break;
-          const cplx<R> x = Yk[r * wp + row] - acc[r];
-          xbuf[r * wp + row] = x;
+          const cplx<R> x = yk[r * wp + row] - acc[r];
+          xn[r * wp + row] = x;
           store_out<R>(a.out, ny, W, nr, r, k, row, x);
         }
       }
     }
     __syncthreads();
     if (sh_abort) return;
-    if (tid == 0 && q + pipe.stages < n) pipe.issue(slot, k - dir * pipe.stages, a.G, a.st, pr, a.Y);
+    cur ^= 1;
+    if (tid == 0 && q + pipe.stages < n) pipe.issue(slot, k - dir * pipe.stages, a.E, a.Y);
   }
 }
 
@@ -1064,7 +1112,7 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
 //             X_s = xhat_s + Psi_s X_{s+1} from the half's last segment
 //             (X_{s+1} = x_m) back to its first (carry_b in place).
 // The products and the segment values come through a TMA pipeline:
-// stage = [M_s | carry row s].
+// stage = [M_s | carry row s]; the running value is double-buffered.
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, const cplx<R>* prod,
                                                               int backward) {
@@ -1075,13 +1123,14 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   uint64_t* bar = (uint64_t*)smem_raw;
-  cplx<R>* prev = (cplx<R>*)(smem_raw + 128);
-  cplx<R>* vtmp = prev + NR * wp;
-  cplx<R>* buf = (cplx<R>*)(((uintptr_t)(vtmp + NR * wp) + 127) & ~(uintptr_t)127);
-  const size_t se = a.gstride + (size_t)nr * wp;
+  cplx<R>* prev = (cplx<R>*)(smem_raw + 128);   // 2 x NR x wp
+  const int VS = NR * wp;
+  cplx<R>* vtmp = prev + 2 * VS;
+  cplx<R>* buf = (cplx<R>*)(((uintptr_t)(vtmp + VS) + 127) & ~(uintptr_t)127);
+  const size_t se = a.mstride + (size_t)nr * wp;
   const int stages = a.stages;
   cplx<R>* carry = backward ? a.carry_b : a.carry_f;
-  const uint32_t mb = (uint32_t)(a.gstride * sizeof(cplx<R>));
+  const uint32_t mb = (uint32_t)(a.mstride * sizeof(cplx<R>));
   const uint32_t vb = (uint32_t)((size_t)nr * wp * sizeof(cplx<R>));
   // step i handles segment seg_of(i)
   const int nsteps = backward ? nh : nh - 1;
@@ -1090,8 +1139,8 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
     const int sg = seg_of(i);
     fence_proxy_async_smem();
     mbar_expect_tx(&bar[slot], mb + vb);
-    tma_load_1d(buf + (size_t)slot * se, prod + (size_t)sg * a.gstride, mb, &bar[slot]);
-    tma_load_1d(buf + (size_t)slot * se + a.gstride, carry + (size_t)sg * nr * wp, vb, &bar[slot]);
+    tma_load_1d(buf + (size_t)slot * se, prod + (size_t)sg * a.mstride, mb, &bar[slot]);
+    tma_load_1d(buf + (size_t)slot * se + a.mstride, carry + (size_t)sg * nr * wp, vb, &bar[slot]);
   };
   const cplx<R> zero = mk<R>(0, 0);
   if (tid == 0) {
@@ -1101,16 +1150,17 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
   }
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
+  for (int i = tid; i < 2 * VS; i += nthr) prev[i] = zero;   // both buffers (padding is read)
+  __syncthreads();
   if (!backward) {
-    for (int i = tid; i < NR * wp; i += nthr)
-      prev[i] = (i < nr * wp) ? a.carry_f[(size_t)s_first * nr * wp + i] : zero;
+    for (int i = tid; i < nr * wp; i += nthr) prev[i] = a.carry_f[(size_t)s_first * nr * wp + i];
   } else {
     // meeting row: v = f_m - C_m y_{m-1} - B_m y_{m+1}, x_m = G_m v
     const int m = a.mid;
     const cplx<R>* stm = a.st + (size_t)m * 9 * wp;
     const cplx<R>* yu = a.carry_f + (size_t)(a.S0 - 1) * nr * wp;
     const cplx<R>* yd = a.carry_f + (size_t)(P - 1) * nr * wp;
-    for (int i = tid; i < NR * wp; i += nthr) {
+    for (int i = tid; i < VS; i += nthr) {
       const int r = i / wp, e = i - r * wp;
       cplx<R> v = zero;
       if (r < nr && e < W) {
@@ -1134,51 +1184,43 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
         for (int r = 0; r < NR; ++r)
           if (r < nr) {
             prev[r * wp + row] = acc[r];
-            if (h == 0) {
-              a.carry_b[((size_t)P * nr + r) * wp + row] = acc[r];
-              store_out<R>(a.out, a.ny, W, nr, r, m, row, acc[r]);
-            }
+            if (h == 0) store_out<R>(a.out, a.ny, W, nr, r, m, row, acc[r]);
           }
     }
-    for (int i = tid; i < NR * wp; i += nthr) {   // padding and unused right-hand sides
-      const int r = i / wp, e = i - r * wp;
-      if (r >= nr || e >= W) prev[i] = zero;
-    }
+    __syncthreads();
+    if (h == 0)   // the whole row, zero padding included
+      for (int i = tid; i < nr * wp; i += nthr) a.carry_b[(size_t)P * nr * wp + i] = prev[i];
   }
   __syncthreads();
   if (tid == 0)
     for (int i = 0; i < stages && i < nsteps; ++i) issue(i, i);
   uint32_t phase_bits = 0;
+  int cur = 0;
   for (int i = 0; i < nsteps; ++i) {
     const int sg = seg_of(i);
     const int slot = i % stages;
     if (!mbar_wait(&bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
-    __syncthreads();
-    if (sh_abort) return;
     const cplx<R>* M = buf + (size_t)slot * se;
-    const cplx<R>* hat = M + a.gstride;
-    cplx<R> res[NR];
-    int myrow = -1;
+    const cplx<R>* hat = M + a.mstride;
+    const cplx<R>* pp = prev + cur * VS;
+    cplx<R>* pn = prev + (cur ^ 1) * VS;
     for (int rb = 0; rb < W; rb += ngroups) {
       const int row = rb + grp;
-      gemv_rows<R, NR>(M, W, prev, wp, W, nr, row, lane, acc);
+      gemv_op<R, NR>(M, wp, pp, wp, W, nr, row, lane, acc);
       if (lane == 0 && row < W) {
-        myrow = row;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) res[r] = (r < nr) ? hat[r * wp + row] + acc[r] : zero;
-      }
-    }
-    __syncthreads();   // everyone has read prev
-    if (myrow >= 0) {
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r >= nr) break;
-        prev[r * wp + myrow] = res[r];
-        carry[((size_t)sg * nr + r) * wp + myrow] = res[r];
+        for (int r = 0; r < NR; ++r) {
+          if (r >= nr) break;
+          const cplx<R> res = hat[r * wp + row] + acc[r];
+          pn[r * wp + row] = res;
+          carry[((size_t)sg * nr + r) * wp + row] = res;
+        }
       }
     }
     __syncthreads();
+    if (sh_abort) return;
+    cur ^= 1;
     if (tid == 0 && i + stages < nsteps) issue(slot, i + stages);
   }
 }
@@ -1188,14 +1230,14 @@ template <typename R>
 static size_t solve_smem(const Slab& S, int nr, int NR, int stages) {
   const size_t el = sizeof(cplx<R>);
   size_t fixed = 128 + 2 * (size_t)NR * S.wp * el + 128;
-  size_t stage = (S.gstride + 3 * (size_t)S.wp + (size_t)nr * S.wp) * el;
+  size_t stage = (S.mstride + (size_t)nr * S.wp) * el;
   return fixed + (size_t)stages * stage;
 }
 
 template <typename R>
 static size_t carry_smem(const Slab& S, int nr, int NR, int stages) {
   const size_t el = sizeof(cplx<R>);
-  return 128 + 2 * (size_t)NR * S.wp * el + 128 + (size_t)stages * (S.gstride + (size_t)nr * S.wp) * el;
+  return 128 + 3 * (size_t)NR * S.wp * el + 128 + (size_t)stages * (S.mstride + (size_t)nr * S.wp) * el;
 }
 
 constexpr size_t kSmemLimit = 225 * 1024;
@@ -1226,12 +1268,15 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   for (int j = 1; j <= J; ++j) maxW = std::max(maxW, L.slabs[j].W);
   const size_t smem_f = factor_smem_bytes(maxW, 9, el, BW);
   const size_t smem_m = factor_smem_bytes(maxW, 15, el, BW);
-  const size_t smem_p = (2 * (size_t)maxW * maxW + 3 * (size_t)maxW) * el;
+  // products: M, T, the couplings and, when it fits, A_t
+  const size_t smem_p2 = (2 * (size_t)maxW * maxW + 3 * (size_t)maxW) * el;
+  const int stage_a = smem_p2 + (size_t)maxW * maxW * el <= kSmemLimit ? 1 : 0;
+  const size_t smem_p = smem_p2 + (stage_a ? (size_t)maxW * maxW * el : 0);
   // delayed updates: rows per update warp (RPW) and columns per lane (CPL);
   // register tiles of the product GEMMs: 4 x 4 while they fit, else 4 x 8
   const int rpw = (maxW + kUpdateWarps - 1) / kUpdateWarps;
   const int TC = ((maxW + 3) / 4) * ((maxW + 3) / 4) <= kThreads ? 4 : 8;
-  if (maxW > 128 || rpw > 11 || smem_m > kSmemLimit)
+  if (maxW > 128 || rpw > 11 || smem_m > kSmemLimit || smem_p > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the blocked factorisation (W=" +
                                  std::to_string(maxW) + ")");
   std::vector<FactorDesc> fd;
@@ -1244,11 +1289,12 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
     md.push_back(MidDesc{S.W, S.wp, m, S.st, S.G, S.gstride});
     for (int q = 0; q < P; ++q) {
       const int4 sg = L.seg[q];
-      if (q != 0 && q != L.S0)      // Phi of the first segment of a half is never used
-        pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 0, S.st, S.G, S.gstride,
-                              (cplx<R>*)S.Phi + (size_t)q * S.gstride});
-      pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 1, S.st, S.G, S.gstride,
-                            (cplx<R>*)S.Psi + (size_t)q * S.gstride});
+      // (Phi of the first segment of a half is never used: operators only)
+      pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 0, (q != 0 && q != L.S0) ? 1 : 0,
+                            stage_a, S.st, S.G, S.F, S.gstride, S.mstride,
+                            (cplx<R>*)S.Phi + (size_t)q * S.mstride});
+      pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 1, 1, stage_a, S.st, S.G, S.E, S.gstride,
+                            S.mstride, (cplx<R>*)S.Psi + (size_t)q * S.mstride});
     }
   }
   const size_t b_fd = sizeof(FactorDesc) * fd.size(), b_md = sizeof(MidDesc) * md.size();
@@ -1295,6 +1341,7 @@ static void set_solve_attrs() {
   HZ_CU(cudaFuncSetAttribute(slab_fwd_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
   HZ_CU(cudaFuncSetAttribute(slab_bwd_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
   HZ_CU(cudaFuncSetAttribute(slab_carry_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  HZ_CU(cudaFuncSetAttribute(slab_rhs_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
   done = true;
 }
 
@@ -1309,7 +1356,6 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   const size_t smem = solve_smem<R>(S, nr, NR, a.stages);
   const double el = sizeof(cplx<R>);
   const double gbytes = (double)L.ny * S.W * S.W * el;          // one pass over G_0..G_{ny-1}
-  const double cbytes = (double)L.ny * 3 * S.W * el;            // one pass over the couplings
   const double vbytes = (double)nr * L.ny * S.W * el;           // one slab-sized vector
   const double pbytes = (double)P * S.W * S.W * el;             // one set of segment products
   auto T = [&](const char* tag, double bytes, auto&& fn) {
@@ -1317,26 +1363,25 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   };
   // one 4-thread group per row of G: round W * kTPR up to whole warps
   const int nthr = std::min(kThreads, std::max(128, (S.W * kTPR + 31) / 32 * 32));
-  const size_t gtotal = (size_t)L.ny * nr * S.wp;
   SolveArgs<R> ac = a;
   ac.stages = pick_carry_stages<R>(S, nr, NR);
   const size_t csm = carry_smem<R>(S, nr, NR, ac.stages);
-  T("slab_gather", 2 * vbytes, [&] {
-    slab_gather_kernel<R><<<cdiv(gtotal, 256), 256, 0, s>>>(a);
+  T("slab_rhs", gbytes + 2 * vbytes, [&] {
+    slab_rhs_kernel<R, NR><<<L.ny, nthr, (size_t)NR * S.wp * sizeof(cplx<R>), s>>>(a);
   });
-  T("slab_fwd_pass1", gbytes + cbytes + vbytes, [&] {
+  T("slab_fwd_pass1", gbytes + vbytes, [&] {
     slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 0, 0);
   });
   T("slab_carry", pbytes, [&] {
     slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, (const cplx<R>*)S.Phi, 0);
   });
-  T("slab_fwd_bwd1", 2 * gbytes + 2 * cbytes + 3 * vbytes, [&] {
+  T("slab_fwd_bwd1", 2 * gbytes + 3 * vbytes, [&] {
     slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 1, 1);
   });
   T("slab_carry", pbytes, [&] {
     slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, (const cplx<R>*)S.Psi, 1);
   });
-  T("slab_bwd", gbytes + cbytes + 2 * vbytes, [&] {
+  T("slab_bwd", gbytes + 2 * vbytes, [&] {
     slab_bwd_kernel<R, NR><<<P, nthr, smem, s>>>(a);
   });
   h->launches += 6;
@@ -1350,6 +1395,7 @@ static void run_solve(hz_handle* h, Level& L, Slab& S, const Rhs<R>& rhs, const 
   if (n_rhs < 1 || n_rhs > kNRMax) throw Failure(HZ_EINVAL, "right-hand sides per slab launch must be 1..8");
   SolveArgs<R> a;
   a.W = S.W; a.wp = S.wp; a.ny = L.ny; a.nr = n_rhs;
+  a.F = (const cplx<R>*)S.F; a.E = (const cplx<R>*)S.E; a.mstride = S.mstride;
   a.P = L.P; a.S0 = L.S0; a.mid = L.mid; a.seg = L.seg_dev;
   a.st = (const cplx<R>*)S.st; a.G = (const cplx<R>*)S.G; a.gstride = S.gstride;
   a.stages = 1;
