@@ -45,6 +45,9 @@ def _args():
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--workload", type=int, default=CONFIG_INDEX, choices=[1, 2, 3],
                     help="benchmark configuration (default 2, the headline workload)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="profiling only: the workload's recipe at this interior size (not a bench line)")
+    ap.add_argument("--J", type=int, default=0, help="profiling only: slab count with --n")
     return ap.parse_args()
 
 
@@ -61,6 +64,13 @@ def _peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def _sm_max_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 class ClockSampler:
@@ -168,6 +178,18 @@ def cpu_baseline(cfg, iters_hint):
             "time_to_solution_s_est": t_sol, "host_cores_available": os.cpu_count()}
 
 
+def replica_throughput(ms_step, dof_per_rank, ws, device):
+    """Whole-job Mdof/s of ws independent replicas: every rank solved dof_per_rank
+    unknowns; the job time is the slowest rank's (max over ranks)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms_step)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t)
+    return ms_step, ws * dof_per_rank / (ms_step / 1000.0) / 1e6
+
+
 def reference_arm(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -232,6 +254,8 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     cfg = synth.workload(args.workload)
+    if args.n:
+        cfg = synth.scaled_workload(args.workload, args.n, J=args.J or None)
     m = synth.medium(cfg)
     b = synth.sources(cfg)
     solver = hz.Solver.from_workload(cfg, m=m)
@@ -280,12 +304,7 @@ def main():
             "slab_factor", "slab_middle", "segment_product"]
     kt = {t: solver.kernel_timing(t) for t in tags}
     solver.enable_timing(False)
-    ms_step = total_ms / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t)
-    value = ws * cfg.ndof * cfg.n_src / (ms_step / 1000.0) / 1e6
+    ms_step, value = replica_throughput(total_ms / args.steps, cfg.ndof * cfg.n_src, ws, "cuda")
 
     # end to end through the C ABI with host buffers (pinned), copies included
     f_host = torch.from_numpy(b).pin_memory()
@@ -300,25 +319,52 @@ def main():
     e2e_ms = statistics.mean(e2e_ms[1:])
     nbytes = cfg.ndof * cfg.n_src * 16
 
-    # dominant slab kernel: the largest summed time among the per-kernel tags
+    # Roofline of the dominant kernel (largest summed device time over the
+    # timed steps).  The factorisation is bounded by FP32 arithmetic (complex64
+    # Gauss-Jordan, 8 W^3 flop per block row plus the 48 W^2 flop Schur update):
+    # peak = SMs x 128 FP32 lanes x 2 flop x maximum SM clock.  The substitution
+    # kernels are bounded by HBM: peak = the measured copy bandwidth.
     peak, peak_kind = _peaks()
     per_kernel = {t: {"ms": v[0], "launches": v[1], "bytes": v[2]} for t, v in kt.items() if v[1] > 0}
-    kernels = {t: v for t, v in per_kernel.items()
-               if t not in ("slab_solve", "slab_factor", "slab_middle", "segment_product")}
-    dom = max(kernels, key=lambda t: kernels[t]["ms"])
-    d = kernels[dom]
-    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
-    sol = per_kernel.get("slab_solve")
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": _traffic(dom),
+    widths = [solver.slab_info(j)["W"] for j in range(1, cfg.J + 1)]
+    ny_sweep = (cfg.n // 2 + 2 * cfg.w_out - 1) if cfg.two_grid else cfg.N
+    factor_flop = sum((ny_sweep - 1) * (8.0 * w ** 3 + 48.0 * w ** 2) for w in widths)
+    props = torch.cuda.get_device_properties(local)
+    sm_max = _sm_max_mhz()
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    indiv = {t: v for t, v in per_kernel.items() if t != "slab_solve"}
+    dom = max(indiv, key=lambda t: indiv[t]["ms"])
+    hbm_tags = [t for t in indiv if t not in ("slab_factor", "slab_middle", "segment_product")]
+    dom_hbm = max(hbm_tags, key=lambda t: indiv[t]["ms"])
+
+    def hbm_line(tag):
+        d = indiv[tag]
+        ach = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+        return {"bound": "hbm", "kernel": tag, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": _traffic(tag),
                 "avg_launch_us": 1000 * d["ms"] / d["launches"],
-                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"]}
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
+
+    if dom == "slab_factor":
+        d = indiv[dom]
+        ach = factor_flop / (d["ms"] / d["launches"] / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": ach / alu_peak,
+                    "peak_source": (f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x "
+                                    f"2 flop x {sm_max:.0f} MHz"),
+                    "traffic": _traffic(dom), "avg_launch_us": 1000 * d["ms"] / d["launches"],
+                    "algorithmic_flop_per_launch": factor_flop,
+                    "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
+        roofline["hbm_kernel"] = hbm_line(dom_hbm)
+    else:
+        roofline = hbm_line(dom)
+    sol = per_kernel.get("slab_solve")
     if sol:
         roofline["slab_solve_sequence"] = {
             "achieved_gbs": sol["bytes"] / (sol["ms"] / 1000.0) / 1e9,
             "avg_us": 1000 * sol["ms"] / sol["launches"], "solves": sol["launches"],
-            "note": "whole subdomain solve (all its kernels), method-minimal bytes (G read twice)"}
+            "note": "whole subdomain solve (all its kernels), method-minimal bytes (operators read twice)"}
 
     line = {"metric": METRIC, "value": value, "unit": "Mdof/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
