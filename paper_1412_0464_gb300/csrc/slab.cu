@@ -34,6 +34,7 @@
 #include "hz_internal.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 namespace hz {
@@ -97,6 +98,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* f
   return true;
 }
 
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+__device__ __forceinline__ cplx<float> ldcg(const cplx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk(v.x, v.y);
+}
+__device__ __forceinline__ cplx<double> ldcg(const cplx<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk(v.x, v.y);
+}
+
 constexpr int kThreads = 512;
 constexpr int kTPR = 4;                 // threads cooperating on one row of a GEMV
 constexpr int kGroups = kThreads / kTPR;
@@ -113,8 +125,7 @@ constexpr int kNRMax = 8;               // right-hand sides per launch
 // panel columns only (shuffles, no block barrier), the pivot rows' other
 // columns follow from the short recurrence
 // rowmod_t = (S[r_t] - sum_{s<t} colmod_s[r_t] rowmod_s) inv_t, and all
-// threads apply the delayed rank-BW update S -= Cm^T R in 4 x TC register
-// tiles.  Three block barriers per panel.
+// threads apply the delayed rank-BW update S -= Cm^T R in row strips.
 __device__ __forceinline__ cplx<float> crcp(cplx<float> a) {
   const float d = __frcp_rn(a.re * a.re + a.im * a.im);
   return mk(a.re * d, -a.im * d);
@@ -129,12 +140,6 @@ __device__ __forceinline__ cplx<double> crcp(cplx<double> a) {
 template <typename R>
 struct FactorPanel { static constexpr int BW = 4; };
 
-// Register tile of one thread in a W x W product or update: rows i0..i0+3,
-// columns j0..j0+TC-1.
-struct Tile {
-  bool own;
-  int i0, j0;
-};
 // Warps of the delayed Gauss-Jordan updates: those that do not share a
 // scheduler with warp 0 (warp w runs on sub-partition w mod 4), so that the
 // panel warp keeps its issue slots while the update runs beside it.  Each
@@ -151,47 +156,43 @@ __device__ __forceinline__ Strip strip_of(int tid) {
   return s;
 }
 
-template <int TC>
-__device__ __forceinline__ Tile tile_of(int W, int idx) {
-  const int ntc = (W + TC - 1) / TC, ntr = (W + 3) / 4;
-  Tile t;
-  t.own = idx >= 0 && idx < ntr * ntc;
-  t.i0 = t.own ? (idx / ntc) * 4 : 0;
-  t.j0 = t.own ? (idx % ntc) * TC : 0;
-  return t;
-}
-
-// dst = base - A B for W x W row-major operands in shared or global memory
-// (A with row stride lda, the others W); base may be null (zero) or alias dst.
-// The caller synchronises.
-template <typename R, int TC>
-__device__ __forceinline__ void gemm_sub(const cplx<R>* A, const cplx<R>* B, const cplx<R>* base,
-                                         cplx<R>* dst, int W, const Tile& t, int lda = -1) {
-  if (lda < 0) lda = W;
-  if (!t.own) return;
+// dst = -A B for W x W operands (A with row stride lda in shared or global
+// memory, B and dst dense W x W in shared memory), all kThreads threads: warp w
+// takes rows w*RPW .. w*RPW+RPW-1, lane l takes columns l, l+32, ... (CPL of
+// them).  A reads are broadcasts and B / dst accesses are consecutive across
+// the warp, so no shared-memory access conflicts.  The caller synchronises.
+template <typename R, int RPW, int CPL>
+__device__ __forceinline__ void gemm_strip_neg(const cplx<R>* A, int lda, const cplx<R>* B,
+                                               cplx<R>* dst, int W) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = warp * RPW;
+  if (i0 >= W) return;
   const cplx<R> zero = mk<R>(0, 0);
-  cplx<R> acc[4][TC];
+  cplx<R> acc[RPW][CPL];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RPW; ++a)
 #pragma unroll
-    for (int b = 0; b < TC; ++b) acc[a][b] = zero;
+    for (int b = 0; b < CPL; ++b) acc[a][b] = zero;
   for (int l = 0; l < W; ++l) {
-    cplx<R> av[4], bv[TC];
+    cplx<R> bv[CPL];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = (t.i0 + a < W) ? A[(t.i0 + a) * lda + l] : zero;
+    for (int b = 0; b < CPL; ++b) {
+      const int j = lane + 32 * b;
+      bv[b] = (j < W) ? B[l * W + j] : zero;
+    }
 #pragma unroll
-    for (int b = 0; b < TC; ++b) bv[b] = (t.j0 + b < W) ? B[l * W + t.j0 + b] : zero;
+    for (int a = 0; a < RPW; ++a) {
+      const cplx<R> av = (i0 + a < W) ? A[(i0 + a) * lda + l] : zero;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < TC; ++b) cfma(acc[a][b], av[a], bv[b]);
+      for (int b = 0; b < CPL; ++b) cfma(acc[a][b], av, bv[b]);
+    }
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RPW; ++a)
 #pragma unroll
-    for (int b = 0; b < TC; ++b) {
-      const int i = t.i0 + a, j = t.j0 + b;
-      if (i < W && j < W) dst[i * W + j] = base ? base[i * W + j] - acc[a][b] : -acc[a][b];
+    for (int b = 0; b < CPL; ++b) {
+      const int i = i0 + a, j = lane + 32 * b;
+      if (i < W && j < W) dst[i * W + j] = -acc[a][b];
     }
 }
 
@@ -459,9 +460,20 @@ struct FactorDesc {
 __host__ __device__ __forceinline__ int lplane(int dir) { return dir > 0 ? 0 : 6; }
 __host__ __device__ __forceinline__ int rplane(int dir) { return dir > 0 ? 6 : 0; }
 
+// Release store / acquire load of a progress counter (gpu scope).
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One elimination chain; if `progress` is given, the number of finished rows
+// is published there (release) after each G_t is stored.
 template <typename R, int RPW, int CPL>
-__global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc* descs) {
-  const FactorDesc d = descs[blockIdx.x];
+__device__ void factor_chain(const FactorDesc& d, int* progress) {
   const int W = d.W, wp = d.wp, tid = threadIdx.x, dir = d.dir;
   const int WW = W * W;
   const Strip su = strip_of<RPW>(tid);
@@ -523,7 +535,16 @@ __global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc*
     }
     __syncthreads();
     gj_inverse<R, RPW, CPL>(S, Gl, w, W, su, G + (size_t)k * d.gstride);
+    if (progress && tid == 0) {   // every thread's G_t stores precede the barrier above
+      __threadfence();
+      st_release(progress, t + 1);
+    }
   }
+}
+
+template <typename R, int RPW, int CPL>
+__global__ void __launch_bounds__(kThreads) slab_factor_kernel(const FactorDesc* descs) {
+  factor_chain<R, RPW, CPL>(descs[blockIdx.x], nullptr);
 }
 
 // sum_{dx, dy} Lc[dx][i] X[i+dx][j-dy] Rc[dy][j-dy]: (L X R)[i][j] for
@@ -605,6 +626,7 @@ __global__ void __launch_bounds__(kThreads) slab_middle_kernel(const MidDesc* de
 struct ProdDesc {
   int W, wp, k0, n, dir, backward, chain;
   int stage;                 // 1: A_t also kept in shared memory for the GEMM
+  int fchain, need;          // elimination chain of the rows and rows it must have finished
   const void* st;
   const void* G;             // [ny][gstride], dense W x W
   void* A;                   // F' (forward) or E' (backward), [ny][mstride], row stride wp
@@ -612,11 +634,9 @@ struct ProdDesc {
   void* out;                 // Phi or Psi block, row stride wp
 };
 
-template <typename R, int TC>
-__global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDesc* descs) {
-  const ProdDesc d = descs[blockIdx.x];
+template <typename R, int RPW, int CPL>
+__device__ void product_task(const ProdDesc& d) {
   const int W = d.W, wp = d.wp, tid = threadIdx.x, WW = W * W;
-  const Tile tl = tile_of<TC>(W, tid);
   const cplx<R>* st = (const cplx<R>*)d.st;
   const cplx<R>* G = (const cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -645,15 +665,15 @@ __global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDes
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         const int c = j - dx;
-        if (c >= 0 && c < W) cfma(acc, Gk[i * W + c], cp[(dx + 1) * W + c]);
+        if (c >= 0 && c < W) cfma(acc, ldcg(Gk + i * W + c), cp[(dx + 1) * W + c]);
       }
       if (d.stage) As[e] = acc;
       Ak[i * wp + j] = acc;
     }
     __syncthreads();
     if (d.chain) {                                   // T = -A_t M
-      if (d.stage) gemm_sub<R, TC>(As, M, nullptr, T, W, tl);
-      else gemm_sub<R, TC>(Ak, M, nullptr, T, W, tl, wp);
+      if (d.stage) gemm_strip_neg<R, RPW, CPL>(As, W, M, T, W);
+      else gemm_strip_neg<R, RPW, CPL>(Ak, wp, M, T, W);
       __syncthreads();
       cplx<R>* x = M;
       M = T;
@@ -663,6 +683,51 @@ __global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDes
   if (d.chain) {
     cplx<R>* out = (cplx<R>*)d.out;
     for (int e = tid; e < WW; e += kThreads) out[(e / W) * wp + e % W] = M[e];
+  }
+}
+
+template <typename R, int RPW, int CPL>
+__global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDesc* descs) {
+  product_task<R, RPW, CPL>(descs[blockIdx.x]);
+}
+
+// Factorisation and products in one cooperative launch (all CTAs resident):
+// CTAs 0..nf-1 run the elimination chains and publish their progress; the
+// others take product tasks in readiness order and wait (bounded, 10 s, then
+// the device flag) until the chain has finished the task's rows.
+template <typename R, int RPW, int CPL, int PRPW, int PCPL>
+__global__ void __launch_bounds__(kThreads) slab_factor_fused_kernel(
+    const FactorDesc* fd, int nf, const ProdDesc* pd, int np, int* progress, int* next_task,
+    int* flag) {
+  if ((int)blockIdx.x < nf) {
+    factor_chain<R, RPW, CPL>(fd[blockIdx.x], progress + blockIdx.x);
+    return;
+  }
+  __shared__ int sh_task, sh_abort;
+  while (true) {
+    if (threadIdx.x == 0) {
+      sh_task = atomicAdd(next_task, 1);
+      sh_abort = 0;
+      if (sh_task < np) {
+        const ProdDesc& d = pd[sh_task];
+        if (ld_acquire(progress + d.fchain) < d.need) {
+          const uint64_t t0 = gtimer();
+          while (ld_acquire(progress + d.fchain) < d.need) {
+            __nanosleep(2000);
+            if (gtimer() - t0 > 10000000000ull) {
+              atomicExch(flag, DEV_TIMEOUT);
+              sh_abort = 1;
+              break;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int task = sh_task;
+    if (task >= np || sh_abort) return;
+    product_task<R, PRPW, PCPL>(pd[task]);
+    __syncthreads();
   }
 }
 
@@ -1275,7 +1340,6 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   // delayed updates: rows per update warp (RPW) and columns per lane (CPL);
   // register tiles of the product GEMMs: 4 x 4 while they fit, else 4 x 8
   const int rpw = (maxW + kUpdateWarps - 1) / kUpdateWarps;
-  const int TC = ((maxW + 3) / 4) * ((maxW + 3) / 4) <= kThreads ? 4 : 8;
   if (maxW > 128 || rpw > 11 || smem_m > kSmemLimit || smem_p > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the blocked factorisation (W=" +
                                  std::to_string(maxW) + ")");
@@ -1290,13 +1354,19 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
     for (int q = 0; q < P; ++q) {
       const int4 sg = L.seg[q];
       // (Phi of the first segment of a half is never used: operators only)
+      // rows of the segment are final once its chain has passed them
+      const int fchain = 2 * (j - 1) + (sg.z > 0 ? 0 : 1);
+      const int need = (sg.z > 0 ? sg.x : L.ny - 1 - sg.x) + sg.y;
       pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 0, (q != 0 && q != L.S0) ? 1 : 0,
-                            stage_a, S.st, S.G, S.F, S.gstride, S.mstride,
+                            stage_a, fchain, need, S.st, S.G, S.F, S.gstride, S.mstride,
                             (cplx<R>*)S.Phi + (size_t)q * S.mstride});
-      pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 1, 1, stage_a, S.st, S.G, S.E, S.gstride,
-                            S.mstride, (cplx<R>*)S.Psi + (size_t)q * S.mstride});
+      pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 1, 1, stage_a, fchain, need, S.st, S.G,
+                            S.E, S.gstride, S.mstride, (cplx<R>*)S.Psi + (size_t)q * S.mstride});
     }
   }
+  // product tasks in the order their rows become final
+  std::stable_sort(pd.begin(), pd.end(),
+                   [](const ProdDesc& x, const ProdDesc& y) { return x.need < y.need; });
   const size_t b_fd = sizeof(FactorDesc) * fd.size(), b_md = sizeof(MidDesc) * md.size();
   const size_t b_pd = sizeof(ProdDesc) * pd.size();
   unsigned char* d_desc = (unsigned char*)dmalloc(b_fd + b_md + b_pd);
@@ -1306,32 +1376,78 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), b_fd, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaMemcpyAsync(d_md, md.data(), b_md, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaMemcpyAsync(d_pd, pd.data(), b_pd, cudaMemcpyHostToDevice, s));
-  auto run = [&](auto kf, auto km, auto kp) {
-    HZ_CU(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+  int* d_sync = (int*)dmalloc(sizeof(int) * (fd.size() + 1));   // chain progress, task counter
+  HZ_CU(cudaMemsetAsync(d_sync, 0, sizeof(int) * (fd.size() + 1), s));
+  int coop = 0;
+  HZ_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
+  auto run = [&](auto kf, auto km, auto kp, auto kfused) {
     HZ_CU(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m));
-    HZ_CU(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
-    timed(h, "slab_factor", 0.0, s, [&] { kf<<<(unsigned)fd.size(), kThreads, smem_f, s>>>(d_fd); });
-    timed(h, "slab_middle", 0.0, s, [&] { km<<<(unsigned)md.size(), kThreads, smem_m, s>>>(d_md); });
-    timed(h, "segment_product", 0.0, s,
-          [&] { kp<<<(unsigned)pd.size(), kThreads, smem_p, s>>>(d_pd); });
-    h->launches += 3;
-  };
-  auto prod = [&](auto kp) {
-    if (maxW <= 64) {
-      if (rpw <= 4) run(slab_factor_kernel<R, 4, 2>, slab_middle_kernel<R, 4, 2>, kp);
-      else run(slab_factor_kernel<R, 6, 2>, slab_middle_kernel<R, 6, 2>, kp);
-    } else if (maxW <= 96) {
-      if (rpw <= 6) run(slab_factor_kernel<R, 6, 3>, slab_middle_kernel<R, 6, 3>, kp);
-      else run(slab_factor_kernel<R, 8, 3>, slab_middle_kernel<R, 8, 3>, kp);
+    // one cooperative launch: the chains and, beside them on the other SMs,
+    // the product tasks as their rows become final
+    const size_t smem_u = std::max(smem_f, smem_p);
+    HZ_CU(cudaFuncSetAttribute(kfused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u));
+    int per_sm = 0;
+    HZ_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfused, kThreads, smem_u));
+    const long resident = (long)per_sm * h->sms;
+    const int nf = (int)fd.size(), np = (int)pd.size();
+    if (coop && resident > nf) {
+      const unsigned grid = (unsigned)std::min<long>(resident, (long)nf + np);
+      const FactorDesc* a0 = d_fd;
+      const ProdDesc* a2 = d_pd;
+      int* a4 = d_sync;
+      int* a5 = d_sync + nf;
+      int* a6 = h->dev_flag;
+      void* args[] = {(void*)&a0, (void*)&nf, (void*)&a2, (void*)&np, (void*)&a4, (void*)&a5,
+                      (void*)&a6};
+      timed(h, "slab_factor", 0.0, s, [&] {
+        HZ_CU(cudaLaunchCooperativeKernel((const void*)kfused, dim3(grid), dim3(kThreads), args,
+                                          smem_u, s));
+      });
+      h->launches += 1;
     } else {
-      run(slab_factor_kernel<R, 11, 4>, slab_middle_kernel<R, 11, 4>, kp);
+      HZ_CU(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+      HZ_CU(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
+      timed(h, "slab_factor", 0.0, s, [&] { kf<<<(unsigned)nf, kThreads, smem_f, s>>>(d_fd); });
+      timed(h, "segment_product", 0.0, s,
+            [&] { kp<<<(unsigned)np, kThreads, smem_p, s>>>(d_pd); });
+      h->launches += 2;
     }
+    timed(h, "slab_middle", 0.0, s, [&] { km<<<(unsigned)md.size(), kThreads, smem_m, s>>>(d_md); });
+    h->launches += 1;
   };
-  if (TC == 4) prod(segment_product_kernel<R, 4>);
-  else prod(segment_product_kernel<R, 8>);
+  // factor: update strips (RPW rows, CPL columns per lane); product GEMMs:
+  // 16 warps x PRPW rows, PCPL columns per lane
+  auto with_prod = [&](auto kf, auto km, auto tag_rpw, auto tag_cpl) {
+    constexpr int FR = decltype(tag_rpw)::value, FC = decltype(tag_cpl)::value;
+    if (maxW <= 64)
+      run(kf, km, segment_product_kernel<R, 4, 2>, slab_factor_fused_kernel<R, FR, FC, 4, 2>);
+    else if (maxW <= 80)
+      run(kf, km, segment_product_kernel<R, 5, 3>, slab_factor_fused_kernel<R, FR, FC, 5, 3>);
+    else if (maxW <= 96)
+      run(kf, km, segment_product_kernel<R, 6, 3>, slab_factor_fused_kernel<R, FR, FC, 6, 3>);
+    else
+      run(kf, km, segment_product_kernel<R, 8, 4>, slab_factor_fused_kernel<R, FR, FC, 8, 4>);
+  };
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using I4 = std::integral_constant<int, 4>;
+  if (maxW <= 64) {
+    if (rpw <= 4) with_prod(slab_factor_kernel<R, 4, 2>, slab_middle_kernel<R, 4, 2>, I4{}, I2{});
+    else with_prod(slab_factor_kernel<R, 6, 2>, slab_middle_kernel<R, 6, 2>,
+                   std::integral_constant<int, 6>{}, I2{});
+  } else if (maxW <= 96) {
+    if (rpw <= 6) with_prod(slab_factor_kernel<R, 6, 3>, slab_middle_kernel<R, 6, 3>,
+                            std::integral_constant<int, 6>{}, I3{});
+    else with_prod(slab_factor_kernel<R, 8, 3>, slab_middle_kernel<R, 8, 3>,
+                   std::integral_constant<int, 8>{}, I3{});
+  } else {
+    with_prod(slab_factor_kernel<R, 11, 4>, slab_middle_kernel<R, 11, 4>,
+              std::integral_constant<int, 11>{}, I4{});
+  }
   HZ_CU(cudaGetLastError());
   HZ_CU(cudaStreamSynchronize(s));
   dfree(d_desc);
+  dfree(d_sync);
 }
 
 template <typename R, int NR>
