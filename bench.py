@@ -301,7 +301,7 @@ def main():
     clk = clocks.stop()
     gpu_launches = solver.stats()["kernel_launches"] - launches0
     tags = ["slab_rhs", "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", "slab_solve",
-            "slab_factor", "slab_middle", "segment_product"]
+            "slab_factor", "slab_middle", "segment_product", "stencil_c64", "stencil_c128"]
     kt = {t: solver.kernel_timing(t) for t in tags}
     solver.enable_timing(False)
     ms_step, value = replica_throughput(total_ms / args.steps, cfg.ndof * cfg.n_src, ws, "cuda")
@@ -334,7 +334,8 @@ def main():
     alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     indiv = {t: v for t, v in per_kernel.items() if t != "slab_solve"}
     dom = max(indiv, key=lambda t: indiv[t]["ms"])
-    hbm_tags = [t for t in indiv if t not in ("slab_factor", "slab_middle", "segment_product")]
+    hbm_tags = [t for t in indiv if t not in ("slab_factor", "slab_middle", "segment_product",
+                                              "stencil_c64", "stencil_c128")]
     dom_hbm = max(hbm_tags, key=lambda t: indiv[t]["ms"])
 
     def hbm_line(tag):
@@ -359,6 +360,9 @@ def main():
         roofline["hbm_kernel"] = hbm_line(dom_hbm)
     else:
         roofline = hbm_line(dom)
+    # the matrix-free stencil kernels (Eq. 40 apply / residual / Jacobi): complex64
+    # in the two-grid smoother, complex128 for the GMRES operator (FP64 pipe)
+    roofline["stencil"] = {t: hbm_line(t) for t in ("stencil_c64", "stencil_c128") if t in indiv}
     sol = per_kernel.get("slab_solve")
     if sol:
         roofline["slab_solve_sequence"] = {

@@ -144,7 +144,7 @@ hz_status hz_precond(hz_handle* h, const hz_c128* r_dev, hz_c128* z_dev, int n_r
  * HZ_EINVAL before any work; HZ_ENOTCONV if a solve missed tol (results are
  * still written).  Requires hz_factor.  The first call allocates
  * 3 * max_rhs * N^d complex128 of work space owned by the handle. */
-hz_status hz_misfit_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_dev,
+hz_status hz_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_dev,
                          int n_rec, const hz_c128* d_dev, double* grad_dev, double* phi,
                          void* stream, hz_stats* stats);
 

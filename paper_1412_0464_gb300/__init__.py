@@ -57,7 +57,7 @@ _SIGNATURES = {
     "hz_solve_host": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P, ctypes.POINTER(hz_stats)]),
     "hz_apply": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P]),
     "hz_precond": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, _P]),
-    "hz_misfit_grad": (ctypes.c_int, [_H, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P,
+    "hz_grad": (ctypes.c_int, [_H, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P,
                                       ctypes.POINTER(ctypes.c_double), _P, ctypes.POINTER(hz_stats)]),
     "hz_slab_info": (ctypes.c_int, [_H, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5),
     "hz_slab_solve": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
@@ -210,10 +210,10 @@ class Solver:
         self._check(lib().hz_precond(self.h, _ptr(rb), _ptr(z), rb.shape[0], _stream(stream)))
         return z[0] if r.dim() == 2 else z
 
-    def misfit_grad(self, src, rec, d, stream=None, check=True):
+    def grad(self, src, rec, d, stream=None, check=True):
         """(Phi, dPhi/dm, stats) for point sources at flat indices ``src``,
         receivers at flat indices ``rec`` and observed data ``d``
-        ([n_src, n_rec] complex128); see hz_misfit_grad."""
+        ([n_src, n_rec] complex128); see hz_grad."""
         import torch
         src = torch.as_tensor(src).to(device="cuda", dtype=torch.int32).contiguous()
         rec = torch.as_tensor(rec).to(device="cuda", dtype=torch.int32).contiguous()
@@ -222,7 +222,7 @@ class Solver:
         grad = torch.empty(self.shape, dtype=torch.float64, device="cuda")
         phi = ctypes.c_double()
         st = hz_stats()
-        code = lib().hz_misfit_grad(self.h, _ptr(src), src.numel(), _ptr(rec), rec.numel(), _ptr(d),
+        code = lib().hz_grad(self.h, _ptr(src), src.numel(), _ptr(rec), rec.numel(), _ptr(d),
                                     _ptr(grad), ctypes.byref(phi), _stream(stream), ctypes.byref(st))
         if check:
             self._check(code)

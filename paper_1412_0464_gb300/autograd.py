@@ -1,4 +1,4 @@
-"""PyTorch autograd wrapper of the receiver misfit (hz_misfit_grad).
+"""PyTorch autograd wrapper of the receiver misfit (hz_grad).
 
 ``misfit(m, solver, src, rec, d)`` returns Phi(m) as a 0-d tensor whose
 backward gives dPhi/dm from the adjoint-state gradient computed on the device
@@ -16,7 +16,7 @@ class _Misfit(torch.autograd.Function):
     def forward(ctx, m, solver, src, rec, d):
         solver.set_medium(m.detach())
         solver.factor()
-        phi, grad, _ = solver.misfit_grad(src, rec, d)
+        phi, grad, _ = solver.grad(src, rec, d)
         ctx.save_for_backward(grad.to(m.dtype))
         return torch.tensor(phi, dtype=m.dtype, device=m.device)
 
@@ -27,5 +27,5 @@ class _Misfit(torch.autograd.Function):
 
 
 def misfit(m: torch.Tensor, solver, src, rec, d) -> torch.Tensor:
-    """Phi(m) = 1/2 sum |u_s(rec) - d_s|^2 with a gradient in m (see hz_misfit_grad)."""
+    """Phi(m) = 1/2 sum |u_s(rec) - d_s|^2 with a gradient in m (see hz_grad)."""
     return _Misfit.apply(m, solver, src, rec, d)

@@ -282,13 +282,13 @@ hz_status hz_precond(hz_handle* h, const hz_c128* r_dev, hz_c128* z_dev, int n_r
   });
 }
 
-hz_status hz_misfit_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_dev,
+hz_status hz_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_dev,
                          int n_rec, const hz_c128* d_dev, double* grad_dev, double* phi,
                          void* stream, hz_stats* stats) {
   if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   hz_status st = guarded(h, [&] {
-    if (!h->factored) throw Failure(HZ_ENOTFACTORED, "hz_misfit_grad before hz_factor");
+    if (!h->factored) throw Failure(HZ_ENOTFACTORED, "hz_grad before hz_factor");
     if (n_src < 1 || n_rec < 0) throw Failure(HZ_EINVAL, "need n_src >= 1 and n_rec >= 0");
     if (!src_dev || !grad_dev || !phi || (n_rec > 0 && (!rec_dev || !d_dev)))
       throw Failure(HZ_EINVAL, "NULL argument");

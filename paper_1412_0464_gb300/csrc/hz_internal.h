@@ -86,6 +86,8 @@ struct AxisTables {
   double* h_cell = nullptr;  // [N+1] cell sizes (device)
   c64* a_node32 = nullptr;
   c64* a_cell32 = nullptr;
+  c128* ia_node = nullptr;   // [N] 1/alpha at unknowns = 1 + i sigma/omega (fine level only)
+  c64* ia_node32 = nullptr;
 };
 
 // Slab j: core columns lo..hi, wl/wr added PML columns, W = width.

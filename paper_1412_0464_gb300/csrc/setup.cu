@@ -35,7 +35,7 @@ __device__ __forceinline__ c128 pml_alpha(double sigma, double omega) {
 // sigma = C d^2, d = distance beyond the interior box [w_out h, (n_cells-w_out) h].
 __global__ void fine_axis_kernel(int N, int n_cells, int w_out, double h, double C,
                                  double omega, c128* a_node, c128* a_cell, double* h_cell,
-                                 c64* a_node32, c64* a_cell32) {
+                                 c64* a_node32, c64* a_cell32, c128* ia_node, c64* ia_node32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > N) return;
   double lo = w_out * h, hi = (n_cells - w_out) * h;
@@ -45,6 +45,9 @@ __global__ void fine_axis_kernel(int N, int n_cells, int w_out, double h, double
     c128 a = pml_alpha(C * d * d, omega);
     a_node[i] = a;
     a_node32[i] = ccast<float>(a);
+    const c128 ia = mk(1.0, C * d * d / omega);   // 1/alpha, exactly
+    ia_node[i] = ia;
+    ia_node32[i] = ccast<float>(ia);
   }
   double x = (i + 0.5) * h;
   double d = fmax(0.0, fmax(lo - x, x - hi));
@@ -222,6 +225,7 @@ static void alloc_axis(AxisTables& a, int N) {
 
 static void free_axis(AxisTables& a) {
   dfree(a.a_node); dfree(a.a_cell); dfree(a.h_cell); dfree(a.a_node32); dfree(a.a_cell32);
+  dfree(a.ia_node); dfree(a.ia_node32);
   a = AxisTables{};
 }
 
@@ -239,9 +243,11 @@ void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const d
   double C = (w_out > 0) ? h->p.s_pml_out * h->c_pml / std::pow(w_out * hh, 3) : 0.0;
   for (AxisTables* a : {&L.ax, &L.ay}) {
     alloc_axis(*a, L.nx);
-    fine_axis_kernel<<<cdiv(L.nx + 1, 256), 256, 0, s>>>(L.nx, n_cells, w_out, hh, C,
-                                                         h->p.omega, a->a_node, a->a_cell,
-                                                         a->h_cell, a->a_node32, a->a_cell32);
+    a->ia_node = (c128*)dmalloc(sizeof(c128) * L.nx);
+    a->ia_node32 = (c64*)dmalloc(sizeof(c64) * L.nx);
+    fine_axis_kernel<<<cdiv(L.nx + 1, 256), 256, 0, s>>>(
+        L.nx, n_cells, w_out, hh, C, h->p.omega, a->a_node, a->a_cell, a->h_cell, a->a_node32,
+        a->a_cell32, a->ia_node, a->ia_node32);
   }
   size_t nn = (size_t)L.nx * L.ny;
   if (!L.m) L.m = (double*)dmalloc(sizeof(double) * nn);

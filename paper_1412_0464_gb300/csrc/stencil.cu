@@ -1,7 +1,7 @@
 // Matrix-free Helmholtz operator kernels.
 //
 // Fine level: Eq. 40 multiplied by h^2, coefficients recomputed on the fly
-// from m and the 1-D PML tables (alpha at unknowns and at cell midpoints):
+// from m and the 1-D PML tables (1/alpha at unknowns, alpha at cell midpoints):
 //   (A u)_{k,x} = (1/a2_k)(-a1_{x-1/2} u_{k,x-1} + (a1_{x-1/2}+a1_{x+1/2}) u_{k,x} - a1_{x+1/2} u_{k,x+1})
 //               + (1/a1_x)(-a2_{k-1/2} u_{k-1,x} + (a2_{k-1/2}+a2_{k+1/2}) u_{k,x} - a2_{k+1/2} u_{k+1,x})
 //               - h^2 omega^2 m_{k,x} / (a1_x a2_k) u_{k,x}
@@ -13,11 +13,11 @@ namespace hz {
 
 template <typename R> struct Tab;
 template <> struct Tab<double> {
-  static const c128* node(const AxisTables& a) { return a.a_node; }
+  static const c128* inode(const AxisTables& a) { return a.ia_node; }
   static const c128* cell(const AxisTables& a) { return a.a_cell; }
 };
 template <> struct Tab<float> {
-  static const c64* node(const AxisTables& a) { return a.a_node32; }
+  static const c64* inode(const AxisTables& a) { return a.ia_node32; }
   static const c64* cell(const AxisTables& a) { return a.a_cell32; }
 };
 template <typename R> struct Med;
@@ -36,9 +36,9 @@ struct FdArgs {
 template <typename R>
 __device__ __forceinline__ cplx<R> fd_row(const cplx<R>* __restrict__ u, int nx, int ny, int k,
                                           int x, R h2w2, const R* __restrict__ m,
-                                          const cplx<R>* __restrict__ a1n,
+                                          const cplx<R>* __restrict__ ia1n,
                                           const cplx<R>* __restrict__ a1c,
-                                          const cplx<R>* __restrict__ a2n,
+                                          const cplx<R>* __restrict__ ia2n,
                                           const cplx<R>* __restrict__ a2c, cplx<R>* diag) {
   const cplx<R> z = mk<R>(0, 0);
   cplx<R> uc = u[(size_t)k * nx + x];
@@ -46,8 +46,8 @@ __device__ __forceinline__ cplx<R> fd_row(const cplx<R>* __restrict__ u, int nx,
   cplx<R> ur = (x < nx - 1) ? u[(size_t)k * nx + x + 1] : z;
   cplx<R> ud = (k > 0) ? u[(size_t)(k - 1) * nx + x] : z;
   cplx<R> uu = (k < ny - 1) ? u[(size_t)(k + 1) * nx + x] : z;
-  cplx<R> ia2 = cinv(a2n[k]);
-  cplx<R> ia1 = cinv(a1n[x]);
+  cplx<R> ia2 = ia2n[k];
+  cplx<R> ia1 = ia1n[x];
   cplx<R> l = a1c[x], r = a1c[x + 1], d = a2c[k], up = a2c[k + 1];
   cplx<R> tx = (l + r) * uc - l * ul - r * ur;
   cplx<R> ty = (d + up) * uc - d * ud - up * uu;
@@ -119,14 +119,24 @@ static void launch_op(hz_handle* h, const Level& L, int mode, const cplx<R>* f,
   dim3 block(128);
   dim3 grid(cdiv(L.nx, 128), L.ny, n_rhs);
   R h2w2 = (R)(L.h * L.h * h->p.omega * h->p.omega);
+  // algorithmic bytes: u read and y written once per dof, f once for modes 1 and
+  // 2, and the medium (finite differences) or the 9 planes (stored stencil)
+  const double el = sizeof(cplx<R>), dofs = (double)L.nx * L.ny * n_rhs;
+  const double coef = L.fe ? 9.0 * el : (double)sizeof(R);
+  const double bytes = dofs * (2.0 * el + (mode >= 1 ? el : 0.0) + coef);
+  const char* tag = sizeof(R) == 4 ? "stencil_c64" : "stencil_c128";
   if (L.fe)
-    op_kernel<R, true><<<grid, block, 0, s>>>(mode, L.nx, L.ny, h2w2, nullptr, nullptr, nullptr,
-                                              nullptr, nullptr, Planes<R>::st(L), f, u, y,
-                                              (R)omega_jac);
+    timed(h, tag, bytes, s, [&] {
+      op_kernel<R, true><<<grid, block, 0, s>>>(mode, L.nx, L.ny, h2w2, nullptr, nullptr, nullptr,
+                                                nullptr, nullptr, Planes<R>::st(L), f, u, y,
+                                                (R)omega_jac);
+    });
   else
-    op_kernel<R, false><<<grid, block, 0, s>>>(
-        mode, L.nx, L.ny, h2w2, Med<R>::m(L), Tab<R>::node(L.ax), Tab<R>::cell(L.ax),
-        Tab<R>::node(L.ay), Tab<R>::cell(L.ay), nullptr, f, u, y, (R)omega_jac);
+    timed(h, tag, bytes, s, [&] {
+      op_kernel<R, false><<<grid, block, 0, s>>>(
+          mode, L.nx, L.ny, h2w2, Med<R>::m(L), Tab<R>::inode(L.ax), Tab<R>::cell(L.ax),
+          Tab<R>::inode(L.ay), Tab<R>::cell(L.ay), nullptr, f, u, y, (R)omega_jac);
+    });
   h->launches++;
   HZ_CU(cudaGetLastError());
 }

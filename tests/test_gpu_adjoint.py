@@ -1,4 +1,4 @@
-"""Parity of the device adjoint gradient (hz_misfit_grad) with the oracle's
+"""Parity of the device adjoint gradient (hz_grad) with the oracle's
 (oracle/adjoint.py, exact sparse solves).
 
 Tolerance: both sides compute the same FP64 quantities; the device solves
@@ -49,7 +49,7 @@ def _case(n, two_grid=True, precision="mixed", max_rhs=8, sweep="X"):
 def test_gradient_matches_oracle(n, two_grid, precision, max_rhs, sweep):
     cfg, m_true, m0, c_pml, src, rec, d, s = _case(n, two_grid, precision, max_rhs, sweep)
     s.factor()
-    phi, g, st = s.misfit_grad(src, rec, d)
+    phi, g, st = s.grad(src, rec, d)
     phi_o, g_o, _ = adjoint.misfit_and_gradient(Problem(cfg, m0, two_grid=False, c_pml=c_pml),
                                                 src, rec, d)
     g = g.cpu().numpy()
@@ -63,7 +63,7 @@ def test_gradient_zero_at_true_model():
     cfg, m_true, m0, c_pml, src, rec, d, s = _case(64)
     s.set_medium(m_true)
     s.factor()
-    phi, g, _ = s.misfit_grad(src, rec, d)
+    phi, g, _ = s.grad(src, rec, d)
     _, g0, _ = adjoint.misfit_and_gradient(Problem(cfg, m0, two_grid=False, c_pml=c_pml),
                                            src, rec, d)
     assert phi <= 1e-16 * np.sum(np.abs(d) ** 2)
@@ -73,14 +73,14 @@ def test_gradient_zero_at_true_model():
 def test_gradient_repeatable_and_batch_independent():
     cfg, m_true, m0, c_pml, src, rec, d, s = _case(64, max_rhs=8)
     s.factor()
-    phi1, g1, _ = s.misfit_grad(src, rec, d)
-    phi2, g2, _ = s.misfit_grad(src, rec, d)
+    phi1, g1, _ = s.grad(src, rec, d)
+    phi2, g2, _ = s.grad(src, rec, d)
     assert phi1 == phi2 and torch.equal(g1, g2)          # deterministic reductions
     # one source at a time: the sum over sources of single-source gradients
     gs = torch.zeros_like(g1)
     ps = 0.0
     for k in range(len(src)):
-        p, g, _ = s.misfit_grad(src[k:k + 1], rec, d[k:k + 1])
+        p, g, _ = s.grad(src[k:k + 1], rec, d[k:k + 1])
         ps += p
         gs += g
     assert abs(ps - phi1) <= 1e-8 * phi1
@@ -94,7 +94,7 @@ def test_autograd_function():
     phi = misfit(m, s, src, rec, d)
     phi.backward()
     s.factor()
-    phi_ref, g_ref, _ = s.misfit_grad(src, rec, d)
+    phi_ref, g_ref, _ = s.grad(src, rec, d)
     assert abs(phi.item() - phi_ref) <= 1e-12 * phi_ref
     assert torch.allclose(m.grad, g_ref, rtol=0, atol=1e-12 * g_ref.abs().max().item())
 
@@ -103,16 +103,37 @@ def test_gradient_errors():
     hz = _hz()
     cfg, m_true, m0, c_pml, src, rec, d, s = _case(64)
     with pytest.raises(hz.HzError, match="HZ_ENOTFACTORED"):
-        s.misfit_grad(src, rec, d)
+        s.grad(src, rec, d)
     s.factor()
     bad = rec.copy()
     bad[3] = cfg.ndof
     with pytest.raises(hz.HzError, match="receiver index outside"):
-        s.misfit_grad(src, bad, d)
+        s.grad(src, bad, d)
     bad_src = src.copy()
     bad_src[0] = -1
     with pytest.raises(hz.HzError, match="source index outside"):
-        s.misfit_grad(bad_src, rec, d)
+        s.grad(bad_src, rec, d)
     # the handle stays usable after rejected calls
-    phi, g, _ = s.misfit_grad(src, rec, d)
+    phi, g, _ = s.grad(src, rec, d)
     assert np.isfinite(phi) and torch.isfinite(g).all()
+
+
+def test_gradient_finite_differences_four_directions():
+    """Central differences of the device misfit along 4 seeded directions
+    (property at any size; the solves stop at 1e-10, eps = 1e-4 relative)."""
+    cfg, m_true, m0, c_pml, src, rec, d, s = _case(128)
+    s.factor()
+    phi0, g, _ = s.grad(src, rec, d)
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(20141204)
+    eps = 1e-4
+    for _ in range(4):
+        dm = rng.standard_normal(m0.shape) * m0
+        vals = []
+        for sgn in (1.0, -1.0):
+            s.set_medium(m0 + sgn * eps * dm)
+            s.factor()
+            vals.append(s.grad(src, rec, d)[0])
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        an = float(np.sum(g * dm))
+        assert abs(fd - an) <= 1e-4 * abs(an) + 1e-9 * phi0, (fd, an)
