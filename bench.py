@@ -43,6 +43,7 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 8-source batched leg")
     ap.add_argument("--workload", type=int, default=CONFIG_INDEX, choices=[1, 2, 3],
                     help="benchmark configuration (default 2, the headline workload)")
     ap.add_argument("--n", type=int, default=0,
@@ -409,6 +410,34 @@ def main():
                             "unit": "Mdof/s", "iters": it64,
                             "speedup_mixed_vs_fp64": t64 / (ms_step / 1000.0)}
         s64.close()
+    if rank == 0 and ws == 1 and not args.no_batched and cfg.n_src == 1 and not args.n:
+        # the same workload with 8 seeded sources solved together (multiple
+        # right-hand sides through every kernel): one factorisation + one solve
+        import dataclasses
+        cfg8 = dataclasses.replace(cfg, n_src=8)
+        b8 = torch.from_numpy(synth.sources(cfg8)).cuda()
+        s8 = hz.Solver.from_workload(cfg8, m=m)
+        s8.factor()
+        s8.solve(b8)
+        ts, it8, rr8 = [], 0, 0.0
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s8.factor()
+            _, st8 = s8.solve(b8)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            it8, rr8 = st8["iters_max"], st8["relres_max"]
+        t8 = statistics.mean(ts) / 1000.0
+        line["batched"] = {"n_rhs": 8, "time_to_solution_s": t8,
+                           "value": 8 * cfg.ndof / t8 / 1e6, "unit": "Mdof/s (dof x right-hand sides)",
+                           "iters_max": it8, "relres_max": rr8,
+                           "speedup_per_rhs_vs_single": 8 * (ms_step / 1000.0) / t8}
+        s8.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload != 3:
         line["cpu_baseline"] = cpu_baseline(cfg, max(iters))
     if rank == 0:
