@@ -301,8 +301,9 @@ def main():
     barrier()
     clk = clocks.stop()
     gpu_launches = solver.stats()["kernel_launches"] - launches0
-    tags = ["slab_rhs", "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", "slab_solve",
-            "slab_factor", "slab_middle", "segment_product", "stencil_c64", "stencil_c128"]
+    tags = ["slab_rhs", "slab_fwd_pass1", "slab_carry", "slab_carry_bound", "slab_fwd_bwd1",
+            "slab_bwd", "slab_solve", "slab_factor", "slab_middle", "segment_product",
+            "segment_prefix", "stencil_c64", "stencil_c128"]
     kt = {t: solver.kernel_timing(t) for t in tags}
     solver.enable_timing(False)
     ms_step, value = replica_throughput(total_ms / args.steps, cfg.ndof * cfg.n_src, ws, "cuda")
@@ -336,7 +337,7 @@ def main():
     indiv = {t: v for t, v in per_kernel.items() if t != "slab_solve"}
     dom = max(indiv, key=lambda t: indiv[t]["ms"])
     hbm_tags = [t for t in indiv if t not in ("slab_factor", "slab_middle", "segment_product",
-                                              "stencil_c64", "stencil_c128")]
+                                              "segment_prefix", "stencil_c64", "stencil_c128")]
     dom_hbm = max(hbm_tags, key=lambda t: indiv[t]["ms"])
 
     def hbm_line(tag):

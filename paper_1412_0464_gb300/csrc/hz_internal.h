@@ -103,10 +103,13 @@ struct Slab {
   void* E = nullptr;         //   and E'_k = G_k R_k [ny][mstride]
   void* Phi = nullptr;       // forward segment transfer products [P][mstride]
   void* Psi = nullptr;       // backward segment transfer products [P][mstride]
+  void* PhiP = nullptr;      // in-group prefix products of Phi [P][mstride] (see Level::grp)
+  void* PsiP = nullptr;      // in-group prefix products of Psi [P][mstride]
   void* inj = nullptr;       // injection coefficients [4][ny][3] (T row0, T row1, T~ row0, T~ row1)
   void* Y = nullptr;         // right-hand side, then forward solution rows [ny][n_rhs][wp]
-  void* carry_f = nullptr;   // forward segment end values [P][n_rhs][wp]
-  void* carry_b = nullptr;   // backward segment start values [P+1][n_rhs][wp] ([P]: meeting row)
+  void* carry_f = nullptr;   // forward segment end values [P+NG][n_rhs][wp] ([P+g]: group g's end)
+  void* carry_b = nullptr;   // backward segment start values [P+1+NG][n_rhs][wp] ([P]: meeting
+                             // row, [P+1+g]: group g's start)
 };
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.
@@ -129,8 +132,14 @@ struct Level {
   std::vector<Slab> slabs;        // index 1..J (0 unused)
   int mid = 0;                     // meeting row of the two elimination chains
   int P = 2, S0 = 1;               // segments per slab solve; the first S0 on the top chain
-  std::vector<int4> seg;           // per segment: first row, rows, direction (+1 / -1)
+  std::vector<int4> seg;           // per segment: first row, rows, direction (+1 / -1), group
   int4* seg_dev = nullptr;
+  // Segment groups (two-level carries): consecutive segments of one half;
+  // the first G0 groups on the top chain.  Per group: first and last segment,
+  // half, index within the half.
+  int NG = 2, G0 = 1;
+  std::vector<int4> grp;
+  int4* grp_dev = nullptr;
 };
 
 // Per-kernel event timing (enabled for roofline reporting): every launch of a

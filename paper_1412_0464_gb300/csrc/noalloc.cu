@@ -70,8 +70,8 @@ extern "C" hz_status hz_slab_solve_noalloc(hz_handle* h, int j, const hz_c128* f
     const size_t W = L.slabs[j].W, wp = L.slabs[j].wp;
     const size_t field = (size_t)n_rhs * L.ny * W;           // one slab-sized field
     const size_t rows = (size_t)n_rhs * L.ny * wp;           // forward rows (padded)
-    const size_t carry_f = (size_t)L.P * n_rhs * wp;         // forward segment carries
-    const size_t carry_b = (size_t)(L.P + 1) * n_rhs * wp;   // backward ones and the meeting row
+    const size_t carry_f = (size_t)(L.P + L.NG) * n_rhs * wp;       // forward carries, group ends
+    const size_t carry_b = (size_t)(L.P + 1 + L.NG) * n_rhs * wp;   // backward ones, meeting row
     const size_t need = (mixed ? 2 * align256(field * el) : 0) + align256(rows * el) +
                         align256(carry_f * el) + align256(carry_b * el);
     if (need > kScratchBytes)

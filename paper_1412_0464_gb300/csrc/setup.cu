@@ -322,14 +322,18 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
     S.Y = dmalloc(sizeof(cplx<R>) * (size_t)h->p.max_rhs * L.ny * S.wp);
   }
   // Twisted elimination: chains from rows 0 and ny-1 meet at row mid.  Each
-  // chain is cut into segments for the parallel substitution; automatic
-  // count P ~ 2 sqrt(ny) (balances the segment runs, ~4 ny / P steps, against
-  // the two carry chains, ~P / 2 steps each and run side by side).
+  // chain is cut into P/2 segments of L ~ ny / P rows for the parallel
+  // substitution, and the segments of a half into about sqrt(P/2) groups for
+  // the two-level carries.  Sequential steps of a solve per half: ~4 L in
+  // the segment passes plus ~4 sqrt(P/2) in the carries; the minimum lies at
+  // P/2 ~ ny^(2/3).  Automatic P is that, capped at the SM count (every
+  // segment pass is one CTA per segment, one wave).
   if (L.ny < 3) throw Failure(HZ_EINVAL, "a slab needs at least 3 rows");
   L.mid = (L.ny - 1) / 2;
   const int ntop = L.mid, nbot = L.ny - 1 - L.mid;
   int P = h->p.segments;
-  if (P <= 0) P = (int)std::lround(2.0 * std::sqrt((double)L.ny));
+  if (P <= 0) P = std::min(2 * (int)std::lround(std::pow((double)L.ny, 2.0 / 3.0)),
+                           std::max(2, h->sms));
   P = std::max(2, std::min(P, L.ny - 1));
   int S0 = (P * ntop + L.ny / 2) / (L.ny - 1);      // segments in proportion to the chain lengths
   S0 = std::max(1, std::min(S0, std::min(P - 1, ntop)));
@@ -346,16 +350,37 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
     const int a0 = (int)((long long)nbot * q / S1), a1 = (int)((long long)nbot * (q + 1) / S1);
     L.seg[S0 + q] = int4{L.ny - 1 - a0, a1 - a0, -1, 0};
   }
-  L.seg_dev = (int4*)dmalloc(sizeof(int4) * P);
+  // groups: about sqrt(segments) per half, sizes differing by at most one
+  L.grp.clear();
+  auto make_groups = [&](int s_first, int nh, int half) {
+    const int ng = std::max(1, std::min(nh, (int)std::lround(std::sqrt((double)nh))));
+    for (int c = 0; c < ng; ++c) {
+      const int a0 = s_first + nh * c / ng, a1 = s_first + nh * (c + 1) / ng;
+      const int gi = (int)L.grp.size();
+      L.grp.push_back(int4{a0, a1 - 1, half, c});
+      for (int q = a0; q < a1; ++q) L.seg[q].w = gi;
+    }
+    return ng;
+  };
+  L.G0 = make_groups(0, S0, 0);
+  L.NG = L.G0 + make_groups(S0, S1, 1);
+  L.seg_dev = (int4*)dmalloc(sizeof(int4) * (P + L.NG));
+  L.grp_dev = L.seg_dev + P;
   HZ_CU(cudaMemcpyAsync(L.seg_dev, L.seg.data(), sizeof(int4) * P, cudaMemcpyHostToDevice, s));
+  HZ_CU(cudaMemcpyAsync(L.grp_dev, L.grp.data(), sizeof(int4) * L.NG, cudaMemcpyHostToDevice, s));
   for (int j = 1; j <= L.J; ++j) {
     Slab& S = L.slabs[j];
-    S.Phi = dmalloc(sizeof(cplx<R>) * S.mstride * P);
-    S.Psi = dmalloc(sizeof(cplx<R>) * S.mstride * P);
-    S.carry_f = dmalloc(sizeof(cplx<R>) * (size_t)P * h->p.max_rhs * S.wp);
-    S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)(P + 1) * h->p.max_rhs * S.wp);
-    HZ_CU(cudaMemsetAsync(S.Phi, 0, sizeof(cplx<R>) * S.mstride * P, s));      // zero padding
-    HZ_CU(cudaMemsetAsync(S.Psi, 0, sizeof(cplx<R>) * S.mstride * P, s));
+    const size_t pb = sizeof(cplx<R>) * S.mstride * P;
+    S.Phi = dmalloc(pb);
+    S.Psi = dmalloc(pb);
+    S.PhiP = dmalloc(pb);
+    S.PsiP = dmalloc(pb);
+    S.carry_f = dmalloc(sizeof(cplx<R>) * (size_t)(P + L.NG) * h->p.max_rhs * S.wp);
+    S.carry_b = dmalloc(sizeof(cplx<R>) * (size_t)(P + 1 + L.NG) * h->p.max_rhs * S.wp);
+    HZ_CU(cudaMemsetAsync(S.Phi, 0, pb, s));      // zero padding
+    HZ_CU(cudaMemsetAsync(S.Psi, 0, pb, s));
+    HZ_CU(cudaMemsetAsync(S.PhiP, 0, pb, s));
+    HZ_CU(cudaMemsetAsync(S.PsiP, 0, pb, s));
   }
   HZ_CU(cudaStreamSynchronize(s));
 }
@@ -371,6 +396,7 @@ void free_level(Level& L) {
   for (Slab& S : L.slabs) {
     free_axis(S.ax);
     dfree(S.st); dfree(S.G); dfree(S.F); dfree(S.E); dfree(S.Phi); dfree(S.Psi);
+    dfree(S.PhiP); dfree(S.PsiP);
     dfree(S.inj); dfree(S.Y);
     dfree(S.carry_f); dfree(S.carry_b);
   }

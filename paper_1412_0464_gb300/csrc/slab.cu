@@ -24,8 +24,14 @@
 // x_t = y_t + E_t x_{t+1} (E_t = -G_t R_t).  Per segment the products
 // Phi = F_last ... F_first and Psi = E_first ... E_last are formed at factor
 // time; a solve runs each segment from a zero start (all segments of both
-// chains in parallel), carries the segment end values through Phi / Psi (the
-// two chains in parallel), and re-runs each segment from its true start.
+// chains in parallel), carries the segment end values through Phi / Psi, and
+// re-runs each segment from its true start.  The carries are two-level: the
+// segments of a half form groups of about sqrt(P/2); the carry inside every
+// group runs from a zero group start (all groups in parallel), one short
+// chain per half carries the group boundary values through the in-group
+// prefix products PhiP / PsiP (formed after the factorisation), and each
+// segment's true start follows from its in-group value by one more product
+// with PhiP / PsiP in the prologue of the re-run.
 //
 // Every substitution step reads its operands -- the factor block G_k, the
 // coupling row and the right-hand-side row -- through one stage of a
@@ -156,14 +162,15 @@ __device__ __forceinline__ Strip strip_of(int tid) {
   return s;
 }
 
-// dst = -A B for W x W operands (A with row stride lda in shared or global
-// memory, B and dst dense W x W in shared memory), all kThreads threads: warp w
-// takes rows w*RPW .. w*RPW+RPW-1, lane l takes columns l, l+32, ... (CPL of
-// them).  A reads are broadcasts and B / dst accesses are consecutive across
-// the warp, so no shared-memory access conflicts.  The caller synchronises.
-template <typename R, int RPW, int CPL>
-__device__ __forceinline__ void gemm_strip_neg(const cplx<R>* A, int lda, const cplx<R>* B,
-                                               cplx<R>* dst, int W) {
+// dst = -A B (NEG) or A B for W x W operands (A with row stride lda in shared
+// or global memory, B and dst dense W x W in shared memory), all kThreads
+// threads: warp w takes rows w*RPW .. w*RPW+RPW-1, lane l takes columns l,
+// l+32, ... (CPL of them).  A reads are broadcasts and B / dst accesses are
+// consecutive across the warp, so no shared-memory access conflicts.  The
+// caller synchronises.
+template <typename R, int RPW, int CPL, bool NEG = true>
+__device__ __forceinline__ void gemm_strip(const cplx<R>* A, int lda, const cplx<R>* B,
+                                           cplx<R>* dst, int W) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = warp * RPW;
   if (i0 >= W) return;
@@ -192,7 +199,7 @@ __device__ __forceinline__ void gemm_strip_neg(const cplx<R>* A, int lda, const 
 #pragma unroll
     for (int b = 0; b < CPL; ++b) {
       const int i = i0 + a, j = lane + 32 * b;
-      if (i < W && j < W) dst[i * W + j] = -acc[a][b];
+      if (i < W && j < W) dst[i * W + j] = NEG ? -acc[a][b] : acc[a][b];
     }
 }
 
@@ -672,8 +679,8 @@ __device__ void product_task(const ProdDesc& d) {
     }
     __syncthreads();
     if (d.chain) {                                   // T = -A_t M
-      if (d.stage) gemm_strip_neg<R, RPW, CPL>(As, W, M, T, W);
-      else gemm_strip_neg<R, RPW, CPL>(Ak, wp, M, T, W);
+      if (d.stage) gemm_strip<R, RPW, CPL>(As, W, M, T, W);
+      else gemm_strip<R, RPW, CPL>(Ak, wp, M, T, W);
       __syncthreads();
       cplx<R>* x = M;
       M = T;
@@ -689,6 +696,52 @@ __device__ void product_task(const ProdDesc& d) {
 template <typename R, int RPW, int CPL>
 __global__ void __launch_bounds__(kThreads) segment_product_kernel(const ProdDesc* descs) {
   product_task<R, RPW, CPL>(descs[blockIdx.x]);
+}
+
+// In-group prefix products of the segment transfer products (one CTA per
+// group and direction): along the group's segments in carry order
+// q_0, q_1, ... (increasing q for Phi, decreasing for Psi)
+//   Pi_{q_0} = M_{q_0},   Pi_{q_i} = M_{q_i} Pi_{q_{i-1}},
+// so that a segment value of the carry recurrence v_q = vhat_q + M_q v_prev
+// follows from its in-group value (zero start) as v_q = v_q^loc + Pi_q v_in,
+// v_in the value entering the group.
+struct PrefixDesc {
+  int W, wp, q0, n, dir;
+  const void* src;            // Phi or Psi [P][mstride]
+  void* dst;                  // PhiP or PsiP [P][mstride]
+  size_t mstride;
+};
+
+template <typename R, int RPW, int CPL>
+__global__ void __launch_bounds__(kThreads) segment_prefix_kernel(const PrefixDesc* descs) {
+  const PrefixDesc d = descs[blockIdx.x];
+  const int W = d.W, wp = d.wp, tid = threadIdx.x, WW = W * W;
+  const cplx<R>* src = (const cplx<R>*)d.src;
+  cplx<R>* dst = (cplx<R>*)d.dst;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* M = (cplx<R>*)smem_raw;
+  cplx<R>* T = M + WW;
+  {
+    const cplx<R>* s0 = src + (size_t)d.q0 * d.mstride;
+    cplx<R>* d0 = dst + (size_t)d.q0 * d.mstride;
+    for (int e = tid; e < WW; e += kThreads) {
+      const int i = e / W, j = e - i * W;
+      const cplx<R> v = ldcg(s0 + i * wp + j);
+      M[e] = v;
+      d0[i * wp + j] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = 1; i < d.n; ++i) {
+    const int q = d.q0 + d.dir * i;
+    gemm_strip<R, RPW, CPL, false>(src + (size_t)q * d.mstride, wp, M, T, W);
+    __syncthreads();
+    cplx<R>* out = dst + (size_t)q * d.mstride;
+    for (int e = tid; e < WW; e += kThreads) out[(e / W) * wp + e % W] = T[e];
+    cplx<R>* x = M;
+    M = T;
+    T = x;
+  }
 }
 
 // Factorisation and products in one cooperative launch (all CTAs resident):
@@ -764,7 +817,13 @@ template <typename R>
 struct SolveArgs {
   int W, wp, ny, nr;
   int P, S0, mid;             // segments (the first S0 on the top chain), meeting row
-  const int4* seg;            // per segment: first row, rows, direction (+1 top, -1 bottom)
+  const int4* seg;            // per segment: first row, rows, direction (+1 top, -1 bottom), group
+  int NG, G0;                 // segment groups (the first G0 on the top chain)
+  const int4* grp;            // per group: first segment, last segment, half, index in the half
+  const cplx<R>* Phi;         // [P][mstride] segment transfer products (forward)
+  const cplx<R>* Psi;         //   (backward)
+  const cplx<R>* PhiP;        // [P][mstride] their in-group prefix products
+  const cplx<R>* PsiP;
   const cplx<R>* st;          // [ny][9][wp]
   const cplx<R>* G;           // [ny][gstride]: G_k = S_k^-1
   const cplx<R>* F;           // [ny][mstride]: F'_k = G_k L_k (coupling to the previous chain row)
@@ -773,8 +832,10 @@ struct SolveArgs {
   size_t mstride;             // elements per F', E', Phi, Psi block (W rows of stride wp)
   int stages;
   cplx<R>* Y;                 // [ny][nr][wp]: G_k f_k, then forward rows y_k
-  cplx<R>* carry_f;           // [P][nr][wp]: segment end values of the forward recurrence
-  cplx<R>* carry_b;           // [P+1][nr][wp]: segment start values of the backward one; [P]: x_m
+  cplx<R>* carry_f;           // [P+NG][nr][wp]: segment end values of the forward recurrence
+                              //   (in-group values, zero group start); [P+g]: group g's true end
+  cplx<R>* carry_b;           // [P+1+NG][nr][wp]: segment start values of the backward one
+                              //   (in-group); [P]: x_m; [P+1+g]: group g's true start
   int* flag;
   Rhs<R> rhs;
   Out<R> out;
@@ -967,8 +1028,9 @@ __global__ void __launch_bounds__(kThreads) slab_rhs_kernel(SolveArgs<R> a) {
 // Forward recurrence over segment s along its chain, t = 0..n-1, rows
 // k_t = k0 + dir t:  y_t = g_t - F'_t y_{t-1}  (g_t = G_t f_t, F'_t = G_t L_t).
 //   mode 0: zero start, store only the last y into carry_f[s];
-//   mode 1: start from carry_f[s-1] (zero for the first segment of each
-//           half), store every y into Y (over g); if bwd1, then run the
+//   mode 1: start from the true end value of segment s-1 (zero for the
+//           first segment of each half), store every y into Y (over g); if
+//           bwd1, then run the
 //           backward recurrence x_t = y_t - E'_t x_{t+1} (E'_t = G_t R_t)
 //           over the segment from a zero start and store x_0 into carry_b[s].
 template <typename R, int NR>
@@ -990,22 +1052,43 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
     for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
     mbar_fence_init();
   }
+  // Start value (mode 1): the true end y of segment q = s-1.  In the first
+  // group of a half the in-group values are true; otherwise one fix-up step
+  // y_q = carry_f[q] + PhiP_q y_in (y_in: the previous group's true end)
+  // runs as pipeline item 0, ahead of the rows.
+  const int q = s - 1;
+  int fix = 0;
+  const cplx<R>* vin = nullptr;
+  if (mode == 1 && !first) {
+    const int gi = a.seg[q].w;
+    if (gi == (s >= a.S0 ? a.G0 : 0)) {
+      vin = a.carry_f + (size_t)q * nr * wp;
+    } else {
+      fix = 1;
+      vin = a.carry_f + (size_t)(a.P + gi - 1) * nr * wp;
+    }
+  }
   // both buffers in full: the paired loads of the GEMV also read the padding
   for (int i = tid; i < 2 * VS; i += nthr) {
     const int r = i / wp, e = i - r * wp;
-    vec[i] = (i < VS && mode == 1 && !first && r < nr) ? a.carry_f[((size_t)(s - 1) * nr + r) * wp + e]
-                                                         : zero;
+    vec[i] = (i < VS && vin && r < nr && e < W) ? vin[r * wp + e] : zero;
   }
   __syncthreads();
+  const int nit = n + fix;
+  auto issue_item = [&](int slot, int it) {
+    if (it < fix) pipe.issue(slot, q, a.PhiP, a.carry_f);
+    else pipe.issue(slot, k0 + dir * (it - fix), a.F, a.Y);
+  };
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + dir * i, a.F, a.Y);
+    for (int i = 0; i < pipe.stages && i < nit; ++i) issue_item(i, i);
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
   int cur = 0;
-  for (int t = 0; t < n; ++t) {
-    const int k = k0 + dir * t;
-    const int slot = t % pipe.stages;
+  for (int it = 0; it < nit; ++it) {
+    const bool fx = it < fix;
+    const int k = k0 + dir * (it - fix);
+    const int slot = it % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Mk = pipe.slot(slot);
@@ -1019,16 +1102,16 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (r >= nr) break;
-          const cplx<R> y = gk[r * wp + row] - acc[r];
+          const cplx<R> y = fx ? gk[r * wp + row] + acc[r] : gk[r * wp + row] - acc[r];
           yn[r * wp + row] = y;
-          if (mode == 1) a.Y[((size_t)k * nr + r) * wp + row] = y;
+          if (mode == 1 && !fx) a.Y[((size_t)k * nr + r) * wp + row] = y;
         }
       }
     }
     __syncthreads();
     if (sh_abort) return;
     cur ^= 1;
-    if (tid == 0 && t + pipe.stages < n) pipe.issue(slot, k + dir * pipe.stages, a.F, a.Y);
+    if (tid == 0 && it + pipe.stages < nit) issue_item(slot, it + pipe.stages);
   }
   if (mode == 0) {
     for (int i = tid; i < nr * wp; i += nthr) a.carry_f[(size_t)s * nr * wp + i] = vec[cur * VS + i];
@@ -1105,9 +1188,9 @@ __device__ __forceinline__ void store_out(const Out<R>& o, int ny, int W, int nr
   if (o.B4 && (row == o.e4 || row == o.e4 + 1)) o.B4[((size_t)(row - o.e4) * nr + r) * ny + k] = x;
 }
 
-// Final backward recurrence over segment s from x_{n} = the next segment's
-// start value carry_b[s+1] (last segment of a half: the meeting row's
-// x_m = carry_b[P]), with the epilogue of Table 2.
+// Final backward recurrence over segment s from x_{n} = the true start value
+// of segment s+1 (last segment of a half: the meeting row's x_m = carry_b[P]),
+// with the epilogue of Table 2.
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
   const int s = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, ny = a.ny, nr = a.nr;
@@ -1115,7 +1198,18 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
   const int4 sd = a.seg[s];
   const int k0 = sd.x, n = sd.y, dir = sd.z;
   const bool last = (s == a.S0 - 1 || s == a.P - 1);
-  const int from = last ? a.P : s + 1;
+  // Start value: x_m after the last segment of a half; otherwise the true
+  // start of segment q = s+1 by one fix-up step x_q = carry_b[q] + PsiP_q x_in
+  // (pipeline item 0; x_in: the true start of the next group towards the
+  // meeting row, or x_m).
+  const int q = s + 1;
+  const int fix = last ? 0 : 1;
+  const cplx<R>* vin = a.carry_b + (size_t)a.P * nr * wp;
+  if (!last) {
+    const int gi = a.seg[q].w;
+    const int glast = s >= a.S0 ? a.NG - 1 : a.G0 - 1;
+    if (gi != glast) vin = a.carry_b + (size_t)(a.P + 2 + gi) * nr * wp;
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   Pipe<R> pipe;
@@ -1130,19 +1224,24 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
   }
   for (int i = tid; i < 2 * VS; i += nthr) {   // both buffers (padding is read)
     const int r = i / wp, e = i - r * wp;
-    vec[i] = (i < VS && r < nr) ? a.carry_b[((size_t)from * nr + r) * wp + e] : zero;
+    vec[i] = (i < VS && r < nr && e < W) ? vin[r * wp + e] : zero;
   }
   __syncthreads();
+  const int nit = n + fix;
+  auto issue_item = [&](int slot, int it) {
+    if (it < fix) pipe.issue(slot, q, a.PsiP, a.carry_b);
+    else pipe.issue(slot, k0 + dir * (n - 1 - (it - fix)), a.E, a.Y);
+  };
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < n; ++i) pipe.issue(i, k0 + dir * (n - 1 - i), a.E, a.Y);
+    for (int i = 0; i < pipe.stages && i < nit; ++i) issue_item(i, i);
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
   int cur = 0;
-  for (int q = 0; q < n; ++q) {
-    const int t = n - 1 - q;
-    const int k = k0 + dir * t;
-    const int slot = q % pipe.stages;
+  for (int it = 0; it < nit; ++it) {
+    const bool fx = it < fix;
+    const int k = k0 + dir * (n - 1 - (it - fix));
+    const int slot = it % pipe.stages;
     if (!mbar_wait(&pipe.bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
     const cplx<R>* Mk = pipe.slot(slot);
@@ -1156,35 +1255,41 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (r >= nr) break;
-          const cplx<R> x = yk[r * wp + row] - acc[r];
+          const cplx<R> x = fx ? yk[r * wp + row] + acc[r] : yk[r * wp + row] - acc[r];
           xn[r * wp + row] = x;
-          store_out<R>(a.out, ny, W, nr, r, k, row, x);
+          if (!fx) store_out<R>(a.out, ny, W, nr, r, k, row, x);
         }
       }
     }
     __syncthreads();
     if (sh_abort) return;
     cur ^= 1;
-    if (tid == 0 && q + pipe.stages < n) pipe.issue(slot, k - dir * pipe.stages, a.E, a.Y);
+    if (tid == 0 && it + pipe.stages < nit) issue_item(slot, it + pipe.stages);
   }
 }
 
-// Segment carries along each half (one CTA per half).
-//   forward:  Y_s = yhat_s + Phi_s Y_{s-1} over the half's segments after the
-//             first (carry_f in place: the true last y of every segment);
-//   backward: first the meeting row x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1})
-//             (stored in carry_b[P] and the output by the first CTA), then
-//             X_s = xhat_s + Psi_s X_{s+1} from the half's last segment
-//             (X_{s+1} = x_m) back to its first (carry_b in place).
-// The products and the segment values come through a TMA pipeline:
-// stage = [M_s | carry row s]; the running value is double-buffered.
+// Two-level segment carries.  Every kind runs the recurrence
+//   v_i = hat_i + M_i v_{i-1}
+// over a list of segments through a TMA pipeline (stage = [M_i | hat row]),
+// the running value double-buffered:
+//   kind 0 (forward, one CTA per group): segments q_lo+1 .. q_hi from
+//          v = carry_f[q_lo] (zero group start), M = Phi_q; the in-group
+//          values replace yhat in carry_f[q];
+//   kind 1 (backward, one CTA per group): q_hi-1 .. q_lo from carry_b[q_hi],
+//          M = Psi_q, in carry_b[q];
+//   kind 2 (forward, one CTA per half): the half's groups g = 1, 2, ... from
+//          the first group's end (its in-group values are true), M = PhiP of
+//          the group's last segment, hat = its in-group value; v = the
+//          group's true end, stored in carry_f[P+g];
+//   kind 3 (backward, one CTA per half): first the meeting row
+//          x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1}) (stored in carry_b[P] and
+//          the output by the first CTA), then the half's groups from the
+//          meeting row outwards, M = PsiP of the group's first segment; v =
+//          the group's true start, stored in carry_b[P+1+g].
 template <typename R, int NR>
-__global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, const cplx<R>* prod,
-                                                              int backward) {
-  const int h = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr, P = a.P;
+__global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, int kind) {
+  const int b = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr, P = a.P;
   const int nthr = blockDim.x, ngroups = nthr / kTPR;
-  const int s_first = h ? a.S0 : 0;
-  const int nh = h ? P - a.S0 : a.S0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh_abort;
   uint64_t* bar = (uint64_t*)smem_raw;
@@ -1193,19 +1298,42 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
   cplx<R>* vtmp = prev + 2 * VS;
   cplx<R>* buf = (cplx<R>*)(((uintptr_t)(vtmp + VS) + 127) & ~(uintptr_t)127);
   const size_t se = a.mstride + (size_t)nr * wp;
+  const size_t RW = (size_t)nr * wp;            // elements per carry row
   const int stages = a.stages;
-  cplx<R>* carry = backward ? a.carry_b : a.carry_f;
+  const bool bwd = (kind & 1) != 0;
+  cplx<R>* carry = bwd ? a.carry_b : a.carry_f;
+  const cplx<R>* prod = kind == 0 ? a.Phi : kind == 1 ? a.Psi : kind == 2 ? a.PhiP : a.PsiP;
   const uint32_t mb = (uint32_t)(a.mstride * sizeof(cplx<R>));
-  const uint32_t vb = (uint32_t)((size_t)nr * wp * sizeof(cplx<R>));
-  // step i handles segment seg_of(i)
-  const int nsteps = backward ? nh : nh - 1;
-  auto seg_of = [&](int i) { return backward ? s_first + nh - 1 - i : s_first + 1 + i; };
+  const uint32_t vb = (uint32_t)(RW * sizeof(cplx<R>));
+  int4 gr = make_int4(0, 0, 0, 0);
+  int g_first = 0, ng = 0, nsteps;
+  if (kind < 2) {
+    gr = a.grp[b];
+    nsteps = gr.y - gr.x;
+  } else {
+    g_first = b ? a.G0 : 0;
+    ng = b ? a.NG - a.G0 : a.G0;
+    nsteps = kind == 2 ? ng - 1 : ng;
+  }
+  // segment (product and hat row) of step i, and the row its result goes to
+  auto seg_of = [&](int i) -> int {
+    if (kind == 0) return gr.x + 1 + i;
+    if (kind == 1) return gr.y - 1 - i;
+    if (kind == 2) return a.grp[g_first + 1 + i].y;
+    return a.grp[g_first + ng - 1 - i].x;
+  };
+  auto out_row = [&](int i) -> size_t {
+    if (kind == 0) return (size_t)(gr.x + 1 + i);
+    if (kind == 1) return (size_t)(gr.y - 1 - i);
+    if (kind == 2) return (size_t)(P + g_first + 1 + i);
+    return (size_t)(P + 1 + g_first + ng - 1 - i);
+  };
   auto issue = [&](int slot, int i) {
     const int sg = seg_of(i);
     fence_proxy_async_smem();
     mbar_expect_tx(&bar[slot], mb + vb);
     tma_load_1d(buf + (size_t)slot * se, prod + (size_t)sg * a.mstride, mb, &bar[slot]);
-    tma_load_1d(buf + (size_t)slot * se + a.mstride, carry + (size_t)sg * nr * wp, vb, &bar[slot]);
+    tma_load_1d(buf + (size_t)slot * se + a.mstride, carry + (size_t)sg * RW, vb, &bar[slot]);
   };
   const cplx<R> zero = mk<R>(0, 0);
   if (tid == 0) {
@@ -1216,15 +1344,27 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
   for (int i = tid; i < 2 * VS; i += nthr) prev[i] = zero;   // both buffers (padding is read)
+  if (kind >= 2) {   // the group-boundary rows in full (zero padding)
+    for (int i = tid; i < nsteps * (int)RW; i += nthr) {
+      const int st = i / (int)RW, e = i % wp;
+      if (e >= W) carry[out_row(st) * RW + i % RW] = zero;
+    }
+  }
   __syncthreads();
-  if (!backward) {
-    for (int i = tid; i < nr * wp; i += nthr) prev[i] = a.carry_f[(size_t)s_first * nr * wp + i];
+  if (kind < 3) {
+    const size_t srow = kind == 0 ? gr.x : kind == 1 ? gr.y : a.grp[g_first].y;
+    for (int i = tid; i < (int)RW; i += nthr) {
+      const cplx<R> v = (i % wp < W) ? carry[srow * RW + i] : zero;
+      prev[i] = v;
+      if (kind == 2) carry[(size_t)(P + g_first) * RW + i] = v;
+    }
   } else {
-    // meeting row: v = f_m - C_m y_{m-1} - B_m y_{m+1}, x_m = G_m v
+    // meeting row: v = f_m - C_m y_{m-1} - B_m y_{m+1}, x_m = G_m v; y_{m-1}
+    // and y_{m+1} are the true ends of the last groups of the two halves
     const int m = a.mid;
     const cplx<R>* stm = a.st + (size_t)m * 9 * wp;
-    const cplx<R>* yu = a.carry_f + (size_t)(a.S0 - 1) * nr * wp;
-    const cplx<R>* yd = a.carry_f + (size_t)(P - 1) * nr * wp;
+    const cplx<R>* yu = a.carry_f + (size_t)(P + a.G0 - 1) * RW;
+    const cplx<R>* yd = a.carry_f + (size_t)(P + a.NG - 1) * RW;
     for (int i = tid; i < VS; i += nthr) {
       const int r = i / wp, e = i - r * wp;
       cplx<R> v = zero;
@@ -1249,12 +1389,12 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
         for (int r = 0; r < NR; ++r)
           if (r < nr) {
             prev[r * wp + row] = acc[r];
-            if (h == 0) store_out<R>(a.out, a.ny, W, nr, r, m, row, acc[r]);
+            if (b == 0) store_out<R>(a.out, a.ny, W, nr, r, m, row, acc[r]);
           }
     }
     __syncthreads();
-    if (h == 0)   // the whole row, zero padding included
-      for (int i = tid; i < nr * wp; i += nthr) a.carry_b[(size_t)P * nr * wp + i] = prev[i];
+    if (b == 0)   // the whole row, zero padding included
+      for (int i = tid; i < (int)RW; i += nthr) a.carry_b[(size_t)P * RW + i] = prev[i];
   }
   __syncthreads();
   if (tid == 0)
@@ -1262,7 +1402,7 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
   uint32_t phase_bits = 0;
   int cur = 0;
   for (int i = 0; i < nsteps; ++i) {
-    const int sg = seg_of(i);
+    const size_t orow = out_row(i);
     const int slot = i % stages;
     if (!mbar_wait(&bar[slot], (phase_bits >> slot) & 1u, a.flag)) sh_abort = 1;
     phase_bits ^= 1u << slot;
@@ -1279,7 +1419,7 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, co
           if (r >= nr) break;
           const cplx<R> res = hat[r * wp + row] + acc[r];
           pn[r * wp + row] = res;
-          carry[((size_t)sg * nr + r) * wp + row] = res;
+          carry[orow * RW + r * wp + row] = res;
         }
       }
     }
@@ -1340,12 +1480,14 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   // delayed updates: rows per update warp (RPW) and columns per lane (CPL);
   // register tiles of the product GEMMs: 4 x 4 while they fit, else 4 x 8
   const int rpw = (maxW + kUpdateWarps - 1) / kUpdateWarps;
-  if (maxW > 128 || rpw > 11 || smem_m > kSmemLimit || smem_p > kSmemLimit)
+  if (maxW > 128 || rpw > 11 || smem_m > kSmemLimit || smem_p > kSmemLimit ||
+      2 * (size_t)maxW * maxW * el > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the blocked factorisation (W=" +
                                  std::to_string(maxW) + ")");
   std::vector<FactorDesc> fd;
   std::vector<MidDesc> md;
   std::vector<ProdDesc> pd;
+  std::vector<PrefixDesc> xd;
   for (int j = 1; j <= J; ++j) {
     const Slab& S = L.slabs[j];
     fd.push_back(FactorDesc{S.W, S.wp, 0, m, +1, S.st, S.G, S.gstride});
@@ -1363,24 +1505,34 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
       pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 1, 1, stage_a, fchain, need, S.st, S.G,
                             S.E, S.gstride, S.mstride, (cplx<R>*)S.Psi + (size_t)q * S.mstride});
     }
+    // in-group prefix products: forward for every group but the first of a
+    // half (whose in-group values are already true), backward for all
+    for (const int4& g : L.grp) {
+      const int n = g.y - g.x + 1;
+      if (g.w != 0) xd.push_back(PrefixDesc{S.W, S.wp, g.x, n, +1, S.Phi, S.PhiP, S.mstride});
+      xd.push_back(PrefixDesc{S.W, S.wp, g.y, n, -1, S.Psi, S.PsiP, S.mstride});
+    }
   }
   // product tasks in the order their rows become final
   std::stable_sort(pd.begin(), pd.end(),
                    [](const ProdDesc& x, const ProdDesc& y) { return x.need < y.need; });
   const size_t b_fd = sizeof(FactorDesc) * fd.size(), b_md = sizeof(MidDesc) * md.size();
-  const size_t b_pd = sizeof(ProdDesc) * pd.size();
-  unsigned char* d_desc = (unsigned char*)dmalloc(b_fd + b_md + b_pd);
+  const size_t b_pd = sizeof(ProdDesc) * pd.size(), b_xd = sizeof(PrefixDesc) * xd.size();
+  unsigned char* d_desc = (unsigned char*)dmalloc(b_fd + b_md + b_pd + b_xd);
   FactorDesc* d_fd = (FactorDesc*)d_desc;
   MidDesc* d_md = (MidDesc*)(d_desc + b_fd);
   ProdDesc* d_pd = (ProdDesc*)(d_desc + b_fd + b_md);
+  PrefixDesc* d_xd = (PrefixDesc*)(d_desc + b_fd + b_md + b_pd);
   HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), b_fd, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaMemcpyAsync(d_md, md.data(), b_md, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaMemcpyAsync(d_pd, pd.data(), b_pd, cudaMemcpyHostToDevice, s));
+  HZ_CU(cudaMemcpyAsync(d_xd, xd.data(), b_xd, cudaMemcpyHostToDevice, s));
   int* d_sync = (int*)dmalloc(sizeof(int) * (fd.size() + 1));   // chain progress, task counter
   HZ_CU(cudaMemsetAsync(d_sync, 0, sizeof(int) * (fd.size() + 1), s));
   int coop = 0;
   HZ_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
-  auto run = [&](auto kf, auto km, auto kp, auto kfused) {
+  const size_t smem_x = 2 * (size_t)maxW * maxW * el;   // prefix products: M, T
+  auto run = [&](auto kf, auto km, auto kp, auto kfused, auto kx) {
     HZ_CU(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m));
     // one cooperative launch: the chains and, beside them on the other SMs,
     // the product tasks as their rows become final
@@ -1413,20 +1565,27 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
       h->launches += 2;
     }
     timed(h, "slab_middle", 0.0, s, [&] { km<<<(unsigned)md.size(), kThreads, smem_m, s>>>(d_md); });
-    h->launches += 1;
+    HZ_CU(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
+    timed(h, "segment_prefix", 0.0, s,
+          [&] { kx<<<(unsigned)xd.size(), kThreads, smem_x, s>>>(d_xd); });
+    h->launches += 2;
   };
   // factor: update strips (RPW rows, CPL columns per lane); product GEMMs:
   // 16 warps x PRPW rows, PCPL columns per lane
   auto with_prod = [&](auto kf, auto km, auto tag_rpw, auto tag_cpl) {
     constexpr int FR = decltype(tag_rpw)::value, FC = decltype(tag_cpl)::value;
     if (maxW <= 64)
-      run(kf, km, segment_product_kernel<R, 4, 2>, slab_factor_fused_kernel<R, FR, FC, 4, 2>);
+      run(kf, km, segment_product_kernel<R, 4, 2>, slab_factor_fused_kernel<R, FR, FC, 4, 2>,
+          segment_prefix_kernel<R, 4, 2>);
     else if (maxW <= 80)
-      run(kf, km, segment_product_kernel<R, 5, 3>, slab_factor_fused_kernel<R, FR, FC, 5, 3>);
+      run(kf, km, segment_product_kernel<R, 5, 3>, slab_factor_fused_kernel<R, FR, FC, 5, 3>,
+          segment_prefix_kernel<R, 5, 3>);
     else if (maxW <= 96)
-      run(kf, km, segment_product_kernel<R, 6, 3>, slab_factor_fused_kernel<R, FR, FC, 6, 3>);
+      run(kf, km, segment_product_kernel<R, 6, 3>, slab_factor_fused_kernel<R, FR, FC, 6, 3>,
+          segment_prefix_kernel<R, 6, 3>);
     else
-      run(kf, km, segment_product_kernel<R, 8, 4>, slab_factor_fused_kernel<R, FR, FC, 8, 4>);
+      run(kf, km, segment_product_kernel<R, 8, 4>, slab_factor_fused_kernel<R, FR, FC, 8, 4>,
+          segment_prefix_kernel<R, 8, 4>);
   };
   using I2 = std::integral_constant<int, 2>;
   using I3 = std::integral_constant<int, 3>;
@@ -1473,7 +1632,8 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   const double el = sizeof(cplx<R>);
   const double gbytes = (double)L.ny * S.W * S.W * el;          // one pass over G_0..G_{ny-1}
   const double vbytes = (double)nr * L.ny * S.W * el;           // one slab-sized vector
-  const double pbytes = (double)P * S.W * S.W * el;             // one set of segment products
+  const double lbytes = (double)(P - L.NG) * S.W * S.W * el;   // in-group carry products
+  const double bbytes = (double)L.NG * S.W * S.W * el;          // group-boundary products
   auto T = [&](const char* tag, double bytes, auto&& fn) {
     if (tagged) timed(h, tag, bytes, s, fn); else fn();
   };
@@ -1488,19 +1648,17 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   T("slab_fwd_pass1", gbytes + vbytes, [&] {
     slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 0, 0);
   });
-  T("slab_carry", pbytes, [&] {
-    slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, (const cplx<R>*)S.Phi, 0);
-  });
+  T("slab_carry", lbytes, [&] { slab_carry_kernel<R, NR><<<L.NG, nthr, csm, s>>>(ac, 0); });
+  T("slab_carry_bound", bbytes, [&] { slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, 2); });
   T("slab_fwd_bwd1", 2 * gbytes + 3 * vbytes, [&] {
     slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 1, 1);
   });
-  T("slab_carry", pbytes, [&] {
-    slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, (const cplx<R>*)S.Psi, 1);
-  });
+  T("slab_carry", lbytes, [&] { slab_carry_kernel<R, NR><<<L.NG, nthr, csm, s>>>(ac, 1); });
+  T("slab_carry_bound", bbytes, [&] { slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, 3); });
   T("slab_bwd", gbytes + 2 * vbytes, [&] {
     slab_bwd_kernel<R, NR><<<P, nthr, smem, s>>>(a);
   });
-  h->launches += 6;
+  h->launches += 8;
   HZ_CU(cudaGetLastError());
 }
 
@@ -1513,6 +1671,9 @@ static void run_solve(hz_handle* h, Level& L, Slab& S, const Rhs<R>& rhs, const 
   a.W = S.W; a.wp = S.wp; a.ny = L.ny; a.nr = n_rhs;
   a.F = (const cplx<R>*)S.F; a.E = (const cplx<R>*)S.E; a.mstride = S.mstride;
   a.P = L.P; a.S0 = L.S0; a.mid = L.mid; a.seg = L.seg_dev;
+  a.NG = L.NG; a.G0 = L.G0; a.grp = L.grp_dev;
+  a.Phi = (const cplx<R>*)S.Phi; a.Psi = (const cplx<R>*)S.Psi;
+  a.PhiP = (const cplx<R>*)S.PhiP; a.PsiP = (const cplx<R>*)S.PsiP;
   a.st = (const cplx<R>*)S.st; a.G = (const cplx<R>*)S.G; a.gstride = S.gstride;
   a.stages = 1;
   a.Y = Y; a.carry_f = cf; a.carry_b = cb;
@@ -1571,7 +1732,7 @@ void slab_solve_raw(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* u
 }
 
 // Slab solve of a raw right-hand side with caller-provided work buffers
-// (Y [ny][n_rhs][wp], segment carries [P][n_rhs][wp] each); the same kernels
+// (Y [ny][n_rhs][wp], segment carries [P+NG] and [P+1+NG] rows of n_rhs x wp); the same kernels
 // as slab_solve_raw, no allocation, no timing events.
 template <typename R>
 void slab_solve_raw_scratch(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud,

@@ -53,7 +53,7 @@ def test_apply_matches_oracle(idx, n, w_out, J):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 3e-4)])
-@pytest.mark.parametrize("segments", [1, 0, 5])
+@pytest.mark.parametrize("segments", [1, 0, 5, 24])
 @pytest.mark.parametrize("idx,n,w_out,J", CASES[:2])
 def test_slab_solve_matches_oracle(idx, n, w_out, J, precision, tol, segments):
     hz = _hz()
