@@ -75,6 +75,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// Transaction bytes without an arrival: the phase cannot complete before the
+// (later) arrive.expect_tx of the same phase.
+__device__ __forceinline__ void mbar_expect_tx_noarrive(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream still runs;
+// pdl_wait() returns once the predecessor has completed and its memory
+// operations are visible (immediately for a kernel launched without the
+// attribute).  pdl_trigger() lets the successor start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -117,7 +130,6 @@ __device__ __forceinline__ cplx<double> ldcg(const cplx<double>* p) {
 
 constexpr int kThreads = 512;
 constexpr int kTPR = 4;                 // threads cooperating on one row of a GEMV
-constexpr int kGroups = kThreads / kTPR;
 constexpr int kNRMax = 8;               // right-hand sides per launch
 
 // --------------------------------------------------------------- factorisation
@@ -890,6 +902,19 @@ struct Pipe {
     tma_load_1d(dst, M + (size_t)k * gstride, mb, &bar[i]);
     if (rows) tma_load_1d(dst + gstride, rows + (size_t)k * nr * wp, vb, &bar[i]);
   }
+  // The same in two halves: the matrix (written before the solve began, so
+  // it may be fetched before pdl_wait) and, after pdl_wait, the vector row
+  // with the stage's arrival.
+  __device__ void issue_matrix(int i, int k, const cplx<R>* M) const {
+    const uint32_t mb = (uint32_t)(gstride * sizeof(cplx<R>));
+    mbar_expect_tx_noarrive(&bar[i], mb);
+    tma_load_1d(slot(i), M + (size_t)k * gstride, mb, &bar[i]);
+  }
+  __device__ void issue_vector(int i, int k, const cplx<R>* rows) const {
+    const uint32_t vb = (uint32_t)((size_t)nr * wp * sizeof(cplx<R>));
+    mbar_expect_tx(&bar[i], vb);
+    tma_load_1d(slot(i) + gstride, rows + (size_t)k * nr * wp, vb, &bar[i]);
+  }
 };
 
 // acc[r] = sum_j M[row][j] v[r][j] for r < nr; every thread of the block calls
@@ -994,6 +1019,7 @@ __device__ __forceinline__ void init_pipe(Pipe<R>& pipe, unsigned char* smem, co
 // independent.
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_rhs_kernel(SolveArgs<R> a) {
+  pdl_trigger();   // the first segment pass may start fetching its operators
   const int k = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr;
   const int nthr = blockDim.x, ngroups = nthr / kTPR;
   const int grp = tid / kTPR, lane = tid % kTPR;
@@ -1047,11 +1073,6 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
   init_pipe<R>(pipe, smem_raw, a, NR, &vec);
   const int VS = NR * wp;
   const cplx<R> zero = mk<R>(0, 0);
-  if (tid == 0) {
-    sh_abort = 0;
-    for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
-    mbar_fence_init();
-  }
   // Start value (mode 1): the true end y of segment q = s-1.  In the first
   // group of a half the in-group values are true; otherwise one fix-up step
   // y_q = carry_f[q] + PhiP_q y_in (y_in: the previous group's true end)
@@ -1068,19 +1089,35 @@ __global__ void __launch_bounds__(kThreads) slab_fwd_kernel(SolveArgs<R> a, int 
       vin = a.carry_f + (size_t)(a.P + gi - 1) * nr * wp;
     }
   }
-  // both buffers in full: the paired loads of the GEMV also read the padding
-  for (int i = tid; i < 2 * VS; i += nthr) {
-    const int r = i / wp, e = i - r * wp;
-    vec[i] = (i < VS && vin && r < nr && e < W) ? vin[r * wp + e] : zero;
-  }
-  __syncthreads();
   const int nit = n + fix;
   auto issue_item = [&](int slot, int it) {
     if (it < fix) pipe.issue(slot, q, a.PhiP, a.carry_f);
     else pipe.issue(slot, k0 + dir * (it - fix), a.F, a.Y);
   };
+  // the operator blocks of the first stages before the predecessor ends
+  const int npre = min(pipe.stages, nit);
+  if (tid == 0) {
+    sh_abort = 0;
+    for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
+    mbar_fence_init();
+    for (int i = 0; i < npre; ++i) {
+      if (i < fix) pipe.issue_matrix(i, q, a.PhiP);
+      else pipe.issue_matrix(i, k0 + dir * (i - fix), a.F);
+    }
+  }
+  pdl_trigger();
+  pdl_wait();
+  // both buffers in full: the paired loads of the GEMV also read the padding
+  for (int i = tid; i < 2 * VS; i += nthr) {
+    const int r = i / wp, e = i - r * wp;
+    vec[i] = (i < VS && vin && r < nr && e < W) ? vin[r * wp + e] : zero;
+  }
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < nit; ++i) issue_item(i, i);
+    for (int i = 0; i < npre; ++i) {
+      if (i < fix) pipe.issue_vector(i, q, a.carry_f);
+      else pipe.issue_vector(i, k0 + dir * (i - fix), a.Y);
+    }
+  __syncthreads();
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
@@ -1217,23 +1254,33 @@ __global__ void __launch_bounds__(kThreads) slab_bwd_kernel(SolveArgs<R> a) {
   init_pipe<R>(pipe, smem_raw, a, NR, &vec);
   const int VS = NR * wp;
   const cplx<R> zero = mk<R>(0, 0);
-  if (tid == 0) {
-    sh_abort = 0;
-    for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
-    mbar_fence_init();
-  }
-  for (int i = tid; i < 2 * VS; i += nthr) {   // both buffers (padding is read)
-    const int r = i / wp, e = i - r * wp;
-    vec[i] = (i < VS && r < nr && e < W) ? vin[r * wp + e] : zero;
-  }
-  __syncthreads();
   const int nit = n + fix;
   auto issue_item = [&](int slot, int it) {
     if (it < fix) pipe.issue(slot, q, a.PsiP, a.carry_b);
     else pipe.issue(slot, k0 + dir * (n - 1 - (it - fix)), a.E, a.Y);
   };
+  const int npre = min(pipe.stages, nit);
+  if (tid == 0) {
+    sh_abort = 0;
+    for (int i = 0; i < pipe.stages; ++i) mbar_init(&pipe.bar[i], 1);
+    mbar_fence_init();
+    for (int i = 0; i < npre; ++i) {
+      if (i < fix) pipe.issue_matrix(i, q, a.PsiP);
+      else pipe.issue_matrix(i, k0 + dir * (n - 1 - (i - fix)), a.E);
+    }
+  }
+  pdl_trigger();
+  pdl_wait();
+  for (int i = tid; i < 2 * VS; i += nthr) {   // both buffers (padding is read)
+    const int r = i / wp, e = i - r * wp;
+    vec[i] = (i < VS && r < nr && e < W) ? vin[r * wp + e] : zero;
+  }
   if (tid == 0)
-    for (int i = 0; i < pipe.stages && i < nit; ++i) issue_item(i, i);
+    for (int i = 0; i < npre; ++i) {
+      if (i < fix) pipe.issue_vector(i, q, a.carry_b);
+      else pipe.issue_vector(i, k0 + dir * (n - 1 - (i - fix)), a.Y);
+    }
+  __syncthreads();
   uint32_t phase_bits = 0;
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
@@ -1336,11 +1383,20 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, in
     tma_load_1d(buf + (size_t)slot * se + a.mstride, carry + (size_t)sg * RW, vb, &bar[slot]);
   };
   const cplx<R> zero = mk<R>(0, 0);
+  // the products of the first stages before the predecessor ends; their
+  // hat rows (written by the predecessor) after pdl_wait
+  const int npre = min(stages, nsteps);
   if (tid == 0) {
     sh_abort = 0;
     for (int i = 0; i < stages; ++i) mbar_init(&bar[i], 1);
     mbar_fence_init();
+    for (int i = 0; i < npre; ++i) {
+      mbar_expect_tx_noarrive(&bar[i], mb);
+      tma_load_1d(buf + (size_t)i * se, prod + (size_t)seg_of(i) * a.mstride, mb, &bar[i]);
+    }
   }
+  pdl_trigger();
+  pdl_wait();
   const int grp = tid / kTPR, lane = tid % kTPR;
   cplx<R> acc[NR];
   for (int i = tid; i < 2 * VS; i += nthr) prev[i] = zero;   // both buffers (padding is read)
@@ -1398,7 +1454,10 @@ __global__ void __launch_bounds__(kThreads) slab_carry_kernel(SolveArgs<R> a, in
   }
   __syncthreads();
   if (tid == 0)
-    for (int i = 0; i < stages && i < nsteps; ++i) issue(i, i);
+    for (int i = 0; i < npre; ++i) {
+      mbar_expect_tx(&bar[i], vb);
+      tma_load_1d(buf + (size_t)i * se + a.mstride, carry + (size_t)seg_of(i) * RW, vb, &bar[i]);
+    }
   uint32_t phase_bits = 0;
   int cur = 0;
   for (int i = 0; i < nsteps; ++i) {
@@ -1620,8 +1679,30 @@ static void set_solve_attrs() {
   done = true;
 }
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// its predecessor in the stream runs; it fetches only data written before the
+// solve began until pdl_wait() (every kernel launched this way calls it
+// before touching its predecessor's results).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  HZ_CU(cudaLaunchKernelEx(&cfg, k, args...));
+}
+
 // Launch sequence of one slab solve; `tagged` brackets the kernels with
-// timing events (when timing is on).
+// timing events (when timing is on).  The slab_rhs kernel is an ordinary
+// launch (it follows arbitrary work); the seven after it overlap their
+// prologues with their predecessors.
 template <typename R, int NR>
 static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaStream_t s,
                          bool tagged) {
@@ -1645,19 +1726,16 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   T("slab_rhs", gbytes + 2 * vbytes, [&] {
     slab_rhs_kernel<R, NR><<<L.ny, nthr, (size_t)NR * S.wp * sizeof(cplx<R>), s>>>(a);
   });
-  T("slab_fwd_pass1", gbytes + vbytes, [&] {
-    slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 0, 0);
-  });
-  T("slab_carry", lbytes, [&] { slab_carry_kernel<R, NR><<<L.NG, nthr, csm, s>>>(ac, 0); });
-  T("slab_carry_bound", bbytes, [&] { slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, 2); });
-  T("slab_fwd_bwd1", 2 * gbytes + 3 * vbytes, [&] {
-    slab_fwd_kernel<R, NR><<<P, nthr, smem, s>>>(a, 1, 1);
-  });
-  T("slab_carry", lbytes, [&] { slab_carry_kernel<R, NR><<<L.NG, nthr, csm, s>>>(ac, 1); });
-  T("slab_carry_bound", bbytes, [&] { slab_carry_kernel<R, NR><<<2, nthr, csm, s>>>(ac, 3); });
-  T("slab_bwd", gbytes + 2 * vbytes, [&] {
-    slab_bwd_kernel<R, NR><<<P, nthr, smem, s>>>(a);
-  });
+  const unsigned nt = (unsigned)nthr;
+  T("slab_fwd_pass1", gbytes + vbytes,
+    [&] { launch_pdl(slab_fwd_kernel<R, NR>, P, nt, smem, s, a, 0, 0); });
+  T("slab_carry", lbytes, [&] { launch_pdl(slab_carry_kernel<R, NR>, L.NG, nt, csm, s, ac, 0); });
+  T("slab_carry_bound", bbytes, [&] { launch_pdl(slab_carry_kernel<R, NR>, 2, nt, csm, s, ac, 2); });
+  T("slab_fwd_bwd1", 2 * gbytes + 3 * vbytes,
+    [&] { launch_pdl(slab_fwd_kernel<R, NR>, P, nt, smem, s, a, 1, 1); });
+  T("slab_carry", lbytes, [&] { launch_pdl(slab_carry_kernel<R, NR>, L.NG, nt, csm, s, ac, 1); });
+  T("slab_carry_bound", bbytes, [&] { launch_pdl(slab_carry_kernel<R, NR>, 2, nt, csm, s, ac, 3); });
+  T("slab_bwd", gbytes + 2 * vbytes, [&] { launch_pdl(slab_bwd_kernel<R, NR>, P, nt, smem, s, a); });
   h->launches += 8;
   HZ_CU(cudaGetLastError());
 }
