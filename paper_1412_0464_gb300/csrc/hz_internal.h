@@ -88,6 +88,9 @@ struct AxisTables {
   c64* a_cell32 = nullptr;
   c128* ia_node = nullptr;   // [N] 1/alpha at unknowns = 1 + i sigma/omega (fine level only)
   c64* ia_node32 = nullptr;
+  // unknowns in_lo..in_hi have alpha = 1 exactly at the node and both
+  // adjacent cells (the PML-free interior; fine level only, empty if none)
+  int in_lo = 1, in_hi = 0;
 };
 
 // Slab j: core columns lo..hi, wl/wr added PML columns, W = width.

@@ -248,6 +248,27 @@ void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const d
     fine_axis_kernel<<<cdiv(L.nx + 1, 256), 256, 0, s>>>(
         L.nx, n_cells, w_out, hh, C, h->p.omega, a->a_node, a->a_cell, a->h_cell, a->a_node32,
         a->a_cell32, a->ia_node, a->ia_node32);
+    HZ_CU(cudaGetLastError());
+    // PML-free interior (the operator's coefficients are real there): the
+    // longest run of unknowns with 1/alpha = 1 at the node and alpha = 1 at
+    // both adjacent cells, read back from the tables just built
+    std::vector<c128> ia(L.nx), ac(L.nx + 1);
+    HZ_CU(cudaMemcpyAsync(ia.data(), a->ia_node, sizeof(c128) * L.nx, cudaMemcpyDeviceToHost, s));
+    HZ_CU(cudaMemcpyAsync(ac.data(), a->a_cell, sizeof(c128) * (L.nx + 1), cudaMemcpyDeviceToHost,
+                          s));
+    HZ_CU(cudaStreamSynchronize(s));
+    auto one = [](const c128& v) { return v.re == 1.0 && v.im == 0.0; };
+    int best_lo = 1, best_hi = 0, run = -1;
+    for (int i = 0; i <= L.nx; ++i) {
+      const bool ok = i < L.nx && one(ia[i]) && one(ac[i]) && one(ac[i + 1]);
+      if (ok && run < 0) run = i;
+      if (!ok && run >= 0) {
+        if (i - 1 - run > best_hi - best_lo) { best_lo = run; best_hi = i - 1; }
+        run = -1;
+      }
+    }
+    a->in_lo = best_lo;
+    a->in_hi = best_hi;
   }
   size_t nn = (size_t)L.nx * L.ny;
   if (!L.m) L.m = (double*)dmalloc(sizeof(double) * nn);

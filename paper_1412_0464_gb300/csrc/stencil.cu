@@ -6,8 +6,15 @@
 //               + (1/a1_x)(-a2_{k-1/2} u_{k-1,x} + (a2_{k-1/2}+a2_{k+1/2}) u_{k,x} - a2_{k+1/2} u_{k+1,x})
 //               - h^2 omega^2 m_{k,x} / (a1_x a2_k) u_{k,x}
 // with a_{i-1/2} = cell i and a_{i+1/2} = cell i+1, Dirichlet zeros outside.
+// In the PML-free interior (alpha = 1 at the node and both adjacent cells
+// along both axes) the coefficients are real and the row reduces to
+//   (A u)_{k,x} = (4 - h^2 omega^2 m_{k,x}) u_{k,x} - u_{k,x-1} - u_{k,x+1} - u_{k-1,x} - u_{k+1,x},
+// about a fifth of the general row's arithmetic (which matters most for the
+// complex128 operator: GB300's FP64 pipe is narrow).
 // Coarse level: a stored 9-point stencil (9 coefficient planes).
 #include "hz_internal.h"
+
+#include <utility>
 
 namespace hz {
 
@@ -56,6 +63,23 @@ __device__ __forceinline__ cplx<R> fd_row(const cplx<R>* __restrict__ u, int nx,
   return ia2 * tx + ia1 * ty - mass * uc;
 }
 
+// Interior row (real coefficients); *diag = the real diagonal entry.
+template <typename R>
+__device__ __forceinline__ cplx<R> fd_row_interior(const cplx<R>* __restrict__ u, int nx, int ny,
+                                                   int k, int x, R h2w2, const R* __restrict__ m,
+                                                   R* diag) {
+  const cplx<R> z = mk<R>(0, 0);
+  const cplx<R> uc = u[(size_t)k * nx + x];
+  const cplx<R> ul = (x > 0) ? u[(size_t)k * nx + x - 1] : z;
+  const cplx<R> ur = (x < nx - 1) ? u[(size_t)k * nx + x + 1] : z;
+  const cplx<R> ud = (k > 0) ? u[(size_t)(k - 1) * nx + x] : z;
+  const cplx<R> uu = (k < ny - 1) ? u[(size_t)(k + 1) * nx + x] : z;
+  const R c = (R)4 - h2w2 * m[(size_t)k * nx + x];
+  *diag = c;
+  return mk<R>(c * uc.re - ((ul.re + ur.re) + (ud.re + uu.re)),
+               c * uc.im - ((ul.im + ur.im) + (ud.im + uu.im)));
+}
+
 template <typename R>
 __device__ __forceinline__ cplx<R> st_row(const cplx<R>* __restrict__ u, int nx, int ny, int k,
                                           int x, const cplx<R>* __restrict__ st,
@@ -80,6 +104,8 @@ __device__ __forceinline__ cplx<R> st_row(const cplx<R>* __restrict__ u, int nx,
 
 // mode 0: y = A u;  mode 1: y = f - A u;
 // mode 2 (Jacobi): y = u + omega (f - A u) / diag(A)
+// (finite differences: rows x in [xlo, xhi], k in [ylo, yhi] take the
+// interior form)
 template <typename R, bool STORED>
 __global__ void __launch_bounds__(256) op_kernel(int mode, int nx, int ny, R h2w2,
                                                  const R* __restrict__ m,
@@ -90,18 +116,34 @@ __global__ void __launch_bounds__(256) op_kernel(int mode, int nx, int ny, R h2w
                                                  const cplx<R>* __restrict__ st,
                                                  const cplx<R>* __restrict__ f,
                                                  const cplx<R>* __restrict__ u,
-                                                 cplx<R>* __restrict__ y, R omega_jac) {
+                                                 cplx<R>* __restrict__ y, R omega_jac,
+                                                 int xlo, int xhi, int ylo, int yhi) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
   int r = blockIdx.z;
   if (x >= nx) return;
   size_t off = (size_t)r * nx * ny;
   const cplx<R>* ur = u + off;
+  size_t i = off + (size_t)k * nx + x;
+  if (!STORED && x >= xlo && x <= xhi && k >= ylo && k <= yhi) {
+    R dr;
+    const cplx<R> au = fd_row_interior<R>(ur, nx, ny, k, x, h2w2, m, &dr);
+    if (mode == 0) {
+      y[i] = au;
+    } else if (mode == 1) {
+      y[i] = f[i] - au;
+    } else {
+      const R s = omega_jac / dr;
+      const cplx<R> res = f[i] - au;
+      const cplx<R> uc = ur[(size_t)k * nx + x];
+      y[i] = mk<R>(uc.re + s * res.re, uc.im + s * res.im);
+    }
+    return;
+  }
   cplx<R> dg;
   cplx<R> au = STORED ? st_row<R>(ur, nx, ny, k, x, st, mode == 2 ? &dg : nullptr)
                       : fd_row<R>(ur, nx, ny, k, x, h2w2, m, a1n, a1c, a2n, a2c,
                                   mode == 2 ? &dg : nullptr);
-  size_t i = off + (size_t)k * nx + x;
   if (mode == 0) {
     y[i] = au;
   } else if (mode == 1) {
@@ -129,13 +171,14 @@ static void launch_op(hz_handle* h, const Level& L, int mode, const cplx<R>* f,
     timed(h, tag, bytes, s, [&] {
       op_kernel<R, true><<<grid, block, 0, s>>>(mode, L.nx, L.ny, h2w2, nullptr, nullptr, nullptr,
                                                 nullptr, nullptr, Planes<R>::st(L), f, u, y,
-                                                (R)omega_jac);
+                                                (R)omega_jac, 1, 0, 1, 0);
     });
   else
     timed(h, tag, bytes, s, [&] {
       op_kernel<R, false><<<grid, block, 0, s>>>(
           mode, L.nx, L.ny, h2w2, Med<R>::m(L), Tab<R>::inode(L.ax), Tab<R>::cell(L.ax),
-          Tab<R>::inode(L.ay), Tab<R>::cell(L.ay), nullptr, f, u, y, (R)omega_jac);
+          Tab<R>::inode(L.ay), Tab<R>::cell(L.ay), nullptr, f, u, y, (R)omega_jac, L.ax.in_lo,
+          L.ax.in_hi, L.ay.in_lo, L.ay.in_hi);
     });
   h->launches++;
   HZ_CU(cudaGetLastError());
@@ -154,15 +197,19 @@ void level_residual(hz_handle* h, const Level& L, const cplx<R>* f, const cplx<R
 }
 
 // nu omega-Jacobi steps u <- u + omega D^-1 (f - A u) (Section 4.1), ping-pong
-// between u and t; the result ends in u.
+// between u and t; the result ends in u (one copy when nu is odd).
 template <typename R>
 void jacobi_steps(hz_handle* h, const Level& L, const cplx<R>* f, cplx<R>* u, cplx<R>* t,
                   int nu, double omega_jac, int n_rhs, cudaStream_t s) {
+  cplx<R>* a = u;
+  cplx<R>* b = t;
   for (int i = 0; i < nu; ++i) {
-    launch_op<R>(h, L, 2, f, u, t, n_rhs, omega_jac, s);
-    HZ_CU(cudaMemcpyAsync(u, t, sizeof(cplx<R>) * (size_t)n_rhs * L.nx * L.ny,
-                          cudaMemcpyDeviceToDevice, s));
+    launch_op<R>(h, L, 2, f, a, b, n_rhs, omega_jac, s);
+    std::swap(a, b);
   }
+  if (a != u)
+    HZ_CU(cudaMemcpyAsync(u, a, sizeof(cplx<R>) * (size_t)n_rhs * L.nx * L.ny,
+                          cudaMemcpyDeviceToDevice, s));
 }
 
 void apply_fine64(hz_handle* h, const c128* u, c128* y, int n_rhs, cudaStream_t s) {
