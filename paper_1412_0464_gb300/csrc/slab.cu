@@ -1016,30 +1016,49 @@ __device__ __forceinline__ void init_pipe(Pipe<R>& pipe, unsigned char* smem, co
 // SubdomSolve (Table 2): the slab right-hand side (gather + transmission
 // injection) of block row k, premultiplied by its factor block: Y[k] =
 // G_k f_k (the meeting row keeps f_m).  One CTA per block row; every row is
-// independent.
+// independent.  G_k comes into shared memory by one bulk copy, issued before
+// pdl_wait (the factors are written before the solve begins); the gather
+// reads the predecessor's results after it.
 template <typename R, int NR>
 __global__ void __launch_bounds__(kThreads) slab_rhs_kernel(SolveArgs<R> a) {
-  pdl_trigger();   // the first segment pass may start fetching its operators
   const int k = blockIdx.x, tid = threadIdx.x, W = a.W, wp = a.wp, nr = a.nr;
   const int nthr = blockDim.x, ngroups = nthr / kTPR;
   const int grp = tid / kTPR, lane = tid % kTPR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* f = (cplx<R>*)smem_raw;   // NR x wp
+  __shared__ int sh_abort;
+  uint64_t* bar = (uint64_t*)smem_raw;
+  cplx<R>* f = (cplx<R>*)(smem_raw + 128);   // NR x wp
+  cplx<R>* Gs = (cplx<R>*)(((uintptr_t)(f + NR * wp) + 127) & ~(uintptr_t)127);
+  const bool mid = (k == a.mid);
+  const uint32_t gb = (uint32_t)(a.gstride * sizeof(cplx<R>));
+  if (tid == 0) {
+    sh_abort = 0;
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    if (!mid) {
+      mbar_expect_tx(bar, gb);
+      tma_load_1d(Gs, a.G + (size_t)k * a.gstride, gb, bar);
+    }
+  }
+  pdl_trigger();
+  pdl_wait();
   for (int i = tid; i < NR * wp; i += nthr) {
     const int r = i / wp, e = i - r * wp;
     f[i] = (r < nr && e < W) ? rhs_at<R>(a.rhs, a.ny, W, nr, r, k, e) : mk<R>(0, 0);
   }
   __syncthreads();
   cplx<R>* Yk = a.Y + (size_t)k * nr * wp;
-  if (k == a.mid) {
+  if (mid) {
     for (int i = tid; i < nr * wp; i += nthr) Yk[i] = f[i];
     return;
   }
+  if (!mbar_wait(bar, 0, a.flag)) sh_abort = 1;
+  __syncthreads();
+  if (sh_abort) return;
   cplx<R> acc[NR];
-  const cplx<R>* Gk = a.G + (size_t)k * a.gstride;
   for (int rb = 0; rb < W; rb += ngroups) {
     const int row = rb + grp;
-    gemv_rows<R, NR>(Gk, W, f, wp, W, nr, row, lane, acc);
+    gemv_rows<R, NR>(Gs, W, f, wp, W, nr, row, lane, acc);
     if (lane == 0 && row < W)
 #pragma unroll
       for (int r = 0; r < NR; ++r)
@@ -1700,9 +1719,8 @@ static void launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_
 }
 
 // Launch sequence of one slab solve; `tagged` brackets the kernels with
-// timing events (when timing is on).  The slab_rhs kernel is an ordinary
-// launch (it follows arbitrary work); the seven after it overlap their
-// prologues with their predecessors.
+// timing events (when timing is on).  All eight kernels overlap their
+// prologues with their predecessors (programmatic dependent launch).
 template <typename R, int NR>
 static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaStream_t s,
                          bool tagged) {
@@ -1723,9 +1741,9 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   SolveArgs<R> ac = a;
   ac.stages = pick_carry_stages<R>(S, nr, NR);
   const size_t csm = carry_smem<R>(S, nr, NR, ac.stages);
-  T("slab_rhs", gbytes + 2 * vbytes, [&] {
-    slab_rhs_kernel<R, NR><<<L.ny, nthr, (size_t)NR * S.wp * sizeof(cplx<R>), s>>>(a);
-  });
+  const size_t rsmem = 256 + ((size_t)NR * S.wp + S.gstride) * sizeof(cplx<R>);
+  T("slab_rhs", gbytes + 2 * vbytes,
+    [&] { launch_pdl(slab_rhs_kernel<R, NR>, L.ny, (unsigned)nthr, rsmem, s, a); });
   const unsigned nt = (unsigned)nthr;
   T("slab_fwd_pass1", gbytes + vbytes,
     [&] { launch_pdl(slab_fwd_kernel<R, NR>, P, nt, smem, s, a, 0, 0); });
