@@ -37,6 +37,10 @@
 // coupling row and the right-hand-side row -- through one stage of a
 // shared-memory pipeline filled by TMA bulk copies (cp.async.bulk +
 // mbarrier); the step itself touches only shared memory and registers.
+//
+// Templates only: slab_c64.cu and slab_c128.cu instantiate the complex64 and
+// complex128 paths in two translation units compiled side by side.
+#pragma once
 #include "hz_internal.h"
 
 #include <algorithm>
@@ -158,20 +162,47 @@ __device__ __forceinline__ cplx<double> crcp(cplx<double> a) {
 template <typename R>
 struct FactorPanel { static constexpr int BW = 4; };
 
-// Warps of the delayed Gauss-Jordan updates: those that do not share a
-// scheduler with warp 0 (warp w runs on sub-partition w mod 4), so that the
-// panel warp keeps its issue slots while the update runs beside it.  Each
-// takes a strip of RPW consecutive rows.
-constexpr int kUpdateWarps = kThreads / 32 / 4 * 3;
+// Warps of the delayed Gauss-Jordan updates.  The 12 warps that do not share
+// a scheduler with the panel warp 0 (warp w runs on sub-partition w mod 4)
+// take strips of RPW consecutive rows; the three that do (warps 4, 8, 12)
+// take the few rows left over, and start only once warp 0 has finished its
+// panel (named barrier 1), so that they do not take issue slots from the
+// latency-bound panel elimination.
+constexpr int kMainUpdateWarps = kThreads / 32 / 4 * 3;
+constexpr int kLateUpdateWarps = kThreads / 32 / 4 - 1;
 struct Strip {
-  int row0;        // first row of this warp's strip, -1: not an update warp
+  int row0;        // first row of this warp's strip, -1: no rows
+  int nrows;       // rows of the strip (<= RPW)
+  bool late;       // shares warp 0's sub-partition (waits for the panel)
 };
 template <int RPW>
-__device__ __forceinline__ Strip strip_of(int tid) {
+__device__ __forceinline__ Strip strip_of(int tid, int W) {
   const int warp = tid >> 5;
   Strip s;
-  s.row0 = ((warp & 3) == 0) ? -1 : ((warp >> 2) * 3 + (warp & 3) - 1) * RPW;
+  s.late = warp != 0 && (warp & 3) == 0;
+  if (warp == 0) {
+    s.row0 = -1;
+    s.nrows = 0;
+  } else if (!s.late) {
+    s.row0 = ((warp >> 2) * 3 + (warp & 3) - 1) * RPW;
+    s.nrows = min(RPW, W - s.row0);
+  } else {
+    const int rest = max(0, W - kMainUpdateWarps * RPW);
+    const int rps = (rest + kLateUpdateWarps - 1) / kLateUpdateWarps;
+    s.row0 = kMainUpdateWarps * RPW + ((warp >> 2) - 1) * rps;
+    s.nrows = min(rps, W - s.row0);
+  }
+  if (s.nrows <= 0) {
+    s.row0 = -1;
+    s.nrows = 0;
+  }
   return s;
+}
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // dst = -A B (NEG) or A B for W x W operands (A with row stride lda in shared
@@ -326,6 +357,51 @@ __device__ __forceinline__ void panel_dispatch(cplx<R>* S, cplx<R>* Cm, const cp
     panel_elim<R, BW, 4>(S, Cm, Cp, Rp, pbw, pinv, prow, piv, used, W, p0, bw, lane);
 }
 
+// Delayed rank-pbw update S -= Cp^T Rm on rows row0 .. row0+nrows-1 (nrows <=
+// RPW) and columns lane + 32 b outside panels q-1 (from pp0) and q (p0, bw):
+// one warp, RPW x CPL complex accumulators in registers.
+template <typename R, int RPW, int CPL, int BW>
+__device__ __forceinline__ void strip_update(cplx<R>* S, const cplx<R>* Cp, const cplx<R>* Rm,
+                                             int W, int row0, int nrows, int pp0, int p0, int bw,
+                                             int pbw, int lane) {
+  const cplx<R> zero = mk<R>(0, 0);
+  cplx<R> acc[RPW][CPL];
+#pragma unroll
+  for (int a = 0; a < RPW; ++a)
+#pragma unroll
+    for (int b = 0; b < CPL; ++b) {
+      const int i = row0 + a, j = lane + 32 * b;
+      acc[a][b] = (a < nrows && j < W) ? S[i * W + j] : zero;
+    }
+#pragma unroll
+  for (int t = 0; t < BW; ++t) {
+    if (t >= pbw) break;
+    cplx<R> rv[CPL];
+#pragma unroll
+    for (int b = 0; b < CPL; ++b) {
+      const int j = lane + 32 * b;
+      rv[b] = (j < W && (j < pp0 || j >= p0 + bw)) ? Rm[t * W + j] : zero;
+    }
+#pragma unroll
+    for (int a = 0; a < RPW; ++a) {
+      const int i = row0 + a;
+      const cplx<R> cv = (a < nrows) ? Cp[t * W + i] : zero;   // same address across the warp
+#pragma unroll
+      for (int b = 0; b < CPL; ++b) {
+        acc[a][b].re -= cv.re * rv[b].re - cv.im * rv[b].im;
+        acc[a][b].im -= cv.re * rv[b].im + cv.im * rv[b].re;
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < RPW; ++a)
+#pragma unroll
+    for (int b = 0; b < CPL; ++b) {
+      const int i = row0 + a, j = lane + 32 * b;
+      if (a < nrows && j < W && (j < pp0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
+    }
+}
+
 // Shared-memory work areas of the Gauss-Jordan inverse.
 template <typename R>
 struct GJWork {
@@ -367,44 +443,17 @@ __device__ void gj_inverse(cplx<R>* S, cplx<R>* Gl, const GJWork<R>& w, int W, c
     if (warp == 0) {
       if (bw > 0)
         panel_dispatch<R, BW>(S, Cq, Cp, w.Rm, pbw, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
-    } else if (pbw > 0 && su.row0 >= 0) {
+      if (pbw > 0) named_bar_arrive(1, 32 * (1 + kLateUpdateWarps));
+    } else if (pbw > 0 && (su.late || su.row0 >= 0)) {
+      if (su.late) named_bar_sync(1, 32 * (1 + kLateUpdateWarps));
+    }
+    if (warp != 0 && pbw > 0 && su.row0 >= 0) {
       // delayed rank-pbw update of panel q-1 on every column outside panels
-      // q-1 and q: this warp's rows row0 .. row0+RPW-1, columns lane + 32 b
-      cplx<R> acc[RPW][CPL];
-#pragma unroll
-      for (int a = 0; a < RPW; ++a)
-#pragma unroll
-        for (int b = 0; b < CPL; ++b) {
-          const int i = su.row0 + a, j = lane + 32 * b;
-          acc[a][b] = (i < W && j < W) ? S[i * W + j] : zero;
-        }
-#pragma unroll
-      for (int t = 0; t < BW; ++t) {
-        if (t >= pbw) break;
-        cplx<R> rv[CPL];
-#pragma unroll
-        for (int b = 0; b < CPL; ++b) {
-          const int j = lane + 32 * b;
-          rv[b] = (j < W && (j < pp0 || j >= p0 + bw)) ? w.Rm[t * W + j] : zero;
-        }
-#pragma unroll
-        for (int a = 0; a < RPW; ++a) {
-          const int i = su.row0 + a;
-          const cplx<R> cv = (i < W) ? Cp[t * W + i] : zero;     // same address across the warp
-#pragma unroll
-          for (int b = 0; b < CPL; ++b) {
-            acc[a][b].re -= cv.re * rv[b].re - cv.im * rv[b].im;
-            acc[a][b].im -= cv.re * rv[b].im + cv.im * rv[b].re;
-          }
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < RPW; ++a)
-#pragma unroll
-        for (int b = 0; b < CPL; ++b) {
-          const int i = su.row0 + a, j = lane + 32 * b;
-          if (i < W && j < W && (j < pp0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
-        }
+      // q-1 and q (a late warp has at most one row: a one-row tile)
+      if (su.late)
+        strip_update<R, 1, CPL, BW>(S, Cp, w.Rm, W, su.row0, su.nrows, pp0, p0, bw, pbw, lane);
+      else
+        strip_update<R, RPW, CPL, BW>(S, Cp, w.Rm, W, su.row0, su.nrows, pp0, p0, bw, pbw, lane);
     }
     __syncthreads();
     if (bw == 0) break;
@@ -471,6 +520,7 @@ static size_t factor_smem_bytes(int W, int ncpl, size_t el, int BW) {
 // dir = +1, B_k for dir = -1) and R_{t-1} that of row k_{t-1} to k_t.
 struct FactorDesc {
   int W, wp, k0, n, dir;
+  int diag;                  // couplings L, R diagonal (5-point stencil): one-pass Schur update
   const void* st;
   void* G;
   size_t gstride;
@@ -495,7 +545,7 @@ template <typename R, int RPW, int CPL>
 __device__ void factor_chain(const FactorDesc& d, int* progress) {
   const int W = d.W, wp = d.wp, tid = threadIdx.x, dir = d.dir;
   const int WW = W * W;
-  const Strip su = strip_of<RPW>(tid);
+  const Strip su = strip_of<RPW>(tid, W);
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -507,6 +557,8 @@ __device__ void factor_chain(const FactorDesc& d, int* progress) {
   cplx<R>* cR = cD + 3 * W;                      // R_{t-1} (3 x W)
   const cplx<R> zero = mk<R>(0, 0);
   const int pl = lplane(dir), pr = rplane(dir);
+  cplx<R>* Gp = Gl;                              // G_{t-1}
+  cplx<R>* Sp = S;                               // the other W x W buffer
 
   for (int t = 0; t < d.n; ++t) {
     const int k = d.k0 + dir * t;
@@ -518,42 +570,57 @@ __device__ void factor_chain(const FactorDesc& d, int* progress) {
       cR[i] = (t > 0) ? st[(size_t)(k - dir) * 9 * wp + (pr + q) * wp + e] : zero;
     }
     __syncthreads();
-    if (t > 0) {
-      for (int e = tid; e < WW; e += kThreads) {      // X = G_{t-1} R_{t-1} into S
+    // Gp holds G_{t-1}; S_t is formed in the other buffer (or, for
+    // tridiagonal couplings, in Gp after X = G_{t-1} R_{t-1} went to the
+    // other), inverted in place, and G_t lands in the remaining one.
+    cplx<R>* Sx = Sp;        // S_t
+    cplx<R>* Gx = Gp;        // receives G_t
+    if (t > 0 && d.diag) {
+      for (int e = tid; e < WW; e += kThreads) {      // S_t = D - L_t G_{t-1} R_{t-1}
+        const int i = e / W, j = e - i * W;
+        cplx<R> v = -(cL[W + i] * Gp[e] * cR[W + j]);
+        const int dd = j - i;
+        if (dd >= -1 && dd <= 1) v = v + cD[(dd + 1) * W + i];
+        Sp[e] = v;
+      }
+    } else if (t > 0) {
+      for (int e = tid; e < WW; e += kThreads) {      // X = G_{t-1} R_{t-1} into Sp
         const int i = e / W, j = e - i * W;
         cplx<R> acc = zero;
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const int c = j - dx;
-          if (c >= 0 && c < W) cfma(acc, Gl[i * W + c], cR[(dx + 1) * W + c]);
+          if (c >= 0 && c < W) cfma(acc, Gp[i * W + c], cR[(dx + 1) * W + c]);
         }
-        S[e] = acc;
+        Sp[e] = acc;
       }
       __syncthreads();
-      for (int e = tid; e < WW; e += kThreads) {      // Gl = D - L X
+      for (int e = tid; e < WW; e += kThreads) {      // S_t = D - L X into Gp
         const int i = e / W, j = e - i * W;
         cplx<R> acc = zero;
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const int rr = i + dx;
-          if (rr >= 0 && rr < W) cfma(acc, cL[(dx + 1) * W + i], S[rr * W + j]);
+          if (rr >= 0 && rr < W) cfma(acc, cL[(dx + 1) * W + i], Sp[rr * W + j]);
         }
         cplx<R> v = -acc;
         const int dd = j - i;
         if (dd >= -1 && dd <= 1) v = v + cD[(dd + 1) * W + i];
-        Gl[e] = v;
+        Gp[e] = v;
       }
-      __syncthreads();
-      for (int e = tid; e < WW; e += kThreads) S[e] = Gl[e];
+      Sx = Gp;
+      Gx = Sp;
     } else {
       for (int e = tid; e < WW; e += kThreads) {
         const int i = e / W, j = e - i * W;
         const int dd = j - i;
-        S[e] = (dd >= -1 && dd <= 1) ? cD[(dd + 1) * W + i] : zero;
+        Sp[e] = (dd >= -1 && dd <= 1) ? cD[(dd + 1) * W + i] : zero;
       }
     }
     __syncthreads();
-    gj_inverse<R, RPW, CPL>(S, Gl, w, W, su, G + (size_t)k * d.gstride);
+    gj_inverse<R, RPW, CPL>(Sx, Gx, w, W, su, G + (size_t)k * d.gstride);
+    Gp = Gx;
+    Sp = Sx;
     if (progress && tid == 0) {   // every thread's G_t stores precede the barrier above
       __threadfence();
       st_release(progress, t + 1);
@@ -600,7 +667,7 @@ template <typename R, int RPW, int CPL>
 __global__ void __launch_bounds__(kThreads) slab_middle_kernel(const MidDesc* descs) {
   const MidDesc d = descs[blockIdx.x];
   const int W = d.W, wp = d.wp, m = d.m, tid = threadIdx.x, WW = W * W;
-  const Strip su = strip_of<RPW>(tid);
+  const Strip su = strip_of<RPW>(tid, W);
   const cplx<R>* st = (const cplx<R>*)d.st;
   cplx<R>* G = (cplx<R>*)d.G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1557,7 +1624,9 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   const size_t smem_p = smem_p2 + (stage_a ? (size_t)maxW * maxW * el : 0);
   // delayed updates: rows per update warp (RPW) and columns per lane (CPL);
   // register tiles of the product GEMMs: 4 x 4 while they fit, else 4 x 8
-  const int rpw = (maxW + kUpdateWarps - 1) / kUpdateWarps;
+  // (the 12 main update warps take RPW rows each; at most 3 rows are left to
+  // the three late warps)
+  const int rpw = std::max(1, (maxW - kLateUpdateWarps + kMainUpdateWarps - 1) / kMainUpdateWarps);
   if (maxW > 128 || rpw > 11 || smem_m > kSmemLimit || smem_p > kSmemLimit ||
       2 * (size_t)maxW * maxW * el > kSmemLimit)
     throw Failure(HZ_EINVAL, "slab too wide for the blocked factorisation (W=" +
@@ -1568,8 +1637,9 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   std::vector<PrefixDesc> xd;
   for (int j = 1; j <= J; ++j) {
     const Slab& S = L.slabs[j];
-    fd.push_back(FactorDesc{S.W, S.wp, 0, m, +1, S.st, S.G, S.gstride});
-    fd.push_back(FactorDesc{S.W, S.wp, L.ny - 1, L.ny - 1 - m, -1, S.st, S.G, S.gstride});
+    const int dg = L.fe ? 0 : 1;   // finite differences: 5-point, diagonal couplings
+    fd.push_back(FactorDesc{S.W, S.wp, 0, m, +1, dg, S.st, S.G, S.gstride});
+    fd.push_back(FactorDesc{S.W, S.wp, L.ny - 1, L.ny - 1 - m, -1, dg, S.st, S.G, S.gstride});
     md.push_back(MidDesc{S.W, S.wp, m, S.st, S.G, S.gstride});
     for (int q = 0; q < P; ++q) {
       const int4 sg = L.seg[q];
@@ -1668,18 +1738,18 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   using I2 = std::integral_constant<int, 2>;
   using I3 = std::integral_constant<int, 3>;
   using I4 = std::integral_constant<int, 4>;
+  using I5 = std::integral_constant<int, 5>;
+  using I6 = std::integral_constant<int, 6>;
+  using I8 = std::integral_constant<int, 8>;
+  using I11 = std::integral_constant<int, 11>;
   if (maxW <= 64) {
     if (rpw <= 4) with_prod(slab_factor_kernel<R, 4, 2>, slab_middle_kernel<R, 4, 2>, I4{}, I2{});
-    else with_prod(slab_factor_kernel<R, 6, 2>, slab_middle_kernel<R, 6, 2>,
-                   std::integral_constant<int, 6>{}, I2{});
+    else with_prod(slab_factor_kernel<R, 5, 2>, slab_middle_kernel<R, 5, 2>, I5{}, I2{});
   } else if (maxW <= 96) {
-    if (rpw <= 6) with_prod(slab_factor_kernel<R, 6, 3>, slab_middle_kernel<R, 6, 3>,
-                            std::integral_constant<int, 6>{}, I3{});
-    else with_prod(slab_factor_kernel<R, 8, 3>, slab_middle_kernel<R, 8, 3>,
-                   std::integral_constant<int, 8>{}, I3{});
+    if (rpw <= 6) with_prod(slab_factor_kernel<R, 6, 3>, slab_middle_kernel<R, 6, 3>, I6{}, I3{});
+    else with_prod(slab_factor_kernel<R, 8, 3>, slab_middle_kernel<R, 8, 3>, I8{}, I3{});
   } else {
-    with_prod(slab_factor_kernel<R, 11, 4>, slab_middle_kernel<R, 11, 4>,
-              std::integral_constant<int, 11>{}, I4{});
+    with_prod(slab_factor_kernel<R, 11, 4>, slab_middle_kernel<R, 11, 4>, I11{}, I4{});
   }
   HZ_CU(cudaGetLastError());
   HZ_CU(cudaStreamSynchronize(s));
@@ -1841,20 +1911,5 @@ void slab_solve_raw_scratch(hz_handle* h, Level& L, int j, const cplx<R>* fd, cp
   o.raw = ud; o.e2 = -1; o.e4 = -1;
   run_solve<R>(h, L, S, q, o, n_rhs, s, Y, carry_f, carry_b, false);
 }
-
-template void factor_level<float>(hz_handle*, Level&, cudaStream_t);
-template void factor_level<double>(hz_handle*, Level&, cudaStream_t);
-template void subdom_solve<float>(hz_handle*, Level&, int, const c64*, int, int, int, int, bool,
-                                  const c64*, bool, c64*, bool, const c64*, bool, c64*, c64*, int,
-                                  cudaStream_t);
-template void subdom_solve<double>(hz_handle*, Level&, int, const c128*, int, int, int, int, bool,
-                                   const c128*, bool, c128*, bool, const c128*, bool, c128*, c128*,
-                                   int, cudaStream_t);
-template void slab_solve_raw<float>(hz_handle*, Level&, int, const c64*, c64*, int, cudaStream_t);
-template void slab_solve_raw<double>(hz_handle*, Level&, int, const c128*, c128*, int, cudaStream_t);
-template void slab_solve_raw_scratch<float>(hz_handle*, Level&, int, const c64*, c64*, int,
-                                            cudaStream_t, c64*, c64*, c64*);
-template void slab_solve_raw_scratch<double>(hz_handle*, Level&, int, const c128*, c128*, int,
-                                             cudaStream_t, c128*, c128*, c128*);
 
 }  // namespace hz
