@@ -165,15 +165,14 @@ struct FactorPanel { static constexpr int BW = 4; };
 // Warps of the delayed Gauss-Jordan updates.  The 12 warps that do not share
 // a scheduler with the panel warp 0 (warp w runs on sub-partition w mod 4)
 // take strips of RPW consecutive rows; the three that do (warps 4, 8, 12)
-// take the few rows left over, and start only once warp 0 has finished its
-// panel (named barrier 1), so that they do not take issue slots from the
-// latency-bound panel elimination.
+// take at most one leftover row each, so that they take few issue slots from
+// the latency-bound panel elimination beside them.
 constexpr int kMainUpdateWarps = kThreads / 32 / 4 * 3;
 constexpr int kLateUpdateWarps = kThreads / 32 / 4 - 1;
 struct Strip {
   int row0;        // first row of this warp's strip, -1: no rows
   int nrows;       // rows of the strip (<= RPW)
-  bool late;       // shares warp 0's sub-partition (waits for the panel)
+  bool late;       // shares warp 0's sub-partition (at most one row)
 };
 template <int RPW>
 __device__ __forceinline__ Strip strip_of(int tid, int W) {
@@ -198,12 +197,7 @@ __device__ __forceinline__ Strip strip_of(int tid, int W) {
   }
   return s;
 }
-__device__ __forceinline__ void named_bar_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-__device__ __forceinline__ void named_bar_arrive(int id, int count) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
+
 
 // dst = -A B (NEG) or A B for W x W operands (A with row stride lda in shared
 // or global memory, B and dst dense W x W in shared memory), all kThreads
@@ -359,47 +353,53 @@ __device__ __forceinline__ void panel_dispatch(cplx<R>* S, cplx<R>* Cm, const cp
 
 // Delayed rank-pbw update S -= Cp^T Rm on rows row0 .. row0+nrows-1 (nrows <=
 // RPW) and columns lane + 32 b outside panels q-1 (from pp0) and q (p0, bw):
-// one warp, RPW x CPL complex accumulators in registers.
+// one warp.  The pbw x CPL rowmod values of this lane's columns stay in
+// registers; the rows are updated one after the other (CPL accumulators),
+// with the colmod entries of a row read as broadcasts.
+template <typename R, int CPL, int BW>
+__device__ __forceinline__ void strip_row(cplx<R>* Srow, const cplx<R>* Cp, int W, int i,
+                                          const cplx<R> (&rv)[BW][CPL], const bool (&ok)[CPL],
+                                          int pbw) {
+  cplx<R> x[CPL];
+#pragma unroll
+  for (int b = 0; b < CPL; ++b) x[b] = ok[b] ? Srow[32 * b] : mk<R>(0, 0);
+#pragma unroll
+  for (int t = 0; t < BW; ++t) {
+    const cplx<R> cv = (t < pbw) ? Cp[t * W + i] : mk<R>(0, 0);   // same address across the warp
+#pragma unroll
+    for (int b = 0; b < CPL; ++b) {
+      x[b].re -= cv.re * rv[t][b].re - cv.im * rv[t][b].im;
+      x[b].im -= cv.re * rv[t][b].im + cv.im * rv[t][b].re;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < CPL; ++b)
+    if (ok[b]) Srow[32 * b] = x[b];
+}
+
 template <typename R, int RPW, int CPL, int BW>
 __device__ __forceinline__ void strip_update(cplx<R>* S, const cplx<R>* Cp, const cplx<R>* Rm,
                                              int W, int row0, int nrows, int pp0, int p0, int bw,
                                              int pbw, int lane) {
-  const cplx<R> zero = mk<R>(0, 0);
-  cplx<R> acc[RPW][CPL];
+  bool ok[CPL];
 #pragma unroll
-  for (int a = 0; a < RPW; ++a)
-#pragma unroll
-    for (int b = 0; b < CPL; ++b) {
-      const int i = row0 + a, j = lane + 32 * b;
-      acc[a][b] = (a < nrows && j < W) ? S[i * W + j] : zero;
-    }
-#pragma unroll
-  for (int t = 0; t < BW; ++t) {
-    if (t >= pbw) break;
-    cplx<R> rv[CPL];
-#pragma unroll
-    for (int b = 0; b < CPL; ++b) {
-      const int j = lane + 32 * b;
-      rv[b] = (j < W && (j < pp0 || j >= p0 + bw)) ? Rm[t * W + j] : zero;
-    }
-#pragma unroll
-    for (int a = 0; a < RPW; ++a) {
-      const int i = row0 + a;
-      const cplx<R> cv = (a < nrows) ? Cp[t * W + i] : zero;   // same address across the warp
-#pragma unroll
-      for (int b = 0; b < CPL; ++b) {
-        acc[a][b].re -= cv.re * rv[b].re - cv.im * rv[b].im;
-        acc[a][b].im -= cv.re * rv[b].im + cv.im * rv[b].re;
-      }
-    }
+  for (int b = 0; b < CPL; ++b) {
+    const int j = lane + 32 * b;
+    ok[b] = j < W && (j < pp0 || j >= p0 + bw);
   }
+  cplx<R> rv[BW][CPL];
 #pragma unroll
-  for (int a = 0; a < RPW; ++a)
+  for (int t = 0; t < BW; ++t)
 #pragma unroll
-    for (int b = 0; b < CPL; ++b) {
-      const int i = row0 + a, j = lane + 32 * b;
-      if (a < nrows && j < W && (j < pp0 || j >= p0 + bw)) S[i * W + j] = acc[a][b];
-    }
+    for (int b = 0; b < CPL; ++b)
+      rv[t][b] = (t < pbw && ok[b]) ? Rm[t * W + lane + 32 * b] : mk<R>(0, 0);
+  cplx<R>* S0 = S + (size_t)row0 * W + lane;
+  if (nrows == RPW) {
+#pragma unroll
+    for (int a = 0; a < RPW; ++a) strip_row<R, CPL, BW>(S0 + a * W, Cp, W, row0 + a, rv, ok, pbw);
+  } else {
+    for (int a = 0; a < nrows; ++a) strip_row<R, CPL, BW>(S0 + a * W, Cp, W, row0 + a, rv, ok, pbw);
+  }
 }
 
 // Shared-memory work areas of the Gauss-Jordan inverse.
@@ -443,11 +443,7 @@ __device__ void gj_inverse(cplx<R>* S, cplx<R>* Gl, const GJWork<R>& w, int W, c
     if (warp == 0) {
       if (bw > 0)
         panel_dispatch<R, BW>(S, Cq, Cp, w.Rm, pbw, w.pinv, w.prow, w.piv, w.used, W, p0, bw, lane);
-      if (pbw > 0) named_bar_arrive(1, 32 * (1 + kLateUpdateWarps));
-    } else if (pbw > 0 && (su.late || su.row0 >= 0)) {
-      if (su.late) named_bar_sync(1, 32 * (1 + kLateUpdateWarps));
-    }
-    if (warp != 0 && pbw > 0 && su.row0 >= 0) {
+    } else if (pbw > 0 && su.row0 >= 0) {
       // delayed rank-pbw update of panel q-1 on every column outside panels
       // q-1 and q (a late warp has at most one row: a one-row tile)
       if (su.late)
