@@ -200,12 +200,13 @@ __device__ __forceinline__ Strip strip_of(int tid, int W) {
 
 
 // dst = -A B (NEG) or A B for W x W operands (A with row stride lda in shared
-// or global memory, B and dst dense W x W in shared memory), all kThreads
+// or global memory, read through L2 only if CG; B and dst dense W x W in
+// shared memory), all kThreads
 // threads: warp w takes rows w*RPW .. w*RPW+RPW-1, lane l takes columns l,
 // l+32, ... (CPL of them).  A reads are broadcasts and B / dst accesses are
 // consecutive across the warp, so no shared-memory access conflicts.  The
 // caller synchronises.
-template <typename R, int RPW, int CPL, bool NEG = true>
+template <typename R, int RPW, int CPL, bool NEG = true, bool CG = false>
 __device__ __forceinline__ void gemm_strip(const cplx<R>* A, int lda, const cplx<R>* B,
                                            cplx<R>* dst, int W) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,7 +227,8 @@ __device__ __forceinline__ void gemm_strip(const cplx<R>* A, int lda, const cplx
     }
 #pragma unroll
     for (int a = 0; a < RPW; ++a) {
-      const cplx<R> av = (i0 + a < W) ? A[(i0 + a) * lda + l] : zero;
+      const cplx<R> av = (i0 + a < W) ? (CG ? ldcg(A + (i0 + a) * lda + l) : A[(i0 + a) * lda + l])
+                                      : zero;
 #pragma unroll
       for (int b = 0; b < CPL; ++b) cfma(acc[a][b], av, bv[b]);
     }
@@ -453,23 +455,33 @@ __device__ void gj_inverse(cplx<R>* S, cplx<R>* Gl, const GJWork<R>& w, int W, c
     }
     __syncthreads();
     if (bw == 0) break;
-    // rowmod of panel q's pivots on the other columns:
-    // R_t = (S[r_t] - sum_{s<t} colmod_s[r_t] R_s) inv_t
-    for (int j = tid; j < W; j += kThreads) {
-      if (j >= p0 && j < p0 + bw) continue;
+    // rowmod of panel q's pivots on the other columns (one thread per column,
+    // W <= kThreads): R_t = (S[r_t] - sum_{s<t} colmod_s[r_t] R_s) inv_t.  All
+    // operands are loaded before the short recurrence runs.
+    if (tid < W && (tid < p0 || tid >= p0 + bw)) {
+      const int j = tid;
+      int r[BW];
+      cplx<R> u[BW], iv[BW], c[BW][BW];
+#pragma unroll
+      for (int t = 0; t < BW; ++t) r[t] = (t < bw) ? w.prow[t] : 0;
+#pragma unroll
+      for (int t = 0; t < BW; ++t) {
+        u[t] = S[r[t] * W + j];
+        iv[t] = w.pinv[t];
+#pragma unroll
+        for (int s2 = 0; s2 < t; ++s2) c[t][s2] = Cq[s2 * W + r[t]];
+      }
       cplx<R> rw[BW];
 #pragma unroll
       for (int t = 0; t < BW; ++t) {
         if (t >= bw) break;
-        const int r = w.prow[t];
-        cplx<R> acc = S[r * W + j];
+        cplx<R> acc = u[t];
 #pragma unroll
         for (int s2 = 0; s2 < t; ++s2) {
-          const cplx<R> c = Cq[s2 * W + r];
-          acc.re -= c.re * rw[s2].re - c.im * rw[s2].im;
-          acc.im -= c.re * rw[s2].im + c.im * rw[s2].re;
+          acc.re -= c[t][s2].re * rw[s2].re - c[t][s2].im * rw[s2].im;
+          acc.im -= c[t][s2].re * rw[s2].im + c[t][s2].im * rw[s2].re;
         }
-        rw[t] = acc * w.pinv[t];
+        rw[t] = acc * iv[t];
         w.Rm[t * W + j] = rw[t];
       }
     }
@@ -714,6 +726,11 @@ struct ProdDesc {
   void* A;                   // F' (forward) or E' (backward), [ny][mstride], row stride wp
   size_t gstride, mstride;
   void* out;                 // Phi or Psi block, row stride wp
+  // fused launch only: a product task counts itself done in group counter
+  // `gctr`; a prefix task (prefix = 1: the in-group prefix products of one
+  // group and direction, k0 = first segment, n = segments, dir = +-1, from the
+  // products in A to `out`) waits until counter `gctr` reaches `gneed`
+  int prefix, gctr, gneed;
 };
 
 template <typename R, int RPW, int CPL>
@@ -819,6 +836,40 @@ __global__ void __launch_bounds__(kThreads) segment_prefix_kernel(const PrefixDe
   }
 }
 
+// In-group prefix products of one group and direction (see
+// segment_prefix_kernel) inside the fused launch: the products were written
+// by other CTAs of the same launch, so they are read through L2 only.
+template <typename R, int RPW, int CPL>
+__device__ void prefix_task(const ProdDesc& d) {
+  const int W = d.W, wp = d.wp, tid = threadIdx.x, WW = W * W;
+  const cplx<R>* src = (const cplx<R>*)d.A;
+  cplx<R>* dst = (cplx<R>*)d.out;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* M = (cplx<R>*)smem_raw;
+  cplx<R>* T = M + WW;
+  {
+    const cplx<R>* s0 = src + (size_t)d.k0 * d.mstride;
+    cplx<R>* d0 = dst + (size_t)d.k0 * d.mstride;
+    for (int e = tid; e < WW; e += kThreads) {
+      const int i = e / W, j = e - i * W;
+      const cplx<R> v = ldcg(s0 + i * wp + j);
+      M[e] = v;
+      d0[i * wp + j] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = 1; i < d.n; ++i) {
+    const int q = d.k0 + d.dir * i;
+    gemm_strip<R, RPW, CPL, false, true>(src + (size_t)q * d.mstride, wp, M, T, W);
+    __syncthreads();
+    cplx<R>* out = dst + (size_t)q * d.mstride;
+    for (int e = tid; e < WW; e += kThreads) out[(e / W) * wp + e % W] = T[e];
+    cplx<R>* x = M;
+    M = T;
+    T = x;
+  }
+}
+
 // Factorisation and products in one cooperative launch (all CTAs resident):
 // CTAs 0..nf-1 run the elimination chains and publish their progress; the
 // others take product tasks in readiness order and wait (bounded, 10 s, then
@@ -826,7 +877,7 @@ __global__ void __launch_bounds__(kThreads) segment_prefix_kernel(const PrefixDe
 template <typename R, int RPW, int CPL, int PRPW, int PCPL>
 __global__ void __launch_bounds__(kThreads) slab_factor_fused_kernel(
     const FactorDesc* fd, int nf, const ProdDesc* pd, int np, int* progress, int* next_task,
-    int* flag) {
+    int* gdone, int* flag) {
   if ((int)blockIdx.x < nf) {
     factor_chain<R, RPW, CPL>(fd[blockIdx.x], progress + blockIdx.x);
     return;
@@ -849,12 +900,35 @@ __global__ void __launch_bounds__(kThreads) slab_factor_fused_kernel(
             }
           }
         }
+        // a prefix task also waits for its group's products (all of them
+        // precede it in the task order, so resident CTAs hold them)
+        if (!sh_abort && d.prefix && ld_acquire(gdone + d.gctr) < d.gneed) {
+          const uint64_t t0 = gtimer();
+          while (ld_acquire(gdone + d.gctr) < d.gneed) {
+            __nanosleep(1000);
+            if (gtimer() - t0 > 10000000000ull) {
+              atomicExch(flag, DEV_TIMEOUT);
+              sh_abort = 1;
+              break;
+            }
+          }
+        }
       }
     }
     __syncthreads();
     const int task = sh_task;
     if (task >= np || sh_abort) return;
-    product_task<R, PRPW, PCPL>(pd[task]);
+    const ProdDesc& d = pd[task];
+    if (d.prefix) {
+      prefix_task<R, PRPW, PCPL>(d);
+    } else {
+      product_task<R, PRPW, PCPL>(d);
+      __syncthreads();
+      if (threadIdx.x == 0 && d.gctr >= 0) {   // every thread's stores precede the barrier
+        __threadfence();
+        atomicAdd(gdone + d.gctr, 1);
+      }
+    }
     __syncthreads();
   }
 }
@@ -1629,8 +1703,11 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
                                  std::to_string(maxW) + ")");
   std::vector<FactorDesc> fd;
   std::vector<MidDesc> md;
-  std::vector<ProdDesc> pd;
-  std::vector<PrefixDesc> xd;
+  std::vector<ProdDesc> pd, pf;   // product tasks; prefix tasks of the fused launch
+  std::vector<PrefixDesc> xd;     // prefix tasks of the separate launch
+  const int NG = L.NG;
+  // group completion counter of slab j, direction bwd (0: Phi, 1: Psi), group g
+  auto gctr = [&](int j, int bwd, int g) { return ((j - 1) * 2 + bwd) * NG + g; };
   for (int j = 1; j <= J; ++j) {
     const Slab& S = L.slabs[j];
     const int dg = L.fe ? 0 : 1;   // finite differences: 5-point, diagonal couplings
@@ -1645,34 +1722,55 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
       const int need = (sg.z > 0 ? sg.x : L.ny - 1 - sg.x) + sg.y;
       pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 0, (q != 0 && q != L.S0) ? 1 : 0,
                             stage_a, fchain, need, S.st, S.G, S.F, S.gstride, S.mstride,
-                            (cplx<R>*)S.Phi + (size_t)q * S.mstride});
+                            (cplx<R>*)S.Phi + (size_t)q * S.mstride, 0, gctr(j, 0, sg.w), 0});
       pd.push_back(ProdDesc{S.W, S.wp, sg.x, sg.y, sg.z, 1, 1, stage_a, fchain, need, S.st, S.G,
-                            S.E, S.gstride, S.mstride, (cplx<R>*)S.Psi + (size_t)q * S.mstride});
+                            S.E, S.gstride, S.mstride, (cplx<R>*)S.Psi + (size_t)q * S.mstride, 0,
+                            gctr(j, 1, sg.w), 0});
     }
     // in-group prefix products: forward for every group but the first of a
-    // half (whose in-group values are already true), backward for all
-    for (const int4& g : L.grp) {
+    // half (whose in-group values are already true), backward for all; a
+    // group is complete once the chain has finished its last segment
+    for (int gi = 0; gi < NG; ++gi) {
+      const int4 g = L.grp[gi];
       const int n = g.y - g.x + 1;
-      if (g.w != 0) xd.push_back(PrefixDesc{S.W, S.wp, g.x, n, +1, S.Phi, S.PhiP, S.mstride});
+      const int4 last = L.seg[g.y];
+      const int fchain = 2 * (j - 1) + (last.z > 0 ? 0 : 1);
+      const int need = (last.z > 0 ? last.x : L.ny - 1 - last.x) + last.y;
+      if (g.w != 0) {
+        xd.push_back(PrefixDesc{S.W, S.wp, g.x, n, +1, S.Phi, S.PhiP, S.mstride});
+        pf.push_back(ProdDesc{S.W, S.wp, g.x, n, +1, 0, 0, 0, fchain, need, nullptr, nullptr,
+                              S.Phi, 0, S.mstride, S.PhiP, 1, gctr(j, 0, gi), n});
+      }
       xd.push_back(PrefixDesc{S.W, S.wp, g.y, n, -1, S.Psi, S.PsiP, S.mstride});
+      pf.push_back(ProdDesc{S.W, S.wp, g.y, n, -1, 1, 0, 0, fchain, need, nullptr, nullptr, S.Psi,
+                            0, S.mstride, S.PsiP, 1, gctr(j, 1, gi), n});
     }
   }
-  // product tasks in the order their rows become final
-  std::stable_sort(pd.begin(), pd.end(),
-                   [](const ProdDesc& x, const ProdDesc& y) { return x.need < y.need; });
+  // tasks in the order their rows become final; a prefix task after every
+  // product task of its group (equal needs: products first)
+  auto by_need = [](const ProdDesc& x, const ProdDesc& y) { return x.need < y.need; };
+  std::stable_sort(pd.begin(), pd.end(), by_need);
+  std::vector<ProdDesc> pdx(pd);
+  pdx.insert(pdx.end(), pf.begin(), pf.end());
+  std::stable_sort(pdx.begin(), pdx.end(), by_need);
   const size_t b_fd = sizeof(FactorDesc) * fd.size(), b_md = sizeof(MidDesc) * md.size();
   const size_t b_pd = sizeof(ProdDesc) * pd.size(), b_xd = sizeof(PrefixDesc) * xd.size();
-  unsigned char* d_desc = (unsigned char*)dmalloc(b_fd + b_md + b_pd + b_xd);
+  const size_t b_pdx = sizeof(ProdDesc) * pdx.size();
+  unsigned char* d_desc = (unsigned char*)dmalloc(b_fd + b_md + b_pd + b_xd + b_pdx);
   FactorDesc* d_fd = (FactorDesc*)d_desc;
   MidDesc* d_md = (MidDesc*)(d_desc + b_fd);
   ProdDesc* d_pd = (ProdDesc*)(d_desc + b_fd + b_md);
   PrefixDesc* d_xd = (PrefixDesc*)(d_desc + b_fd + b_md + b_pd);
+  ProdDesc* d_pdx = (ProdDesc*)(d_desc + b_fd + b_md + b_pd + b_xd);
   HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), b_fd, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaMemcpyAsync(d_md, md.data(), b_md, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaMemcpyAsync(d_pd, pd.data(), b_pd, cudaMemcpyHostToDevice, s));
   HZ_CU(cudaMemcpyAsync(d_xd, xd.data(), b_xd, cudaMemcpyHostToDevice, s));
-  int* d_sync = (int*)dmalloc(sizeof(int) * (fd.size() + 1));   // chain progress, task counter
-  HZ_CU(cudaMemsetAsync(d_sync, 0, sizeof(int) * (fd.size() + 1), s));
+  HZ_CU(cudaMemcpyAsync(d_pdx, pdx.data(), b_pdx, cudaMemcpyHostToDevice, s));
+  // chain progress [nf], task counter [1], group completion counters [2 J NG]
+  const size_t nsync = fd.size() + 1 + (size_t)2 * J * NG;
+  int* d_sync = (int*)dmalloc(sizeof(int) * nsync);
+  HZ_CU(cudaMemsetAsync(d_sync, 0, sizeof(int) * nsync, s));
   int coop = 0;
   HZ_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
   const size_t smem_x = 2 * (size_t)maxW * maxW * el;   // prefix products: M, T
@@ -1685,16 +1783,18 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
     int per_sm = 0;
     HZ_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfused, kThreads, smem_u));
     const long resident = (long)per_sm * h->sms;
-    const int nf = (int)fd.size(), np = (int)pd.size();
-    if (coop && resident > nf) {
-      const unsigned grid = (unsigned)std::min<long>(resident, (long)nf + np);
+    const int nf = (int)fd.size(), np = (int)pd.size(), npx = (int)pdx.size();
+    const bool fused = coop && resident > nf;
+    if (fused) {
+      const unsigned grid = (unsigned)std::min<long>(resident, (long)nf + npx);
       const FactorDesc* a0 = d_fd;
-      const ProdDesc* a2 = d_pd;
+      const ProdDesc* a2 = d_pdx;
       int* a4 = d_sync;
       int* a5 = d_sync + nf;
-      int* a6 = h->dev_flag;
-      void* args[] = {(void*)&a0, (void*)&nf, (void*)&a2, (void*)&np, (void*)&a4, (void*)&a5,
-                      (void*)&a6};
+      int* a6 = d_sync + nf + 1;
+      int* a7 = h->dev_flag;
+      void* args[] = {(void*)&a0, (void*)&nf, (void*)&a2, (void*)&npx, (void*)&a4, (void*)&a5,
+                      (void*)&a6, (void*)&a7};
       timed(h, "slab_factor", 0.0, s, [&] {
         HZ_CU(cudaLaunchCooperativeKernel((const void*)kfused, dim3(grid), dim3(kThreads), args,
                                           smem_u, s));
@@ -1709,10 +1809,13 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
       h->launches += 2;
     }
     timed(h, "slab_middle", 0.0, s, [&] { km<<<(unsigned)md.size(), kThreads, smem_m, s>>>(d_md); });
-    HZ_CU(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
-    timed(h, "segment_prefix", 0.0, s,
-          [&] { kx<<<(unsigned)xd.size(), kThreads, smem_x, s>>>(d_xd); });
-    h->launches += 2;
+    h->launches += 1;
+    if (!fused) {   // (inside the fused launch otherwise)
+      HZ_CU(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
+      timed(h, "segment_prefix", 0.0, s,
+            [&] { kx<<<(unsigned)xd.size(), kThreads, smem_x, s>>>(d_xd); });
+      h->launches += 1;
+    }
   };
   // factor: update strips (RPW rows, CPL columns per lane); product GEMMs:
   // 16 warps x PRPW rows, PCPL columns per lane
