@@ -537,6 +537,18 @@ struct FactorDesc {
 __host__ __device__ __forceinline__ int lplane(int dir) { return dir > 0 ? 0 : 6; }
 __host__ __device__ __forceinline__ int rplane(int dir) { return dir > 0 ? 6 : 0; }
 
+// Asynchronous global -> shared copy of one complex element (cp.async); the
+// copies of a thread complete at its cp_async_wait_all.
+template <typename R>
+__device__ __forceinline__ void cp_async_el(cplx<R>* dst, const cplx<R>* src) {
+  if constexpr (sizeof(cplx<R>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Release store / acquire load of a progress counter (gpu scope).
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -548,7 +560,7 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 }
 
 // One elimination chain; if `progress` is given, the number of finished rows
-// is published there (release) after each G_t is stored.
+// is published there (release) after every fourth G_t and the last one.
 template <typename R, int RPW, int CPL>
 __device__ void factor_chain(const FactorDesc& d, int* progress) {
   const int W = d.W, wp = d.wp, tid = threadIdx.x, dir = d.dir;
@@ -559,24 +571,39 @@ __device__ void factor_chain(const FactorDesc& d, int* progress) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>*S, *Gl, *cpl;
   GJWork<R> w;
-  factor_smem<R>(smem_raw, W, 9, &S, &Gl, &w, &cpl);
-  cplx<R>* cL = cpl;                             // L_t (3 x W)
-  cplx<R>* cD = cL + 3 * W;                      // D (3 x W)
-  cplx<R>* cR = cD + 3 * W;                      // R_{t-1} (3 x W)
+  factor_smem<R>(smem_raw, W, 18, &S, &Gl, &w, &cpl);
   const cplx<R> zero = mk<R>(0, 0);
   const int pl = lplane(dir), pr = rplane(dir);
   cplx<R>* Gp = Gl;                              // G_{t-1}
   cplx<R>* Sp = S;                               // the other W x W buffer
+  // couplings of row t in buffer t & 1: L_t, D_t, R_{t-1} (3 x W each); those
+  // of row t+1 are copied (cp.async) while row t is inverted
+  auto stage = [&](cplx<R>* cb, int t, bool async) {
+    const int k = d.k0 + dir * t;
+    const cplx<R>* stk = st + (size_t)k * 9 * wp;
+    const cplx<R>* stp = st + (size_t)(k - dir) * 9 * wp;
+    for (int i = tid; i < 3 * W; i += kThreads) {
+      const int q = i / W, e = i - q * W;
+      if (async) {
+        cp_async_el(cb + i, stk + (pl + q) * wp + e);
+        cp_async_el(cb + 3 * W + i, stk + (3 + q) * wp + e);
+        cp_async_el(cb + 6 * W + i, stp + (pr + q) * wp + e);
+      } else {
+        cb[i] = stk[(pl + q) * wp + e];
+        cb[3 * W + i] = stk[(3 + q) * wp + e];
+        cb[6 * W + i] = (t > 0) ? stp[(pr + q) * wp + e] : zero;
+      }
+    }
+    if (async) cp_async_commit();
+  };
+  stage(cpl, 0, false);
 
   for (int t = 0; t < d.n; ++t) {
     const int k = d.k0 + dir * t;
-    const cplx<R>* stk = st + (size_t)k * 9 * wp;
-    for (int i = tid; i < 3 * W; i += kThreads) {     // stage the couplings
-      const int q = i / W, e = i - q * W;
-      cL[i] = stk[(pl + q) * wp + e];
-      cD[i] = stk[(3 + q) * wp + e];
-      cR[i] = (t > 0) ? st[(size_t)(k - dir) * 9 * wp + (pr + q) * wp + e] : zero;
-    }
+    cplx<R>* cL = cpl + (t & 1) * 9 * W;           // L_t (3 x W)
+    cplx<R>* cD = cL + 3 * W;                      // D (3 x W)
+    cplx<R>* cR = cD + 3 * W;                      // R_{t-1} (3 x W)
+    if (t > 0) cp_async_wait_all();
     __syncthreads();
     // Gp holds G_{t-1}; S_t is formed in the other buffer (or, for
     // tridiagonal couplings, in Gp after X = G_{t-1} R_{t-1} went to the
@@ -626,10 +653,14 @@ __device__ void factor_chain(const FactorDesc& d, int* progress) {
       }
     }
     __syncthreads();
+    if (t + 1 < d.n) stage(cpl + ((t + 1) & 1) * 9 * W, t + 1, true);
     gj_inverse<R, RPW, CPL>(Sx, Gx, w, W, su, G + (size_t)k * d.gstride);
     Gp = Gx;
     Sp = Sx;
-    if (progress && tid == 0) {   // every thread's G_t stores precede the barrier above
+    // every thread's G_t stores precede the barrier that ends gj_inverse; the
+    // fence stalls thread 0 (and through the next barrier the chain), so the
+    // progress is published every 4 rows and at the last row
+    if (progress && tid == 0 && (((t + 1) & 3) == 0 || t + 1 == d.n)) {
       __threadfence();
       st_release(progress, t + 1);
     }
@@ -1686,7 +1717,7 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   const size_t el = sizeof(cplx<R>);
   int maxW = 0;
   for (int j = 1; j <= J; ++j) maxW = std::max(maxW, L.slabs[j].W);
-  const size_t smem_f = factor_smem_bytes(maxW, 9, el, BW);
+  const size_t smem_f = factor_smem_bytes(maxW, 18, el, BW);
   const size_t smem_m = factor_smem_bytes(maxW, 15, el, BW);
   // products: M, T, the couplings and, when it fits, A_t
   const size_t smem_p2 = (2 * (size_t)maxW * maxW + 3 * (size_t)maxW) * el;
