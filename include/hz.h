@@ -70,7 +70,8 @@ typedef struct {
   double tol;           /* stop at ||b - A u||_2 / ||b||_2 <= tol (per right-hand side) */
   int    max_rhs;       /* right-hand sides per hz_solve call (buffer capacity) */
   int    segments;      /* block-row segments per slab solve, over both elimination
-                         * chains (0: automatic, about 2 sqrt(N_y); at least 2) */
+                         * chains (0: automatic, about 2 N_y^(2/3) capped at the SM
+                         * count; at least 2) */
   double c_pml;         /* PML "typical velocity" (Section 2.1); 0: mean of c over the
                          * unknowns, recomputed by hz_setup / hz_set_medium */
 } hz_params;
@@ -185,9 +186,14 @@ hz_status hz_get_stats(const hz_handle* h, hz_stats* out);
  * and the algorithmic bytes those launches move (method minimum: each
  * factor block read once per pass, vectors once).  Tags: "slab_solve" (one
  * whole subdomain solve of SubdomSolve, Table 2), its kernels "slab_rhs",
- * "slab_fwd_pass1", "slab_carry", "slab_fwd_bwd1", "slab_bwd", and the
- * factorisation kernels "slab_factor", "slab_middle", "segment_product"
- * (bytes 0).  Unknown tags return zeros. */
+ * "slab_fwd_pass1", "slab_carry" (in-group segment carries),
+ * "slab_carry_bound" (group boundary carries), "slab_fwd_bwd1", "slab_bwd";
+ * the factorisation kernels "slab_factor" (on devices with cooperative
+ * launch: the elimination chains together with the operator, segment and
+ * prefix products), "slab_middle", and, without cooperative launch,
+ * "segment_product" and "segment_prefix" (bytes 0); the matrix-free operator
+ * "stencil_c64", "stencil_c128" (Eq. 40 apply, residual, Jacobi step).
+ * Unknown tags return zeros. */
 hz_status hz_enable_timing(hz_handle* h, int on);
 hz_status hz_kernel_timing(hz_handle* h, const char* tag, double* ms, long long* launches,
                            double* bytes);
