@@ -29,7 +29,7 @@
 // segments of a half form groups of about sqrt(P/2); the carry inside every
 // group runs from a zero group start (all groups in parallel), one short
 // chain per half carries the group boundary values through the in-group
-// prefix products PhiP / PsiP (formed after the factorisation), and each
+// prefix products PhiP / PsiP (formed with the factorisation), and each
 // segment's true start follows from its in-group value by one more product
 // with PhiP / PsiP in the prologue of the re-run.
 //
