@@ -55,15 +55,28 @@ __global__ void __launch_bounds__(kRedThreads) multi_dot_kernel(const c128* __re
 }
 
 // out[r][i] (+)= sum_blk partial[r][i][blk]  (fixed order: deterministic)
+// One warp per (rhs, vector): lane l sums partials l, l + 32, ..., then a
+// shuffle tree (fixed order, so the result is repeatable).
 __global__ void reduce_partials_kernel(const double* partial, int nblk, int nv, int nr, c128* out,
                                        int ostride) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= nv * nr) return;
-  const double* p = partial + (size_t)t * nblk * 2;
+  const double2* p = reinterpret_cast<const double2*>(partial + (size_t)t * nblk * 2);
   double re = 0, im = 0;
-  for (int b = 0; b < nblk; ++b) { re += p[2 * b]; im += p[2 * b + 1]; }
-  int r = t / nv, i = t - r * nv;
-  out[(size_t)r * ostride + i] = mk(re, im);
+  for (int b = lane; b < nblk; b += 32) {
+    const double2 v = p[b];
+    re += v.x;
+    im += v.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    const int r = t / nv, i = t - r * nv;
+    out[(size_t)r * ostride + i] = mk(re, im);
+  }
 }
 
 // hc[r][i] += hc2[r][i] for i < nv
@@ -213,7 +226,7 @@ struct Gm {
   void dots(const c128* V, size_t vstride, int nv, const c128* w, c128* out, int ostride) {
     dim3 grid(kRedBlocks, nr);
     multi_dot_kernel<<<grid, kRedThreads, 0, s>>>(V, vstride, nv, w, n, nr, h->red);
-    reduce_partials_kernel<<<cdiv(nv * nr, 64), 64, 0, s>>>(h->red, kRedBlocks, nv, nr, out, ostride);
+    reduce_partials_kernel<<<cdiv(nv * nr, 4), 128, 0, s>>>(h->red, kRedBlocks, nv, nr, out, ostride);
     h->launches += 2;
   }
 };
