@@ -44,6 +44,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-source batched leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient leg")
     ap.add_argument("--workload", type=int, default=CONFIG_INDEX, choices=[1, 2, 3],
                     help="benchmark configuration (default 2, the headline workload)")
     ap.add_argument("--n", type=int, default=0,
@@ -144,6 +145,49 @@ def _traffic(tag):
         return None
     e = d.get("kernels", {}).get(tag)
     return None if e is None else e.get("dram_bytes_per_launch_full_size")
+
+
+def adjoint_leg(hz, synth, stream, flush, n=512, reps=3):
+    """hz_grad on the 2-D adjoint workload (smooth random medium, blurred start
+    model, 8 sources and 16 receivers, two-grid, J = 4, mixed): one gradient
+    step = hz_factor at the start model + hz_grad (forward and adjoint solves
+    of the 8 sources, misfit, gradient).  The observed data are the receiver
+    values of the true model's solution computed by the same solver."""
+    import numpy as np
+    import torch
+    cfg = synth.adjoint_workload_2d(n)
+    m_true, m0 = synth.medium(cfg, "true"), synth.medium(cfg, "start")
+    c_pml = float(np.mean(1.0 / np.sqrt(m0)))
+    src = np.array([int(i) * cfg.N + int(j) for i, j in synth.source_nodes(cfg)])
+    rec = synth.receivers(cfg)
+    st = hz.Solver.from_workload(cfg, m=m_true, c_pml=c_pml)
+    st.factor()
+    u, _ = st.solve(torch.from_numpy(synth.sources(cfg)).cuda())
+    d = u.reshape(cfg.n_src, -1)[:, torch.from_numpy(rec).cuda()].contiguous()
+    st.close()
+    s0 = hz.Solver.from_workload(cfg, m=m0, c_pml=c_pml)
+    s0.factor()
+    s0.grad(src, rec, d)
+    ts, phi, info = [], 0.0, {}
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s0.factor()
+        phi, g, info = s0.grad(src, rec, d)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    s0.close()
+    t = statistics.mean(ts) / 1000.0
+    return {"workload": f"{cfg.name}: {cfg.N}x{cfg.N} dof, J={cfg.J}, two-grid, mixed, "
+                        f"{cfg.n_src} sources, {cfg.n_rec} receivers",
+            "step": "hz_factor + hz_grad (forward + adjoint solves, misfit, gradient)",
+            "time_s": t, "value": 2 * cfg.n_src * cfg.ndof / t / 1e6,
+            "unit": "Mdof/s (dof x solves: forward and adjoint per source)",
+            "misfit": phi, "iters_max": info.get("iters_max"), "relres_max": info.get("relres_max")}
 
 
 def cpu_baseline(cfg, iters_hint):
@@ -459,6 +503,8 @@ def main():
                            "iters_max": it8, "relres_max": rr8,
                            "speedup_per_rhs_vs_single": 8 * (ms_step / 1000.0) / t8}
         s8.close()
+    if rank == 0 and ws == 1 and not args.no_adjoint and not args.n and args.workload == 2:
+        line["adjoint"] = adjoint_leg(hz, synth, stream, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload != 3:
         line["cpu_baseline"] = cpu_baseline(cfg, max(iters))
     if rank == 0:
