@@ -347,14 +347,17 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
   // substitution, and the segments of a half into about sqrt(P/2) groups for
   // the two-level carries.  Sequential steps of a solve per half: ~4 L in
   // the segment passes plus ~4 sqrt(P/2) in the carries; the minimum lies at
-  // P/2 ~ ny^(2/3).  Automatic P is that, capped at the SM count (every
-  // segment pass is one CTA per segment, one wave).
+  // P/2 ~ ny^(2/3).  Automatic P is that, capped so that every segment pass
+  // (one CTA per segment) is one wave: twice the SM count in complex64 (two
+  // segment CTAs with 2-stage pipelines share an SM), the SM count in
+  // complex128 (one CTA with its full pipeline per SM).
   if (L.ny < 3) throw Failure(HZ_EINVAL, "a slab needs at least 3 rows");
   L.mid = (L.ny - 1) / 2;
   const int ntop = L.mid, nbot = L.ny - 1 - L.mid;
   int P = h->p.segments;
+  const int per_sm = (h->p.precision == HZ_MIXED) ? 2 : 1;
   if (P <= 0) P = std::min(2 * (int)std::lround(std::pow((double)L.ny, 2.0 / 3.0)),
-                           std::max(2, h->sms));
+                           std::max(2, per_sm * h->sms));
   P = std::max(2, std::min(P, L.ny - 1));
   int S0 = (P * ntop + L.ny / 2) / (L.ny - 1);      // segments in proportion to the chain lengths
   S0 = std::max(1, std::min(S0, std::min(P - 1, ntop)));

@@ -1927,6 +1927,10 @@ static void launch_solve(hz_handle* h, Level& L, Slab& S, SolveArgs<R> a, cudaSt
   set_solve_attrs<R, NR>();
   const int P = L.P, nr = a.nr;
   a.stages = pick_stages<R>(S, nr, NR);
+  // more segments than SMs: shallower pipelines, so that two segment CTAs
+  // share an SM and every segment pass stays one wave
+  if (P > h->sms)
+    while (a.stages > 1 && solve_smem<R>(S, nr, NR, a.stages) > (size_t)110 * 1024) --a.stages;
   const size_t smem = solve_smem<R>(S, nr, NR, a.stages);
   const double el = sizeof(cplx<R>);
   const double gbytes = (double)L.ny * S.W * S.W * el;          // one pass over G_0..G_{ny-1}
