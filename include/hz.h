@@ -153,6 +153,23 @@ hz_status hz_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_de
  * added PML columns wl (left) / wr (right), width W = hi-lo+1+wl+wr. */
 hz_status hz_slab_info(const hz_handle* h, int j, int* lo, int* hi, int* wl, int* wr, int* W);
 
+/* Layout of the parallel-in-y slab substitution (the twisted block LU that
+ * implements SubdomSolve, Table 2) for a slab of ny block rows; host only, no
+ * handle and no GPU needed.  segments: as hz_params.segments (<= 0:
+ * automatic, about 2 ny^(2/3), capped at max_auto; hz_setup uses twice the SM
+ * count in mixed precision, the SM count in plain FP64).  Outputs (host):
+ * *mid = the row where the two elimination chains meet, *P segments, the
+ * first *S0 on the top chain, *NG segment groups of the two-level carries,
+ * the first *G0 on the top chain.  seg_out (capacity seg_cap entries of 4
+ * ints, may be NULL): per segment first row, rows, direction (+1 top chain,
+ * -1 bottom chain), group; grp_out (capacity grp_cap entries of 4 ints, may be
+ * NULL): per group first segment, last segment, half (0 top, 1 bottom), index
+ * within the half.  HZ_EINVAL for ny < 3, a NULL count pointer or a capacity
+ * below the counts (the counts are still written). */
+hz_status hz_segment_layout(int ny, int segments, int max_auto, int* mid, int* P, int* S0,
+                            int* NG, int* G0, int* seg_out, int seg_cap, int* grp_out,
+                            int grp_cap);
+
 /* u_d = (A^(j))^-1 f_d for slab j (1..J) of the sweep level: f_dev, u_dev are
  * n_rhs * N_t * W complex128 ([rhs][y][local x]).  Requires hz_factor. */
 hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,

@@ -60,6 +60,8 @@ _SIGNATURES = {
     "hz_grad": (ctypes.c_int, [_H, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P,
                                       ctypes.POINTER(ctypes.c_double), _P, ctypes.POINTER(hz_stats)]),
     "hz_slab_info": (ctypes.c_int, [_H, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5),
+    "hz_segment_layout": (ctypes.c_int, [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int)] * 5
+                          + [_P, ctypes.c_int, _P, ctypes.c_int]),
     "hz_slab_solve": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hz_slab_solve_noalloc": (ctypes.c_int, [_H, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "hz_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(hz_stats)]),
@@ -73,6 +75,28 @@ _SIGNATURES = {
 }
 
 _lib = None
+
+
+def segment_layout(ny, segments=0, max_auto=304):
+    """Layout of the parallel-in-y slab substitution (hz_segment_layout; host
+    only): dict with mid, P, S0, NG, G0 and int arrays seg [P, 4] (first row,
+    rows, direction, group) and grp [NG, 4] (first segment, last segment, half,
+    index within the half)."""
+    import numpy as np
+    c = [ctypes.c_int() for _ in range(5)]
+    code = lib().hz_segment_layout(int(ny), int(segments), int(max_auto),
+                                   *[ctypes.byref(x) for x in c], None, 0, None, 0)
+    if code != 0:
+        raise HzError(code, "hz_segment_layout failed")
+    mid, P, S0, NG, G0 = (x.value for x in c)
+    seg = np.zeros((P, 4), dtype=np.int32)
+    grp = np.zeros((NG, 4), dtype=np.int32)
+    code = lib().hz_segment_layout(int(ny), int(segments), int(max_auto),
+                                   *[ctypes.byref(x) for x in c], seg.ctypes.data, P,
+                                   grp.ctypes.data, NG)
+    if code != 0:
+        raise HzError(code, "hz_segment_layout failed")
+    return dict(mid=mid, P=P, S0=S0, NG=NG, G0=G0, seg=seg, grp=grp)
 
 
 def declared_symbols(header: str = HEADER):

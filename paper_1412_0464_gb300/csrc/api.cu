@@ -321,6 +321,41 @@ hz_status hz_slab_info(const hz_handle* h, int j, int* lo, int* hi, int* wl, int
   return HZ_OK;
 }
 
+hz_status hz_segment_layout(int ny, int segments, int max_auto, int* mid, int* P, int* S0,
+                            int* NG, int* G0, int* seg_out, int seg_cap, int* grp_out,
+                            int grp_cap) {
+  if (!mid || !P || !S0 || !NG || !G0) return fail(nullptr, HZ_EINVAL, "NULL count pointer");
+  if (ny < 3) return fail(nullptr, HZ_EINVAL, "a slab needs at least 3 rows");
+  SegmentLayout L;
+  try {
+    L = segment_layout(ny, segments, max_auto);
+  } catch (const Failure& f) {
+    return fail(nullptr, f.st, f.msg);
+  }
+  *mid = L.mid;
+  *P = L.P;
+  *S0 = L.S0;
+  *NG = L.NG;
+  *G0 = L.G0;
+  if ((seg_out && seg_cap < L.P) || (grp_out && grp_cap < L.NG))
+    return fail(nullptr, HZ_EINVAL, "output capacity below the segment or group count");
+  if (seg_out)
+    for (int q = 0; q < L.P; ++q) {
+      seg_out[4 * q] = L.seg[q].x;
+      seg_out[4 * q + 1] = L.seg[q].y;
+      seg_out[4 * q + 2] = L.seg[q].z;
+      seg_out[4 * q + 3] = L.seg[q].w;
+    }
+  if (grp_out)
+    for (int g = 0; g < L.NG; ++g) {
+      grp_out[4 * g] = L.grp[g].x;
+      grp_out[4 * g + 1] = L.grp[g].y;
+      grp_out[4 * g + 2] = L.grp[g].z;
+      grp_out[4 * g + 3] = L.grp[g].w;
+    }
+  return HZ_OK;
+}
+
 hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,
                         void* stream) {
   if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");

@@ -145,6 +145,16 @@ struct Level {
   int4* grp_dev = nullptr;
 };
 
+// Layout of the parallel-in-y slab substitution for a slab of ny block rows:
+// meeting row, segments (first row, rows, direction +1 top / -1 bottom,
+// group) and segment groups (first segment, last segment, half, index within
+// the half).  segments <= 0: automatic, ~2 ny^(2/3) capped at max_auto.
+struct SegmentLayout {
+  int mid = 0, P = 0, S0 = 0, G0 = 0, NG = 0;
+  std::vector<int4> seg, grp;
+};
+SegmentLayout segment_layout(int ny, int segments, int max_auto);
+
 // Per-kernel event timing (enabled for roofline reporting): every launch of a
 // tagged kernel is bracketed by two events on its own stream.
 struct TagTiming {

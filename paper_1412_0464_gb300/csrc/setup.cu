@@ -234,6 +234,45 @@ __global__ void to_float_kernel(const double* a, float* b, size_t n) {
   if (i < n) b[i] = (float)a[i];
 }
 
+SegmentLayout segment_layout(int ny, int segments, int max_auto) {
+  if (ny < 3) throw Failure(HZ_EINVAL, "a slab needs at least 3 rows");
+  SegmentLayout L;
+  L.mid = (ny - 1) / 2;
+  const int ntop = L.mid, nbot = ny - 1 - L.mid;
+  int P = segments;
+  if (P <= 0) P = std::min(2 * (int)std::lround(std::pow((double)ny, 2.0 / 3.0)), std::max(2, max_auto));
+  P = std::max(2, std::min(P, ny - 1));
+  int S0 = (P * ntop + ny / 2) / (ny - 1);      // segments in proportion to the chain lengths
+  S0 = std::max(1, std::min(S0, std::min(P - 1, ntop)));
+  const int S1 = std::min(P - S0, nbot);
+  P = S0 + S1;
+  L.P = P;
+  L.S0 = S0;
+  L.seg.assign(P, int4{0, 0, 0, 0});
+  for (int q = 0; q < S0; ++q) {
+    const int a0 = (int)((long long)ntop * q / S0), a1 = (int)((long long)ntop * (q + 1) / S0);
+    L.seg[q] = int4{a0, a1 - a0, +1, 0};
+  }
+  for (int q = 0; q < S1; ++q) {
+    const int a0 = (int)((long long)nbot * q / S1), a1 = (int)((long long)nbot * (q + 1) / S1);
+    L.seg[S0 + q] = int4{ny - 1 - a0, a1 - a0, -1, 0};
+  }
+  // groups: about sqrt(segments) per half, sizes differing by at most one
+  auto make_groups = [&](int s_first, int nh, int half) {
+    const int ng = std::max(1, std::min(nh, (int)std::lround(std::sqrt((double)nh))));
+    for (int c = 0; c < ng; ++c) {
+      const int a0 = s_first + nh * c / ng, a1 = s_first + nh * (c + 1) / ng;
+      const int gi = (int)L.grp.size();
+      L.grp.push_back(int4{a0, a1 - 1, half, c});
+      for (int q = a0; q < a1; ++q) L.seg[q].w = gi;
+    }
+    return ng;
+  };
+  L.G0 = make_groups(0, S0, 0);
+  L.NG = L.G0 + make_groups(S0, S1, 1);
+  return L;
+}
+
 void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const double* m_dev,
                     cudaStream_t s) {
   int n_cells = n + 2 * w_out;
@@ -351,43 +390,16 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
   // (one CTA per segment) is one wave: twice the SM count in complex64 (two
   // segment CTAs with 2-stage pipelines share an SM), the SM count in
   // complex128 (one CTA with its full pipeline per SM).
-  if (L.ny < 3) throw Failure(HZ_EINVAL, "a slab needs at least 3 rows");
-  L.mid = (L.ny - 1) / 2;
-  const int ntop = L.mid, nbot = L.ny - 1 - L.mid;
-  int P = h->p.segments;
   const int per_sm = (h->p.precision == HZ_MIXED) ? 2 : 1;
-  if (P <= 0) P = std::min(2 * (int)std::lround(std::pow((double)L.ny, 2.0 / 3.0)),
-                           std::max(2, per_sm * h->sms));
-  P = std::max(2, std::min(P, L.ny - 1));
-  int S0 = (P * ntop + L.ny / 2) / (L.ny - 1);      // segments in proportion to the chain lengths
-  S0 = std::max(1, std::min(S0, std::min(P - 1, ntop)));
-  int S1 = std::min(P - S0, nbot);
-  P = S0 + S1;
-  L.P = P;
-  L.S0 = S0;
-  L.seg.assign(P, int4{0, 0, 0, 0});
-  for (int q = 0; q < S0; ++q) {
-    const int a0 = (int)((long long)ntop * q / S0), a1 = (int)((long long)ntop * (q + 1) / S0);
-    L.seg[q] = int4{a0, a1 - a0, +1, 0};
-  }
-  for (int q = 0; q < S1; ++q) {
-    const int a0 = (int)((long long)nbot * q / S1), a1 = (int)((long long)nbot * (q + 1) / S1);
-    L.seg[S0 + q] = int4{L.ny - 1 - a0, a1 - a0, -1, 0};
-  }
-  // groups: about sqrt(segments) per half, sizes differing by at most one
-  L.grp.clear();
-  auto make_groups = [&](int s_first, int nh, int half) {
-    const int ng = std::max(1, std::min(nh, (int)std::lround(std::sqrt((double)nh))));
-    for (int c = 0; c < ng; ++c) {
-      const int a0 = s_first + nh * c / ng, a1 = s_first + nh * (c + 1) / ng;
-      const int gi = (int)L.grp.size();
-      L.grp.push_back(int4{a0, a1 - 1, half, c});
-      for (int q = a0; q < a1; ++q) L.seg[q].w = gi;
-    }
-    return ng;
-  };
-  L.G0 = make_groups(0, S0, 0);
-  L.NG = L.G0 + make_groups(S0, S1, 1);
+  SegmentLayout lay = segment_layout(L.ny, h->p.segments, std::max(2, per_sm * h->sms));
+  L.mid = lay.mid;
+  L.P = lay.P;
+  L.S0 = lay.S0;
+  L.G0 = lay.G0;
+  L.NG = lay.NG;
+  L.seg = lay.seg;
+  L.grp = lay.grp;
+  const int P = L.P;
   L.seg_dev = (int4*)dmalloc(sizeof(int4) * (P + L.NG));
   L.grp_dev = L.seg_dev + P;
   HZ_CU(cudaMemcpyAsync(L.seg_dev, L.seg.data(), sizeof(int4) * P, cudaMemcpyHostToDevice, s));
