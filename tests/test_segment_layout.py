@@ -74,6 +74,17 @@ def test_two_level_carries_reproduce_the_sequential_carries(ny, P):
     """Forward carry Y_s = yhat_s + Phi_s Y_{s-1} (first segment of a half: its
     own yhat) and backward carry X_s = xhat_s + Psi_s X_{s+1} (last segment of
     a half: from x_m) along each half, with random W x W transfer matrices."""
+    assert _carry_mismatches(ny, P, planted=False) == 0
+
+
+@pytest.mark.parametrize("ny,P", [(101, 0), (1039, 0)])
+def test_planted_boundary_mistake_is_caught(ny, P):
+    """The check is not vacuous: a fix-up that reads the wrong group boundary
+    (the segment's own group instead of the previous one) fails it."""
+    assert _carry_mismatches(ny, P, planted=True) > 0
+
+
+def _carry_mismatches(ny, P, planted):
     lay = hz.segment_layout(ny, P, 304)
     Pn, S0, G0, NG, seg, grp = lay["P"], lay["S0"], lay["G0"], lay["NG"], lay["seg"], lay["grp"]
     rng = np.random.default_rng(ny + Pn)
@@ -131,21 +142,23 @@ def test_two_level_carries_reproduce_the_sequential_carries(ny, P):
             v = lb[q] + PsiP[q] @ v
             Tb[g] = v
     # the meeting row reads the true ends of both halves' last groups
-    assert np.allclose(Tf[G0 - 1], Y[S0 - 1]) and np.allclose(Tf[NG - 1], Y[Pn - 1])
+    bad = int(not (np.allclose(Tf[G0 - 1], Y[S0 - 1]) and np.allclose(Tf[NG - 1], Y[Pn - 1])))
     # fix-up of every segment start
+    prev = 0 if planted else 1
     for s in range(Pn):
         if s not in (0, S0):               # forward re-run of segment s starts from Y_{s-1}
             q = s - 1
             g = seg[q, 3]
             first_group = g == (G0 if s >= S0 else 0)
-            start = lf[q] if first_group else lf[q] + PhiP[q] @ Tf[g - 1]
-            assert np.allclose(start, Y[q]), ("forward", s)
+            start = lf[q] if first_group else lf[q] + PhiP[q] @ Tf[g - prev]
+            bad += int(not np.allclose(start, Y[q]))
         if s not in (S0 - 1, Pn - 1):      # backward re-run of segment s starts from X_{s+1}
             q = s + 1
             g = seg[q, 3]
             last_group = g == (NG - 1 if s >= S0 else G0 - 1)
-            vin = xm if last_group else Tb[g + 1]
-            assert np.allclose(lb[q] + PsiP[q] @ vin, X[q]), ("backward", s)
+            vin = xm if last_group else Tb[g + prev]
+            bad += int(not np.allclose(lb[q] + PsiP[q] @ vin, X[q]))
+    return bad
 
 
 def test_layout_rejects_bad_arguments():
