@@ -90,11 +90,25 @@ def _bc(v, l, d):
     return v.reshape(shape)
 
 
-def assemble(axes: list[Axis], k2cell: np.ndarray, omega: float, H: float) -> sp.csr_matrix:
+def _stiff_factor(alpha_cell: np.ndarray, h_cell: np.ndarray) -> np.ndarray:
+    """alpha_l / h_l: the factor of the differentiated axis in the cell sum (Eqs. 59-61)."""
+    return alpha_cell / h_cell
+
+
+def _other_factor(alpha_cell: np.ndarray, h_cell: np.ndarray) -> np.ndarray:
+    """h_m / alpha_m: the factor of every other axis in the cell sum (Eqs. 59-61)."""
+    return h_cell / alpha_cell
+
+
+def assemble(axes: list[Axis], k2cell: np.ndarray, omega: float, H: float,
+             coeffs=None) -> sp.csr_matrix:
     """H_FE (Eq. 61) on the rectilinear mesh ``axes`` with cellwise k^2.
 
     ``k2cell`` has shape (N_0+1, ..., N_{d-1}+1); ``H`` is the reference
     spacing used in G = 2 pi / (H k) for the per-cell coefficients.
+    ``coeffs`` (tests only) replaces the Table 9 values c_j by fixed ones;
+    c = (4/9, 4/9, 2/3) in 2-D and (8/27, 4/9, 2/9, 4/9, 4/9) in 3-D give the
+    constants of exactly integrated multilinear elements.
     """
     d = len(axes)
     Ns = [ax.N for ax in axes]
@@ -105,7 +119,8 @@ def assemble(axes: list[Axis], k2cell: np.ndarray, omega: float, H: float) -> sp
     vol = functools.reduce(np.multiply, [_bc(hc[l], l, d) for l in range(d)])
     palpha = functools.reduce(np.multiply, [_bc(ac[l], l, d) for l in range(d)])
     inv_G = H * np.sqrt(k2cell) / (2.0 * np.pi)
-    I, Jc = fe_constants(coefficients(inv_G, d), d)
+    c = coefficients(inv_G, d) if coeffs is None else [np.full(cshape, float(v)) for v in coeffs]
+    I, Jc = fe_constants(c, d)
     mass = vol * k2cell / palpha
     idx = np.indices(cshape)
     rows, cols, vals = [], [], []
@@ -116,9 +131,9 @@ def assemble(axes: list[Axis], k2cell: np.ndarray, omega: float, H: float) -> sp
             for l in range(d):
                 ham_o = sum(int(a[m] != b[m]) for m in range(d) if m != l)
                 sgn = -1.0 if a[l] == b[l] else 1.0
-                other = functools.reduce(np.multiply, [_bc(hc[m] / ac[m], m, d)
+                other = functools.reduce(np.multiply, [_bc(_other_factor(ac[m], hc[m]), m, d)
                                                        for m in range(d) if m != l], 1.0)
-                val = val - sgn * _bc(ac[l] / hc[l], l, d) * other * Jc[ham_o]
+                val = val - sgn * _bc(_stiff_factor(ac[l], hc[l]), l, d) * other * Jc[ham_o]
             val = np.broadcast_to(val, cshape)
             ia = [idx[l] + a[l] - 1 for l in range(d)]
             ib = [idx[l] + b[l] - 1 for l in range(d)]
