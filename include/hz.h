@@ -176,20 +176,23 @@ hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_de
                         void* stream);
 
 /* hz_slab_solve without any device allocation.  (The paper has no
- * counterpart: this serves callers that cannot allocate device memory at the
- * time of the call -- code inside a CUDA stream capture, schedulers that
- * forbid allocation after start-up, applications that own all device
- * memory through their own pool.)  Same arguments, layout and result as
+ * counterpart.)  It serves callers that must not allocate device memory
+ * once they are running: real-time or embedded schedulers that forbid
+ * allocation after start-up, and applications that hand all device memory
+ * to their own pool allocator, where a cudaMalloc inside the library could
+ * fail or fragment that pool.  Same arguments, layout and result as
  * hz_slab_solve.  Its work space is a fixed 8 MiB device array inside the
  * library, present on every GPU that loads the library until the process
  * exits; a call needing more (about 3 * n_rhs * N_t * W complex values in
  * mixed precision, n_rhs * N_t * W in FP64, plus segment carries) returns
- * HZ_EINVAL.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's contents: calls whose GPU work overlaps (two streams, two host
- * threads) race and give wrong results.  The call synchronises `stream`
- * before returning.  Requires hz_factor. */
+ * HZ_EINVAL before any GPU work.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current
+ * and keeps it; make that first call before any stream capture, and do not
+ * call this entry point after cudaDeviceReset (the kept address would be
+ * stale).  All calls share the one array and it keeps the last call's
+ * contents: calls whose GPU work overlaps (two streams, two host threads)
+ * race and give wrong results.  The call synchronises `stream` before
+ * returning.  Requires hz_factor. */
 hz_status hz_slab_solve_noalloc(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_dev,
                                 int n_rhs, void* stream);
 
@@ -214,6 +217,24 @@ hz_status hz_get_stats(const hz_handle* h, hz_stats* out);
 hz_status hz_enable_timing(hz_handle* h, int on);
 hz_status hz_kernel_timing(hz_handle* h, const char* tag, double* ms, long long* launches,
                            double* bytes);
+
+/* Measured fused multiply-add throughput of the current device in TFLOP/s
+ * (2 flop per FMA), FP32 for precision = HZ_MIXED, FP64 for HZ_PLAIN_FP64:
+ * the denominator of the ALU rooflines of the factorisation kernels.  (The
+ * paper has no counterpart: a measurement utility.)  Runs about a second of
+ * FMA chains on every SM of the device on `stream`; *tflops (host) receives
+ * the best of three timed launches.  HZ_EINVAL for a NULL pointer or another
+ * precision value. */
+hz_status hz_alu_peak(int precision, double* tflops, void* stream);
+
+/* Test hooks (environment variables, read at every call; unset in
+ * production).  HZ_TEST_ALLOC_LIMIT=<bytes>: every device allocation of at
+ * least that size fails as an out-of-memory error (HZ_ENOMEM paths).
+ * HZ_TEST_WAIT_LIMIT_NS=<ns>: limit of the fused factorisation's bounded
+ * wait for elimination-chain progress (default 10 s); 0 makes the waiting
+ * CTAs give up at once, so hz_factor returns HZ_ETIMEOUT without any hang.
+ * HZ_TEST_NO_COOP=1: factor with separate launches, as on devices without
+ * cooperative launch. */
 
 const char* hz_last_error(const hz_handle* h);
 const char* hz_status_string(hz_status s);

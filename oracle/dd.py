@@ -69,7 +69,8 @@ class SweepingDD:
     """
 
     def __init__(self, axes: list[Axis], medium: np.ndarray, medium_kind: str, builder,
-                 A: sp.spmatrix, J: int, w: int, s_dd: float, c_pml: float, omega: float):
+                 A: sp.spmatrix, J: int, w: int, s_dd: float, c_pml: float, omega: float,
+                 only=None):
         self.axes, self.medium, self.kind, self.builder = axes, medium, medium_kind, builder
         self.A = A.tocsr()
         self.J, self.w, self.s_dd, self.c_pml, self.omega = J, w, s_dd, c_pml, omega
@@ -77,7 +78,10 @@ class SweepingDD:
         self.N = self.shape[-1]
         self.nt = int(np.prod(self.shape[:-1])) if len(self.shape) > 1 else 1
         self.beta, self.beta_t = partition(self.N, J)
-        self.slabs = [None] + [self._make_slab(j) for j in range(1, J + 1)]
+        # ``only`` (tests at large sizes): build just these slabs; the sweeps
+        # need all of them
+        self.slabs = [None] + [self._make_slab(j) if only is None or j in only else None
+                               for j in range(1, J + 1)]
         self._blocks = {}
 
     # ----------------------------------------------------------------- set-up

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "hz_kernel_timing": (ctypes.c_int, [_H, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "hz_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "hz_last_error": (ctypes.c_char_p, [_H]),
     "hz_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hz_destroy": (None, [_H]),
@@ -97,6 +98,17 @@ def segment_layout(ny, segments=0, max_auto=304):
     if code != 0:
         raise HzError(code, "hz_segment_layout failed")
     return dict(mid=mid, P=P, S0=S0, NG=NG, G0=G0, seg=seg, grp=grp)
+
+
+def alu_peak(precision="mixed", stream=None):
+    """Measured FMA throughput of the current device, TFLOP/s (hz_alu_peak):
+    FP32 for "mixed", FP64 for "fp64"."""
+    v = ctypes.c_double()
+    code = lib().hz_alu_peak(HZ_MIXED if precision == "mixed" else HZ_PLAIN_FP64,
+                             ctypes.byref(v), _stream(stream))
+    if code != HZ_OK:
+        raise HzError(code, lib().hz_last_error(None).decode())
+    return v.value
 
 
 def declared_symbols(header: str = HEADER):
@@ -257,18 +269,34 @@ class Solver:
         self._check(lib().hz_slab_info(self.h, j, *[ctypes.byref(v) for v in vals]))
         return dict(zip(("lo", "hi", "wl", "wr", "W"), (v.value for v in vals)))
 
-    def slab_solve(self, j, fd, stream=None):
+    def _slab_field(self, j, fd, out=None):
+        """Checks a slab field [n_rhs, N_t, W] (or [N_t, W]) before the C call,
+        which trusts n_rhs * N_t * W complex128 device elements."""
         import torch
+        if not isinstance(fd, torch.Tensor) or fd.dtype != torch.complex128 or not fd.is_cuda:
+            raise TypeError("slab fields are complex128 CUDA tensors")
+        W = self.slab_info(j)["W"]
+        nt = self.shape[0] if len(self.shape) == 2 else self.shape[0] * self.shape[1]
         fb = (fd[None] if fd.dim() == 2 else fd).contiguous()
-        u = torch.empty_like(fb)
+        if fb.dim() != 3 or tuple(fb.shape[1:]) != (nt, W):
+            raise ValueError(f"slab {j} field must be [n_rhs, {nt}, {W}], got {tuple(fd.shape)}")
+        if out is None:
+            out = torch.empty_like(fb)
+        elif (out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous()
+              or tuple(out.shape) != tuple(fb.shape)):
+            raise ValueError("out must be a contiguous complex128 CUDA tensor shaped like the input")
+        return fb, out
+
+    def slab_solve(self, j, fd, stream=None):
+        fb, u = self._slab_field(j, fd)
         self._check(lib().hz_slab_solve(self.h, j, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream)))
         return u[0] if fd.dim() == 2 else u
 
-    def slab_solve_noalloc(self, j, fd, stream=None):
-        """slab_solve through the entry point that allocates no device memory."""
-        import torch
-        fb = (fd[None] if fd.dim() == 2 else fd).contiguous()
-        u = torch.empty_like(fb)
+    def slab_solve_noalloc(self, j, fd, stream=None, out=None):
+        """slab_solve through the entry point that allocates no device memory
+        (``out``, if given, receives the result: then this call allocates
+        nothing either)."""
+        fb, u = self._slab_field(j, fd, out)
         self._check(lib().hz_slab_solve_noalloc(self.h, j, _ptr(fb), _ptr(u), fb.shape[0],
                                                 _stream(stream)))
         return u[0] if fd.dim() == 2 else u

@@ -96,6 +96,12 @@ void validate(const hz_params* p) {
 
 }  // namespace
 
+namespace hz {
+hz_status run_guarded(hz_handle* h, const std::function<void()>& body) {
+  return guarded(h, body);
+}
+}  // namespace hz
+
 extern "C" {
 
 const char* hz_status_string(hz_status s) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -117,6 +118,7 @@ struct Slab {
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.
 struct Level {
+  bool dim3d = false;        // 3-D level (slabs handled by the dense-block path)
   int nx = 0, ny = 0;        // unknowns along x (sweep) and y
   double h = 0;              // uniform spacing (finite differences)
   bool fe = false;           // stored 9-point operator (coarse FE level)
@@ -143,6 +145,8 @@ struct Level {
   int NG = 2, G0 = 1;
   std::vector<int4> grp;
   int4* grp_dev = nullptr;
+  void* fac_desc = nullptr;        // factorisation task descriptors (device, built once)
+  int* fac_sync = nullptr;         // their progress / task / group counters (device)
 };
 
 // Layout of the parallel-in-y slab substitution for a slab of ny block rows:
@@ -299,6 +303,10 @@ void misfit_grad(hz_handle* h, const int* src, int n_src, const int* rec, int n_
                  const c128* d, double* grad, double* phi_out, cudaStream_t s);
 void apply_fine64(hz_handle* h, const c128* u, c128* y, int n_rhs, cudaStream_t s);
 
+// api.cu: runs `body`, maps hz::Failure, std::exception and a pending CUDA
+// error to a status (recorded in the handle), never throws.
+hz_status run_guarded(hz_handle* h, const std::function<void()>& body);
+
 // util
 template <typename To, typename From>
 void cast_copy(const cplx<From>* a, cplx<To>* b, size_t n, cudaStream_t s);
@@ -306,5 +314,8 @@ void check_dev_flag(hz_handle* h, cudaStream_t s);
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 void* dmalloc(size_t bytes);
 void dfree(void* p);
+// Test hook: the integer value of environment variable `name`, or -1 if it
+// is unset or not a number (read at every call; see include/hz.h).
+long long test_hook(const char* name);
 
 }  // namespace hz

@@ -1,12 +1,11 @@
 // hz_slab_solve_noalloc: a slab solve that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they need a solve:
-// code running while a CUDA stream is being captured into a graph (an
-// allocation there is not captured and may break the capture), real-time or
-// embedded schedulers that forbid allocation after initialisation, and
-// applications that hand the whole device memory to their own pool.  This
-// entry point serves them: its work buffers live in one fixed device array
-// defined below, so the call itself never allocates.
+// Some callers must not allocate device memory once they are running:
+// real-time or embedded schedulers that forbid allocation after
+// initialisation, and applications that hand the whole device memory to their
+// own pool allocator (a cudaMalloc inside the library could then fail, or
+// fragment the pool).  This entry point serves them: its work buffers live in
+// one fixed device array defined below, so the call itself never allocates.
 //
 // The array is a file-scope __device__ variable: every GPU that loads this
 // library holds kScratchBytes of it until the process exits.  In host code
@@ -14,7 +13,8 @@
 // device address; passing it to a kernel would fault (or, where the GPU can
 // reach host memory, silently use the wrong memory).  The device address is
 // obtained once per device with cudaGetSymbolAddress, with that device
-// current, on the first call made on that device.
+// current, on the first call made on that device, and kept for the life of
+// the process (calls after cudaDeviceReset are not supported).
 #include "hz_internal.h"
 
 #include <mutex>
@@ -56,12 +56,13 @@ extern "C" hz_status hz_slab_solve_noalloc(hz_handle* h, int j, const hz_c128* f
                                            hz_c128* u_dev, int n_rhs, void* stream) {
   if (!h) return HZ_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  try {
+  return run_guarded(h, [&] {
     if (!h->sweep) throw Failure(HZ_EINVAL, "handle has no sweep level");
     Level& L = *h->sweep;
     if (j < 1 || j > L.J) throw Failure(HZ_EINVAL, "slab index out of range");
     if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
     if (!f_dev || !u_dev) throw Failure(HZ_EINVAL, "NULL field pointer");
+    if (L.dim3d) throw Failure(HZ_EINVAL, "the no-allocation slab solve serves 2-D slabs only");
     int dev = 0;
     HZ_CU(cudaGetDevice(&dev));
     if (dev != h->dev) throw Failure(HZ_EINVAL, "the handle's device is not the current device");
@@ -102,12 +103,5 @@ extern "C" hz_status hz_slab_solve_noalloc(hz_handle* h, int j, const hz_c128* f
     }
     HZ_CU(cudaStreamSynchronize(s));
     check_dev_flag(h, s);
-    h->err.st = HZ_OK;
-    h->err.msg.clear();
-    return HZ_OK;
-  } catch (const Failure& f) {
-    h->err.st = f.st;
-    h->err.msg = f.msg;
-    return f.st;
-  }
+  });
 }

@@ -5,12 +5,27 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 namespace hz {
+
+long long test_hook(const char* name) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return -1;
+  char* end = nullptr;
+  const long long x = std::strtoll(v, &end, 10);
+  return (end && *end == 0) ? x : -1;
+}
 
 void* dmalloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
+  // test hook: a request of at least HZ_TEST_ALLOC_LIMIT bytes fails as if
+  // the device were out of memory (exercises the HZ_ENOMEM paths on the host)
+  const long long limit = test_hook("HZ_TEST_ALLOC_LIMIT");
+  if (limit >= 0 && (long long)bytes >= limit)
+    throw Failure(HZ_ENOMEM, "cudaMalloc(" + std::to_string(bytes) +
+                                 ") refused by HZ_TEST_ALLOC_LIMIT");
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -441,6 +456,7 @@ void free_level(Level& L) {
   free_axis(L.ay);
   dfree(L.m); dfree(L.m32); dfree(L.st128); dfree(L.st64); dfree(L.seg_dev);
   dfree(L.k2c); dfree(L.ifp); dfree(L.refined); dfree(L.q0); dfree(L.q1);
+  dfree(L.fac_desc); dfree(L.fac_sync);
   L = Level{};
 }
 

@@ -903,12 +903,14 @@ __device__ void prefix_task(const ProdDesc& d) {
 
 // Factorisation and products in one cooperative launch (all CTAs resident):
 // CTAs 0..nf-1 run the elimination chains and publish their progress; the
-// others take product tasks in readiness order and wait (bounded, 10 s, then
-// the device flag) until the chain has finished the task's rows.
+// others take product tasks in readiness order and wait (bounded by wait_ns,
+// 10 s unless a test shortens it, then the device flag) until the chain has
+// finished the task's rows.  A worker that gives up returns; the chains never
+// wait, so the launch always ends.
 template <typename R, int RPW, int CPL, int PRPW, int PCPL>
 __global__ void __launch_bounds__(kThreads) slab_factor_fused_kernel(
     const FactorDesc* fd, int nf, const ProdDesc* pd, int np, int* progress, int* next_task,
-    int* gdone, int* flag) {
+    int* gdone, int* flag, unsigned long long wait_ns) {
   if ((int)blockIdx.x < nf) {
     factor_chain<R, RPW, CPL>(fd[blockIdx.x], progress + blockIdx.x);
     return;
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(kThreads) slab_factor_fused_kernel(
           const uint64_t t0 = gtimer();
           while (ld_acquire(progress + d.fchain) < d.need) {
             __nanosleep(2000);
-            if (gtimer() - t0 > 10000000000ull) {
+            if (gtimer() - t0 > wait_ns) {
               atomicExch(flag, DEV_TIMEOUT);
               sh_abort = 1;
               break;
@@ -937,7 +939,7 @@ __global__ void __launch_bounds__(kThreads) slab_factor_fused_kernel(
           const uint64_t t0 = gtimer();
           while (ld_acquire(gdone + d.gctr) < d.gneed) {
             __nanosleep(1000);
-            if (gtimer() - t0 > 10000000000ull) {
+            if (gtimer() - t0 > wait_ns) {
               atomicExch(flag, DEV_TIMEOUT);
               sh_abort = 1;
               break;
@@ -1787,23 +1789,36 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   const size_t b_fd = sizeof(FactorDesc) * fd.size(), b_md = sizeof(MidDesc) * md.size();
   const size_t b_pd = sizeof(ProdDesc) * pd.size(), b_xd = sizeof(PrefixDesc) * xd.size();
   const size_t b_pdx = sizeof(ProdDesc) * pdx.size();
-  unsigned char* d_desc = (unsigned char*)dmalloc(b_fd + b_md + b_pd + b_xd + b_pdx);
+  // chain progress [nf], task counter [1], group completion counters [2 J NG]
+  const size_t nsync = fd.size() + 1 + (size_t)2 * J * NG;
+  // The descriptors depend only on the slab geometry and buffers, which are
+  // fixed from set-up on: they are uploaded by the first factorisation of
+  // the level and kept (with the sync counters) until the level is freed,
+  // so later factorisations allocate nothing.
+  if (!L.fac_desc) {
+    L.fac_desc = dmalloc(b_fd + b_md + b_pd + b_xd + b_pdx);
+    L.fac_sync = (int*)dmalloc(sizeof(int) * nsync);
+    unsigned char* d = (unsigned char*)L.fac_desc;
+    HZ_CU(cudaMemcpyAsync(d, fd.data(), b_fd, cudaMemcpyHostToDevice, s));
+    HZ_CU(cudaMemcpyAsync(d + b_fd, md.data(), b_md, cudaMemcpyHostToDevice, s));
+    HZ_CU(cudaMemcpyAsync(d + b_fd + b_md, pd.data(), b_pd, cudaMemcpyHostToDevice, s));
+    HZ_CU(cudaMemcpyAsync(d + b_fd + b_md + b_pd, xd.data(), b_xd, cudaMemcpyHostToDevice, s));
+    HZ_CU(cudaMemcpyAsync(d + b_fd + b_md + b_pd + b_xd, pdx.data(), b_pdx,
+                          cudaMemcpyHostToDevice, s));
+  }
+  unsigned char* d_desc = (unsigned char*)L.fac_desc;
   FactorDesc* d_fd = (FactorDesc*)d_desc;
   MidDesc* d_md = (MidDesc*)(d_desc + b_fd);
   ProdDesc* d_pd = (ProdDesc*)(d_desc + b_fd + b_md);
   PrefixDesc* d_xd = (PrefixDesc*)(d_desc + b_fd + b_md + b_pd);
   ProdDesc* d_pdx = (ProdDesc*)(d_desc + b_fd + b_md + b_pd + b_xd);
-  HZ_CU(cudaMemcpyAsync(d_fd, fd.data(), b_fd, cudaMemcpyHostToDevice, s));
-  HZ_CU(cudaMemcpyAsync(d_md, md.data(), b_md, cudaMemcpyHostToDevice, s));
-  HZ_CU(cudaMemcpyAsync(d_pd, pd.data(), b_pd, cudaMemcpyHostToDevice, s));
-  HZ_CU(cudaMemcpyAsync(d_xd, xd.data(), b_xd, cudaMemcpyHostToDevice, s));
-  HZ_CU(cudaMemcpyAsync(d_pdx, pdx.data(), b_pdx, cudaMemcpyHostToDevice, s));
-  // chain progress [nf], task counter [1], group completion counters [2 J NG]
-  const size_t nsync = fd.size() + 1 + (size_t)2 * J * NG;
-  int* d_sync = (int*)dmalloc(sizeof(int) * nsync);
+  int* d_sync = L.fac_sync;
   HZ_CU(cudaMemsetAsync(d_sync, 0, sizeof(int) * nsync, s));
   int coop = 0;
   HZ_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev));
+  if (test_hook("HZ_TEST_NO_COOP") > 0) coop = 0;        // exercises the separate launches
+  const long long hook_ns = test_hook("HZ_TEST_WAIT_LIMIT_NS");
+  const unsigned long long wait_ns = hook_ns >= 0 ? (unsigned long long)hook_ns : 10000000000ull;
   const size_t smem_x = 2 * (size_t)maxW * maxW * el;   // prefix products: M, T
   auto run = [&](auto kf, auto km, auto kp, auto kfused, auto kx) {
     HZ_CU(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m));
@@ -1824,8 +1839,9 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
       int* a5 = d_sync + nf;
       int* a6 = d_sync + nf + 1;
       int* a7 = h->dev_flag;
+      unsigned long long a8 = wait_ns;
       void* args[] = {(void*)&a0, (void*)&nf, (void*)&a2, (void*)&npx, (void*)&a4, (void*)&a5,
-                      (void*)&a6, (void*)&a7};
+                      (void*)&a6, (void*)&a7, (void*)&a8};
       timed(h, "slab_factor", 0.0, s, [&] {
         HZ_CU(cudaLaunchCooperativeKernel((const void*)kfused, dim3(grid), dim3(kThreads), args,
                                           smem_u, s));
@@ -1883,8 +1899,6 @@ void factor_level(hz_handle* h, Level& L, cudaStream_t s) {
   }
   HZ_CU(cudaGetLastError());
   HZ_CU(cudaStreamSynchronize(s));
-  dfree(d_desc);
-  dfree(d_sync);
 }
 
 template <typename R, int NR>

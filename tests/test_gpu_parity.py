@@ -36,6 +36,11 @@ def _rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
 
+def _close(a, b, tol):
+    """Relative L2 error and element-wise error (against the largest |b|) both <= tol."""
+    return _rel(a, b) <= tol and np.abs(a - b).max() <= tol * np.abs(b).max()
+
+
 CASES = [(1, 60, 6, 4), (2, 90, 8, 6), (2, 101, 7, 4)]   # (config, n, w_out, J); ragged widths
 
 
@@ -69,7 +74,7 @@ def test_slab_solve_matches_oracle(idx, n, w_out, J, precision, tol, segments):
         fd = _rand((cfg.N, sl.W), 10 + j)
         ud = s.slab_solve(j, torch.from_numpy(fd).cuda()).cpu().numpy()
         ref = sl.lu.solve(fd.ravel()).reshape(fd.shape)
-        assert _rel(ud, ref) <= tol, (j, _rel(ud, ref))
+        assert _close(ud, ref, tol), (j, _rel(ud, ref), np.abs(ud - ref).max() / np.abs(ref).max())
 
 
 @pytest.mark.parametrize("sweep", ["X", "UD"])
@@ -85,7 +90,7 @@ def test_preconditioner_matches_oracle(idx, n, w_out, J, sweep, precision, tol):
     z = s.precond(torch.from_numpy(f).cuda()).cpu().numpy()
     for r in range(2):
         ref = p.dd.apply(f[r], sweep)
-        assert _rel(z[r], ref) <= tol
+        assert _close(z[r], ref, tol)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -110,6 +115,9 @@ def test_solve_matches_oracle(idx, n, w_out, J, precision):
 
 
 def test_solve_full_config2_mixed():
+    """The full configuration-2 solve in mixed precision against the plain-FP64
+    GPU arm (the oracle's GMRES is too slow here; its assembled A checks the
+    true residual): same iteration count within one, u within 1e-5."""
     hz = _hz()
     cfg = synth.workload(2)
     m = synth.medium(cfg)
@@ -118,13 +126,18 @@ def test_solve_full_config2_mixed():
     axes = [mesh.fine_axis(cfg.n_cells, cfg.w_out, cfg.h, cfg.s_out, c_pml) for _ in range(2)]
     A = fd.assemble(axes, cfg.omega ** 2 * m, cfg.omega)
     b = synth.sources(cfg)[0]
-    s = hz.Solver.from_workload(cfg, m=m)
-    s.factor()
-    u, st = s.solve(torch.from_numpy(b).cuda())
-    u = u.cpu().numpy()
-    relres = np.linalg.norm(A @ u.ravel() - b.ravel()) / np.linalg.norm(b)
-    assert st["relres_max"] <= cfg.tol and relres <= 1.05 * cfg.tol
-    assert st["iters_max"] <= 40
+    out = {}
+    for precision in ("mixed", "fp64"):
+        s = hz.Solver.from_workload(cfg, m=m, precision=precision)
+        s.factor()
+        u, st = s.solve(torch.from_numpy(b).cuda())
+        u = u.cpu().numpy()
+        relres = np.linalg.norm(A @ u.ravel() - b.ravel()) / np.linalg.norm(b)
+        assert st["relres_max"] <= cfg.tol and relres <= 1.05 * cfg.tol
+        out[precision] = (u, st["iters_max"])
+        s.close()
+    assert abs(out["mixed"][1] - out["fp64"][1]) <= 1
+    assert _rel(out["mixed"][0], out["fp64"][0]) <= 1e-5
 
 
 def test_multiple_right_hand_sides():
@@ -176,7 +189,7 @@ def test_two_grid_coarse_slabs_match_oracle(idx, n, w_out, J):
         fd = _rand((sl.A.shape[0] // sl.W, sl.W), 40 + j)
         ud = s.slab_solve(j, torch.from_numpy(fd).cuda()).cpu().numpy()
         ref = sl.lu.solve(fd.ravel()).reshape(fd.shape)
-        assert _rel(ud, ref) <= 1e-9
+        assert _close(ud, ref, 1e-9)
 
 
 @pytest.mark.parametrize("sweep", ["X", "UD"])
@@ -192,7 +205,7 @@ def test_two_grid_preconditioner_matches_oracle(idx, n, w_out, J, sweep, precisi
     z = s.precond(torch.from_numpy(f).cuda()).cpu().numpy()
     for r in range(2):
         ref = p.precondition(f[r]).reshape(cfg.shape)
-        assert _rel(z[r], ref) <= tol
+        assert _close(z[r], ref, tol)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
