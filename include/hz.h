@@ -11,14 +11,18 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- * Grid.  Along each axis there are n interior cells of size h = 1/n and w_out
- *   PML cells on each side: n_cells = n + 2 w_out cells, N = n_cells - 1
- *   unknowns (Dirichlet nodes on the outer boundary, Section 2.2).
- * Layout.  Fields are dense, contiguous, [rhs][y][x] (2-D), x fastest; x is
- *   the sweep axis.  Complex values are interleaved (re, im) doubles.
- * System.  A is Eq. 40 multiplied by h^d (complex symmetric).  The right-hand
- *   side b of A u = b is h^d f / (alpha_1 alpha_2): a unit point source
- *   f = h^-d at an interior node is b = 1 there.
+ * Grid.  A rectangle (2-D) or box (3-D).  Along axis l there are n[l]
+ *   interior cells of size h and w_out PML cells on each side:
+ *   n[l] + 2 w_out cells and N_l = n[l] + 2 w_out - 1 unknowns (Dirichlet
+ *   nodes on the outer boundary, Section 2.2).  x (l = 0) is the sweep axis;
+ *   n_dof = prod_l N_l and N_t = n_dof / N_x (the transverse unknowns).
+ * Layout.  Fields are dense, contiguous, [rhs][y][x] (2-D) or [rhs][z][y][x]
+ *   (3-D), x fastest.  Complex values are interleaved (re, im) doubles.
+ * System.  A is Eq. 40 multiplied by h^d (complex symmetric; in 3-D the
+ *   7-point analogue, each second difference divided by the PML factors of
+ *   the other two axes).  The right-hand side b of A u = b is
+ *   h^d f / prod_l alpha_l: a unit point source f = h^-d at an interior node
+ *   is b = 1 there.
  * Memory.  Every array argument is a DEVICE pointer owned by the caller and
  *   borrowed only for the duration of the call (work is enqueued on `stream`
  *   and the call returns after it has completed unless stated otherwise).
@@ -52,9 +56,11 @@ enum { HZ_SWEEP_UD = 0, HZ_SWEEP_X = 1 };        /* SweepingPrecUD / SweepingPre
 enum { HZ_PLAIN_FP64 = 0, HZ_MIXED = 1 };        /* preconditioner in complex128 / complex64 */
 
 typedef struct {
-  int    dim;           /* 2 (3-D is not built yet: HZ_EINVAL) */
-  int    n;             /* interior cells per axis (even when two_grid) */
+  int    dim;           /* 2 or 3 */
+  int    n[3];          /* interior cells along x (the sweep axis), y, z (n[2]: 3-D only;
+                         * even when two_grid) */
   int    w_out;         /* outer PML cells per side */
+  double h;             /* cell size of every axis (0: 1 / n[0]) */
   double omega;         /* angular frequency; k = omega / c, k^2 = omega^2 m */
   double s_pml_out;     /* outer PML strength S_pml (Section 2.1) */
   double s_pml_dd;      /* DD PML strength (Section 6.1: 15/20/25 for w = 3/4/5) */
@@ -68,7 +74,7 @@ typedef struct {
   int    gmres_m;       /* GMRES restart length */
   int    max_iter;      /* cap on preconditioned GMRES iterations */
   double tol;           /* stop at ||b - A u||_2 / ||b||_2 <= tol (per right-hand side) */
-  int    max_rhs;       /* right-hand sides per hz_solve call (buffer capacity) */
+  int    max_rhs;       /* right-hand sides per hz_solve call (buffer capacity, 1..64) */
   int    segments;      /* block-row segments per slab solve, over both elimination
                          * chains (0: automatic, about 2 N_y^(2/3) capped at the SM
                          * count; at least 2) */
@@ -90,7 +96,7 @@ typedef struct {
 typedef struct hz_handle hz_handle;
 
 /* Create a solver for the grid and parameters in *p.  m_dev: squared slowness
- * 1/c^2 at the N^d unknowns, FP64, device, copied into the handle.  c_pml
+ * 1/c^2 at the n_dof unknowns, FP64, device, copied into the handle.  c_pml
  * (the "typical velocity" of Section 2.1) is p->c_pml, or the mean of c over
  * the unknowns when p->c_pml is 0.
  * Builds the PML tables (Eq. 5, alpha below Eq. 40), the slab partition
@@ -107,13 +113,13 @@ hz_status hz_set_medium(hz_handle* h, const double* m_dev);
 hz_status hz_factor(hz_handle* h, void* stream);
 
 /* Solve A u_r = f_r for r < n_rhs by GMRES(m) with the configured
- * preconditioner, x0 = 0.  f_dev, u_dev: n_rhs * N^d complex128, device.
+ * preconditioner, x0 = 0.  f_dev, u_dev: n_rhs * n_dof complex128, device.
  * stats (host, may be NULL) is filled.  Returns HZ_ENOTCONV if any right-hand
  * side missed tol within max_iter (u holds the last iterate). */
 hz_status hz_solve(hz_handle* h, const hz_c128* f_dev, hz_c128* u_dev, int n_rhs,
                    void* stream, hz_stats* stats);
 
-/* Same as hz_solve with HOST arrays f_host / u_host (n_rhs * N^d complex128,
+/* Same as hz_solve with HOST arrays f_host / u_host (n_rhs * n_dof complex128,
  * pinned or pageable): the host<->device copies are part of the call.  The
  * first call allocates two device staging buffers owned by the handle. */
 hz_status hz_solve_host(hz_handle* h, const hz_c128* f_host, hz_c128* u_host, int n_rhs,
@@ -133,18 +139,18 @@ hz_status hz_precond(hz_handle* h, const hz_c128* r_dev, hz_c128* z_dev, int n_r
  * (the adjoint-state method; the paper supplies the solver, Eq. 40 the
  * derivative of A):
  *   Phi = 1/2 sum_s sum_q |u_s[rec_q] - d[s][q]|^2,  A u_s = e_{src_s} (b = 1),
- *   grad[i] = dPhi/dm_i = omega^2 Re( h^2 / (alpha_x alpha_y)_i sum_s mu_{s,i} u_{s,i} ),
+ *   grad[i] = dPhi/dm_i = omega^2 Re( h^d / (prod_l alpha_l)_i sum_s mu_{s,i} u_{s,i} ),
  * with A mu_s = conj(sum_q (u_s[rec_q] - d[s][q]) e_{rec_q}) (A is complex
  * symmetric, so the adjoint solve reuses the preconditioner) and the PML held
  * fixed (set p->c_pml to keep it fixed across hz_set_medium calls).
  * src_dev: n_src flat unknown indices (int32, device); rec_dev: n_rec flat
  * indices (int32, device; repeats add up); d_dev: observed data [n_src][n_rec]
- * complex128 (device); grad_dev: N^d doubles (device, overwritten); *phi
+ * complex128 (device); grad_dev: n_dof doubles (device, overwritten); *phi
  * (host) receives Phi.  Sources are solved max_rhs at a time (one forward and
  * one adjoint GMRES solve per batch).  Indices outside the grid give
  * HZ_EINVAL before any work; HZ_ENOTCONV if a solve missed tol (results are
  * still written).  Requires hz_factor.  The first call allocates
- * 3 * max_rhs * N^d complex128 of work space owned by the handle. */
+ * 3 * max_rhs * n_dof complex128 of work space owned by the handle. */
 hz_status hz_grad(hz_handle* h, const int* src_dev, int n_src, const int* rec_dev,
                          int n_rec, const hz_c128* d_dev, double* grad_dev, double* phi,
                          void* stream, hz_stats* stats);

@@ -161,13 +161,19 @@ def averaging_1d(i_fp: np.ndarray, refined: np.ndarray, n_fine_cells: int) -> np
     return W
 
 
-def coarse_k2(k2_fine: np.ndarray, i_fp: np.ndarray, refined: np.ndarray) -> np.ndarray:
-    """Coarse cellwise k^2 from fine nodal k^2 (edge values copied to the Dirichlet nodes)."""
+def coarse_k2(k2_fine: np.ndarray, i_fp, refined) -> np.ndarray:
+    """Coarse cellwise k^2 from fine nodal k^2 (edge values copied to the Dirichlet nodes).
+
+    ``i_fp`` / ``refined`` describe one axis (used for all) or are lists with
+    one entry per array axis.
+    """
+    d = k2_fine.ndim
+    if not isinstance(i_fp, (list, tuple)):
+        i_fp, refined = [i_fp] * d, [refined] * d
     kp = np.pad(k2_fine, 1, mode="edge")
-    n_fine_cells = kp.shape[0] - 1
-    W = averaging_1d(i_fp, refined, n_fine_cells)
     out = kp
-    for l in range(k2_fine.ndim):
+    for l in range(d):
+        W = averaging_1d(i_fp[l], refined[l], kp.shape[l] - 1)
         out = np.moveaxis(np.tensordot(W, np.moveaxis(out, l, 0), axes=(1, 0)), 0, l)
     return out
 

@@ -34,16 +34,14 @@ class Problem:
         h = cfg.h
         # "typical velocity" of the PML (Section 2.1): mean wave speed unless fixed
         self.c_pml = float(np.mean(1.0 / np.sqrt(self.m))) if c_pml is None else float(c_pml)
-        self.axes = [mesh.fine_axis(cfg.n_cells, cfg.w_out, h, cfg.s_out, self.c_pml)
-                     for _ in range(cfg.dim)]
+        self.axes = [mesh.fine_axis(c + 2 * cfg.w_out, cfg.w_out, h, cfg.s_out, self.c_pml)
+                     for c in cfg.cells]
         self.k2 = self.omega ** 2 * self.m
         self.A = fd.assemble(self.axes, self.k2, self.omega)
         if self.two_grid:
-            co = [mesh.coarse_axis(cfg.n, cfg.w_out, h, cfg.s_out, self.c_pml)
-                  for _ in range(cfg.dim)]
+            co = [mesh.coarse_axis(c, cfg.w_out, h, cfg.s_out, self.c_pml) for c in cfg.cells]
             self.caxes = [c[0] for c in co]
-            i_fp, refined = co[0][1], co[0][2]
-            self.k2c = fe.coarse_k2(self.k2, i_fp, refined)
+            self.k2c = fe.coarse_k2(self.k2, [c[1] for c in co], [c[2] for c in co])
             H = 2.0 * h
             omega = self.omega
 
@@ -51,7 +49,8 @@ class Problem:
                 return fe.assemble(axes, med, omega, H)
 
             self.Ac = builder(self.caxes, self.k2c)
-            self.P = fe.prolongation([fe.prolongation_1d(c[1], c[2], cfg.N) for c in co])
+            self.P = fe.prolongation([fe.prolongation_1d(c[1], c[2], N)
+                                      for c, N in zip(co, cfg.shape)])
             self.dd = dd.SweepingDD(self.caxes, self.k2c, "cell", builder, self.Ac, self.J,
                                     self.w_dd, self.s_dd, self.c_pml, omega)
         else:

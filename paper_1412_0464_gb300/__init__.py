@@ -25,7 +25,8 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 class hz_params(ctypes.Structure):
     _fields_ = [
-        ("dim", ctypes.c_int), ("n", ctypes.c_int), ("w_out", ctypes.c_int),
+        ("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("w_out", ctypes.c_int),
+        ("h", ctypes.c_double),
         ("omega", ctypes.c_double), ("s_pml_out", ctypes.c_double), ("s_pml_dd", ctypes.c_double),
         ("J", ctypes.c_int), ("w_dd", ctypes.c_int), ("sweep", ctypes.c_int),
         ("two_grid", ctypes.c_int), ("nu", ctypes.c_int), ("omega_jac", ctypes.c_double),
@@ -154,18 +155,33 @@ def _ptr(t):
 class Solver:
     """One Helmholtz problem on the device: set-up, factorisation and solves.
 
-    ``m`` is the squared slowness 1/c^2 on the N x N unknowns (torch float64
-    tensor on the GPU, or anything ``torch.as_tensor`` accepts).
+    ``m`` is the squared slowness 1/c^2 on the unknowns, array order
+    ([z][y][x]; torch float64 tensor on the GPU, or anything
+    ``torch.as_tensor`` accepts).  ``n`` is the interior cell count along x
+    (the sweep axis); ``dims`` (array order, last entry n) gives every axis
+    its own count (rectangles, boxes); ``dim`` is 2 or 3.
     """
 
     def __init__(self, m, *, n, w_out, omega, J, w_dd, s_dd, s_out=20.0, sweep="X",
                  precision="mixed", gmres_m=30, max_iter=500, tol=1e-6, max_rhs=1,
-                 two_grid=False, nu=3, omega_jac=0.8, segments=0, c_pml=0.0):
+                 two_grid=False, nu=3, omega_jac=0.8, segments=0, c_pml=0.0, dim=2, dims=None,
+                 h=0.0):
         import torch
+        dims = tuple(dims) if dims is not None else (n,) * dim
+        assert len(dims) == dim and dims[-1] == n
+        self.dims = dims
         self.N = n + 2 * w_out - 1
-        self.shape = (self.N, self.N)
+        self.shape = tuple(c + 2 * w_out - 1 for c in dims)
+        # transverse unknowns of the level that carries the slabs (the coarse
+        # level of the two-grid cycle, else the fine grid)
+        cells_t = [c // 2 if two_grid else c for c in dims[:-1]]
+        self.slab_nt = 1
+        for c in cells_t:
+            self.slab_nt *= c + 2 * w_out - 1
         p = hz_params()
-        p.dim, p.n, p.w_out, p.omega = 2, n, w_out, omega
+        p.dim, p.w_out, p.omega, p.h = dim, w_out, omega, h
+        for l, c in enumerate(reversed(dims)):      # hz_params.n is (x, y, z)
+            p.n[l] = c
         p.s_pml_out, p.s_pml_dd, p.J, p.w_dd = s_out, s_dd, J, w_dd
         p.sweep = HZ_SWEEP_X if sweep == "X" else HZ_SWEEP_UD
         p.two_grid, p.nu, p.omega_jac = int(two_grid), nu, omega_jac
@@ -189,7 +205,7 @@ class Solver:
         kw = dict(n=cfg.n, w_out=cfg.w_out, omega=cfg.omega, J=cfg.J, w_dd=cfg.w_dd, s_dd=cfg.s_dd,
                   s_out=cfg.s_out, sweep=cfg.sweep, precision=cfg.precision, gmres_m=cfg.gmres_m,
                   tol=cfg.tol, max_rhs=cfg.n_src, two_grid=cfg.two_grid, nu=cfg.nu,
-                  omega_jac=cfg.omega_jac)
+                  omega_jac=cfg.omega_jac, dim=cfg.dim, dims=cfg.cells)
         kw.update(over)
         return cls(m, **kw)
 
@@ -209,11 +225,23 @@ class Solver:
         self._check(lib().hz_factor(self.h, _stream(stream)))
         self.factored = True
 
-    def solve(self, f, stream=None, check=True):
-        """u with A u = f (f: complex128 CUDA tensor [n_rhs, N, N] or [N, N])."""
+    def _field(self, f, cuda=True):
+        """(batch [n_rhs, *shape] contiguous, single) for a grid field f of
+        shape ``self.shape`` or [n_rhs, *shape], complex128 (the C calls trust
+        n_rhs * n_dof elements)."""
         import torch
-        single = f.dim() == 2
+        if f.dtype != torch.complex128 or f.is_cuda != cuda:
+            raise TypeError(f"fields are complex128 {'CUDA' if cuda else 'host'} tensors")
+        single = f.dim() == len(self.shape)
         fb = (f[None] if single else f).contiguous()
+        if tuple(fb.shape[1:]) != tuple(self.shape):
+            raise ValueError(f"field must be [n_rhs, {self.shape}] or {self.shape}, got {tuple(f.shape)}")
+        return fb, single
+
+    def solve(self, f, stream=None, check=True):
+        """u with A u = f (f: complex128 CUDA tensor [n_rhs, *shape] or shape)."""
+        import torch
+        fb, single = self._field(f)
         u = torch.empty_like(fb)
         st = hz_stats()
         code = lib().hz_solve(self.h, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream), ctypes.byref(st))
@@ -224,27 +252,26 @@ class Solver:
     def solve_host(self, f_host, stream=None):
         """Same with host (CPU) tensors; the copies are part of the call."""
         import torch
-        fb = f_host[None] if f_host.dim() == 2 else f_host
-        fb = fb.contiguous()
+        fb, single = self._field(f_host, cuda=False)
         u = torch.empty_like(fb)
         st = hz_stats()
         self._check(lib().hz_solve_host(self.h, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream),
                                         ctypes.byref(st)))
-        return (u[0] if f_host.dim() == 2 else u), st.as_dict()
+        return (u[0] if single else u), st.as_dict()
 
     def apply(self, u, stream=None):
         import torch
-        ub = (u[None] if u.dim() == 2 else u).contiguous()
+        ub, single = self._field(u)
         y = torch.empty_like(ub)
         self._check(lib().hz_apply(self.h, _ptr(ub), _ptr(y), ub.shape[0], _stream(stream)))
-        return y[0] if u.dim() == 2 else y
+        return y[0] if single else y
 
     def precond(self, r, stream=None):
         import torch
-        rb = (r[None] if r.dim() == 2 else r).contiguous()
+        rb, single = self._field(r)
         z = torch.empty_like(rb)
         self._check(lib().hz_precond(self.h, _ptr(rb), _ptr(z), rb.shape[0], _stream(stream)))
-        return z[0] if r.dim() == 2 else z
+        return z[0] if single else z
 
     def grad(self, src, rec, d, stream=None, check=True):
         """(Phi, dPhi/dm, stats) for point sources at flat indices ``src``,
@@ -276,7 +303,7 @@ class Solver:
         if not isinstance(fd, torch.Tensor) or fd.dtype != torch.complex128 or not fd.is_cuda:
             raise TypeError("slab fields are complex128 CUDA tensors")
         W = self.slab_info(j)["W"]
-        nt = self.shape[0] if len(self.shape) == 2 else self.shape[0] * self.shape[1]
+        nt = self.slab_nt
         fb = (fd[None] if fd.dim() == 2 else fd).contiguous()
         if fb.dim() != 3 or tuple(fb.shape[1:]) != (nt, W):
             raise ValueError(f"slab {j} field must be [n_rhs, {nt}, {W}], got {tuple(fd.shape)}")

@@ -41,18 +41,22 @@ __global__ void receiver_residual_kernel(const c128* u, size_t n, const int* rec
   phi[k] = 0.5 * acc;
 }
 
-// grad_i += omega^2 Re( h^2 / (alpha_x[ix] alpha_y[iy]) * sum_k mu_k,i u_k,i )
+// grad_i += omega^2 Re( h^d / (alpha_x alpha_y [alpha_z])_i * sum_k mu_k,i u_k,i )
+// (scale = omega^2 h^d; az is null in 2-D)
 __global__ void grad_accumulate_kernel(const c128* u, const c128* mu, int nb, int nx, int ny,
-                                       const c128* ax, const c128* ay, double scale,
-                                       double* grad) {
-  const size_t n = (size_t)nx * ny;
+                                       int nz, const c128* ax, const c128* ay, const c128* az,
+                                       double scale, double* grad) {
+  const size_t n = (size_t)nx * ny * nz;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     c128 acc = mk<double>(0.0, 0.0);
     for (int k = 0; k < nb; ++k) cfma(acc, mu[(size_t)k * n + i], u[(size_t)k * n + i]);
-    const int iy = (int)(i / nx), ix = (int)(i - (size_t)iy * nx);
-    const c128 w = cinv(ax[ix] * ay[iy]);
-    grad[i] += scale * (w * acc).re;
+    const size_t iyz = i / nx;
+    const int ix = (int)(i - iyz * nx);
+    const int iy = (int)(iyz % ny), iz = (int)(iyz / ny);
+    c128 pa = ax[ix] * ay[iy];
+    if (az) pa = pa * az[iz];
+    grad[i] += scale * (cinv(pa) * acc).re;
   }
 }
 
@@ -61,7 +65,7 @@ __global__ void grad_accumulate_kernel(const c128* u, const c128* mu, int nb, in
 void misfit_grad(hz_handle* h, const int* src, int n_src, const int* rec, int n_rec,
                  const c128* d, double* grad, double* phi_out, cudaStream_t s) {
   Level& F = h->fine;
-  const size_t n = (size_t)F.nx * F.ny;
+  const size_t n = F.size();
   // Indices are validated on the host before any kernel uses them.
   std::vector<int> hs(n_src), hr(n_rec);
   HZ_CU(cudaMemcpyAsync(hs.data(), src, sizeof(int) * n_src, cudaMemcpyDeviceToHost, s));
@@ -81,7 +85,8 @@ void misfit_grad(hz_handle* h, const int* src, int n_src, const int* rec, int n_
     h->gr_phi = (double*)dmalloc(sizeof(double) * R);
   }
   HZ_CU(cudaMemsetAsync(grad, 0, sizeof(double) * n, s));
-  const double scale = h->p.omega * h->p.omega * F.h * F.h;
+  const double scale =
+      h->p.omega * h->p.omega * F.h * F.h * (F.dim3d ? F.h : 1.0);   // omega^2 h^d
   double phi = 0.0;
   int iters_max = 0;
   double relres_max = 0.0;
@@ -103,16 +108,17 @@ void misfit_grad(hz_handle* h, const int* src, int n_src, const int* rec, int n_
   for (int s0 = 0; s0 < n_src; s0 += R) {
     const int nb = std::min(R, n_src - s0);
     HZ_CU(cudaMemsetAsync(h->gr_b, 0, sizeof(c128) * n * nb, s));
-    point_sources_kernel<<<1, 32, 0, s>>>(h->gr_b, n, src + s0, nb);
+    point_sources_kernel<<<1, 64, 0, s>>>(h->gr_b, n, src + s0, nb);
     h->launches++;
     solve(h->gr_b, h->gr_u, nb);
     HZ_CU(cudaMemsetAsync(h->gr_b, 0, sizeof(c128) * n * nb, s));
-    receiver_residual_kernel<<<1, 32, 0, s>>>(h->gr_u, n, rec, n_rec, d + (size_t)s0 * n_rec,
+    receiver_residual_kernel<<<1, 64, 0, s>>>(h->gr_u, n, rec, n_rec, d + (size_t)s0 * n_rec,
                                               h->gr_b, h->gr_phi, nb);
     h->launches++;
     solve(h->gr_b, h->gr_mu, nb);
-    grad_accumulate_kernel<<<4 * 152, 256, 0, s>>>(h->gr_u, h->gr_mu, nb, F.nx, F.ny,
-                                                    F.ax.a_node, F.ay.a_node, scale, grad);
+    grad_accumulate_kernel<<<4 * h->sms, 256, 0, s>>>(
+        h->gr_u, h->gr_mu, nb, F.nx, F.ny, F.nz, F.ax.a_node, F.ay.a_node,
+        F.dim3d ? F.az.a_node : nullptr, scale, grad);
     h->launches++;
     HZ_CU(cudaMemcpyAsync(hphi.data(), h->gr_phi, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     HZ_CU(cudaStreamSynchronize(s));

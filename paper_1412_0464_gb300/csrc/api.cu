@@ -18,10 +18,18 @@ thread_local std::string g_last_error;
 
 // Fine level (finite differences, Eq. 40) and, for two-grid, the coarse FE
 // level that carries the domain decomposition; then the slabs.
+double spacing(const hz_params& p) { return p.h > 0 ? p.h : 1.0 / p.n[0]; }
+
+size_t n_dof(const hz_params& p) {
+  size_t n = 1;
+  for (int l = 0; l < p.dim; ++l) n *= (size_t)(p.n[l] + 2 * p.w_out - 1);
+  return n;
+}
+
 void build_levels(hz_handle* h, const double* m_dev) {
   const hz_params& p = h->p;
-  const double hh = 1.0 / p.n;
-  build_level_fd(h, h->fine, p.n, p.w_out, hh, m_dev, h->s2);
+  const double hh = spacing(p);
+  build_level_fd(h, h->fine, p.n, p.w_out, hh, m_dev, p.dim == 3, h->s2);
   if (p.two_grid) {
     build_level_fe(h, h->coarse, h->fine, p.n, p.w_out, hh, h->s2);
     h->sweep = &h->coarse;
@@ -74,8 +82,13 @@ void release_work(hz_handle* h) {
 void validate(const hz_params* p) {
   auto bad = [](const std::string& m) { throw Failure(HZ_EINVAL, m); };
   if (!p) bad("params is NULL");
-  if (p->dim != 2) bad("only dim = 2 is built");
-  if (p->n < 4) bad("n must be >= 4");
+  if (p->dim != 2 && p->dim != 3) bad("dim must be 2 or 3");
+  for (int l = 0; l < p->dim; ++l) {
+    if (p->n[l] < 4) bad("every n[l] must be >= 4");
+    if (p->two_grid && (p->n[l] % 2 != 0))
+      bad("two_grid needs an even number of interior cells on every axis");
+  }
+  if (!(p->h >= 0)) bad("h must be >= 0 (0: 1 / n[0])");
   if (p->w_out < 0) bad("w_out must be >= 0");
   if (!(p->omega > 0)) bad("omega must be > 0");
   if (p->J < 1) bad("J must be >= 1");
@@ -87,10 +100,9 @@ void validate(const hz_params* p) {
   if (p->max_iter < 1) bad("max_iter must be >= 1");
   if (!(p->tol > 0)) bad("tol must be > 0");
   if (!(p->c_pml >= 0)) bad("c_pml must be >= 0 (0: mean wave speed)");
-  if (p->max_rhs < 1 || p->max_rhs > 8) bad("max_rhs must be in 1..8");
-  if (p->two_grid && (p->n % 2 != 0)) bad("two_grid needs an even number of interior cells");
+  if (p->max_rhs < 1 || p->max_rhs > 64) bad("max_rhs must be in 1..64");
   if (p->two_grid && (p->nu < 0 || !(p->omega_jac > 0))) bad("bad smoother parameters");
-  int N = p->two_grid ? 2 * p->w_out + p->n / 2 - 1 : p->n + 2 * p->w_out - 1;
+  int N = p->two_grid ? 2 * p->w_out + p->n[0] / 2 - 1 : p->n[0] + 2 * p->w_out - 1;
   if (N / p->J < 4) bad("slabs too thin: fewer than 4 columns per slab");
 }
 
@@ -139,23 +151,22 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
     HZ_CU(cudaEventCreateWithFlags(&h->evB, cudaEventDisableTiming));
     h->dev_flag = (int*)dmalloc(sizeof(int));
     HZ_CU(cudaMemsetAsync(h->dev_flag, 0, sizeof(int), h->s2));
-    const int N = p->n + 2 * p->w_out - 1;
-    const double hh = 1.0 / p->n;
-    h->c_pml = p->c_pml > 0 ? p->c_pml : mean_velocity(m_dev, (size_t)N * N, h->s2);
+    const size_t n = n_dof(*p);
+    h->c_pml = p->c_pml > 0 ? p->c_pml : mean_velocity(m_dev, n, h->s2);
     build_levels(h, m_dev);
-    const size_t n = (size_t)N * N;
     const size_t ps = prec_size(*p);
     const int R = p->max_rhs, m = p->gmres_m;
     Level& L = *h->sweep;
-    const size_t nl = (size_t)L.nx * L.ny;
+    const size_t nl = L.size();
     h->pr_r = dmalloc(ps * nl * R);
     h->pr_u = dmalloc(ps * nl * R);
     h->pr_u2 = dmalloc(ps * nl * R);
     h->pr_g = dmalloc(ps * nl * R);
-    h->pr_B1 = dmalloc(ps * 2 * R * L.ny);
-    h->pr_B2 = dmalloc(ps * 2 * R * L.ny);
-    HZ_CU(cudaMemsetAsync(h->pr_B1, 0, ps * 2 * R * L.ny, h->s2));
-    HZ_CU(cudaMemsetAsync(h->pr_B2, 0, ps * 2 * R * L.ny, h->s2));
+    // transmission buffers [2][R][N_t]: the two layers passed between slabs
+    h->pr_B1 = dmalloc(ps * 2 * R * L.nt());
+    h->pr_B2 = dmalloc(ps * 2 * R * L.nt());
+    HZ_CU(cudaMemsetAsync(h->pr_B1, 0, ps * 2 * R * L.nt(), h->s2));
+    HZ_CU(cudaMemsetAsync(h->pr_B2, 0, ps * 2 * R * L.nt(), h->s2));
     if (p->two_grid) {
       h->tg_u = dmalloc(ps * n * R);
       h->tg_r = dmalloc(ps * n * R);
@@ -187,8 +198,7 @@ hz_status hz_set_medium(hz_handle* h, const double* m_dev) {
     const hz_params p = h->p;
     free_level(h->fine);
     free_level(h->coarse);
-    const int N = p.n + 2 * p.w_out - 1;
-    h->c_pml = p.c_pml > 0 ? p.c_pml : mean_velocity(m_dev, (size_t)N * N, h->s2);
+    h->c_pml = p.c_pml > 0 ? p.c_pml : mean_velocity(m_dev, n_dof(p), h->s2);
     build_levels(h, m_dev);
     h->factored = false;
     h->stats.t_setup_s = now_s() - t0;
@@ -200,10 +210,19 @@ hz_status hz_factor(hz_handle* h, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   return guarded(h, [&] {
     double t0 = now_s();
-    if (h->p.precision == HZ_MIXED)
-      factor_level<float>(h, *h->sweep, s);
-    else
-      factor_level<double>(h, *h->sweep, s);
+    h->factored = false;
+    Level& L = *h->sweep;
+    if (L.dim3d) {
+      if (h->p.precision == HZ_MIXED)
+        factor_level3d<float>(h, L, s);
+      else
+        factor_level3d<double>(h, L, s);
+    } else {
+      if (h->p.precision == HZ_MIXED)
+        factor_level<float>(h, L, s);
+      else
+        factor_level<double>(h, L, s);
+    }
     check_dev_flag(h, s);
     h->factored = true;
     h->stats.t_factor_s = now_s() - t0;
@@ -240,12 +259,12 @@ hz_status hz_solve_host(hz_handle* h, const hz_c128* f_host, hz_c128* u_host, in
                         void* stream, hz_stats* stats) {
   if (!h) return fail(nullptr, HZ_EINVAL, "handle is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = (size_t)h->fine.nx * h->fine.ny * n_rhs;
+  const size_t n = h->fine.size() * n_rhs;
   hz_status st = guarded(h, [&] {
     if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
     if (!f_host || !u_host) throw Failure(HZ_EINVAL, "NULL field pointer");
     if (!h->stage_f) {   // allocated once, on the first host call
-      const size_t cap = (size_t)h->fine.nx * h->fine.ny * h->p.max_rhs;
+      const size_t cap = h->fine.size() * h->p.max_rhs;
       h->stage_f = (c128*)dmalloc(sizeof(c128) * cap);
       h->stage_u = (c128*)dmalloc(sizeof(c128) * cap);
     }
@@ -374,13 +393,18 @@ hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_de
     if (j < 1 || j > L.J) throw Failure(HZ_EINVAL, "slab index out of range");
     if (n_rhs < 1 || n_rhs > h->p.max_rhs) throw Failure(HZ_EINVAL, "n_rhs out of range");
     if (!f_dev || !u_dev) throw Failure(HZ_EINVAL, "NULL field pointer");
-    const size_t n = (size_t)n_rhs * L.ny * L.slabs[j].W;
+    const size_t n = (size_t)n_rhs * L.nt() * L.slabs[j].W;
     if (h->p.precision == HZ_MIXED) {
       tf = dmalloc(sizeof(c64) * n);
       tu = dmalloc(sizeof(c64) * n);
       cast_copy<float, double>((const c128*)f_dev, (c64*)tf, n, s);
-      slab_solve_raw<float>(h, L, j, (const c64*)tf, (c64*)tu, n_rhs, s);
+      if (L.dim3d)
+        slab_solve_raw3d<float>(h, L, j, (const c64*)tf, (c64*)tu, n_rhs, s);
+      else
+        slab_solve_raw<float>(h, L, j, (const c64*)tf, (c64*)tu, n_rhs, s);
       cast_copy<double, float>((const c64*)tu, (c128*)u_dev, n, s);
+    } else if (L.dim3d) {
+      slab_solve_raw3d<double>(h, L, j, (const c128*)f_dev, (c128*)u_dev, n_rhs, s);
     } else {
       slab_solve_raw<double>(h, L, j, (const c128*)f_dev, (c128*)u_dev, n_rhs, s);
     }
@@ -461,6 +485,7 @@ void hz_destroy(hz_handle* h) {
   dfree(h->gr_u);
   dfree(h->gr_mu);
   dfree(h->gr_phi);
+  dfree(h->gm_state);
   cudaGetLastError();
   delete h;
 }

@@ -16,6 +16,7 @@ namespace hz {
 
 constexpr int kRedBlocks = 296;   // 2 x 148 blocks per right-hand side
 constexpr int kRedThreads = 256;
+constexpr int kMaxRhsThreads = 64;   // one thread per right-hand side (max_rhs <= 64)
 
 // partial[r][i][blk] = sum over the block's chunk of conj(V_i) . w   (i < nv)
 __global__ void __launch_bounds__(kRedThreads) multi_dot_kernel(const c128* __restrict__ V,
@@ -131,8 +132,9 @@ __global__ void scale_kernel(const c128* __restrict__ w, c128* __restrict__ v, s
 __global__ void norm_from_dot_kernel(c128* hc, int hstride, int idx, int nr) {
   int r = threadIdx.x;
   if (r < nr) {
+    // a NaN sum stays NaN (a NaN norm must not read as zero, i.e. converged)
     double v = hc[(size_t)r * hstride + idx].re;
-    hc[(size_t)r * hstride + idx] = mk(sqrt(v > 0 ? v : 0.0), 0.0);
+    hc[(size_t)r * hstride + idx] = mk(isnan(v) ? v : sqrt(v > 0 ? v : 0.0), 0.0);
   }
 }
 
@@ -236,23 +238,28 @@ size_t gmres_red_doubles(int m, int nr) { return (size_t)kRedBlocks * 2 * (m + 2
 
 void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
   Level& F = h->fine;
-  const size_t n = (size_t)F.nx * F.ny;
+  const size_t n = F.size();
   const int m = h->p.gmres_m;
   const size_t vs = n * nr;   // stride between basis vectors
   Gm gm{h, n, nr, m, s};
+  // Arnoldi state for max_rhs right-hand sides: allocated by the first solve
+  // and kept by the handle (a solve allocates nothing after that)
+  const int R = h->p.max_rhs;
+  const size_t b_H = sizeof(c128) * R * (m + 1) * m, b_cs = sizeof(double) * R * m;
+  const size_t b_sn = sizeof(c128) * R * m, b_g = sizeof(c128) * R * (m + 1);
+  const size_t b_res = sizeof(double) * R, b_kd = sizeof(int) * R * 2;
+  const size_t b_y = sizeof(c128) * R * m, b_bn = sizeof(double) * R;
+  if (!h->gm_state) h->gm_state = dmalloc(b_H + b_cs + b_sn + b_g + b_res + b_kd + b_y + b_bn);
+  unsigned char* gp = (unsigned char*)h->gm_state;
   ArnoldiState st;
-  st.H = (c128*)dmalloc(sizeof(c128) * nr * (m + 1) * m);
-  st.cs = (double*)dmalloc(sizeof(double) * nr * m);
-  st.sn = (c128*)dmalloc(sizeof(c128) * nr * m);
-  st.g = (c128*)dmalloc(sizeof(c128) * nr * (m + 1));
-  st.res = (double*)dmalloc(sizeof(double) * nr);
-  st.kdone = (int*)dmalloc(sizeof(int) * nr);
-  c128* y = (c128*)dmalloc(sizeof(c128) * nr * m);
-  double* bnorm_d = (double*)dmalloc(sizeof(double) * nr);
-  struct Free {
-    std::vector<void*> p;
-    ~Free() { for (void* q : p) dfree(q); }
-  } fr{{st.H, st.cs, st.sn, st.g, st.res, st.kdone, y, bnorm_d}};
+  st.H = (c128*)gp;                          gp += b_H;
+  st.g = (c128*)gp;                          gp += b_g;
+  st.sn = (c128*)gp;                         gp += b_sn;
+  c128* y = (c128*)gp;                       gp += b_y;
+  st.cs = (double*)gp;                       gp += b_cs;
+  st.res = (double*)gp;                      gp += b_res;
+  double* bnorm_d = (double*)gp;             gp += b_bn;
+  st.kdone = (int*)gp;
   const int hs = m + 2;
   c128* hc = h->hcol;                    // [nr][hs]
   c128* hc2 = h->hcol + (size_t)nr * hs; // [nr][hs]
@@ -261,7 +268,7 @@ void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
 
   auto norms = [&](const c128* v, std::vector<double>& out) {
     gm.dots(v, vs, 1, v, hc, hs);
-    norm_from_dot_kernel<<<1, 32, 0, s>>>(hc, hs, 0, nr);
+    norm_from_dot_kernel<<<1, kMaxRhsThreads, 0, s>>>(hc, hs, 0, nr);
     std::vector<c128> hb((size_t)nr * hs);
     HZ_CU(cudaMemcpyAsync(hb.data(), hc, sizeof(c128) * nr * hs, cudaMemcpyDeviceToHost, s));
     HZ_CU(cudaStreamSynchronize(s));
@@ -289,9 +296,9 @@ void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
     if (!any || maxit >= h->p.max_iter) break;
     // beta = ||R||, V_0 = R / beta; inactive right-hand sides start with g = 0
     gm.dots(h->R, vs, 1, h->R, hc, hs);
-    norm_from_dot_kernel<<<1, 32, 0, s>>>(hc, hs, 0, nr);
+    norm_from_dot_kernel<<<1, kMaxRhsThreads, 0, s>>>(hc, hs, 0, nr);
     scale_kernel<<<eg, 256, 0, s>>>(h->R, h->V, n, hc, hs, 0);
-    cycle_init_kernel<<<1, 32, 0, s>>>(st, m, nr, hc, hs, 0);
+    cycle_init_kernel<<<1, kMaxRhsThreads, 0, s>>>(st, m, nr, hc, hs, 0);
     h->launches += 3;
     for (int r = 0; r < nr; ++r)
       if (!active[r]) HZ_CU(cudaMemsetAsync(st.g + (size_t)r * (m + 1), 0, sizeof(c128), s));
@@ -308,9 +315,9 @@ void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
       multi_axpy_kernel<<<eg, 256, 0, s>>>(h->V, vs, j + 1, hc2, hs, h->W, n);
       add_coeffs_kernel<<<cdiv((j + 1) * nr, 64), 64, 0, s>>>(hc, hc2, hs, j + 1, nr);
       gm.dots(h->W, vs, 1, h->W, hc + (j + 1), hs);                 // ||w||^2
-      norm_from_dot_kernel<<<1, 32, 0, s>>>(hc, hs, j + 1, nr);
+      norm_from_dot_kernel<<<1, kMaxRhsThreads, 0, s>>>(hc, hs, j + 1, nr);
       scale_kernel<<<eg, 256, 0, s>>>(h->W, h->V + (size_t)(j + 1) * vs, n, hc, hs, j + 1);
-      arnoldi_update_kernel<<<1, 32, 0, s>>>(st, hc, hs, m, j, nr, bnorm_d, tol);
+      arnoldi_update_kernel<<<1, kMaxRhsThreads, 0, s>>>(st, hc, hs, m, j, nr, bnorm_d, tol);
       h->launches += 7;
       HZ_CU(cudaMemcpyAsync(kd.data(), st.kdone, sizeof(int) * nr, cudaMemcpyDeviceToHost, s));
       HZ_CU(cudaStreamSynchronize(s));
@@ -325,7 +332,7 @@ void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
       }
       if (all_frozen || maxit2 >= h->p.max_iter) break;
     }
-    solve_upper_kernel<<<1, 32, 0, s>>>(st, m, nr, y);
+    solve_upper_kernel<<<1, kMaxRhsThreads, 0, s>>>(st, m, nr, y);
     basis_update_kernel<<<eg, 256, 0, s>>>(h->Z, vs, kmax, y, m, u, n);
     level_residual<double>(h, F, f, u, h->R, nr, s);
     h->launches += 2;

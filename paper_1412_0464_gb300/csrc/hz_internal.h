@@ -114,24 +114,38 @@ struct Slab {
   void* carry_f = nullptr;   // forward segment end values [P+NG][n_rhs][wp] ([P+g]: group g's end)
   void* carry_b = nullptr;   // backward segment start values [P+1+NG][n_rhs][wp] ([P]: meeting
                              // row, [P+1+g]: group g's start)
+  // 3-D slabs (dense-block path, slab3d.cu): block rows are the z layers of
+  // B = N_y W unknowns (index b = y W + e); G holds [nz][bstride] dense
+  // inverses, st3 the slab stencil [nz][27][B] (plane (dz+1) 9 + (dy+1) 3 +
+  // (dx+1)), inj3 the transmission coefficients [4][nz][ny][9] ((dz+1) 3 +
+  // (dy+1)), Y the forward / solution layers [nz][n_rhs][B], V the two
+  // chains' step vectors [2][n_rhs][B].
+  int B = 0;
+  size_t bstride = 0;
+  void* st3 = nullptr;
+  void* inj3 = nullptr;
+  void* V = nullptr;
 };
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.
 struct Level {
   bool dim3d = false;        // 3-D level (slabs handled by the dense-block path)
-  int nx = 0, ny = 0;        // unknowns along x (sweep) and y
+  int nx = 0, ny = 0, nz = 1;  // unknowns along x (sweep), y, z (nz = 1 in 2-D)
   double h = 0;              // uniform spacing (finite differences)
-  bool fe = false;           // stored 9-point operator (coarse FE level)
-  AxisTables ax, ay;
+  bool fe = false;           // stored 9-point (2-D) / 27-point (3-D) operator (coarse FE level)
+  AxisTables ax, ay, az;
   double* m = nullptr;       // squared slowness at unknowns (FD level), FP64
   float* m32 = nullptr;      // FP32 copy
-  c128* st128 = nullptr;     // FE level: 9 coefficient planes [9][ny][nx]
+  c128* st128 = nullptr;     // FE level: 9 / 27 coefficient planes [q][nz][ny][nx]
   c64* st64 = nullptr;
-  double* k2c = nullptr;     // FE level: cell k^2 [(ny+1)][(nx+1)]
-  int* ifp = nullptr;        // FE level: coarse node -> fine node (per axis, both axes equal)
-  int* refined = nullptr;    // FE level: coarse cell refined flags
-  int* q0 = nullptr;         // FE level: prolongation sources per fine node
-  int* q1 = nullptr;
+  double* k2c = nullptr;     // FE level: cell k^2 [(nz+1)][(ny+1)][(nx+1)] ((ny+1)(nx+1) in 2-D)
+  int* ifp[3] = {};          // FE level, per axis x, y, z: coarse node -> fine node,
+  int* refined[3] = {};      //   coarse cell refined flags,
+  int* q0[3] = {};           //   prolongation sources per fine node
+  int* q1[3] = {};
+  size_t size() const { return (size_t)nx * ny * nz; }   // unknowns
+  size_t nt() const { return (size_t)ny * nz; }          // transverse unknowns per column
+  int planes() const { return dim3d ? 27 : 9; }           // stored stencil planes (FE level)
   int J = 0, w = 0;
   std::vector<int> beta, beta_t;  // Eq. 17, size J+1
   std::vector<Slab> slabs;        // index 1..J (0 unused)
@@ -147,6 +161,14 @@ struct Level {
   int4* grp_dev = nullptr;
   void* fac_desc = nullptr;        // factorisation task descriptors (device, built once)
   int* fac_sync = nullptr;         // their progress / task / group counters (device)
+  // 3-D factorisation work (slab3d.cu), allocated by the first factorisation:
+  // per chain a dense B x B Schur complement, the panel's colmods [B][NB]
+  // and rowmods [NB][B], pivot rows, their inverse map and pivot flags
+  void* f3_S = nullptr;
+  void* f3_C = nullptr;
+  void* f3_R = nullptr;
+  int* f3_piv = nullptr;
+  void* f3_desc = nullptr;
 };
 
 // Layout of the parallel-in-y slab substitution for a slab of ny block rows:
@@ -218,6 +240,7 @@ struct hz_handle {
   hz::c128* gr_u = nullptr;     //   forward fields,
   hz::c128* gr_mu = nullptr;    //   adjoint fields
   double* gr_phi = nullptr;     //   per right-hand-side misfit [max_rhs]
+  void* gm_state = nullptr;     // GMRES Arnoldi state (Hessenberg, rotations, ...) [max_rhs]
 };
 
 namespace hz {
@@ -246,11 +269,13 @@ void timed(hz_handle* h, const char* tag, double bytes, cudaStream_t s, F&& laun
 namespace hz {
 
 // setup.cu
-void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const double* m_dev,
-                    cudaStream_t s);
-void build_level_fe(hz_handle* h, Level& L, const Level& fine, int n, int w_out, double hh,
-                    cudaStream_t s);
+void build_level_fd(hz_handle* h, Level& L, const int* n_int, int w_out, double hh,
+                    const double* m_dev, bool dim3d, cudaStream_t s);
+void build_level_fe(hz_handle* h, Level& L, const Level& fine, const int* n_int, int w_out,
+                    double hh, cudaStream_t s);
 void build_slabs(hz_handle* h, Level& L, cudaStream_t s);
+void partition(Level& L);
+void slab_geometry(hz_handle* h, Level& L, Slab& S, int j, cudaStream_t s);
 void free_level(Level& L);
 double mean_velocity(const double* m_dev, size_t n, cudaStream_t s);
 
@@ -290,6 +315,25 @@ template <typename R>
 void slab_solve_raw_scratch(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud,
                             int n_rhs, cudaStream_t s, cplx<R>* Y, cplx<R>* carry_f,
                             cplx<R>* carry_b);
+
+// slab3d.cu: 3-D slabs (block rows = z layers, dense B x B blocks)
+template <typename R>
+void build_slabs3d(hz_handle* h, Level& L, cudaStream_t s);
+template <typename R>
+void factor_level3d(hz_handle* h, Level& L, cudaStream_t s);
+template <typename R>
+void subdom_solve3d(hz_handle* h, Level& L, int j, const cplx<R>* f, int a, int b, int at,
+                    int bt, bool tau1, const cplx<R>* B1, bool tau2, cplx<R>* B2, bool tau3,
+                    const cplx<R>* B3, bool tau4, cplx<R>* B4, cplx<R>* u, int n_rhs,
+                    cudaStream_t s);
+template <typename R>
+void slab_solve_raw3d(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud, int n_rhs,
+                      cudaStream_t s);
+
+// stencil3d.cu: 3-D operators (fine 7-point on the fly, coarse 27-point stored)
+template <typename R>
+void launch_op3d(hz_handle* h, const Level& L, int mode, const cplx<R>* f, const cplx<R>* u,
+                 cplx<R>* y, int n_rhs, double omega_jac, cudaStream_t s);
 
 // sweep.cu
 template <typename R>

@@ -288,33 +288,40 @@ SegmentLayout segment_layout(int ny, int segments, int max_auto) {
   return L;
 }
 
-void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const double* m_dev,
-                    cudaStream_t s) {
-  int n_cells = n + 2 * w_out;
-  L.nx = L.ny = n_cells - 1;
+// n_int[l]: interior cells along x, y, z (z only when dim3d).
+void build_level_fd(hz_handle* h, Level& L, const int* n_int, int w_out, double hh,
+                    const double* m_dev, bool dim3d, cudaStream_t s) {
+  L.dim3d = dim3d;
+  L.nx = n_int[0] + 2 * w_out - 1;
+  L.ny = n_int[1] + 2 * w_out - 1;
+  L.nz = dim3d ? n_int[2] + 2 * w_out - 1 : 1;
   L.h = hh;
   L.fe = false;
   double C = (w_out > 0) ? h->p.s_pml_out * h->c_pml / std::pow(w_out * hh, 3) : 0.0;
-  for (AxisTables* a : {&L.ax, &L.ay}) {
-    alloc_axis(*a, L.nx);
-    a->ia_node = (c128*)dmalloc(sizeof(c128) * L.nx);
-    a->ia_node32 = (c64*)dmalloc(sizeof(c64) * L.nx);
-    fine_axis_kernel<<<cdiv(L.nx + 1, 256), 256, 0, s>>>(
-        L.nx, n_cells, w_out, hh, C, h->p.omega, a->a_node, a->a_cell, a->h_cell, a->a_node32,
+  AxisTables* axes[3] = {&L.ax, &L.ay, &L.az};
+  for (int l = 0; l < (dim3d ? 3 : 2); ++l) {
+    AxisTables* a = axes[l];
+    const int n_cells = n_int[l] + 2 * w_out;
+    const int N = n_cells - 1;
+    alloc_axis(*a, N);
+    a->ia_node = (c128*)dmalloc(sizeof(c128) * N);
+    a->ia_node32 = (c64*)dmalloc(sizeof(c64) * N);
+    fine_axis_kernel<<<cdiv(N + 1, 256), 256, 0, s>>>(
+        N, n_cells, w_out, hh, C, h->p.omega, a->a_node, a->a_cell, a->h_cell, a->a_node32,
         a->a_cell32, a->ia_node, a->ia_node32);
     HZ_CU(cudaGetLastError());
     // PML-free interior (the operator's coefficients are real there): the
     // longest run of unknowns with 1/alpha = 1 at the node and alpha = 1 at
     // both adjacent cells, read back from the tables just built
-    std::vector<c128> ia(L.nx), ac(L.nx + 1);
-    HZ_CU(cudaMemcpyAsync(ia.data(), a->ia_node, sizeof(c128) * L.nx, cudaMemcpyDeviceToHost, s));
-    HZ_CU(cudaMemcpyAsync(ac.data(), a->a_cell, sizeof(c128) * (L.nx + 1), cudaMemcpyDeviceToHost,
+    std::vector<c128> ia(N), ac(N + 1);
+    HZ_CU(cudaMemcpyAsync(ia.data(), a->ia_node, sizeof(c128) * N, cudaMemcpyDeviceToHost, s));
+    HZ_CU(cudaMemcpyAsync(ac.data(), a->a_cell, sizeof(c128) * (N + 1), cudaMemcpyDeviceToHost,
                           s));
     HZ_CU(cudaStreamSynchronize(s));
     auto one = [](const c128& v) { return v.re == 1.0 && v.im == 0.0; };
     int best_lo = 1, best_hi = 0, run = -1;
-    for (int i = 0; i <= L.nx; ++i) {
-      const bool ok = i < L.nx && one(ia[i]) && one(ac[i]) && one(ac[i + 1]);
+    for (int i = 0; i <= N; ++i) {
+      const bool ok = i < N && one(ia[i]) && one(ac[i]) && one(ac[i + 1]);
       if (ok && run < 0) run = i;
       if (!ok && run >= 0) {
         if (i - 1 - run > best_hi - best_lo) { best_lo = run; best_hi = i - 1; }
@@ -324,7 +331,7 @@ void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const d
     a->in_lo = best_lo;
     a->in_hi = best_hi;
   }
-  size_t nn = (size_t)L.nx * L.ny;
+  size_t nn = L.size();
   if (!L.m) L.m = (double*)dmalloc(sizeof(double) * nn);
   if (!L.m32) L.m32 = (float*)dmalloc(sizeof(float) * nn);
   HZ_CU(cudaMemcpyAsync(L.m, m_dev, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
@@ -333,13 +340,29 @@ void build_level_fd(hz_handle* h, Level& L, int n, int w_out, double hh, const d
 }
 
 // Partition (Eq. 17): beta_0 = -1, beta_J = N-1, first N mod J slabs one wider.
-static void partition(Level& L) {
+void partition(Level& L) {
   int N = L.nx, J = L.J;
   L.beta.assign(J + 1, 0);
   L.beta[0] = -1;
   for (int j = 0; j < J; ++j) L.beta[j + 1] = L.beta[j] + N / J + (j < N % J ? 1 : 0);
   L.beta_t = L.beta;
   for (int j = 1; j < J; ++j) L.beta_t[j] = L.beta[j] - 1;
+}
+
+// Slab j of the partition: core columns, added PML columns (Eq. 9) and the
+// slab x axis with the DD PML (Eqs. 9-10).
+void slab_geometry(hz_handle* h, Level& L, Slab& S, int j, cudaStream_t s) {
+  S.j = j;
+  S.lo = L.beta_t[j - 1] + 1;
+  S.hi = L.beta[j];
+  S.wl = (j > 1) ? L.w : 0;
+  S.wr = (j < L.J) ? L.w : 0;
+  S.W = S.hi - S.lo + 1 + S.wl + S.wr;
+  alloc_axis(S.ax, S.W);
+  slab_axis_kernel<<<cdiv(S.W + 1, 128), 128, 0, s>>>(
+      S.W, S.lo, S.hi, S.wl, L.ax.a_node, L.ax.a_cell, L.ax.h_cell, h->p.s_pml_dd, h->c_pml,
+      L.w, h->p.omega, S.ax.a_node, S.ax.a_cell, S.ax.h_cell, S.ax.a_node32, S.ax.a_cell32);
+  HZ_CU(cudaGetLastError());
 }
 
 template <typename R>
@@ -349,17 +372,8 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
   int maxW = 0;
   for (int j = 1; j <= L.J; ++j) {
     Slab& S = L.slabs[j];
-    S.j = j;
-    S.lo = L.beta_t[j - 1] + 1;
-    S.hi = L.beta[j];
-    S.wl = (j > 1) ? L.w : 0;
-    S.wr = (j < L.J) ? L.w : 0;
-    S.W = S.hi - S.lo + 1 + S.wl + S.wr;
+    slab_geometry(h, L, S, j, s);
     maxW = std::max(maxW, S.W);
-    alloc_axis(S.ax, S.W);
-    slab_axis_kernel<<<cdiv(S.W + 1, 128), 128, 0, s>>>(
-        S.W, S.lo, S.hi, S.wl, L.ax.a_node, L.ax.a_cell, L.ax.h_cell, h->p.s_pml_dd, h->c_pml,
-        L.w, h->p.omega, S.ax.a_node, S.ax.a_cell, S.ax.h_cell, S.ax.a_node32, S.ax.a_cell32);
     // plane stride padded so that every plane row starts on a 16-byte boundary
     // row stride = 4 (mod 8): rows start on 16-byte boundaries and the eight
     // rows a warp reads in one substitution step fall on disjoint bank groups
@@ -437,6 +451,14 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
 }
 
 void build_slabs(hz_handle* h, Level& L, cudaStream_t s) {
+  if (L.dim3d) {
+    partition(L);
+    if (h->p.precision == HZ_MIXED)
+      build_slabs3d<float>(h, L, s);
+    else
+      build_slabs3d<double>(h, L, s);
+    return;
+  }
   if (h->p.precision == HZ_MIXED)
     build_slabs_t<float>(h, L, s);
   else
@@ -450,13 +472,19 @@ void free_level(Level& L) {
     dfree(S.PhiP); dfree(S.PsiP);
     dfree(S.inj); dfree(S.Y);
     dfree(S.carry_f); dfree(S.carry_b);
+    dfree(S.st3); dfree(S.inj3); dfree(S.V);
   }
   L.slabs.clear();
   free_axis(L.ax);
   free_axis(L.ay);
+  free_axis(L.az);
   dfree(L.m); dfree(L.m32); dfree(L.st128); dfree(L.st64); dfree(L.seg_dev);
-  dfree(L.k2c); dfree(L.ifp); dfree(L.refined); dfree(L.q0); dfree(L.q1);
+  dfree(L.k2c);
+  for (int l = 0; l < 3; ++l) {
+    dfree(L.ifp[l]); dfree(L.refined[l]); dfree(L.q0[l]); dfree(L.q1[l]);
+  }
   dfree(L.fac_desc); dfree(L.fac_sync);
+  dfree(L.f3_S); dfree(L.f3_C); dfree(L.f3_R); dfree(L.f3_piv); dfree(L.f3_desc);
   L = Level{};
 }
 

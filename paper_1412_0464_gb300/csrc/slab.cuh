@@ -980,6 +980,7 @@ struct Rhs {
   const cplx<R>* B3;
   int eb;                     // local column of tilde-beta_j (tau3) or -1
   const cplx<R>* inj;         // [4][ny][3]
+  int bnr, br0;               // transmission buffers: [2][bnr][ny], this launch's rhs from br0
 };
 
 // Epilogue of a slab solve (Table 2): the slab solution's core columns into
@@ -993,6 +994,7 @@ struct Out {
   int e2;
   cplx<R>* B4;                // layers at local e4, e4+1 (tau4)
   int e4;
+  int bnr, br0;               // as in Rhs
 };
 
 template <typename R>
@@ -1034,7 +1036,7 @@ __device__ __forceinline__ cplx<R> rhs_at(const Rhs<R>& q, int ny, int W, int nr
   if (q.ef >= 0 && (e == q.ef || e == q.ef + 1)) {
     int s = e - q.ef;                          // 0: row beta uses B[1]; 1: row beta+1 uses B[0]
     const cplx<R>* c = q.inj + ((size_t)s * ny + k) * 3;
-    const cplx<R>* B = q.B1 + ((size_t)(1 - s) * nr + r) * ny;
+    const cplx<R>* B = q.B1 + ((size_t)(1 - s) * q.bnr + q.br0 + r) * ny;
     for (int dy = -1; dy <= 1; ++dy) {
       int kk = k + dy;
       if (kk >= 0 && kk < ny) cfma(v, c[dy + 1], B[kk]);
@@ -1043,7 +1045,7 @@ __device__ __forceinline__ cplx<R> rhs_at(const Rhs<R>& q, int ny, int W, int nr
   if (q.eb >= 0 && (e == q.eb || e == q.eb + 1)) {
     int s = e - q.eb;
     const cplx<R>* c = q.inj + ((size_t)(2 + s) * ny + k) * 3;
-    const cplx<R>* B = q.B3 + ((size_t)(1 - s) * nr + r) * ny;
+    const cplx<R>* B = q.B3 + ((size_t)(1 - s) * q.bnr + q.br0 + r) * ny;
     for (int dy = -1; dy <= 1; ++dy) {
       int kk = k + dy;
       if (kk >= 0 && kk < ny) cfma(v, c[dy + 1], B[kk]);
@@ -1410,8 +1412,10 @@ __device__ __forceinline__ void store_out(const Out<R>& o, int ny, int W, int nr
   const int g = row - o.wl + o.lo;
   if (o.raw) o.raw[((size_t)r * ny + k) * W + row] = x;
   if (o.u && g > o.ua && g <= o.ub) o.u[((size_t)r * ny + k) * o.nx + g] = x;
-  if (o.B2 && (row == o.e2 || row == o.e2 + 1)) o.B2[((size_t)(row - o.e2) * nr + r) * ny + k] = x;
-  if (o.B4 && (row == o.e4 || row == o.e4 + 1)) o.B4[((size_t)(row - o.e4) * nr + r) * ny + k] = x;
+  if (o.B2 && (row == o.e2 || row == o.e2 + 1))
+    o.B2[((size_t)(row - o.e2) * o.bnr + o.br0 + r) * ny + k] = x;
+  if (o.B4 && (row == o.e4 || row == o.e4 + 1))
+    o.B4[((size_t)(row - o.e4) * o.bnr + o.br0 + r) * ny + k] = x;
 }
 
 // Final backward recurrence over segment s from x_{n} = the true start value
@@ -1980,7 +1984,23 @@ template <typename R>
 static void run_solve(hz_handle* h, Level& L, Slab& S, const Rhs<R>& rhs, const Out<R>& out,
                       int n_rhs, cudaStream_t s, cplx<R>* Y, cplx<R>* cf, cplx<R>* cb,
                       bool tagged) {
-  if (n_rhs < 1 || n_rhs > kNRMax) throw Failure(HZ_EINVAL, "right-hand sides per slab launch must be 1..8");
+  if (n_rhs > kNRMax) {       // chunks of at most kNRMax right-hand sides
+    for (int r0 = 0; r0 < n_rhs; r0 += kNRMax) {
+      const int nr = std::min(kNRMax, n_rhs - r0);
+      Rhs<R> q = rhs;
+      Out<R> o = out;
+      q.bnr = o.bnr = n_rhs;
+      q.br0 = o.br0 = r0;
+      const size_t in_f = (size_t)L.ny * L.nx, in_raw = (size_t)L.ny * S.W;
+      if (q.raw) q.raw += r0 * in_raw;
+      if (q.f) q.f += r0 * in_f;
+      if (o.raw) o.raw += r0 * in_raw;
+      if (o.u) o.u += r0 * in_f;
+      run_solve<R>(h, L, S, q, o, nr, s, Y, cf, cb, tagged);
+    }
+    return;
+  }
+  if (n_rhs < 1) throw Failure(HZ_EINVAL, "right-hand sides per slab launch must be >= 1");
   SolveArgs<R> a;
   a.W = S.W; a.wp = S.wp; a.ny = L.ny; a.nr = n_rhs;
   a.F = (const cplx<R>*)S.F; a.E = (const cplx<R>*)S.E; a.mstride = S.mstride;
@@ -1994,6 +2014,8 @@ static void run_solve(hz_handle* h, Level& L, Slab& S, const Rhs<R>& rhs, const 
   a.flag = h->dev_flag;
   a.rhs = rhs;
   a.out = out;
+  if (a.rhs.bnr == 0) a.rhs.bnr = n_rhs;    // one launch for all right-hand sides
+  if (a.out.bnr == 0) a.out.bnr = n_rhs;
   const double el = sizeof(cplx<R>);
   auto seq = [&] {
     if (n_rhs == 1) launch_solve<R, 1>(h, L, S, a, s, tagged);

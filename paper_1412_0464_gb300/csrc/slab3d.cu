@@ -1,0 +1,956 @@
+// 3-D slabs: set-up, factorisation and solves of the subdomain operators
+// A^(j) (SubdomSolve, Table 2; the paper factors them with a sparse direct
+// solver on CPU process groups, Section 5).
+//
+// A 3-D slab (x width W, all of y and z) is block tridiagonal along z: block
+// row k is the z layer k with B = N_y W unknowns (index b = y W + e).  D_k
+// couples a layer to itself (5-point in (y, x) for finite differences, 9-point
+// for the coarse FE operator), the couplings to the layers k -/+ 1 are
+// diagonal (7-point) or 9-point (27-point FE).  The slab stencil is stored
+// as 27 planes per layer, q = (dz+1) 9 + (dy+1) 3 + (dx+1).
+//
+// Twisted block LU, as for the 2-D slabs: a chain from layer 0 and a chain
+// from layer nz-1 meet at layer m = (nz-1)/2:
+//   S_t = D_{k_t} - L_t G_{t-1} R_{t-1},  G_t = S_t^-1,
+//   S_m = D_m - C_m G_{m-1} B_{m-1} - B_m G_{m+1} C_{m+1},
+// with L_t / R_t the couplings of a layer to the previous / next layer of its
+// chain.  The blocks are dense (B ~ 10^3 - 4 10^3): each inverse is a blocked
+// Gauss-Jordan elimination with implicit partial pivoting (pivot rows are
+// marked, not moved; G[p][piv[q]] = S[piv[p]][q] at the end).  One
+// elimination step with pivot row r for column p is the rank-1 update
+//   S -= c rho^T,  c = S[:, p] - e_r,  rho = S[r, :] / S[r][p] + e_p,
+// which turns column p into the inverse's column.  Panels of NB columns:
+// one CTA per chain eliminates the panel's columns on the panel only and
+// records the colmods c (C, B x NB), the pivot rows and 1 / S[r][p]; the
+// pivot rows' other columns follow from the short recurrence
+//   rho_t = (S[r_t, :] - sum_{s<t} C[r_t][s] rho_s) / S[r_t][p_t];
+// then S -= C R over the other columns is a dense complex GEMM of depth NB.
+// Every launch takes all chains of all slabs at the same step.
+//
+// Solve: forward y_t = G_t (f_t - L_t y_{t-1}) along both chains, meeting
+// x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1}), backward
+// x_t = y_t - G_t R_t x_{t+1}: per layer one sparse coupling apply and one
+// dense GEMV with the stored inverse (a skinny GEMM over the right-hand
+// sides).
+#include "hz_internal.h"
+
+#include <algorithm>
+#include <vector>
+
+namespace hz {
+
+namespace {
+
+constexpr int NB = 32;            // panel width of the blocked Gauss-Jordan inverse
+constexpr int kPanelThreads = 512;
+constexpr int kMaxB = 8192;       // largest block (pivot flags live in shared memory)
+
+template <typename R>
+__device__ __forceinline__ cplx<R> ldg(const cplx<R>* p) { return *p; }
+
+// plane index of the coupling (dz, dy, dx)
+__host__ __device__ __forceinline__ int qidx(int dz, int dy, int dx) {
+  return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+}
+
+// ------------------------------------------------------------------ set-up
+// Slab stencil of the 7-point operator (Eq. 40 in 3-D, times h^3) on the
+// extended slab mesh, k frozen to the adjacent core column in the added PML
+// (Eq. 10).  st3[k][q][y][e]; couplings to Dirichlet nodes are zero.
+template <typename R>
+__global__ void slab3_stencil_fd_kernel(int W, int ny, int nz, int lo, int hi, int wl, int nx,
+                                        double hh, double h2w2, const double* m,
+                                        const c128* sa_node, const c128* sa_cell,
+                                        const c128* ay_node, const c128* ay_cell,
+                                        const c128* az_node, const c128* az_cell, cplx<R>* st) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (e >= W) return;
+  const int g = min(max(e - wl + lo, lo), hi);
+  const double mm = m[((size_t)z * ny + y) * nx + g];
+  const c128 i1 = cinv(sa_node[e]), i2 = cinv(ay_node[y]), i3 = cinv(az_node[z]);
+  const c128 s23 = i2 * i3, s13 = i1 * i3, s12 = i1 * i2;
+  const c128 xl = sa_cell[e], xr = sa_cell[e + 1];
+  const c128 yl = ay_cell[y], yr = ay_cell[y + 1];
+  const c128 zl = az_cell[z], zr = az_cell[z + 1];
+  const c128 zero = mk(0.0, 0.0);
+  c128 v[27];
+  for (int q = 0; q < 27; ++q) v[q] = zero;
+  v[qidx(0, 0, 0)] = hh * (s23 * (xl + xr) + s13 * (yl + yr) + s12 * (zl + zr)) -
+                     (hh * h2w2 * mm) * (s12 * i3);
+  if (e > 0) v[qidx(0, 0, -1)] = -(hh * (s23 * xl));
+  if (e < W - 1) v[qidx(0, 0, 1)] = -(hh * (s23 * xr));
+  if (y > 0) v[qidx(0, -1, 0)] = -(hh * (s13 * yl));
+  if (y < ny - 1) v[qidx(0, 1, 0)] = -(hh * (s13 * yr));
+  if (z > 0) v[qidx(-1, 0, 0)] = -(hh * (s12 * zl));
+  if (z < nz - 1) v[qidx(1, 0, 0)] = -(hh * (s12 * zr));
+  const size_t B = (size_t)ny * W;
+  cplx<R>* out = st + (size_t)z * 27 * B + (size_t)y * W + e;
+  for (int q = 0; q < 27; ++q) out[(size_t)q * B] = ccast<R>(v[q]);
+}
+
+// Transmission coefficients of Eqs. 19-20 (global A entries between the two
+// layers of columns), per (z, y) and transverse offset t = (dz+1) 3 + (dy+1):
+//   inj[0] = +A_{beta,beta+1} (multiplies B[1]), inj[1] = -A_{beta+1,beta} (B[0]),
+//   inj[2] = -A_{bt,bt+1} (B[1]),                inj[3] = +A_{bt+1,bt} (B[0]),
+// beta = beta_{j-1}, bt = tilde-beta_j (-1: no such neighbour).  Finite
+// differences: only t = 4 (dz = dy = 0), A_{x,x+1} = -h alpha_{x+1/2} / (alpha_y alpha_z);
+// FE: read from the level's 27 stored planes.
+template <typename R>
+__global__ void inj3_kernel(int nx, int ny, int nz, int beta, int bt, double hh,
+                            const c128* ax_cell, const c128* ay_node, const c128* az_node,
+                            const c128* st, cplx<R>* inj) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  const int z = blockIdx.y;
+  if (y >= ny) return;
+  const size_t plane = (size_t)nx * ny * nz;
+  const size_t row = ((size_t)z * ny + y);
+  const size_t nt = (size_t)ny * nz;
+  const c128 zero = mk(0.0, 0.0);
+  for (int t = 0; t < 9; ++t) {
+    const int dz = t / 3 - 1, dy = t % 3 - 1;
+    c128 f0 = zero, f1 = zero, b0 = zero, b1 = zero;
+    if (st) {
+      if (beta >= 0) {
+        f0 = st[(size_t)qidx(dz, dy, 1) * plane + row * nx + beta];
+        f1 = -st[(size_t)qidx(dz, dy, -1) * plane + row * nx + beta + 1];
+      }
+      if (bt >= 0) {
+        b0 = -st[(size_t)qidx(dz, dy, 1) * plane + row * nx + bt];
+        b1 = st[(size_t)qidx(dz, dy, -1) * plane + row * nx + bt + 1];
+      }
+    } else if (t == 4) {
+      const c128 s = hh * cinv(ay_node[y] * az_node[z]);
+      const c128 af = beta >= 0 ? -(s * ax_cell[beta + 1]) : zero;
+      const c128 ab = bt >= 0 ? -(s * ax_cell[bt + 1]) : zero;
+      f0 = af; f1 = -af; b0 = -ab; b1 = ab;
+    }
+    const c128 vals[4] = {f0, f1, b0, b1};
+    for (int q = 0; q < 4; ++q) inj[((size_t)q * nt + row) * 9 + t] = ccast<R>(vals[q]);
+  }
+}
+
+}  // namespace
+
+template <typename R>
+void build_slabs3d(hz_handle* h, Level& L, cudaStream_t s) {
+  L.slabs.assign(L.J + 1, Slab{});
+  if (L.nz < 3) throw Failure(HZ_EINVAL, "a 3-D slab needs at least 3 z layers");
+  const size_t el = sizeof(cplx<R>);
+  const int R_ = h->p.max_rhs;
+  for (int j = 1; j <= L.J; ++j) {
+    Slab& S = L.slabs[j];
+    slab_geometry(h, L, S, j, s);
+    S.B = L.ny * S.W;
+    if (S.B > kMaxB)
+      throw Failure(HZ_EINVAL, "3-D slab block too large (N_y W = " + std::to_string(S.B) +
+                                   " > " + std::to_string(kMaxB) + ")");
+    S.bstride = ((size_t)S.B * S.B + 15) / 16 * 16;
+    const size_t B = S.B;
+    S.st3 = dmalloc(el * (size_t)L.nz * 27 * B);
+    HZ_CU(cudaMemsetAsync(S.st3, 0, el * (size_t)L.nz * 27 * B, s));
+    S.inj3 = dmalloc(el * 4 * L.nt() * 9);
+    const int beta = (j > 1) ? L.beta[j - 1] : -1;
+    const int bt = (j < L.J) ? L.beta_t[j] : -1;
+    if (!L.fe) {
+      const double h2w2 = L.h * L.h * h->p.omega * h->p.omega;
+      slab3_stencil_fd_kernel<R><<<dim3(cdiv(S.W, 64), L.ny, L.nz), 64, 0, s>>>(
+          S.W, L.ny, L.nz, S.lo, S.hi, S.wl, L.nx, L.h, h2w2, L.m, S.ax.a_node, S.ax.a_cell,
+          L.ay.a_node, L.ay.a_cell, L.az.a_node, L.az.a_cell, (cplx<R>*)S.st3);
+      inj3_kernel<R><<<dim3(cdiv(L.ny, 128), L.nz), 128, 0, s>>>(
+          L.nx, L.ny, L.nz, beta, bt, L.h, L.ax.a_cell, L.ay.a_node, L.az.a_node, nullptr,
+          (cplx<R>*)S.inj3);
+    } else {
+      slab_stencil_fe<R>(h, L, S, s);
+      inj3_kernel<R><<<dim3(cdiv(L.ny, 128), L.nz), 128, 0, s>>>(
+          L.nx, L.ny, L.nz, beta, bt, L.h, nullptr, nullptr, nullptr, L.st128, (cplx<R>*)S.inj3);
+    }
+    HZ_CU(cudaGetLastError());
+    S.G = dmalloc(el * S.bstride * L.nz);
+    S.Y = dmalloc(el * (size_t)L.nz * R_ * B);
+    S.V = dmalloc(el * 2 * (size_t)R_ * B);
+  }
+  L.mid = (L.nz - 1) / 2;
+  HZ_CU(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------ factorisation
+namespace {
+
+// One elimination chain at one step (or the meeting layer of a slab): the
+// layer k to factor, the Schur terms (previous layers kp with the dz of the
+// coupling k -> kp (L) and kp -> k (R)), the slab's stencil and inverses, and
+// the chain's work buffers.
+template <typename R>
+struct FChain {
+  int B, W, ny;
+  int k, nterm;
+  int kp[2], dzL[2], dzR[2];
+  const cplx<R>* st;   // [nz][27][B]
+  cplx<R>* G;          // [nz][bstride]
+  size_t bstride;
+  cplx<R>* S;          // [B][B] Schur complement, inverted in place
+  cplx<R>* C;          // [B][NB] colmods of the current panel
+  cplx<R>* Rm;         // [NB][B] rowmods of the current panel
+  cplx<R>* pinfo;      // [NB] 1 / pivot of the panel's columns
+  int* piv;            // [B] pivot row of column p
+  int* pinv;           // [B] column whose pivot row is r (-1: not yet a pivot row)
+  int* prow;           // [NB] pivot rows of the panel
+};
+
+// Entry (i, j) of the in-layer block D_k (9-point in (y, x), zero elsewhere).
+template <typename R>
+__device__ __forceinline__ cplx<R> d_entry(const FChain<R>& c, int i, int j) {
+  const int W = c.W;
+  const int yi = i / W, ei = i - yi * W, yj = j / W, ej = j - yj * W;
+  const int dy = yj - yi, dx = ej - ei;
+  if (dy < -1 || dy > 1 || dx < -1 || dx > 1) return mk<R>(0, 0);
+  return c.st[((size_t)c.k * 27 + qidx(0, dy, dx)) * c.B + i];
+}
+
+// T = G_kp R (term `term`): T[a][j] = sum_{(dy,dx)} G_kp[a][b] R_{(dy,dx)}[b],
+// b = j - (dy W + dx) the row of R that couples to column j; written into
+// the G slot of layer k (free until its inverse is written).
+template <typename R>
+__global__ void __launch_bounds__(128) schur_T_kernel(const FChain<R>* chains, int term) {
+  const FChain<R> c = chains[blockIdx.z];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, a = blockIdx.y;
+  if (j >= c.B || a >= c.B) return;
+  const int W = c.W, yj = j / W, ej = j - yj * W;
+  const cplx<R>* Gp = c.G + (size_t)c.kp[term] * c.bstride + (size_t)a * c.B;
+  const cplx<R>* stp = c.st + (size_t)c.kp[term] * 27 * c.B;
+  cplx<R> acc = mk<R>(0, 0);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int yb = yj - dy;
+    if (yb < 0 || yb >= c.ny) continue;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int eb = ej - dx;
+      if (eb < 0 || eb >= W) continue;
+      const int b = yb * W + eb;
+      cfma(acc, Gp[b], stp[(size_t)qidx(c.dzR[term], dy, dx) * c.B + b]);
+    }
+  }
+  c.G[(size_t)c.k * c.bstride + (size_t)a * c.B + j] = acc;
+}
+
+// S[i][j] = (init ? D[i][j] : S[i][j]) - Schur terms.  Finite differences
+// (fe = 0, diagonal couplings): every term, l_i G_kp[i][j] r_j, directly.
+// FE: the one term `term` from T (schur_T_kernel) in the G slot of layer k:
+// sum_{(dy,dx)} L_{(dy,dx)}[i] T[i + dy W + dx][j].  Also marks every row as
+// not yet a pivot row (init).
+template <typename R>
+__global__ void __launch_bounds__(128) schur_S_kernel(const FChain<R>* chains, int term, int init,
+                                                      int fe) {
+  const FChain<R> c = chains[blockIdx.z];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= c.B || i >= c.B) return;
+  if (init && j == 0) c.pinv[i] = -1;
+  cplx<R>* Sij = c.S + (size_t)i * c.B + j;
+  cplx<R> v = init ? d_entry(c, i, j) : *Sij;
+  const cplx<R>* stk = c.st + (size_t)c.k * 27 * c.B;
+  if (!fe) {
+    for (int t = 0; t < c.nterm; ++t) {
+      const cplx<R> l = stk[(size_t)qidx(c.dzL[t], 0, 0) * c.B + i];
+      const cplx<R> r = c.st[((size_t)c.kp[t] * 27 + qidx(c.dzR[t], 0, 0)) * c.B + j];
+      const cplx<R> g = c.G[(size_t)c.kp[t] * c.bstride + (size_t)i * c.B + j];
+      v = v - l * (g * r);
+    }
+  } else if (term >= 0) {
+    const int W = c.W, yi = i / W, ei = i - yi * W;
+    const cplx<R>* T = c.G + (size_t)c.k * c.bstride;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int ya = yi + dy;
+      if (ya < 0 || ya >= c.ny) continue;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ea = ei + dx;
+        if (ea < 0 || ea >= W) continue;
+        const cplx<R> l = stk[(size_t)qidx(c.dzL[term], dy, dx) * c.B + i];
+        v = v - l * T[(size_t)(ya * W + ea) * c.B + j];
+      }
+    }
+  }
+  *Sij = v;
+}
+
+// Pivot key: unpivoted rows rank by |v|^2 (float bits, monotone for
+// non-negative values), ties to the lowest row; pivoted rows are 0, so an
+// unpivoted row always wins (also for NaN or zero columns).
+__device__ __forceinline__ unsigned long long pivot_key(float a2, int row) {
+  const unsigned int bits = __float_as_uint(a2) & 0x7fffffffu;
+  return ((unsigned long long)(bits + 1u) << 32) | (unsigned long long)(0xffffffffu - (unsigned)row);
+}
+
+// Panel [p0, p0 + nbp) of the Gauss-Jordan inverse of one chain's S (one CTA
+// per chain): lane q of a warp holds column p0 + q of a row; warp w takes rows
+// w, w + 16, ...  Each step chooses the pivot row of column p0 + t, forms its
+// scaled panel row, and applies the rank-1 update to the panel columns of
+// every row, recording the colmods (C) and the next column's pivot keys.
+template <typename R>
+__global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>* chains, int p0) {
+  const FChain<R> c = chains[blockIdx.x];
+  const int B = c.B;
+  if (p0 >= B) return;
+  const int nbp = min(NB, B - p0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kPanelThreads / 32;
+  __shared__ unsigned char flag[kMaxB];
+  __shared__ unsigned long long wkey[NW];
+  __shared__ cplx<R> rm[NB];
+  __shared__ int sh_r;
+  for (int i = threadIdx.x; i < B; i += kPanelThreads) flag[i] = c.pinv[i] >= 0;
+  __syncthreads();
+  // keys of column p0
+  unsigned long long best = 0;
+  for (int i = warp; i < B; i += NW) {
+    const cplx<R> v = lane == 0 ? c.S[(size_t)i * B + p0] : mk<R>(0, 0);
+    if (lane == 0 && !flag[i]) {
+      const unsigned long long k = pivot_key((float)cabs2(v), i);
+      best = k > best ? k : best;
+    }
+  }
+  for (int t = 0; t < nbp; ++t) {
+    if (lane == 0) wkey[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long b = 0;
+      for (int w = 0; w < NW; ++w) b = wkey[w] > b ? wkey[w] : b;
+      const int r = (int)(0xffffffffu - (unsigned)(b & 0xffffffffu));
+      sh_r = r;
+      flag[r] = 1;
+      c.piv[p0 + t] = r;
+      c.pinv[r] = p0 + t;
+      c.prow[t] = r;
+    }
+    __syncthreads();
+    const int r = sh_r;
+    if (warp == 0) {
+      const cplx<R> v = lane < nbp ? c.S[(size_t)r * B + p0 + lane] : mk<R>(0, 0);
+      const cplx<R> pv = mk<R>(__shfl_sync(0xffffffffu, v.re, t), __shfl_sync(0xffffffffu, v.im, t));
+      const cplx<R> inv = cinv(pv);
+      cplx<R> x = v * inv;
+      if (lane == t) x = inv + mk<R>(1, 0);
+      if (lane < NB) rm[lane] = x;
+      if (lane == 0) c.pinfo[t] = inv;
+    }
+    __syncthreads();
+    const cplx<R> rq = lane < nbp ? rm[lane] : mk<R>(0, 0);
+    best = 0;
+    for (int i = warp; i < B; i += NW) {
+      cplx<R>* row = c.S + (size_t)i * B + p0;
+      cplx<R> v = lane < nbp ? row[lane] : mk<R>(0, 0);
+      cplx<R> ci = mk<R>(__shfl_sync(0xffffffffu, v.re, t), __shfl_sync(0xffffffffu, v.im, t));
+      if (i == r) ci.re -= (R)1;
+      v = v - ci * rq;
+      if (lane < nbp) row[lane] = v;
+      if (lane == 0) c.C[(size_t)i * NB + t] = ci;
+      if (t + 1 < nbp) {
+        const cplx<R> nv = mk<R>(__shfl_sync(0xffffffffu, v.re, t + 1),
+                                 __shfl_sync(0xffffffffu, v.im, t + 1));
+        if (lane == 0 && !flag[i]) {
+          const unsigned long long k = pivot_key((float)cabs2(nv), i);
+          best = k > best ? k : best;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Pivot rows' other columns (one thread per column j outside the panel):
+//   rho_t[j] = (S[r_t][j] - sum_{s<t} C[r_t][s] rho_s[j]) / S[r_t][p0+t];
+// zero on the panel columns (the panel kernel has finished them).
+template <typename R>
+__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0) {
+  const FChain<R> c = chains[blockIdx.y];
+  const int B = c.B;
+  if (p0 >= B) return;
+  const int nbp = min(NB, B - p0);
+  __shared__ cplx<R> Cp[NB][NB];
+  __shared__ cplx<R> inv[NB];
+  __shared__ int pr[NB];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int t = e / NB, s = e - t * NB;
+    Cp[t][s] = (t < nbp && s < t) ? c.C[(size_t)c.prow[t] * NB + s] : mk<R>(0, 0);
+  }
+  for (int t = threadIdx.x; t < NB; t += blockDim.x) {
+    inv[t] = t < nbp ? c.pinfo[t] : mk<R>(0, 0);
+    pr[t] = t < nbp ? c.prow[t] : 0;
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B) return;
+  if (j >= p0 && j < p0 + nbp) {
+    for (int t = 0; t < NB; ++t) c.Rm[(size_t)t * B + j] = mk<R>(0, 0);
+    return;
+  }
+  cplx<R> rv[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    cplx<R> a = mk<R>(0, 0);
+    if (t < nbp) {
+      a = c.S[(size_t)pr[t] * B + j];
+#pragma unroll
+      for (int s = 0; s < t; ++s) a = a - Cp[t][s] * rv[s];
+      a = a * inv[t];
+    }
+    rv[t] = a;
+    c.Rm[(size_t)t * B + j] = a;
+  }
+}
+
+// S -= C Rm over a 64 x 64 tile per CTA (256 threads, 4 x 4 outputs each:
+// rows ty + 16 a, columns tx + 16 b), depth NB through shared memory.
+template <typename R>
+__global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains, int p0) {
+  const FChain<R> c = chains[blockIdx.z];
+  const int B = c.B;
+  if (p0 >= B) return;
+  const int nbp = min(NB, B - p0);
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (i0 >= B || j0 >= B) return;
+  if (j0 >= p0 && j0 + 64 <= p0 + nbp) return;   // panel columns only: nothing to do
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* Cs = (cplx<R>*)smem_raw;              // [64][NB + 1]
+  cplx<R>* Rs = Cs + 64 * (NB + 1);              // [NB][64]
+  for (int e = threadIdx.x; e < 64 * NB; e += 256) {
+    const int r = e / NB, t = e - r * NB;
+    Cs[r * (NB + 1) + t] = (i0 + r < B && t < nbp) ? c.C[(size_t)(i0 + r) * NB + t] : mk<R>(0, 0);
+    const int t2 = e / 64, q = e - t2 * 64;
+    Rs[t2 * 64 + q] = (j0 + q < B && t2 < nbp) ? c.Rm[(size_t)t2 * B + j0 + q] : mk<R>(0, 0);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cplx<R> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = mk<R>(0, 0);
+#pragma unroll 4
+  for (int t = 0; t < NB; ++t) {
+    cplx<R> cv[4], rv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) cv[a] = Cs[(ty + 16 * a) * (NB + 1) + t];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rv[b] = Rs[t * 64 + tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cfma(acc[a][b], cv[a], rv[b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= B) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      if (j >= B || (j >= p0 && j < p0 + nbp)) continue;
+      cplx<R>* p = c.S + (size_t)i * B + j;
+      *p = *p - acc[a][b];
+    }
+  }
+}
+
+// G_k[p][col] = S[piv[p]][pinv[col]] (undo the implicit pivoting).
+template <typename R>
+__global__ void __launch_bounds__(256) gj_writeout_kernel(const FChain<R>* chains) {
+  const FChain<R> c = chains[blockIdx.z];
+  const int col = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (col >= c.B || p >= c.B) return;
+  c.G[(size_t)c.k * c.bstride + (size_t)p * c.B + col] =
+      c.S[(size_t)c.piv[p] * c.B + c.pinv[col]];
+}
+
+size_t update_smem(size_t el) { return (64 * (NB + 1) + NB * 64) * el; }
+
+// ------------------------------------------------------------------- solves
+// Right-hand side of a 3-D slab solve (SubdomSolve, Table 2) into the layer
+// fields Y[k][r][b] (rhs r of the chunk, layer stride ldl): a raw slab field
+// [nr][N_t][W] (N_t = nz ny), or the gather of the global columns (ga, gb] of
+// f [nr][nz][ny][nx] plus the injections of Eqs. 19-20 at the local columns
+// ef, ef+1 (from B1) and eb, eb+1 (from B3), transmission buffers
+// [2][nr_tot][N_t] (rhs r0 + r).
+template <typename R>
+struct Rhs3 {
+  const cplx<R>* raw;
+  const cplx<R>* f;
+  int nx, lo, wl, ga, gb;
+  const cplx<R>* B1;
+  int ef;
+  const cplx<R>* B3;
+  int eb;
+  const cplx<R>* inj;        // [4][N_t][9]
+  int r0, nr_tot;
+};
+
+template <typename R>
+__global__ void slab3_rhs_kernel(Rhs3<R> q, int W, int ny, int nz, cplx<R>* Y, size_t ldl) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y, r = blockIdx.z;
+  const int B = W * ny;
+  if (b >= B) return;
+  const int y = b / W, e = b - y * W;
+  const size_t nt = (size_t)ny * nz;
+  const int rr = q.r0 + r;
+  cplx<R> v = mk<R>(0, 0);
+  if (q.raw) {
+    v = q.raw[((size_t)r * nz + k) * B + b];
+  } else {
+    const int g = e - q.wl + q.lo;
+    if (g > q.ga && g <= q.gb) v = q.f[(((size_t)r * nz + k) * ny + y) * q.nx + g];
+    auto inject = [&](int s, const cplx<R>* Bf) {   // s: 0..3 (coefficient set)
+      const cplx<R>* c = q.inj + ((size_t)s * nt + (size_t)k * ny + y) * 9;
+      const cplx<R>* Bl = Bf + ((size_t)(1 - (s & 1)) * q.nr_tot + rr) * nt;
+      for (int t = 0; t < 9; ++t) {
+        const int kk = k + t / 3 - 1, yy = y + t % 3 - 1;
+        if (kk >= 0 && kk < nz && yy >= 0 && yy < ny) cfma(v, c[t], Bl[(size_t)kk * ny + yy]);
+      }
+    };
+    if (q.ef >= 0 && e == q.ef) inject(0, q.B1);        // row beta uses B[1]
+    if (q.ef >= 0 && e == q.ef + 1) inject(1, q.B1);    // row beta+1 uses B[0]
+    if (q.eb >= 0 && e == q.eb) inject(2, q.B3);
+    if (q.eb >= 0 && e == q.eb + 1) inject(3, q.B3);
+  }
+  Y[(size_t)k * ldl + (size_t)r * B + b] = v;
+}
+
+// One coupling term applied to a layer field: sum over (dy, dx) of
+// st[k][q(dz, dy, dx)][b] X[r][b + dy W + dx] (only (0, 0) for the 7-point
+// operator).
+template <typename R>
+struct Cpl3 {
+  int k, dz;
+  const cplx<R>* X;          // [nr][B]
+};
+template <typename R>
+struct Piece3 {
+  const cplx<R>* base;       // [nr][B] or null
+  cplx<R>* out;              // [nr][B]
+  int nc;
+  Cpl3<R> c[2];
+};
+template <typename R>
+struct Prep3 {
+  int B, W, ny, nr, diag;
+  R sgn;                     // out = base + sgn * (sum of the couplings)
+  const cplx<R>* st;
+  int np;
+  Piece3<R> p[2];
+};
+
+template <typename R>
+__global__ void slab3_prep_kernel(Prep3<R> a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  const Piece3<R>& P = a.p[blockIdx.z];
+  if (b >= a.B) return;
+  const int y = b / a.W, e = b - y * a.W;
+  cplx<R> acc = mk<R>(0, 0);
+  for (int c = 0; c < P.nc; ++c) {
+    const cplx<R>* st = a.st + (size_t)P.c[c].k * 27 * a.B;
+    const cplx<R>* X = P.c[c].X + (size_t)r * a.B;
+    const int dz = P.c[c].dz;
+    if (a.diag) {
+      cfma(acc, st[(size_t)qidx(dz, 0, 0) * a.B + b], X[b]);
+    } else {
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= a.ny) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ee = e + dx;
+          if (ee < 0 || ee >= a.W) continue;
+          cfma(acc, st[(size_t)qidx(dz, dy, dx) * a.B + b], X[yy * a.W + ee]);
+        }
+      }
+    }
+  }
+  const size_t o = (size_t)r * a.B + b;
+  cplx<R> v = P.base ? P.base[o] : mk<R>(0, 0);
+  v.re += a.sgn * acc.re;
+  v.im += a.sgn * acc.im;
+  P.out[o] = v;
+}
+
+// Dense layer GEMV with the stored inverse, up to two pieces (the two
+// chains): y[r][i] = G[i][:] v[r][:] (mode 0) or y[r][i] - G[i][:] v[r][:]
+// (mode 1), r < NR.  A warp takes kRowsPerWarp rows, its lanes the columns
+// (coalesced rows of G, v reused across the warp's rows), then a shuffle
+// reduction per output.
+constexpr int kRowsPerWarp = 2;
+template <typename R>
+struct GemvPiece {
+  const cplx<R>* G;          // [B][B]
+  const cplx<R>* v;          // [nr][B]
+  cplx<R>* y;                // [nr][B]
+};
+template <typename R>
+struct Gemv3 {
+  int B, nr, mode, np;
+  GemvPiece<R> p[2];
+};
+
+template <typename R, int NR>
+__global__ void __launch_bounds__(256) slab3_gemv_kernel(Gemv3<R> a) {
+  const GemvPiece<R>& P = a.p[blockIdx.y];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * 8 + warp) * kRowsPerWarp;
+  if (i0 >= a.B) return;
+  const int B = a.B;
+  cplx<R> acc[kRowsPerWarp][NR];
+#pragma unroll
+  for (int q = 0; q < kRowsPerWarp; ++q)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[q][r] = mk<R>(0, 0);
+  for (int j = lane; j < B; j += 32) {
+    cplx<R> v[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] = r < a.nr ? P.v[(size_t)r * B + j] : mk<R>(0, 0);
+#pragma unroll
+    for (int q = 0; q < kRowsPerWarp; ++q) {
+      const int i = i0 + q;
+      if (i < B) {
+        const cplx<R> g = P.G[(size_t)i * B + j];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) cfma(acc[q][r], g, v[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kRowsPerWarp; ++q)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[q][r].re += __shfl_xor_sync(0xffffffffu, acc[q][r].re, o);
+        acc[q][r].im += __shfl_xor_sync(0xffffffffu, acc[q][r].im, o);
+      }
+  if (lane < kRowsPerWarp * NR) {
+    const int q = lane / NR, r = lane - q * NR;
+    const int i = i0 + q;
+    if (i < B && r < a.nr) {
+      cplx<R> s = mk<R>(0, 0);
+#pragma unroll
+      for (int qq = 0; qq < kRowsPerWarp; ++qq)
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr)
+          if (qq == q && rr == r) s = acc[qq][rr];
+      cplx<R>* out = P.y + (size_t)r * B + i;
+      *out = a.mode == 0 ? s : *out - s;
+    }
+  }
+}
+
+// Epilogue of a 3-D slab solve (Table 2): the slab solution's core columns
+// (ua, ub] into the global field, the layers at e2, e2+1 (B2) and e4, e4+1
+// (B4) for the transmission, or the whole slab field (raw).
+template <typename R>
+struct Out3 {
+  cplx<R>* raw;              // [nr][N_t][W]
+  cplx<R>* u;                // [nr][nz][ny][nx]
+  int nx, lo, wl, ua, ub;
+  cplx<R>* B2;
+  int e2;
+  cplx<R>* B4;
+  int e4;
+  int r0, nr_tot;
+};
+
+template <typename R>
+__global__ void slab3_out_kernel(Out3<R> o, int W, int ny, int nz, const cplx<R>* Y, size_t ldl) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y, r = blockIdx.z;
+  const int B = W * ny;
+  if (b >= B) return;
+  const int y = b / W, e = b - y * W;
+  const size_t nt = (size_t)ny * nz;
+  const int rr = o.r0 + r;
+  const cplx<R> v = Y[(size_t)k * ldl + (size_t)r * B + b];
+  if (o.raw) {
+    o.raw[((size_t)r * nz + k) * B + b] = v;
+    return;
+  }
+  const int g = e - o.wl + o.lo;
+  if (g > o.ua && g <= o.ub) o.u[(((size_t)r * nz + k) * ny + y) * o.nx + g] = v;
+  const size_t idx = (size_t)k * ny + y;
+  if (o.B2 && (e == o.e2 || e == o.e2 + 1))
+    o.B2[((size_t)(e - o.e2) * o.nr_tot + rr) * nt + idx] = v;
+  if (o.B4 && (e == o.e4 || e == o.e4 + 1))
+    o.B4[((size_t)(e - o.e4) * o.nr_tot + rr) * nt + idx] = v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+// Chains: 2 (j - 1) = top chain of slab j (layers 0 .. m-1), 2 (j - 1) + 1 =
+// bottom chain (layers nz-1 .. m+1); step t factors layer t of the top and
+// nz-1-t of the bottom chains; the meeting step factors layer m of every
+// slab (with the top chain's work buffers).
+template <typename R>
+void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
+  const int J = L.J, nz = L.nz, m = L.mid;
+  const int ntop = m, nbot = nz - 1 - m, T = std::max(ntop, nbot);
+  const size_t el = sizeof(cplx<R>);
+  int Bmax = 0;
+  for (int j = 1; j <= J; ++j) Bmax = std::max(Bmax, L.slabs[j].B);
+  const int nch = 2 * J;
+  const size_t sS = (size_t)Bmax * Bmax, sC = (size_t)Bmax * NB;
+  if (!L.f3_S) {   // work buffers and descriptors: built by the first factorisation, kept
+    L.f3_S = dmalloc(el * sS * nch);
+    L.f3_C = dmalloc(el * sC * nch);
+    L.f3_R = dmalloc(el * sC * nch + el * NB * nch);
+    L.f3_piv = (int*)dmalloc(sizeof(int) * ((size_t)2 * Bmax + NB) * nch);
+    std::vector<FChain<R>> all;
+    auto chain = [&](int j, int c) {
+      const Slab& S = L.slabs[j];
+      FChain<R> f{};
+      f.B = S.B; f.W = S.W; f.ny = L.ny;
+      f.st = (const cplx<R>*)S.st3;
+      f.G = (cplx<R>*)S.G;
+      f.bstride = S.bstride;
+      f.S = (cplx<R>*)L.f3_S + sS * c;
+      f.C = (cplx<R>*)L.f3_C + sC * c;
+      f.Rm = (cplx<R>*)L.f3_R + sC * c;
+      f.pinfo = (cplx<R>*)L.f3_R + sC * nch + (size_t)NB * c;
+      int* ip = L.f3_piv + ((size_t)2 * Bmax + NB) * c;
+      f.piv = ip; f.pinv = ip + Bmax; f.prow = ip + 2 * Bmax;
+      return f;
+    };
+    for (int t = 0; t < T; ++t)
+      for (int j = 1; j <= J; ++j) {
+        if (t < ntop) {
+          FChain<R> f = chain(j, 2 * (j - 1));
+          f.k = t; f.nterm = t > 0 ? 1 : 0;
+          f.kp[0] = t - 1; f.dzL[0] = -1; f.dzR[0] = +1;
+          all.push_back(f);
+        }
+        if (t < nbot) {
+          FChain<R> f = chain(j, 2 * (j - 1) + 1);
+          f.k = nz - 1 - t; f.nterm = t > 0 ? 1 : 0;
+          f.kp[0] = nz - t; f.dzL[0] = +1; f.dzR[0] = -1;
+          all.push_back(f);
+        }
+      }
+    for (int j = 1; j <= J; ++j) {
+      FChain<R> f = chain(j, 2 * (j - 1));
+      f.k = m; f.nterm = 2;
+      f.kp[0] = m - 1; f.dzL[0] = -1; f.dzR[0] = +1;
+      f.kp[1] = m + 1; f.dzL[1] = +1; f.dzR[1] = -1;
+      all.push_back(f);
+    }
+    L.f3_desc = dmalloc(sizeof(FChain<R>) * all.size());
+    HZ_CU(cudaMemcpyAsync(L.f3_desc, all.data(), sizeof(FChain<R>) * all.size(),
+                          cudaMemcpyHostToDevice, s));
+    HZ_CU(cudaFuncSetAttribute(gj_update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)update_smem(el)));
+  }
+  const FChain<R>* desc = (const FChain<R>*)L.f3_desc;
+  const int fe = L.fe ? 1 : 0;
+  auto layer = [&](const FChain<R>* d, int cnt, int nterm) {
+    const dim3 gs(cdiv(Bmax, 128), Bmax, cnt);
+    timed(h, "slab_factor3d_schur", 0.0, s, [&] {
+      if (!fe) {
+        schur_S_kernel<R><<<gs, 128, 0, s>>>(d, -1, 1, 0);
+      } else {
+        schur_S_kernel<R><<<gs, 128, 0, s>>>(d, -1, 1, 1);
+        for (int t = 0; t < nterm; ++t) {
+          schur_T_kernel<R><<<gs, 128, 0, s>>>(d, t);
+          schur_S_kernel<R><<<gs, 128, 0, s>>>(d, t, 0, 1);
+        }
+      }
+    });
+    h->launches += fe ? 1 + 2 * nterm : 1;
+    for (int p0 = 0; p0 < Bmax; p0 += NB) {
+      timed(h, "slab_factor3d_panel", 0.0, s,
+            [&] { gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0); });
+      timed(h, "slab_factor3d_rowmod", 0.0, s,
+            [&] { gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 128), cnt), 128, 0, s>>>(d, p0); });
+      // algorithmic flop of the update: 8 B^2 NB per chain (complex MACs x 8)
+      const double fl = 8.0 * (double)Bmax * Bmax * NB * cnt;
+      timed(h, "slab_factor3d_update", fl, s, [&] {
+        gj_update_kernel<R><<<dim3(cdiv(Bmax, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el), s>>>(
+            d, p0);
+      });
+      h->launches += 3;
+    }
+    timed(h, "slab_factor3d_writeout", 0.0, s,
+          [&] { gj_writeout_kernel<R><<<dim3(cdiv(Bmax, 256), Bmax, cnt), 256, 0, s>>>(d); });
+    h->launches += 1;
+    HZ_CU(cudaGetLastError());
+  };
+  size_t off = 0;
+  for (int t = 0; t < T; ++t) {
+    const int cnt = J * ((t < ntop ? 1 : 0) + (t < nbot ? 1 : 0));
+    layer(desc + off, cnt, t > 0 ? 1 : 0);
+    off += cnt;
+  }
+  layer(desc + off, J, 2);
+  HZ_CU(cudaStreamSynchronize(s));
+}
+
+namespace {
+
+// One 3-D slab solve for right-hand sides [r0, r0 + nr) of nr_tot: rhs
+// gather, forward chains, meeting layer, backward chains, epilogue.
+template <typename R, int NR>
+void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, cudaStream_t s) {
+  const int B = S.B, nz = L.nz, m = L.mid;
+  const int ntop = m, nbot = nz - 1 - m, T = std::max(ntop, nbot);
+  const size_t ldl = (size_t)nr * B;      // layer stride of the chunk's Y
+  cplx<R>* Y = (cplx<R>*)S.Y;
+  cplx<R>* V = (cplx<R>*)S.V;
+  cplx<R>* V1 = V + (size_t)nr * B;
+  const cplx<R>* G = (const cplx<R>*)S.G;
+  auto Yk = [&](int k) { return Y + (size_t)k * ldl; };
+  auto Gk = [&](int k) { return G + (size_t)k * S.bstride; };
+  const double el = sizeof(cplx<R>);
+  const double gbytes = (double)B * B * el;
+  slab3_rhs_kernel<R><<<dim3(cdiv(B, 128), nz, nr), 128, 0, s>>>(q, S.W, L.ny, nz, Y, ldl);
+  Prep3<R> pa{};
+  pa.B = B; pa.W = S.W; pa.ny = L.ny; pa.nr = nr; pa.diag = L.fe ? 0 : 1;
+  pa.st = (const cplx<R>*)S.st3;
+  Gemv3<R> ga{};
+  ga.B = B; ga.nr = nr;
+  const unsigned gblocks = (unsigned)cdiv(B, 8 * kRowsPerWarp);
+  auto prep = [&](int np) {
+    pa.np = np;
+    slab3_prep_kernel<R><<<dim3(cdiv(B, 128), nr, np), 128, 0, s>>>(pa);
+  };
+  auto gemv = [&](int np, int mode) {
+    ga.np = np;
+    ga.mode = mode;
+    timed(h, "slab3_gemv", np * (gbytes + 2.0 * nr * B * el), s,
+          [&] { slab3_gemv_kernel<R, NR><<<dim3(gblocks, np), 256, 0, s>>>(ga); });
+  };
+  // forward: y_t = G_t (f_t - L_t y_{t-1}), both chains per launch
+  for (int t = 0; t < T; ++t) {
+    int np = 0;
+    for (int side = 0; side < 2; ++side) {
+      if (t >= (side == 0 ? ntop : nbot)) continue;
+      const int k = side == 0 ? t : nz - 1 - t;
+      const int kp = side == 0 ? k - 1 : k + 1;
+      cplx<R>* Vp = np == 0 ? V : V1;
+      pa.p[np].base = Yk(k);
+      pa.p[np].out = Vp;
+      pa.p[np].nc = t > 0 ? 1 : 0;
+      pa.p[np].c[0] = Cpl3<R>{k, side == 0 ? -1 : +1, Yk(kp)};
+      ga.p[np] = GemvPiece<R>{Gk(k), Vp, Yk(k)};
+      ++np;
+    }
+    pa.sgn = (R)-1;
+    prep(np);
+    gemv(np, 0);
+  }
+  // meeting: x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1})
+  pa.p[0].base = Yk(m);
+  pa.p[0].out = V;
+  pa.p[0].nc = 2;
+  pa.p[0].c[0] = Cpl3<R>{m, -1, Yk(m - 1)};
+  pa.p[0].c[1] = Cpl3<R>{m, +1, Yk(m + 1)};
+  pa.sgn = (R)-1;
+  prep(1);
+  ga.p[0] = GemvPiece<R>{Gk(m), V, Yk(m)};
+  gemv(1, 0);
+  // backward: x_t = y_t - G_t R_t x_{t+1}, outwards from the meeting layer
+  for (int t = 0; t < T; ++t) {
+    int np = 0;
+    for (int side = 0; side < 2; ++side) {
+      if (t >= (side == 0 ? ntop : nbot)) continue;
+      const int k = side == 0 ? m - 1 - t : m + 1 + t;
+      const int kn = side == 0 ? k + 1 : k - 1;   // the next layer (towards m), solved
+      cplx<R>* Vp = np == 0 ? V : V1;
+      pa.p[np].base = nullptr;
+      pa.p[np].out = Vp;
+      pa.p[np].nc = 1;
+      pa.p[np].c[0] = Cpl3<R>{k, side == 0 ? +1 : -1, Yk(kn)};
+      ga.p[np] = GemvPiece<R>{Gk(k), Vp, Yk(k)};
+      ++np;
+    }
+    pa.sgn = (R)1;
+    prep(np);
+    gemv(np, 1);
+  }
+  slab3_out_kernel<R><<<dim3(cdiv(B, 128), nz, nr), 128, 0, s>>>(o, S.W, L.ny, nz, Y, ldl);
+  h->launches += 2 + 2 * (2 * T + 1);
+  HZ_CU(cudaGetLastError());
+}
+
+// Right-hand sides in chunks of at most 8 (compile-time accumulators of the GEMV).
+template <typename R>
+void run_solve3d_all(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int n_rhs,
+                     size_t in_stride, size_t out_stride, cudaStream_t s) {
+  q.nr_tot = o.nr_tot = n_rhs;
+  for (int r0 = 0; r0 < n_rhs; r0 += 8) {
+    const int nr = std::min(8, n_rhs - r0);
+    Rhs3<R> qc = q;
+    Out3<R> oc = o;
+    qc.r0 = oc.r0 = r0;
+    if (qc.raw) qc.raw += (size_t)r0 * in_stride;
+    if (qc.f) qc.f += (size_t)r0 * in_stride;
+    if (oc.raw) oc.raw += (size_t)r0 * out_stride;
+    if (oc.u) oc.u += (size_t)r0 * out_stride;
+    if (nr == 1) run_solve3d<R, 1>(h, L, S, qc, oc, nr, s);
+    else if (nr == 2) run_solve3d<R, 2>(h, L, S, qc, oc, nr, s);
+    else if (nr <= 4) run_solve3d<R, 4>(h, L, S, qc, oc, nr, s);
+    else run_solve3d<R, 8>(h, L, S, qc, oc, nr, s);
+  }
+}
+
+}  // namespace
+
+template <typename R>
+void subdom_solve3d(hz_handle* h, Level& L, int j, const cplx<R>* f, int a, int b, int at,
+                    int bt, bool tau1, const cplx<R>* B1, bool tau2, cplx<R>* B2, bool tau3,
+                    const cplx<R>* B3, bool tau4, cplx<R>* B4, cplx<R>* u, int n_rhs,
+                    cudaStream_t s) {
+  Slab& S = L.slabs[j];
+  // transmission from or to a missing neighbour is dropped (T^(1) = T~^(J) = 0)
+  tau1 = tau1 && j > 1;
+  tau4 = tau4 && j > 1;
+  tau2 = tau2 && j < L.J;
+  tau3 = tau3 && j < L.J;
+  auto loc = [&](int g) { return g - S.lo + S.wl; };
+  Rhs3<R> q{};
+  q.f = f; q.nx = L.nx; q.lo = S.lo; q.wl = S.wl; q.ga = a; q.gb = b;
+  q.B1 = B1; q.ef = tau1 ? loc(L.beta[j - 1]) : -1;
+  q.B3 = B3; q.eb = tau3 ? loc(L.beta_t[j]) : -1;
+  q.inj = (const cplx<R>*)S.inj3;
+  Out3<R> o{};
+  o.u = u; o.nx = L.nx; o.lo = S.lo; o.wl = S.wl; o.ua = at; o.ub = bt;
+  o.B2 = tau2 ? B2 : nullptr; o.e2 = tau2 ? loc(L.beta[j]) : -1;
+  o.B4 = tau4 ? B4 : nullptr; o.e4 = tau4 ? loc(L.beta_t[j - 1]) : -1;
+  const size_t n = L.size();
+  timed(h, "slab_solve3d", 0.0, s, [&] { run_solve3d_all<R>(h, L, S, q, o, n_rhs, n, n, s); });
+}
+
+template <typename R>
+void slab_solve_raw3d(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>* ud, int n_rhs,
+                      cudaStream_t s) {
+  Slab& S = L.slabs[j];
+  Rhs3<R> q{};
+  q.raw = fd; q.ef = -1; q.eb = -1;
+  Out3<R> o{};
+  o.raw = ud; o.e2 = -1; o.e4 = -1;
+  const size_t n = L.nt() * S.W;
+  run_solve3d_all<R>(h, L, S, q, o, n_rhs, n, n, s);
+}
+
+template void build_slabs3d<float>(hz_handle*, Level&, cudaStream_t);
+template void build_slabs3d<double>(hz_handle*, Level&, cudaStream_t);
+template void factor_level3d<float>(hz_handle*, Level&, cudaStream_t);
+template void factor_level3d<double>(hz_handle*, Level&, cudaStream_t);
+template void subdom_solve3d<float>(hz_handle*, Level&, int, const c64*, int, int, int, int, bool,
+                                    const c64*, bool, c64*, bool, const c64*, bool, c64*, c64*,
+                                    int, cudaStream_t);
+template void subdom_solve3d<double>(hz_handle*, Level&, int, const c128*, int, int, int, int,
+                                     bool, const c128*, bool, c128*, bool, const c128*, bool,
+                                     c128*, c128*, int, cudaStream_t);
+template void slab_solve_raw3d<float>(hz_handle*, Level&, int, const c64*, c64*, int,
+                                      cudaStream_t);
+template void slab_solve_raw3d<double>(hz_handle*, Level&, int, const c128*, c128*, int,
+                                       cudaStream_t);
+
+}  // namespace hz

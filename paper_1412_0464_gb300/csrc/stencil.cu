@@ -226,6 +226,10 @@ template <typename R>
 static void launch_op(hz_handle* h, const Level& L, int mode, const cplx<R>* f,
                       const cplx<R>* u, cplx<R>* y, int n_rhs, double omega_jac,
                       cudaStream_t s) {
+  if (L.dim3d) {
+    launch_op3d<R>(h, L, mode, f, u, y, n_rhs, omega_jac, s);
+    return;
+  }
   dim3 block(128);
   dim3 grid(cdiv(L.nx, 128), L.ny, n_rhs);
   R h2w2 = (R)(L.h * L.h * h->p.omega * h->p.omega);
@@ -284,7 +288,7 @@ void jacobi_steps(hz_handle* h, const Level& L, const cplx<R>* f, cplx<R>* u, cp
     std::swap(a, b);
   }
   if (a != u)
-    HZ_CU(cudaMemcpyAsync(u, a, sizeof(cplx<R>) * (size_t)n_rhs * L.nx * L.ny,
+    HZ_CU(cudaMemcpyAsync(u, a, sizeof(cplx<R>) * (size_t)n_rhs * L.size(),
                           cudaMemcpyDeviceToDevice, s));
 }
 

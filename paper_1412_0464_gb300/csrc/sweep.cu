@@ -8,12 +8,24 @@
 
 namespace hz {
 
+// SubdomSolve (Table 2) on a 2-D slab (twisted block LU along y) or a 3-D
+// slab (dense-block LU along z).
+template <typename R>
+static void sub(hz_handle* h, Level& L, int j, const cplx<R>* f, int a, int b, int at, int bt,
+                bool t1, const cplx<R>* B1, bool t2, cplx<R>* B2, bool t3, const cplx<R>* B3,
+                bool t4, cplx<R>* B4, cplx<R>* u, int nr, cudaStream_t s) {
+  if (L.dim3d)
+    subdom_solve3d<R>(h, L, j, f, a, b, at, bt, t1, B1, t2, B2, t3, B3, t4, B4, u, nr, s);
+  else
+    subdom_solve<R>(h, L, j, f, a, b, at, bt, t1, B1, t2, B2, t3, B3, t4, B4, u, nr, s);
+}
+
 template <typename R>
 static void forward_sweep(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, int j0, int j1,
                           cplx<R>* B, int nr, cudaStream_t s) {
   const auto& be = L.beta;
   for (int j = j0; j <= j1; ++j)
-    subdom_solve<R>(h, L, j, f, be[j - 1], be[j], be[j - 1], be[j], j > 1, B, j < L.J, B, false,
+    sub<R>(h, L, j, f,be[j - 1], be[j], be[j - 1], be[j], j > 1, B, j < L.J, B, false,
                     nullptr, false, nullptr, u, nr, s);
 }
 
@@ -22,21 +34,21 @@ static void backward_sweep(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f,
                            cplx<R>* B, int nr, cudaStream_t s) {
   const auto& bt = L.beta_t;
   for (int j = j0; j >= j1; --j)
-    subdom_solve<R>(h, L, j, f, bt[j - 1], bt[j], bt[j - 1], bt[j], false, nullptr, false,
+    sub<R>(h, L, j, f,bt[j - 1], bt[j], bt[j - 1], bt[j], false, nullptr, false,
                     nullptr, j < L.J, B, j > 1, B, u, nr, s);
 }
 
 template <typename R>
 static void mid_solve_in(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, int j, cplx<R>* B1,
                          cplx<R>* B2, int nr, cudaStream_t s) {
-  subdom_solve<R>(h, L, j, f, L.beta[j - 1], L.beta_t[j], L.beta[j - 1], L.beta_t[j], true, B1,
+  sub<R>(h, L, j, f,L.beta[j - 1], L.beta_t[j], L.beta[j - 1], L.beta_t[j], true, B1,
                   false, nullptr, true, B2, false, nullptr, u, nr, s);
 }
 
 template <typename R>
 static void mid_solve_out(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, int j, cplx<R>* B1,
                           cplx<R>* B2, int nr, cudaStream_t s) {
-  subdom_solve<R>(h, L, j, f, L.beta_t[j - 1], L.beta[j], L.beta_t[j - 1], L.beta[j], false,
+  sub<R>(h, L, j, f,L.beta_t[j - 1], L.beta[j], L.beta_t[j - 1], L.beta[j], false,
                   nullptr, true, B1, false, nullptr, true, B2, u, nr, s);
 }
 
@@ -52,7 +64,7 @@ __global__ void add_kernel(cplx<R>* u, const cplx<R>* v, size_t n) {
 // buffer (u, then u2) and u += u2 at the end.
 template <typename R>
 void sweep_apply(hz_handle* h, Level& L, const cplx<R>* f, cplx<R>* u, int nr, cudaStream_t s) {
-  const size_t n = (size_t)L.nx * L.ny;
+  const size_t n = L.size();
   cplx<R>* g = (cplx<R>*)h->pr_g;
   cplx<R>* u2 = (cplx<R>*)h->pr_u2;
   cplx<R>* B1 = (cplx<R>*)h->pr_B1;
@@ -93,7 +105,7 @@ template <typename R>
 static void tgsp(hz_handle* h, const cplx<R>* f, cplx<R>* u, int nr, cudaStream_t s) {
   Level& F = h->fine;
   Level& C = h->coarse;
-  const size_t nf = (size_t)F.nx * F.ny;
+  const size_t nf = F.size();
   cplx<R>* t = (cplx<R>*)h->tg_t;
   HZ_CU(cudaMemsetAsync(u, 0, sizeof(cplx<R>) * nf * nr, s));
   jacobi_steps<R>(h, F, f, u, t, h->p.nu, h->p.omega_jac, nr, s);
@@ -107,7 +119,7 @@ static void tgsp(hz_handle* h, const cplx<R>* f, cplx<R>* u, int nr, cudaStream_
 template <typename R>
 static void precond_t(hz_handle* h, const c128* r, c128* z, int nr, cudaStream_t s) {
   Level& F = h->fine;
-  const size_t n = (size_t)F.nx * F.ny;
+  const size_t n = F.size();
   if (!h->p.two_grid) {
     if (sizeof(R) == 8) {
       sweep_apply<R>(h, F, (const cplx<R>*)r, (cplx<R>*)z, nr, s);

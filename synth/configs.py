@@ -44,23 +44,34 @@ class Workload:
     precision: str          # "fp64" | "mixed"
     seed: int
     n_rec: int = 0
+    dims: Optional[Tuple[int, ...]] = None   # interior cells per axis (array order z, y, x);
+                                            # None: n on every axis; dims[-1] must equal n
+
+    @property
+    def cells(self) -> Tuple[int, ...]:
+        """Interior cells per axis, array order (z, y, x); x is the sweep axis."""
+        if self.dims is None:
+            return (self.n,) * self.dim
+        assert len(self.dims) == self.dim and self.dims[-1] == self.n
+        return tuple(self.dims)
 
     @property
     def n_cells(self) -> int:
+        """Cells along x (interior + both PML layers)."""
         return self.n + 2 * self.w_out
 
     @property
     def N(self) -> int:
-        """Unknowns per axis."""
+        """Unknowns along x."""
         return self.n_cells - 1
 
     @property
     def shape(self) -> Tuple[int, ...]:
-        return (self.N,) * self.dim
+        return tuple(c + 2 * self.w_out - 1 for c in self.cells)
 
     @property
     def ndof(self) -> int:
-        return self.N ** self.dim
+        return math.prod(self.shape)
 
     @property
     def h(self) -> float:
@@ -115,7 +126,7 @@ def scaled_workload(idx: int, n: int, w_out: Optional[int] = None, J: Optional[i
     """Same medium recipe and frequency rule at a smaller interior size ``n``."""
     w = CONFIGS[idx]
     kw = dataclasses.asdict(w)
-    kw.update(n=n, name=f"{w.name}@n{n}")
+    kw.update(n=n, name=f"{w.name}@n{n}", dims=None)
     if w_out is not None:
         kw["w_out"] = w_out
     if J is not None:

@@ -63,14 +63,15 @@ def velocity(cfg: Workload, which: str = "true") -> np.ndarray:
     if cfg.medium == "grf_layer":
         g = _unit_interval(_smooth_noise(_rng(cfg, _STREAM_MEDIUM), shape, cfg.corr))
         # horizontal layer jump: unknown rows at or below node w_out + 0.6 n
-        y = np.arange(cfg.N).reshape((-1,) + (1,) * (cfg.dim - 1))
-        y_layer = cfg.w_out + int(round(0.6 * cfg.n)) - 1
+        # (the layer is horizontal: across the first array axis, y in 2-D, z in 3-D)
+        y = np.arange(shape[0]).reshape((-1,) + (1,) * (cfg.dim - 1))
+        y_layer = cfg.w_out + int(round(0.6 * cfg.cells[0])) - 1
         step = (y >= y_layer).astype(np.float64)
         c = 1.5 + 3.0 * (0.7 * g + 0.3 * step)
         return np.broadcast_to(c, shape).copy()
     if cfg.medium == "layered3d":
-        z = np.arange(cfg.N) - (cfg.w_out - 1)
-        layer = np.clip((6 * z) // cfg.n, 0, 5)
+        z = np.arange(shape[0]) - (cfg.w_out - 1)
+        layer = np.clip((6 * z) // cfg.cells[0], 0, 5)
         c0 = (1.5 + 0.5 * layer).reshape(-1, 1, 1)
         xi = _smooth_noise(_rng(cfg, _STREAM_PERTURB), shape, cfg.corr)
         xi = xi / np.abs(xi).max()
@@ -91,25 +92,25 @@ def medium(cfg: Workload, which: str = "true") -> np.ndarray:
 
 def source_nodes(cfg: Workload) -> np.ndarray:
     """Unknown indices (``n_src`` x dim, axis order z,y,x) of the point sources."""
-    N, n, w = cfg.N, cfg.n, cfg.w_out
+    n, w = cfg.n, cfg.w_out
+    cells = cfg.cells
     if cfg.medium == "const" and cfg.n_src == 1:
-        return np.full((1, cfg.dim), cfg.n_cells // 2 - 1)
+        return np.array([[c // 2 + w - 1 for c in cells]])
     rng = _rng(cfg, _STREAM_SOURCES)
     if cfg.dim == 2 and cfg.n_rec > 0:
         # sources on the row two cells into the interior, distinct columns
         xs = rng.choice(np.arange(w, w + n - 1), size=cfg.n_src, replace=False)
         return np.stack([np.full(cfg.n_src, w + 2), np.sort(xs)], axis=1)
     if cfg.dim == 2:
-        lo, hi = w + n // 4, w + (3 * n) // 4
-        return rng.integers(lo, hi, size=(cfg.n_src, 2))
+        return np.stack([rng.integers(w + c // 4, w + (3 * c) // 4, size=cfg.n_src)
+                         for c in cells], axis=1)
     # 3-D: sources on a horizontal plane near the top of the interior
     zplane = w + (4 if cfg.n_rec == 0 else 2)
-    lo, hi = w, w + n - 1
-    flat = rng.choice((hi - lo) ** 2, size=cfg.n_src, replace=False)
-    ys, xs = lo + flat // (hi - lo), lo + flat % (hi - lo)
+    ny, nx = cells[1] - 1, cells[2] - 1
+    flat = rng.choice(ny * nx, size=cfg.n_src, replace=False)
     out = np.empty((cfg.n_src, 3), dtype=np.int64)
-    out[:, 0], out[:, 1], out[:, 2] = zplane, ys, xs
-    assert out.max() < N
+    out[:, 0], out[:, 1], out[:, 2] = zplane, w + flat // nx, w + flat % nx
+    assert np.all(out < np.array(cfg.shape))
     return out
 
 
@@ -130,16 +131,17 @@ def receivers(cfg: Workload) -> np.ndarray:
     plane (3-D) or an evenly spaced line on the source row (2-D)."""
     if cfg.n_rec == 0:
         return np.zeros(0, dtype=np.int64)
-    N = cfg.N
+    shape = cfg.shape
     if cfg.dim == 2:
         # a line of receivers on the source row, evenly spaced across the interior
         pos = cfg.w_out - 1 + np.round((np.arange(cfg.n_rec) + 0.5) * cfg.n / cfg.n_rec).astype(np.int64)
-        return (cfg.w_out + 2) * N + pos
+        return (cfg.w_out + 2) * shape[1] + pos
     side = int(round(cfg.n_rec ** 0.5))
     assert side * side == cfg.n_rec
     zplane = cfg.w_out + 2
-    pos = cfg.w_out - 1 + np.round((np.arange(side) + 0.5) * cfg.n / side).astype(np.int64)
-    return (zplane * N * N + pos[:, None] * N + pos[None, :]).reshape(-1)
+    py = cfg.w_out - 1 + np.round((np.arange(side) + 0.5) * cfg.cells[1] / side).astype(np.int64)
+    px = cfg.w_out - 1 + np.round((np.arange(side) + 0.5) * cfg.cells[2] / side).astype(np.int64)
+    return ((zplane * shape[1] + py[:, None]) * shape[2] + px[None, :]).reshape(-1)
 
 
 def fd_directions(cfg: Workload, count: int = 4) -> np.ndarray:

@@ -29,13 +29,19 @@ def _params(**kw):
                 gmres_m=20, max_iter=100, tol=1e-6, max_rhs=1, segments=0)
     base.update(kw)
     for k, v in base.items():
-        setattr(p, k, v)
+        if k == "n":                       # interior cells along x, y, z
+            for l, c in enumerate(v if isinstance(v, tuple) else (v, v, v)):
+                p.n[l] = c
+        else:
+            setattr(p, k, v)
     return p
 
 
-@pytest.mark.parametrize("bad", [dict(dim=3), dict(J=3), dict(n=2), dict(max_rhs=0),
+@pytest.mark.parametrize("bad", [dict(dim=4), dict(dim=1), dict(J=3), dict(n=2),
+                                 dict(n=(40, 2, 40)), dict(dim=3, n=(40, 40, 3)), dict(max_rhs=0),
                                  dict(max_rhs=99), dict(tol=0.0), dict(w_dd=0), dict(J=60),
-                                 dict(precision=7), dict(sweep=5)])
+                                 dict(precision=7), dict(sweep=5), dict(h=-1.0),
+                                 dict(two_grid=1, n=(40, 41, 40))])
 def test_setup_rejects_bad_parameters(L, bad):
     h = ctypes.c_void_p()
     st = L.hz_setup(ctypes.byref(_params(**bad)), ctypes.c_void_p(1), ctypes.byref(h))

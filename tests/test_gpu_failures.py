@@ -106,7 +106,7 @@ def test_allocation_failure_is_enomem_and_recoverable():
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_factor_wait_timeout_then_recovery(precision):
     hz = _hz()
-    cfg = synth.scaled_workload(2, 300, w_out=10, J=4)
+    cfg = synth.scaled_workload(2, 300, w_out=10, J=6)
     s = hz.Solver.from_workload(cfg, precision=precision)
     with _env(HZ_TEST_WAIT_LIMIT_NS=0):
         with pytest.raises(hz.HzError) as e:
