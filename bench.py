@@ -45,8 +45,13 @@ def _args():
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-source batched leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient leg")
-    ap.add_argument("--workload", type=int, default=CONFIG_INDEX, choices=[1, 2, 3],
-                    help="benchmark configuration (default 2, the headline workload)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the configuration 3 and 3-D legs of the default line")
+    ap.add_argument("--n3d", type=int, default=64,
+                    help="interior cells per axis of the reduced 3-D legs (configs 4 and 5)")
+    ap.add_argument("--workload", type=int, default=CONFIG_INDEX, choices=[1, 2, 3, 4, 5],
+                    help="benchmark configuration (default 2, the headline workload; 4 and 5 "
+                         "run at --n3d interior cells unless --n is given)")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the workload's recipe at this interior size (not a bench line)")
     ap.add_argument("--J", type=int, default=0, help="profiling only: slab count with --n")
@@ -147,18 +152,20 @@ def _traffic(tag):
     return None if e is None else e.get("dram_bytes_per_launch_full_size")
 
 
-def adjoint_leg(hz, synth, stream, flush, n=512, reps=3):
+def adjoint_leg(hz, synth, stream, flush, n=512, reps=3, cfg=None):
     """hz_grad on the 2-D adjoint workload (smooth random medium, blurred start
-    model, 8 sources and 16 receivers, two-grid, J = 4, mixed): one gradient
-    step = hz_factor at the start model + hz_grad (forward and adjoint solves
-    of the 8 sources, misfit, gradient).  The observed data are the receiver
-    values of the true model's solution computed by the same solver."""
+    model, 8 sources and 16 receivers, two-grid, J = 4, mixed), or on `cfg`:
+    one gradient step = hz_factor at the start model + hz_grad (forward and
+    adjoint solves of the sources, misfit, gradient).  The observed data are
+    the receiver values of the true model's solution computed by the same
+    solver."""
     import numpy as np
     import torch
-    cfg = synth.adjoint_workload_2d(n)
+    cfg = synth.adjoint_workload_2d(n) if cfg is None else cfg
     m_true, m0 = synth.medium(cfg, "true"), synth.medium(cfg, "start")
     c_pml = float(np.mean(1.0 / np.sqrt(m0)))
-    src = np.array([int(i) * cfg.N + int(j) for i, j in synth.source_nodes(cfg)])
+    src = np.array([np.ravel_multi_index(tuple(int(v) for v in idx), cfg.shape)
+                    for idx in synth.source_nodes(cfg)])
     rec = synth.receivers(cfg)
     st = hz.Solver.from_workload(cfg, m=m_true, c_pml=c_pml)
     st.factor()
@@ -182,17 +189,52 @@ def adjoint_leg(hz, synth, stream, flush, n=512, reps=3):
         ts.append(e0.elapsed_time(e1))
     s0.close()
     t = statistics.mean(ts) / 1000.0
-    return {"workload": f"{cfg.name}: {cfg.N}x{cfg.N} dof, J={cfg.J}, two-grid, mixed, "
-                        f"{cfg.n_src} sources, {cfg.n_rec} receivers",
+    return {"workload": f"{workload_string(cfg)}, mixed, {cfg.n_src} sources, {cfg.n_rec} receivers",
             "step": "hz_factor + hz_grad (forward + adjoint solves, misfit, gradient)",
             "time_s": t, "value": 2 * cfg.n_src * cfg.ndof / t / 1e6,
             "unit": "Mdof/s (dof x solves: forward and adjoint per source)",
             "misfit": phi, "iters_max": info.get("iters_max"), "relres_max": info.get("relres_max")}
 
 
+def workload_leg(hz, synth, cfg, stream, flush, reps=3, note=None, precision=None):
+    """hz_factor + hz_solve of every source of `cfg` in one multi-right-hand-side
+    call: time to 1e-6 (CUDA events, L2 flushed between repetitions), Mdof/s
+    counted as dof x right-hand sides, and the factorisation's share."""
+    import torch
+    m = synth.medium(cfg)
+    b = torch.from_numpy(synth.sources(cfg)).cuda()
+    kw = {} if precision is None else {"precision": precision}
+    s = hz.Solver.from_workload(cfg, m=m, **kw)
+    s.factor()
+    s.solve(b)
+    ts, tf, st = [], [], {}
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        s.factor()
+        e1.record(stream)
+        _, st = s.solve(b)
+        e2.record(stream)
+        e2.synchronize()
+        ts.append(e0.elapsed_time(e2))
+        tf.append(e0.elapsed_time(e1))
+    s.close()
+    t = statistics.mean(ts) / 1000.0
+    out = {"workload": workload_string(cfg), "n_rhs": cfg.n_src,
+           "precision": precision or cfg.precision, "step": "hz_factor + hz_solve",
+           "time_to_solution_s": t, "factor_s": statistics.mean(tf) / 1000.0,
+           "value": cfg.ndof * cfg.n_src / t / 1e6, "unit": "Mdof/s (dof x right-hand sides)",
+           "iters_max": st.get("iters_max"), "relres_max": st.get("relres_max")}
+    if note:
+        out["note"] = note
+    return out
+
+
 def workload_string(cfg):
     """The workload name both arms report in config.workload."""
-    dims = "x".join(str(cfg.N) for _ in range(cfg.dim))
+    dims = "x".join(str(s) for s in cfg.shape)
     return (f"{cfg.name}: {dims} dof, J={cfg.J}, {cfg.sweep}-sweep, w_dd={cfg.w_dd}"
             + (", two-grid" if cfg.two_grid else ""))
 
@@ -293,6 +335,8 @@ def main():
     cfg = synth.workload(args.workload)
     if args.n:
         cfg = synth.scaled_workload(args.workload, args.n, J=args.J or None)
+    elif cfg.dim == 3:      # the full 3-D configurations do not fit (dense slab factors)
+        cfg = synth.scaled_workload(args.workload, args.n3d, J=args.J or None)
     m = synth.medium(cfg)
     b = synth.sources(cfg)
     solver = hz.Solver.from_workload(cfg, m=m)
@@ -355,7 +399,9 @@ def main():
     clk = clocks.stop()
     tags = ["slab_rhs", "slab_fwd_pass1", "slab_carry", "slab_carry_bound", "slab_fwd_bwd1",
             "slab_bwd", "slab_solve", "slab_factor", "slab_middle", "segment_product",
-            "segment_prefix", "stencil_c64", "stencil_c128"]
+            "segment_prefix", "stencil_c64", "stencil_c128",
+            "slab_factor3d_schur", "slab_factor3d_panel", "slab_factor3d_rowmod",
+            "slab_factor3d_update", "slab_factor3d_writeout", "slab3_gemv", "slab_solve3d"]
     kt = {t: solver.kernel_timing(t) for t in tags}
     solver.enable_timing(False)
     ms_step, value = replica_throughput(total_ms / args.steps, cfg.ndof * cfg.n_src, ws, "cuda")
@@ -391,11 +437,13 @@ def main():
     fprec = "mixed" if cfg.precision == "mixed" else "fp64"
     alu_peak = hz.alu_peak(fprec)
     alu_derived = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    indiv = {t: v for t, v in per_kernel.items() if t != "slab_solve"}
+    indiv = {t: v for t, v in per_kernel.items() if t not in ("slab_solve", "slab_solve3d")}
     dom = max(indiv, key=lambda t: indiv[t]["ms"])
     # the kernels that stream the slab operators from HBM (the carries move a few products
-    # each and are latency-bound; the stencils are reported separately below)
-    hbm_tags = [t for t in indiv if t in ("slab_rhs", "slab_fwd_pass1", "slab_fwd_bwd1", "slab_bwd")]
+    # each and are latency-bound; the stencils are reported separately below); in 3-D the
+    # per-layer GEMV with the stored dense inverse
+    hbm_tags = [t for t in indiv
+                if t in ("slab_rhs", "slab_fwd_pass1", "slab_fwd_bwd1", "slab_bwd", "slab3_gemv")]
     dom_hbm = max(hbm_tags, key=lambda t: indiv[t]["ms"])
 
     def hbm_line(tag):
@@ -417,6 +465,19 @@ def main():
                     "peak_fp32_derived": alu_derived,
                     "traffic": _traffic(dom), "avg_launch_us": 1000 * d["ms"] / d["launches"],
                     "algorithmic_flop_per_launch": factor_flop,
+                    "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
+        roofline["hbm_kernel"] = hbm_line(dom_hbm)
+    elif dom == "slab_factor3d_update":
+        # the rank-32 complex GEMM update of the 3-D Gauss-Jordan inverse: its tag
+        # carries the algorithmic flop (8 B^2 32 per chain and panel)
+        d = indiv[dom]
+        ach = d["bytes"] / (d["ms"] / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": ach / alu_peak,
+                    "peak_source": (f"measured {'FP32' if fprec == 'mixed' else 'FP64'} FMA "
+                                    "throughput (hz_alu_peak)"),
+                    "traffic": None, "avg_launch_us": 1000 * d["ms"] / d["launches"],
+                    "algorithmic_flop_per_launch": d["bytes"] / d["launches"],
                     "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
         roofline["hbm_kernel"] = hbm_line(dom_hbm)
     else:
@@ -450,7 +511,9 @@ def main():
             "clocks": clk, "gpu_launches": gpu_launches}
     solver.close()
 
-    if rank == 0 and ws == 1 and not args.no_fp64_arm:
+    # (3-D: the complex128 dense-block inverses run on GB300's narrow FP64 pipe;
+    # no FP64 arm there)
+    if rank == 0 and ws == 1 and not args.no_fp64_arm and cfg.dim == 2:
         s64 = hz.Solver.from_workload(cfg, m=m, precision="fp64")
         s64.factor()
         s64.solve(f_dev)
@@ -502,7 +565,23 @@ def main():
         s8.close()
     if rank == 0 and ws == 1 and not args.no_adjoint and not args.n and args.workload == 2:
         line["adjoint"] = adjoint_leg(hz, synth, stream, flush)
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload != 3:
+    if rank == 0 and ws == 1 and not args.no_extra and not args.n and args.workload == 2:
+        # the other configurations, as side legs of the headline line: the large
+        # 2-D two-grid workload at full size, and the 3-D workloads at n3d
+        # interior cells per axis (their full sizes need more than the GPU's
+        # memory for dense slab factors)
+        line["config3"] = workload_leg(hz, synth, synth.workload(3), stream, flush, reps=2)
+        c4 = synth.scaled_workload(4, args.n3d)
+        line["config4_3d"] = workload_leg(
+            hz, synth, c4, stream, flush, reps=2,
+            note=f"configuration 4 recipe at {args.n3d}^3 interior cells (reduced), "
+                 f"{c4.n_src} sources as right-hand sides of one solve")
+        c5 = synth.scaled_workload(5, args.n3d)
+        line["config5_3d_gradient"] = adjoint_leg(hz, synth, stream, flush, reps=2, cfg=c5)
+        line["config5_3d_gradient"]["note"] = (
+            f"configuration 5 recipe at {args.n3d}^3 interior cells (reduced), two-grid")
+    if (rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload != 3
+            and cfg.dim == 2):
         line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
         print(json.dumps(line))
