@@ -52,7 +52,9 @@ typedef enum {
   HZ_EINACCURATE = 7    /* a residual norm is not finite (NaN / Inf in the data or operator) */
 } hz_status;
 
-enum { HZ_SWEEP_UD = 0, HZ_SWEEP_X = 1 };        /* SweepingPrecUD / SweepingPrecX (Table 3) */
+/* SweepingPrecUD / SweepingPrecX / SweepingPrecNX (Table 3; NX: partial
+ * sweeps inside n_cell groups of subdomains, a comparison pattern) */
+enum { HZ_SWEEP_UD = 0, HZ_SWEEP_X = 1, HZ_SWEEP_NX = 2 };
 enum { HZ_PLAIN_FP64 = 0, HZ_MIXED = 1 };        /* preconditioner in complex128 / complex64 */
 
 typedef struct {
@@ -80,6 +82,10 @@ typedef struct {
                          * count; at least 2) */
   double c_pml;         /* PML "typical velocity" (Section 2.1); 0: mean of c over the
                          * unknowns, recomputed by hz_setup / hz_set_medium */
+  int    n_cell;        /* HZ_SWEEP_NX: cells N_cell (1..(J+1)/2; cell boundaries
+                         * j_cell = 0, round(m (J+1) / N_cell), J+1; centres
+                         * j_mid = (j_cell[m-1] + j_cell[m] + 1) / 2); N_cell = 1
+                         * is the X-sweep.  Ignored by the other patterns */
 } hz_params;
 
 typedef struct {

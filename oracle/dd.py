@@ -229,5 +229,51 @@ class SweepingDD:
         self.forward_sweep(u, g, jm + 1, self.J, B2)
         return u.reshape(self.shape)
 
-    def apply(self, f: np.ndarray, sweep: str = "X") -> np.ndarray:
+    def prec_nx(self, f: np.ndarray, n_cell: int) -> np.ndarray:
+        """SweepingPrecNX(f) (Table 3): intersecting sweeps inside n_cell groups
+        of subdomains ("cells") separated by the boundary subdomains
+        j_cell[1..n_cell-1].
+
+        Readings of the printed listing: j_cell[0] = 0 (with j_cell[n_cell] =
+        J + 1, so that n_cell = 1 is SweepingPrecX); a first-phase MidSolveOut
+        at a cell boundary sends its layers both ways (right into the next
+        cell's forward sweep, B_{2m+1}; left into this cell's backward sweep,
+        B_{2m}); the second-phase MidSolveIn of a cell boundary takes the data
+        of both neighbouring cells, so it follows all cells' sweeps.
+        """
+        f = f.reshape(self.nt, self.N)
+        jc, jm = nx_layout(self.J, n_cell)
+        u = np.zeros_like(f, dtype=np.complex128)
+        B = [[None, None] for _ in range(2 * n_cell + 2)]      # B[1] .. B[2 n_cell + 1]
+        for m in range(1, n_cell):
+            self.mid_solve_out(u, f, jc[m], B[2 * m + 1], B[2 * m])
+        for m in range(1, n_cell + 1):
+            self.forward_sweep(u, f, jc[m - 1] + 1, jm[m] - 1, B[2 * m - 1])
+            self.backward_sweep(u, f, jc[m] - 1, jm[m] + 1, B[2 * m])
+            self.mid_solve_in(u, f, jm[m], B[2 * m - 1], B[2 * m])
+        g = self._residual(f, u)
+        for m in range(1, n_cell + 1):
+            self.mid_solve_out(u, g, jm[m], B[2 * m], B[2 * m - 1])
+            self.backward_sweep(u, g, jm[m] - 1, jc[m - 1] + 1, B[2 * m - 1])
+            self.forward_sweep(u, g, jm[m] + 1, jc[m] - 1, B[2 * m])
+        for m in range(1, n_cell):
+            self.mid_solve_in(u, g, jc[m], B[2 * m], B[2 * m + 1])
+        return u.reshape(self.shape)
+
+    def apply(self, f: np.ndarray, sweep: str = "X", n_cell: int = 2) -> np.ndarray:
+        if sweep == "NX":
+            return self.prec_nx(f, n_cell)
         return self.prec_x(f) if sweep == "X" else self.prec_ud(f)
+
+
+def nx_layout(J: int, n_cell: int):
+    """Cell boundaries j_cell[0..n_cell] (j_cell[0] = 0, j_cell[n_cell] = J + 1,
+    the others equally spaced) and cell centres j_mid[1..n_cell] (j_mid[0]
+    unused), for SweepingPrecNX; n_cell = 1 gives the X-sweep's j_mid = J/2 + 1
+    for even J."""
+    assert 1 <= n_cell <= (J + 1) // 2, "every cell needs at least one subdomain"
+    jc = [0] + [int(round(m * (J + 1) / n_cell)) for m in range(1, n_cell)] + [J + 1]
+    jm = [0] + [(jc[m - 1] + jc[m] + 1) // 2 for m in range(1, n_cell + 1)]
+    for m in range(1, n_cell + 1):
+        assert jc[m - 1] < jm[m] < jc[m]
+    return jc, jm

@@ -19,11 +19,13 @@ class Problem:
     def __init__(self, cfg, m: np.ndarray | None = None, *, sweep: str | None = None,
                  J: int | None = None, w_dd: int | None = None, s_dd: float | None = None,
                  two_grid: bool | None = None, nu: int | None = None,
-                 omega_jac: float | None = None, c_pml: float | None = None):
+                 omega_jac: float | None = None, c_pml: float | None = None,
+                 n_cell: int = 2):
         import synth
         self.cfg = cfg
         self.m = synth.medium(cfg) if m is None else np.asarray(m, dtype=np.float64)
         self.sweep = cfg.sweep if sweep is None else sweep
+        self.n_cell = n_cell              # cells of the NX-sweep (sweep = "NX")
         self.J = cfg.J if J is None else J
         self.w_dd = cfg.w_dd if w_dd is None else w_dd
         self.s_dd = cfg.s_dd if s_dd is None else s_dd
@@ -65,10 +67,10 @@ class Problem:
     def precondition(self, r: np.ndarray) -> np.ndarray:
         r = np.asarray(r).ravel()
         if self.two_grid:
-            out = twogrid.tgsp(r, self.A, self.P, lambda rc: self.dd.apply(rc, self.sweep),
+            out = twogrid.tgsp(r, self.A, self.P, lambda rc: self.dd.apply(rc, self.sweep, self.n_cell),
                                self.nu, self.omega_jac)
         else:
-            out = self.dd.apply(r, self.sweep)
+            out = self.dd.apply(r, self.sweep, self.n_cell)
         return np.asarray(out).ravel()
 
     def apply(self, u: np.ndarray) -> np.ndarray:

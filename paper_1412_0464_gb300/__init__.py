@@ -17,7 +17,7 @@ import re
 from .build import LIB, build  # noqa: F401
 
 HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_ENOTFACTORED, HZ_ENOTCONV, HZ_ETIMEOUT, HZ_EINACCURATE = range(8)
-HZ_SWEEP_UD, HZ_SWEEP_X = 0, 1
+HZ_SWEEP_UD, HZ_SWEEP_X, HZ_SWEEP_NX = 0, 1, 2
 HZ_PLAIN_FP64, HZ_MIXED = 0, 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hz.h")
@@ -32,7 +32,7 @@ class hz_params(ctypes.Structure):
         ("two_grid", ctypes.c_int), ("nu", ctypes.c_int), ("omega_jac", ctypes.c_double),
         ("precision", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_iter", ctypes.c_int),
         ("tol", ctypes.c_double), ("max_rhs", ctypes.c_int), ("segments", ctypes.c_int),
-        ("c_pml", ctypes.c_double),
+        ("c_pml", ctypes.c_double), ("n_cell", ctypes.c_int),
     ]
 
 
@@ -165,7 +165,7 @@ class Solver:
     def __init__(self, m, *, n, w_out, omega, J, w_dd, s_dd, s_out=20.0, sweep="X",
                  precision="mixed", gmres_m=30, max_iter=500, tol=1e-6, max_rhs=1,
                  two_grid=False, nu=3, omega_jac=0.8, segments=0, c_pml=0.0, dim=2, dims=None,
-                 h=0.0):
+                 h=0.0, n_cell=2):
         import torch
         dims = tuple(dims) if dims is not None else (n,) * dim
         assert len(dims) == dim and dims[-1] == n
@@ -183,7 +183,8 @@ class Solver:
         for l, c in enumerate(reversed(dims)):      # hz_params.n is (x, y, z)
             p.n[l] = c
         p.s_pml_out, p.s_pml_dd, p.J, p.w_dd = s_out, s_dd, J, w_dd
-        p.sweep = HZ_SWEEP_X if sweep == "X" else HZ_SWEEP_UD
+        p.sweep = {"X": HZ_SWEEP_X, "UD": HZ_SWEEP_UD, "NX": HZ_SWEEP_NX}[sweep]
+        p.n_cell = n_cell
         p.two_grid, p.nu, p.omega_jac = int(two_grid), nu, omega_jac
         p.precision = HZ_MIXED if precision == "mixed" else HZ_PLAIN_FP64
         p.gmres_m, p.max_iter, p.tol, p.max_rhs, p.segments = gmres_m, max_iter, tol, max_rhs, segments

@@ -69,7 +69,7 @@ double now_s() {
 size_t prec_size(const hz_params& p) { return p.precision == HZ_MIXED ? sizeof(c64) : sizeof(c128); }
 
 void release_work(hz_handle* h) {
-  for (void** q : {&h->pr_r, &h->pr_u, &h->pr_u2, &h->pr_g, &h->pr_B1, &h->pr_B2, &h->tg_u, &h->tg_r,
+  for (void** q : {&h->pr_r, &h->pr_u, &h->pr_u2, &h->pr_g, &h->pr_B1, &h->pr_B2, &h->pr_Bnx, &h->tg_u, &h->tg_r,
                    &h->tg_t}) {
     dfree(*q);
     *q = nullptr;
@@ -92,8 +92,11 @@ void validate(const hz_params* p) {
   if (p->w_out < 0) bad("w_out must be >= 0");
   if (!(p->omega > 0)) bad("omega must be > 0");
   if (p->J < 1) bad("J must be >= 1");
-  if (p->sweep != HZ_SWEEP_UD && p->sweep != HZ_SWEEP_X) bad("sweep must be HZ_SWEEP_UD or HZ_SWEEP_X");
+  if (p->sweep != HZ_SWEEP_UD && p->sweep != HZ_SWEEP_X && p->sweep != HZ_SWEEP_NX)
+    bad("sweep must be HZ_SWEEP_UD, HZ_SWEEP_X or HZ_SWEEP_NX");
   if (p->sweep == HZ_SWEEP_X && (p->J % 2 != 0)) bad("the X-sweep needs an even J");
+  if (p->sweep == HZ_SWEEP_NX && (p->n_cell < 1 || p->n_cell > (p->J + 1) / 2))
+    bad("the NX-sweep needs 1 <= n_cell <= (J + 1) / 2");
   if (p->w_dd < 1) bad("w_dd must be >= 1");
   if (p->precision != HZ_PLAIN_FP64 && p->precision != HZ_MIXED) bad("bad precision");
   if (p->gmres_m < 1 || p->gmres_m > 200) bad("gmres_m must be in 1..200");
@@ -167,6 +170,11 @@ hz_status hz_setup(const hz_params* p, const double* m_dev, hz_handle** out) {
     h->pr_B2 = dmalloc(ps * 2 * R * L.nt());
     HZ_CU(cudaMemsetAsync(h->pr_B1, 0, ps * 2 * R * L.nt(), h->s2));
     HZ_CU(cudaMemsetAsync(h->pr_B2, 0, ps * 2 * R * L.nt(), h->s2));
+    if (p->sweep == HZ_SWEEP_NX) {
+      const size_t nb = ps * 2 * R * L.nt() * (2 * (size_t)p->n_cell + 2);
+      h->pr_Bnx = dmalloc(nb);
+      HZ_CU(cudaMemsetAsync(h->pr_Bnx, 0, nb, h->s2));
+    }
     if (p->two_grid) {
       h->tg_u = dmalloc(ps * n * R);
       h->tg_r = dmalloc(ps * n * R);

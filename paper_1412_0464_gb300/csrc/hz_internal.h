@@ -217,8 +217,9 @@ struct hz_handle {
   void* pr_u = nullptr;      // output on the sweep level
   void* pr_u2 = nullptr;     // second sweep phase output on the sweep level
   void* pr_g = nullptr;      // mid-sweep residual g = f - A u
-  void* pr_B1 = nullptr;     // transmission buffers [2][max_rhs][ny]
+  void* pr_B1 = nullptr;     // transmission buffers [2][max_rhs][N_t]
   void* pr_B2 = nullptr;
+  void* pr_Bnx = nullptr;    // NX-sweep: 2 n_cell + 2 transmission buffers [2][max_rhs][N_t]
   void* tg_u = nullptr;      // two-grid fine work (preconditioner precision)
   void* tg_r = nullptr;
   void* tg_t = nullptr;

@@ -52,6 +52,21 @@ static void mid_solve_out(hz_handle* h, Level& L, cplx<R>* u, const cplx<R>* f, 
                   nullptr, true, B1, false, nullptr, true, B2, u, nr, s);
 }
 
+// SweepingPrecNX (Table 3): cell boundaries j_cell[0..n_cell] (0, equally
+// spaced, J + 1; the listing's j_cell,0 = -1 is read as 0, so that one cell is
+// the X-sweep) and cell centres j_mid[1..n_cell].
+void nx_layout(int J, int n_cell, std::vector<int>& jc, std::vector<int>& jm) {
+  jc.assign(n_cell + 1, 0);
+  jm.assign(n_cell + 1, 0);
+  for (int m = 1; m < n_cell; ++m) jc[m] = (int)std::lround((double)m * (J + 1) / n_cell);
+  jc[n_cell] = J + 1;
+  for (int m = 1; m <= n_cell; ++m) {
+    jm[m] = (jc[m - 1] + jc[m] + 1) / 2;
+    if (!(jc[m - 1] < jm[m] && jm[m] < jc[m]))
+      throw Failure(HZ_EINVAL, "NX-sweep: every cell needs at least one subdomain");
+  }
+}
+
 template <typename R>
 __global__ void add_kernel(cplx<R>* u, const cplx<R>* v, size_t n) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -74,6 +89,29 @@ void sweep_apply(hz_handle* h, Level& L, const cplx<R>* f, cplx<R>* u, int nr, c
     forward_sweep<R>(h, L, u, f, 1, J, B1, nr, s);
     level_residual<R>(h, L, f, u, g, nr, s);
     backward_sweep<R>(h, L, u2, g, J, 1, B1, nr, s);
+  } else if (h->p.sweep == HZ_SWEEP_NX) {           // SweepingPrecNX (one stream)
+    std::vector<int> jc, jm;
+    const int nc = h->p.n_cell;
+    nx_layout(J, nc, jc, jm);
+    const size_t bs = 2 * (size_t)h->p.max_rhs * L.nt();
+    auto Bi = [&](int i) { return (cplx<R>*)h->pr_Bnx + (size_t)i * bs; };
+    // first phase: the cell boundaries send their layers into both
+    // neighbouring cells, then every cell sweeps towards its centre
+    for (int m = 1; m < nc; ++m) mid_solve_out<R>(h, L, u, f, jc[m], Bi(2 * m + 1), Bi(2 * m), nr, s);
+    for (int m = 1; m <= nc; ++m) {
+      forward_sweep<R>(h, L, u, f, jc[m - 1] + 1, jm[m] - 1, Bi(2 * m - 1), nr, s);
+      backward_sweep<R>(h, L, u, f, jc[m] - 1, jm[m] + 1, Bi(2 * m), nr, s);
+      mid_solve_in<R>(h, L, u, f, jm[m], Bi(2 * m - 1), Bi(2 * m), nr, s);
+    }
+    level_residual<R>(h, L, f, u, g, nr, s);
+    // second phase: every cell sweeps outwards from its centre, then the cell
+    // boundaries take the layers of both neighbouring cells
+    for (int m = 1; m <= nc; ++m) {
+      mid_solve_out<R>(h, L, u2, g, jm[m], Bi(2 * m), Bi(2 * m - 1), nr, s);
+      backward_sweep<R>(h, L, u2, g, jm[m] - 1, jc[m - 1] + 1, Bi(2 * m - 1), nr, s);
+      forward_sweep<R>(h, L, u2, g, jm[m] + 1, jc[m] - 1, Bi(2 * m), nr, s);
+    }
+    for (int m = 1; m < nc; ++m) mid_solve_in<R>(h, L, u2, g, jc[m], Bi(2 * m), Bi(2 * m + 1), nr, s);
   } else {
     const int jm = J / 2 + 1;                        // SweepingPrecX
     cudaStream_t s2 = h->s2;
