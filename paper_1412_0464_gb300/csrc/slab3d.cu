@@ -41,6 +41,27 @@ namespace hz {
 
 namespace {
 
+// Programmatic dependent launch: the solve kernels are launched with
+// programmatic stream serialisation, so a kernel's launch and block set-up
+// overlap its predecessor; every such kernel waits for the predecessor's
+// results (griddepcontrol.wait) before touching any data.
+__device__ __forceinline__ void pdl_wait3() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_pdl3(void (*k)(KArgs...), dim3 grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  HZ_CU(cudaLaunchKernelEx(&cfg, k, args...));
+}
+
 constexpr int NB = 32;            // panel width of the blocked Gauss-Jordan inverse
 constexpr int kPanelThreads = 512;
 constexpr int kMaxB = 8192;       // largest block (pivot flags live in shared memory)
@@ -190,7 +211,7 @@ struct FChain {
   cplx<R>* G;          // [nz][bstride]
   size_t bstride;
   cplx<R>* S;          // [B][B] Schur complement, inverted in place
-  cplx<R>* C;          // [B][NB] colmods of the current panel
+  cplx<R>* C;          // [NB][B] colmods of the current panel
   cplx<R>* Rm;         // [NB][B] rowmods of the current panel
   cplx<R>* pinfo;      // [NB] 1 / pivot of the panel's columns
   int* piv;            // [B] pivot row of column p
@@ -346,7 +367,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
       if (i == r) ci.re -= (R)1;
       v = v - ci * rq;
       if (lane < nbp) row[lane] = v;
-      if (lane == 0) c.C[(size_t)i * NB + t] = ci;
+      if (lane == 0) c.C[(size_t)t * B + i] = ci;
       if (t + 1 < nbp) {
         const cplx<R> nv = mk<R>(__shfl_sync(0xffffffffu, v.re, t + 1),
                                  __shfl_sync(0xffffffffu, v.im, t + 1));
@@ -360,21 +381,115 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
   }
 }
 
+// The same panel elimination with the panel held in shared memory (blocks
+// small enough: B (PW + 1) elements): one thread per row (rows tid, tid +
+// 1024, ...), panel rows padded to PW + 1 elements; per step a block-wide
+// pivot-key maximum, the scaled pivot row, and each thread's rank-1 update of
+// its rows with the next column's keys.  The colmods go to C [NB][B].
+constexpr int kSmemPanelThreads = 1024;
+
+template <typename R, int PW>
+__global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const FChain<R>* chains,
+                                                                         int p0) {
+  const FChain<R> c = chains[blockIdx.x];
+  const int B = c.B;
+  if (p0 >= B) return;
+  const int nbp = min(PW, B - p0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int LD = PW + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* P = (cplx<R>*)smem_raw;                                  // [B][LD]
+  unsigned long long* wkey = (unsigned long long*)(P + (size_t)B * LD);   // [32]
+  cplx<R>* rm = (cplx<R>*)(wkey + 32);                              // [PW]
+  int* shr = (int*)(rm + PW);                                       // [4]
+  unsigned char* flag = (unsigned char*)(shr + 4);                  // [B]
+  for (int e = tid; e < B * PW; e += kSmemPanelThreads) {
+    const int i = e / PW, q = e - i * PW;
+    P[i * LD + q] = q < nbp ? c.S[(size_t)i * B + p0 + q] : mk<R>(0, 0);
+  }
+  for (int i = tid; i < B; i += kSmemPanelThreads) flag[i] = c.pinv[i] >= 0;
+  __syncthreads();
+  unsigned long long best = 0;
+  for (int i = tid; i < B; i += kSmemPanelThreads)
+    if (!flag[i]) {
+      const unsigned long long k = pivot_key((float)cabs2(P[i * LD]), i);
+      best = k > best ? k : best;
+    }
+  for (int t = 0; t < nbp; ++t) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+      best = v > best ? v : best;
+    }
+    if (lane == 0) wkey[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long b = wkey[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+        b = v > b ? v : b;
+      }
+      if (lane == 0) {
+        const int r = (int)(0xffffffffu - (unsigned)(b & 0xffffffffu));
+        shr[0] = r;
+        flag[r] = 1;
+        c.piv[p0 + t] = r;
+        c.pinv[r] = p0 + t;
+        c.prow[t] = r;
+      }
+    }
+    __syncthreads();
+    const int r = shr[0];
+    if (tid < PW) {
+      const cplx<R> inv = cinv(P[r * LD + t]);
+      cplx<R> x = P[r * LD + tid] * inv;
+      if (tid == t) x = inv + mk<R>(1, 0);
+      rm[tid] = tid < nbp ? x : mk<R>(0, 0);
+      if (tid == 0) c.pinfo[t] = inv;
+    }
+    __syncthreads();
+    best = 0;
+    for (int i = tid; i < B; i += kSmemPanelThreads) {
+      cplx<R>* row = P + i * LD;
+      cplx<R> ci = row[t];
+      if (i == r) ci.re -= (R)1;
+      c.C[(size_t)t * B + i] = ci;
+#pragma unroll
+      for (int q = 0; q < PW; ++q) row[q] = row[q] - ci * rm[q];
+      if (t + 1 < nbp && !flag[i]) {
+        const unsigned long long k = pivot_key((float)cabs2(row[t + 1]), i);
+        best = k > best ? k : best;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < B * PW; e += kSmemPanelThreads) {
+    const int i = e / PW, q = e - i * PW;
+    if (q < nbp) c.S[(size_t)i * B + p0 + q] = P[i * LD + q];
+  }
+}
+
+template <typename R, int PW>
+size_t panel_smem_bytes(int B) {
+  return (size_t)B * (PW + 1) * sizeof(cplx<R>) + 32 * 8 + PW * sizeof(cplx<R>) + 16 + B + 16;
+}
+
 // Pivot rows' other columns (one thread per column j outside the panel):
 //   rho_t[j] = (S[r_t][j] - sum_{s<t} C[r_t][s] rho_s[j]) / S[r_t][p0+t];
 // zero on the panel columns (the panel kernel has finished them).
 template <typename R>
-__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0) {
+__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0, int nbw) {
   const FChain<R> c = chains[blockIdx.y];
   const int B = c.B;
   if (p0 >= B) return;
-  const int nbp = min(NB, B - p0);
+  const int nbp = min(nbw, B - p0);
   __shared__ cplx<R> Cp[NB][NB];
   __shared__ cplx<R> inv[NB];
   __shared__ int pr[NB];
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int t = e / NB, s = e - t * NB;
-    Cp[t][s] = (t < nbp && s < t) ? c.C[(size_t)c.prow[t] * NB + s] : mk<R>(0, 0);
+    Cp[t][s] = (t < nbp && s < t) ? c.C[(size_t)s * B + c.prow[t]] : mk<R>(0, 0);
   }
   for (int t = threadIdx.x; t < NB; t += blockDim.x) {
     inv[t] = t < nbp ? c.pinfo[t] : mk<R>(0, 0);
@@ -405,11 +520,11 @@ __global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains,
 // S -= C Rm over a 64 x 64 tile per CTA (256 threads, 4 x 4 outputs each:
 // rows ty + 16 a, columns tx + 16 b), depth NB through shared memory.
 template <typename R>
-__global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains, int p0) {
+__global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains, int p0, int nbw) {
   const FChain<R> c = chains[blockIdx.z];
   const int B = c.B;
   if (p0 >= B) return;
-  const int nbp = min(NB, B - p0);
+  const int nbp = min(nbw, B - p0);
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   if (i0 >= B || j0 >= B) return;
   if (j0 >= p0 && j0 + 64 <= p0 + nbp) return;   // panel columns only: nothing to do
@@ -417,10 +532,9 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains,
   cplx<R>* Cs = (cplx<R>*)smem_raw;              // [64][NB + 1]
   cplx<R>* Rs = Cs + 64 * (NB + 1);              // [NB][64]
   for (int e = threadIdx.x; e < 64 * NB; e += 256) {
-    const int r = e / NB, t = e - r * NB;
-    Cs[r * (NB + 1) + t] = (i0 + r < B && t < nbp) ? c.C[(size_t)(i0 + r) * NB + t] : mk<R>(0, 0);
-    const int t2 = e / 64, q = e - t2 * 64;
-    Rs[t2 * 64 + q] = (j0 + q < B && t2 < nbp) ? c.Rm[(size_t)t2 * B + j0 + q] : mk<R>(0, 0);
+    const int t = e / 64, q = e - t * 64;        // colmods [NB][B], rowmods [NB][B]
+    Cs[q * (NB + 1) + t] = (i0 + q < B && t < nbp) ? c.C[(size_t)t * B + i0 + q] : mk<R>(0, 0);
+    Rs[t * 64 + q] = (j0 + q < B && t < nbp) ? c.Rm[(size_t)t * B + j0 + q] : mk<R>(0, 0);
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -544,6 +658,7 @@ struct Prep3 {
 
 template <typename R>
 __global__ void slab3_prep_kernel(Prep3<R> a) {
+  pdl_wait3();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   const Piece3<R>& P = a.p[blockIdx.z];
@@ -577,10 +692,8 @@ __global__ void slab3_prep_kernel(Prep3<R> a) {
 
 // Dense layer GEMV with the stored inverse, up to two pieces (the two
 // chains): y[r][i] = G[i][:] v[r][:] (mode 0) or y[r][i] - G[i][:] v[r][:]
-// (mode 1), r < NR.  A warp takes kRowsPerWarp rows, its lanes the columns
-// (coalesced rows of G, v reused across the warp's rows), then a shuffle
-// reduction per output.
-constexpr int kRowsPerWarp = 2;
+// (mode 1), r < NR.
+constexpr int kGemvRows = 4;
 template <typename R>
 struct GemvPiece {
   const cplx<R>* G;          // [B][B]
@@ -593,54 +706,65 @@ struct Gemv3 {
   GemvPiece<R> p[2];
 };
 
+// A CTA takes kGemvRows rows; its 8 warps split the columns into 8 chunks
+// (many independent loads in flight per SM), each lane accumulates the
+// products of its columns, and the partial sums are reduced across lanes
+// (shuffles) and across the warps (shared memory).
 template <typename R, int NR>
 __global__ void __launch_bounds__(256) slab3_gemv_kernel(Gemv3<R> a) {
+  pdl_wait3();
   const GemvPiece<R>& P = a.p[blockIdx.y];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = (blockIdx.x * 8 + warp) * kRowsPerWarp;
-  if (i0 >= a.B) return;
   const int B = a.B;
-  cplx<R> acc[kRowsPerWarp][NR];
+  const int i0 = blockIdx.x * kGemvRows;
+  if (i0 >= B) return;
+  const int cw = (B + 7) / 8;
+  const int j0 = warp * cw, j1 = min(B, j0 + cw);
+  __shared__ cplx<R> part[8][kGemvRows * NR];
+  // right-hand sides in chunks of NR (the CTA's rows of G stay in cache)
+  for (int r0 = 0; r0 < a.nr; r0 += NR) {
+  const int nrc = min(NR, a.nr - r0);
+  cplx<R> acc[kGemvRows][NR];
 #pragma unroll
-  for (int q = 0; q < kRowsPerWarp; ++q)
+  for (int q = 0; q < kGemvRows; ++q)
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[q][r] = mk<R>(0, 0);
-  for (int j = lane; j < B; j += 32) {
+  for (int j = j0 + lane; j < j1; j += 32) {
     cplx<R> v[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) v[r] = r < a.nr ? P.v[(size_t)r * B + j] : mk<R>(0, 0);
+    for (int r = 0; r < NR; ++r) v[r] = r < nrc ? P.v[(size_t)(r0 + r) * B + j] : mk<R>(0, 0);
 #pragma unroll
-    for (int q = 0; q < kRowsPerWarp; ++q) {
+    for (int q = 0; q < kGemvRows; ++q) {
       const int i = i0 + q;
-      if (i < B) {
-        const cplx<R> g = P.G[(size_t)i * B + j];
+      const cplx<R> g = i < B ? P.G[(size_t)i * B + j] : mk<R>(0, 0);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) cfma(acc[q][r], g, v[r]);
-      }
+      for (int r = 0; r < NR; ++r) cfma(acc[q][r], g, v[r]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < kRowsPerWarp; ++q)
+  for (int q = 0; q < kGemvRows; ++q)
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
+    for (int r = 0; r < NR; ++r) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         acc[q][r].re += __shfl_xor_sync(0xffffffffu, acc[q][r].re, o);
         acc[q][r].im += __shfl_xor_sync(0xffffffffu, acc[q][r].im, o);
       }
-  if (lane < kRowsPerWarp * NR) {
-    const int q = lane / NR, r = lane - q * NR;
+      if (lane == 0) part[warp][q * NR + r] = acc[q][r];
+    }
+  __syncthreads();
+  if (threadIdx.x < kGemvRows * NR) {
+    const int q = threadIdx.x / NR, r = threadIdx.x - q * NR;
     const int i = i0 + q;
-    if (i < B && r < a.nr) {
+    if (i < B && r < nrc) {
       cplx<R> s = mk<R>(0, 0);
 #pragma unroll
-      for (int qq = 0; qq < kRowsPerWarp; ++qq)
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr)
-          if (qq == q && rr == r) s = acc[qq][rr];
-      cplx<R>* out = P.y + (size_t)r * B + i;
+      for (int w = 0; w < 8; ++w) s = s + part[w][threadIdx.x];
+      cplx<R>* out = P.y + (size_t)(r0 + r) * B + i;
       *out = a.mode == 0 ? s : *out - s;
     }
+  }
+  __syncthreads();            // part is reused by the next chunk
   }
 }
 
@@ -749,6 +873,14 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
   }
   const FChain<R>* desc = (const FChain<R>*)L.f3_desc;
   const int fe = L.fe ? 1 : 0;
+  // panels of 16 columns held in shared memory when a block's panel fits,
+  // else panels of NB columns eliminated in place in global memory
+  const size_t psm = panel_smem_bytes<R, 16>(Bmax);
+  const bool smem_panel = psm <= (size_t)225 * 1024;
+  const int nbw = smem_panel ? 16 : NB;
+  if (smem_panel)
+    HZ_CU(cudaFuncSetAttribute(gj_panel_smem_kernel<R, 16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
   auto layer = [&](const FChain<R>* d, int cnt, int nterm) {
     const dim3 gs(cdiv(Bmax, 128), Bmax, cnt);
     timed(h, "slab_factor3d_schur", 0.0, s, [&] {
@@ -763,16 +895,21 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       }
     });
     h->launches += fe ? 1 + 2 * nterm : 1;
-    for (int p0 = 0; p0 < Bmax; p0 += NB) {
-      timed(h, "slab_factor3d_panel", 0.0, s,
-            [&] { gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0); });
-      timed(h, "slab_factor3d_rowmod", 0.0, s,
-            [&] { gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 128), cnt), 128, 0, s>>>(d, p0); });
-      // algorithmic flop of the update: 8 B^2 NB per chain (complex MACs x 8)
-      const double fl = 8.0 * (double)Bmax * Bmax * NB * cnt;
+    for (int p0 = 0; p0 < Bmax; p0 += nbw) {
+      timed(h, "slab_factor3d_panel", 0.0, s, [&] {
+        if (smem_panel)
+          gj_panel_smem_kernel<R, 16><<<cnt, kSmemPanelThreads, psm, s>>>(d, p0);
+        else
+          gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0);
+      });
+      timed(h, "slab_factor3d_rowmod", 0.0, s, [&] {
+        gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 128), cnt), 128, 0, s>>>(d, p0, nbw);
+      });
+      // algorithmic flop of the update: 8 B^2 nb per chain (complex MACs x 8)
+      const double fl = 8.0 * (double)Bmax * Bmax * std::min(nbw, Bmax - p0) * cnt;
       timed(h, "slab_factor3d_update", fl, s, [&] {
         gj_update_kernel<R><<<dim3(cdiv(Bmax, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el), s>>>(
-            d, p0);
+            d, p0, nbw);
       });
       h->launches += 3;
     }
@@ -814,16 +951,16 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
   pa.st = (const cplx<R>*)S.st3;
   Gemv3<R> ga{};
   ga.B = B; ga.nr = nr;
-  const unsigned gblocks = (unsigned)cdiv(B, 8 * kRowsPerWarp);
+  const unsigned gblocks = (unsigned)cdiv(B, kGemvRows);
   auto prep = [&](int np) {
     pa.np = np;
-    slab3_prep_kernel<R><<<dim3(cdiv(B, 128), nr, np), 128, 0, s>>>(pa);
+    launch_pdl3(slab3_prep_kernel<R>, dim3(cdiv(B, 128), nr, np), 128, s, pa);
   };
   auto gemv = [&](int np, int mode) {
     ga.np = np;
     ga.mode = mode;
     timed(h, "slab3_gemv", np * (gbytes + 2.0 * nr * B * el), s,
-          [&] { slab3_gemv_kernel<R, NR><<<dim3(gblocks, np), 256, 0, s>>>(ga); });
+          [&] { launch_pdl3(slab3_gemv_kernel<R, NR>, dim3(gblocks, np), 256, s, ga); });
   };
   // forward: y_t = G_t (f_t - L_t y_{t-1}), both chains per launch
   for (int t = 0; t < T; ++t) {
@@ -878,25 +1015,17 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
   HZ_CU(cudaGetLastError());
 }
 
-// Right-hand sides in chunks of at most 8 (compile-time accumulators of the GEMV).
+// All right-hand sides in one pass; the GEMV takes them in chunks of at most
+// 8 (its compile-time accumulators) inside each launch.
 template <typename R>
 void run_solve3d_all(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int n_rhs,
-                     size_t in_stride, size_t out_stride, cudaStream_t s) {
+                     cudaStream_t s) {
   q.nr_tot = o.nr_tot = n_rhs;
-  for (int r0 = 0; r0 < n_rhs; r0 += 8) {
-    const int nr = std::min(8, n_rhs - r0);
-    Rhs3<R> qc = q;
-    Out3<R> oc = o;
-    qc.r0 = oc.r0 = r0;
-    if (qc.raw) qc.raw += (size_t)r0 * in_stride;
-    if (qc.f) qc.f += (size_t)r0 * in_stride;
-    if (oc.raw) oc.raw += (size_t)r0 * out_stride;
-    if (oc.u) oc.u += (size_t)r0 * out_stride;
-    if (nr == 1) run_solve3d<R, 1>(h, L, S, qc, oc, nr, s);
-    else if (nr == 2) run_solve3d<R, 2>(h, L, S, qc, oc, nr, s);
-    else if (nr <= 4) run_solve3d<R, 4>(h, L, S, qc, oc, nr, s);
-    else run_solve3d<R, 8>(h, L, S, qc, oc, nr, s);
-  }
+  q.r0 = o.r0 = 0;
+  if (n_rhs == 1) run_solve3d<R, 1>(h, L, S, q, o, n_rhs, s);
+  else if (n_rhs == 2) run_solve3d<R, 2>(h, L, S, q, o, n_rhs, s);
+  else if (n_rhs <= 4) run_solve3d<R, 4>(h, L, S, q, o, n_rhs, s);
+  else run_solve3d<R, 8>(h, L, S, q, o, n_rhs, s);
 }
 
 }  // namespace
@@ -922,8 +1051,7 @@ void subdom_solve3d(hz_handle* h, Level& L, int j, const cplx<R>* f, int a, int 
   o.u = u; o.nx = L.nx; o.lo = S.lo; o.wl = S.wl; o.ua = at; o.ub = bt;
   o.B2 = tau2 ? B2 : nullptr; o.e2 = tau2 ? loc(L.beta[j]) : -1;
   o.B4 = tau4 ? B4 : nullptr; o.e4 = tau4 ? loc(L.beta_t[j - 1]) : -1;
-  const size_t n = L.size();
-  timed(h, "slab_solve3d", 0.0, s, [&] { run_solve3d_all<R>(h, L, S, q, o, n_rhs, n, n, s); });
+  timed(h, "slab_solve3d", 0.0, s, [&] { run_solve3d_all<R>(h, L, S, q, o, n_rhs, s); });
 }
 
 template <typename R>
@@ -934,8 +1062,7 @@ void slab_solve_raw3d(hz_handle* h, Level& L, int j, const cplx<R>* fd, cplx<R>*
   q.raw = fd; q.ef = -1; q.eb = -1;
   Out3<R> o{};
   o.raw = ud; o.e2 = -1; o.e4 = -1;
-  const size_t n = L.nt() * S.W;
-  run_solve3d_all<R>(h, L, S, q, o, n_rhs, n, n, s);
+  run_solve3d_all<R>(h, L, S, q, o, n_rhs, s);
 }
 
 template void build_slabs3d<float>(hz_handle*, Level&, cudaStream_t);
