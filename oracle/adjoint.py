@@ -2,8 +2,10 @@
 
 Misfit: Phi(m) = 1/2 sum_s sum_q |u_s(x_q) - d_{s,q}|^2 with A(m) u_s = b_s,
 A the h^d-scaled Eq. 40 and b_s independent of m.  Only the mass term of Eq. 40
-depends on m (k^2 = omega^2 m): dA/dm_i = -omega^2 w_i e_i e_i^T with
-w_i = h^d / prod_l alpha_{l,i}.  The PML parameters (c_pml) are held fixed.
+depends on m (k^2 = omega^2 m s, s = (1 + i beta)^2 in a sponge layer of
+Section 2.1, else 1): dA/dm_i = -omega^2 w_i e_i e_i^T with
+w_i = h^d s_i / prod_l alpha_{l,i}.  The PML and sponge parameters (c_pml) are
+held fixed.
 With r_s = R u_s - d_s (R: sampling at the receivers) and A complex symmetric,
 mu_s solving A mu_s = conj(R^T r_s) gives
 
@@ -25,7 +27,8 @@ def misfit_and_gradient(problem, src_nodes_flat, rec_flat, d_obs):
     A = problem.A.tocsc()
     lu = spla.splu(A)
     n = A.shape[0]
-    w = fd.rhs_scaling(problem.axes, problem.omega).ravel()     # h^d / prod alpha
+    # h^d s / prod alpha
+    w = (fd.rhs_scaling(problem.axes, problem.omega) * problem.sponge).ravel()
     phi = 0.0
     grad = np.zeros(n)
     us = []

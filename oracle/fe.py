@@ -118,7 +118,9 @@ def assemble(axes: list[Axis], k2cell: np.ndarray, omega: float, H: float,
     ac = [ax.alpha_cell(omega) for ax in axes]
     vol = functools.reduce(np.multiply, [_bc(hc[l], l, d) for l in range(d)])
     palpha = functools.reduce(np.multiply, [_bc(ac[l], l, d) for l in range(d)])
-    inv_G = H * np.sqrt(k2cell) / (2.0 * np.pi)
+    # G from the cell's wavenumber; in a sponge (complex k^2 = k^2 (1 + i beta)^2)
+    # from its real part k (reading: the damping does not change the coefficients)
+    inv_G = H * np.real(np.sqrt(k2cell.astype(np.complex128))) / (2.0 * np.pi)
     c = coefficients(inv_G, d) if coeffs is None else [np.full(cshape, float(v)) for v in coeffs]
     I, Jc = fe_constants(c, d)
     mass = vol * k2cell / palpha

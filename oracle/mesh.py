@@ -60,6 +60,35 @@ def fine_axis(n_cells: int, w_out: int, h: float, s_pml: float, c_pml: float) ->
     return Axis(h_cell=np.full(n_cells, h), sigma_node=sigma(x_node), sigma_cell=sigma(x_mid))
 
 
+def sponge_beta_max(damping: float, k_ref: float, width: float) -> float:
+    """beta_max of a quadratic sponge profile beta(d) = beta_max (d / width)^2
+    whose one-way amplitude damping exp(-int k beta dx) = exp(-k beta_max
+    width / 3) equals `damping` at the wavenumber k_ref (Section 2.1: k is
+    replaced by k (1 + i beta) in the sponge; reading: the damping is set at
+    the typical wavenumber omega / c_pml)."""
+    return 3.0 * np.log(1.0 / damping) / (k_ref * width)
+
+
+def sponge_beta(n_cells: int, w_out: int, h: float, beta_max: float) -> np.ndarray:
+    """beta at the unknowns of a uniform axis whose outer w_out cells on both
+    sides form the sponge: quadratic in the distance beyond the interior box
+    (the same geometry as the PML profile of Eq. 5), zero inside."""
+    if w_out == 0:
+        return np.zeros(n_cells - 1)
+    lo, hi = w_out * h, (n_cells - w_out) * h
+    x = np.arange(1, n_cells) * h
+    d = np.maximum(0.0, np.maximum(lo - x, x - hi))
+    return beta_max * (d / (w_out * h)) ** 2
+
+
+def sponge_factor(betas: list) -> np.ndarray:
+    """(1 + i beta)^2 on the tensor grid, beta = sum of the per-axis profiles
+    (reading of beta(x, y)): k^2 -> k^2 (1 + i beta)^2."""
+    import functools
+    b = functools.reduce(np.add.outer, betas) if len(betas) > 1 else betas[0]
+    return (1.0 + 1j * b) ** 2
+
+
 def coarse_axis(n_int: int, w_out: int, h: float, s_pml: float, c_pml: float):
     """PML-aware coarsening of a fine axis (Section 4.2).
 

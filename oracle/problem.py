@@ -36,12 +36,27 @@ class Problem:
         h = cfg.h
         # "typical velocity" of the PML (Section 2.1): mean wave speed unless fixed
         self.c_pml = float(np.mean(1.0 / np.sqrt(self.m))) if c_pml is None else float(c_pml)
-        self.axes = [mesh.fine_axis(c + 2 * cfg.w_out, cfg.w_out, h, cfg.s_out, self.c_pml)
+        # outer boundary layers: PML (Eq. 5), or a sponge (Section 2.1: k ->
+        # k (1 + i beta), no PML: alpha = 1) with the standard two-grid cycle of
+        # Section 4.1 (every cell coarsened)
+        self.boundary = getattr(cfg, "boundary", "pml")
+        sponge = self.boundary == "sponge"
+        s_out = 0.0 if sponge else cfg.s_out
+        self.axes = [mesh.fine_axis(c + 2 * cfg.w_out, cfg.w_out, h, s_out, self.c_pml)
                      for c in cfg.cells]
-        self.k2 = self.omega ** 2 * self.m
+        self.sponge = np.ones(cfg.shape)
+        if sponge:
+            bmax = mesh.sponge_beta_max(cfg.sponge_damping, self.omega / self.c_pml, cfg.w_out * h)
+            self.sponge = mesh.sponge_factor([mesh.sponge_beta(c + 2 * cfg.w_out, cfg.w_out, h, bmax)
+                                              for c in cfg.cells])
+        self.k2 = self.omega ** 2 * self.m * self.sponge
         self.A = fd.assemble(self.axes, self.k2, self.omega)
         if self.two_grid:
-            co = [mesh.coarse_axis(c, cfg.w_out, h, cfg.s_out, self.c_pml) for c in cfg.cells]
+            if sponge:     # standard coarsening: all cells merged in pairs, no PML
+                co = [mesh.coarse_axis(c + 2 * cfg.w_out, 0, h, 0.0, self.c_pml)
+                      for c in cfg.cells]
+            else:
+                co = [mesh.coarse_axis(c, cfg.w_out, h, cfg.s_out, self.c_pml) for c in cfg.cells]
             self.caxes = [c[0] for c in co]
             self.k2c = fe.coarse_k2(self.k2, [c[1] for c in co], [c[2] for c in co])
             H = 2.0 * h

@@ -46,6 +46,8 @@ class Workload:
     n_rec: int = 0
     dims: Optional[Tuple[int, ...]] = None   # interior cells per axis (array order z, y, x);
                                             # None: n on every axis; dims[-1] must equal n
+    boundary: str = "pml"                    # outer layers: "pml" (Eq. 5) | "sponge"
+    sponge_damping: float = 1e-2             # sponge: one-way amplitude damping of the layer
 
     @property
     def cells(self) -> Tuple[int, ...]:

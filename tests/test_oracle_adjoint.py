@@ -1,7 +1,10 @@
 """Pins of the oracle's adjoint gradient (oracle/adjoint.py) to mathematics:
 central finite differences of the misfit (directional and per node), the
 zero gradient at the true model, and the complex symmetry of A that lets the
-adjoint solve reuse A."""
+adjoint solve reuse A; with sponge layers (k^2 = omega^2 m (1 + i beta)^2,
+Section 2.1) the finite differences also pin the sponge factor in dA/dm."""
+
+import dataclasses
 
 import numpy as np
 import pytest
@@ -12,8 +15,8 @@ from oracle import adjoint, problem
 pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
 
 
-def _setup(n=32):
-    cfg = synth.adjoint_workload_2d(n)
+def _setup(n=32, boundary="pml"):
+    cfg = dataclasses.replace(synth.adjoint_workload_2d(n), boundary=boundary)
     m_true = synth.medium(cfg, "true")
     m0 = synth.medium(cfg, "start")
     c_pml = float(np.mean(1.0 / np.sqrt(m0)))
@@ -47,8 +50,9 @@ def test_zero_at_true_model():
     assert np.abs(g).max() < 1e-10
 
 
-def test_directional_finite_difference():
-    cfg, m_true, m0, c_pml, src, rec, d = _setup()
+@pytest.mark.parametrize("boundary", ["pml", "sponge"])
+def test_directional_finite_difference(boundary):
+    cfg, m_true, m0, c_pml, src, rec, d = _setup(boundary=boundary)
     p = problem.Problem(cfg, m0, two_grid=False, c_pml=c_pml)
     phi, g, _ = adjoint.misfit_and_gradient(p, src, rec, d)
     assert phi > 0
@@ -62,10 +66,11 @@ def test_directional_finite_difference():
         assert abs(fd - an) <= 1e-6 * abs(an) + 1e-12 * phi, (fd, an)
 
 
-def test_per_node_finite_difference():
+@pytest.mark.parametrize("boundary", ["pml", "sponge"])
+def test_per_node_finite_difference(boundary):
     """Brute force: the partial derivative at single nodes, including one in
-    the outer PML, one at a source and one at a receiver."""
-    cfg, m_true, m0, c_pml, src, rec, d = _setup()
+    the outer PML (or sponge), one at a source and one at a receiver."""
+    cfg, m_true, m0, c_pml, src, rec, d = _setup(boundary=boundary)
     p = problem.Problem(cfg, m0, two_grid=False, c_pml=c_pml)
     phi, g, _ = adjoint.misfit_and_gradient(p, src, rec, d)
     nodes = [int(src[3]), int(rec[5]), 2 * cfg.N + 3, (cfg.N // 2) * cfg.N + cfg.N // 2]
