@@ -61,14 +61,14 @@ typedef struct {
   int    dim;           /* 2 or 3 */
   int    n[3];          /* interior cells along x (the sweep axis), y, z (n[2]: 3-D only;
                          * even when two_grid) */
-  int    w_out;         /* outer PML cells per side */
+  int    w_out;         /* outer layer (PML or sponge) cells per side */
   double h;             /* cell size of every axis (0: 1 / n[0]) */
   double omega;         /* angular frequency; k = omega / c, k^2 = omega^2 m */
   double s_pml_out;     /* outer PML strength S_pml (Section 2.1) */
   double s_pml_dd;      /* DD PML strength (Section 6.1: 15/20/25 for w = 3/4/5) */
   int    J;             /* slabs along x (even for HZ_SWEEP_X) */
   int    w_dd;          /* DD PML width in cells (Section 2.1: 3..5) */
-  int    sweep;         /* HZ_SWEEP_UD | HZ_SWEEP_X */
+  int    sweep;         /* HZ_SWEEP_UD | HZ_SWEEP_X | HZ_SWEEP_NX */
   int    two_grid;      /* 0: sweep on the fine grid; 1: TGSP (Section 4) */
   int    nu;            /* omega-Jacobi pre- and post-smoothing steps */
   double omega_jac;     /* Jacobi relaxation weight */
@@ -86,7 +86,16 @@ typedef struct {
                          * j_cell = 0, round(m (J+1) / N_cell), J+1; centres
                          * j_mid = (j_cell[m-1] + j_cell[m] + 1) / 2); N_cell = 1
                          * is the X-sweep.  Ignored by the other patterns */
+  int    boundary;      /* outer layers of w_out cells: HZ_BOUNDARY_PML (Eq. 5) or
+                         * HZ_BOUNDARY_SPONGE (Section 2.1: k -> k (1 + i beta), no
+                         * PML; beta = sum over the axes of beta_max (d / (w_out h))^2,
+                         * d the distance beyond the interior box; two_grid then
+                         * coarsens every cell: n[l] + 2 w_out even, Section 4.1) */
+  double sponge_damping;/* sponge: one-way amplitude damping exp(-k beta_max w_out h / 3)
+                         * of the layer at k = omega / c_pml, in (0, 1) */
 } hz_params;
+
+enum { HZ_BOUNDARY_PML = 0, HZ_BOUNDARY_SPONGE = 1 };
 
 typedef struct {
   int    n_rhs;

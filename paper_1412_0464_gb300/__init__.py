@@ -19,6 +19,7 @@ from .build import LIB, build  # noqa: F401
 HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_ENOTFACTORED, HZ_ENOTCONV, HZ_ETIMEOUT, HZ_EINACCURATE = range(8)
 HZ_SWEEP_UD, HZ_SWEEP_X, HZ_SWEEP_NX = 0, 1, 2
 HZ_PLAIN_FP64, HZ_MIXED = 0, 1
+HZ_BOUNDARY_PML, HZ_BOUNDARY_SPONGE = 0, 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hz.h")
 
@@ -32,7 +33,8 @@ class hz_params(ctypes.Structure):
         ("two_grid", ctypes.c_int), ("nu", ctypes.c_int), ("omega_jac", ctypes.c_double),
         ("precision", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_iter", ctypes.c_int),
         ("tol", ctypes.c_double), ("max_rhs", ctypes.c_int), ("segments", ctypes.c_int),
-        ("c_pml", ctypes.c_double), ("n_cell", ctypes.c_int),
+        ("c_pml", ctypes.c_double), ("n_cell", ctypes.c_int), ("boundary", ctypes.c_int),
+        ("sponge_damping", ctypes.c_double),
     ]
 
 
@@ -165,7 +167,7 @@ class Solver:
     def __init__(self, m, *, n, w_out, omega, J, w_dd, s_dd, s_out=20.0, sweep="X",
                  precision="mixed", gmres_m=30, max_iter=500, tol=1e-6, max_rhs=1,
                  two_grid=False, nu=3, omega_jac=0.8, segments=0, c_pml=0.0, dim=2, dims=None,
-                 h=0.0, n_cell=2):
+                 h=0.0, n_cell=2, boundary="pml", sponge_damping=1e-2):
         import torch
         dims = tuple(dims) if dims is not None else (n,) * dim
         assert len(dims) == dim and dims[-1] == n
@@ -173,11 +175,17 @@ class Solver:
         self.N = n + 2 * w_out - 1
         self.shape = tuple(c + 2 * w_out - 1 for c in dims)
         # transverse unknowns of the level that carries the slabs (the coarse
-        # level of the two-grid cycle, else the fine grid)
-        cells_t = [c // 2 if two_grid else c for c in dims[:-1]]
+        # level of the two-grid cycle, else the fine grid; the coarse grid of a
+        # sponge merges every cell in pairs)
+        sponge = boundary == "sponge"
         self.slab_nt = 1
-        for c in cells_t:
-            self.slab_nt *= c + 2 * w_out - 1
+        for c in dims[:-1]:
+            if not two_grid:
+                self.slab_nt *= c + 2 * w_out - 1
+            elif sponge:
+                self.slab_nt *= (c + 2 * w_out) // 2 - 1
+            else:
+                self.slab_nt *= c // 2 + 2 * w_out - 1
         p = hz_params()
         p.dim, p.w_out, p.omega, p.h = dim, w_out, omega, h
         for l, c in enumerate(reversed(dims)):      # hz_params.n is (x, y, z)
@@ -189,6 +197,8 @@ class Solver:
         p.precision = HZ_MIXED if precision == "mixed" else HZ_PLAIN_FP64
         p.gmres_m, p.max_iter, p.tol, p.max_rhs, p.segments = gmres_m, max_iter, tol, max_rhs, segments
         p.c_pml = c_pml
+        p.boundary = {"pml": HZ_BOUNDARY_PML, "sponge": HZ_BOUNDARY_SPONGE}[boundary]
+        p.sponge_damping = sponge_damping
         self.params = p
         md = torch.as_tensor(m, dtype=torch.float64).to("cuda").contiguous()
         assert md.shape == self.shape
@@ -206,7 +216,9 @@ class Solver:
         kw = dict(n=cfg.n, w_out=cfg.w_out, omega=cfg.omega, J=cfg.J, w_dd=cfg.w_dd, s_dd=cfg.s_dd,
                   s_out=cfg.s_out, sweep=cfg.sweep, precision=cfg.precision, gmres_m=cfg.gmres_m,
                   tol=cfg.tol, max_rhs=cfg.n_src, two_grid=cfg.two_grid, nu=cfg.nu,
-                  omega_jac=cfg.omega_jac, dim=cfg.dim, dims=cfg.cells)
+                  omega_jac=cfg.omega_jac, dim=cfg.dim, dims=cfg.cells,
+                  boundary=getattr(cfg, "boundary", "pml"),
+                  sponge_damping=getattr(cfg, "sponge_damping", 1e-2))
         kw.update(over)
         return cls(m, **kw)
 

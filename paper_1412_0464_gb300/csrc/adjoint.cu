@@ -1,8 +1,8 @@
 // Adjoint gradient of the receiver misfit
 //   Phi(m) = 1/2 sum_s sum_q |u_s(x_q) - d_{s,q}|^2,   A(m) u_s = e_{src_s}.
-// Only the mass term of Eq. 40 depends on m (k^2 = omega^2 m), so
-// dA/dm_i = -omega^2 w_i e_i e_i^T with w_i = h^d / (alpha_x alpha_y)_i, the
-// PML held fixed.  A is complex symmetric (Eq. 40), so the adjoint field solves
+// Only the mass term of Eq. 40 depends on m (k^2 = omega^2 m s, s = (1 + i beta)^2
+// in a sponge layer of Section 2.1, else 1), so dA/dm_i = -omega^2 w_i e_i e_i^T
+// with w_i = h^d s_i / (alpha_x alpha_y)_i, the PML and sponge held fixed.  A is complex symmetric (Eq. 40), so the adjoint field solves
 // A mu_s = conj(R^T r_s) with the same preconditioner and factors, and
 //   dPhi/dm_i = omega^2 Re(w_i sum_s mu_{s,i} u_{s,i}).
 // Sources are taken in batches of max_rhs: one forward and one adjoint
@@ -41,10 +41,11 @@ __global__ void receiver_residual_kernel(const c128* u, size_t n, const int* rec
   phi[k] = 0.5 * acc;
 }
 
-// grad_i += omega^2 Re( h^d / (alpha_x alpha_y [alpha_z])_i * sum_k mu_k,i u_k,i )
-// (scale = omega^2 h^d; az is null in 2-D)
+// grad_i += omega^2 Re( h^d s_i / (alpha_x alpha_y [alpha_z])_i * sum_k mu_k,i u_k,i )
+// (scale = omega^2 h^d; az and bz are null in 2-D, bx null without a sponge)
 __global__ void grad_accumulate_kernel(const c128* u, const c128* mu, int nb, int nx, int ny,
                                        int nz, const c128* ax, const c128* ay, const c128* az,
+                                       const double* bx, const double* by, const double* bz,
                                        double scale, double* grad) {
   const size_t n = (size_t)nx * ny * nz;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -56,7 +57,9 @@ __global__ void grad_accumulate_kernel(const c128* u, const c128* mu, int nb, in
     const int iy = (int)(iyz % ny), iz = (int)(iyz / ny);
     c128 pa = ax[ix] * ay[iy];
     if (az) pa = pa * az[iz];
-    grad[i] += scale * (cinv(pa) * acc).re;
+    c128 w = cinv(pa);
+    if (bx) w = w * sponge_s(bx[ix] + by[iy] + (bz ? bz[iz] : 0.0));
+    grad[i] += scale * (w * acc).re;
   }
 }
 
@@ -118,7 +121,8 @@ void misfit_grad(hz_handle* h, const int* src, int n_src, const int* rec, int n_
     solve(h->gr_b, h->gr_mu, nb);
     grad_accumulate_kernel<<<4 * h->sms, 256, 0, s>>>(
         h->gr_u, h->gr_mu, nb, F.nx, F.ny, F.nz, F.ax.a_node, F.ay.a_node,
-        F.dim3d ? F.az.a_node : nullptr, scale, grad);
+        F.dim3d ? F.az.a_node : nullptr, F.ax.beta, F.ay.beta, F.dim3d ? F.az.beta : nullptr,
+        scale, grad);
     h->launches++;
     HZ_CU(cudaMemcpyAsync(hphi.data(), h->gr_phi, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     HZ_CU(cudaStreamSynchronize(s));

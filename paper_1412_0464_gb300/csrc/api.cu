@@ -105,7 +105,17 @@ void validate(const hz_params* p) {
   if (!(p->c_pml >= 0)) bad("c_pml must be >= 0 (0: mean wave speed)");
   if (p->max_rhs < 1 || p->max_rhs > 64) bad("max_rhs must be in 1..64");
   if (p->two_grid && (p->nu < 0 || !(p->omega_jac > 0))) bad("bad smoother parameters");
-  int N = p->two_grid ? 2 * p->w_out + p->n[0] / 2 - 1 : p->n[0] + 2 * p->w_out - 1;
+  if (p->boundary != HZ_BOUNDARY_PML && p->boundary != HZ_BOUNDARY_SPONGE)
+    bad("boundary must be HZ_BOUNDARY_PML or HZ_BOUNDARY_SPONGE");
+  if (p->boundary == HZ_BOUNDARY_SPONGE) {
+    if (p->w_out < 1) bad("a sponge needs w_out >= 1");
+    if (!(p->sponge_damping > 0 && p->sponge_damping < 1)) bad("sponge_damping must be in (0, 1)");
+  }
+  // slab columns of the level carrying the decomposition (the coarse grid of
+  // a sponge keeps no layers: every cell is merged in pairs)
+  int N = !p->two_grid ? p->n[0] + 2 * p->w_out - 1
+          : p->boundary == HZ_BOUNDARY_SPONGE ? (p->n[0] + 2 * p->w_out) / 2 - 1
+                                              : 2 * p->w_out + p->n[0] / 2 - 1;
   if (N / p->J < 4) bad("slabs too thin: fewer than 4 columns per slab");
 }
 

@@ -101,12 +101,16 @@ __device__ __forceinline__ Avg1 avg_axis(int c, const int* ifp, const int* refin
   return a;
 }
 
-// Coarse cell k^2 = omega^2 * tensor average of the fine nodal m.  2-D: z
-// axis trivial (ncz = 1, the single weight 1).
+// Coarse cell k^2 = omega^2 * tensor average of the fine nodal m (times the
+// sponge factor (1 + i beta)^2 when the fine level has a sponge: k2ci then
+// receives the imaginary part).  2-D: z axis trivial (ncz = 1, the single
+// weight 1).
 __global__ void coarse_k2_kernel(int ncx, int ncy, int ncz, int Nfx, int Nfy, int Nfz,
                                  const int* ifpx, const int* refx, const int* ifpy,
                                  const int* refy, const int* ifpz, const int* refz,
-                                 const double* m_fine, double omega2, double* k2c) {
+                                 const double* m_fine, double omega2, double* k2c,
+                                 const double* bfx, const double* bfy, const double* bfz,
+                                 double* k2ci) {
   const int cx = blockIdx.x * blockDim.x + threadIdx.x;
   const int cy = blockIdx.y, cz = blockIdx.z;
   if (cx >= ncx || cy >= ncy || cz >= ncz) return;
@@ -118,19 +122,38 @@ __global__ void coarse_k2_kernel(int ncx, int ncy, int ncz, int Nfx, int Nfy, in
     az.u[0] = az.u[1] = az.u[2] = 0;
     az.w[0] = 0.0; az.w[1] = 1.0; az.w[2] = 0.0;
   }
-  double acc = 0;
+  c128 acc = mk(0.0, 0.0);
   for (int c = 0; c < 3; ++c) {
     if (az.w[c] == 0.0) continue;
     for (int a = 0; a < 3; ++a) {
       if (ay.w[a] == 0.0) continue;
       for (int b = 0; b < 3; ++b) {
         if (ax.w[b] == 0.0) continue;
-        acc += az.w[c] * ay.w[a] * ax.w[b] *
-               m_fine[((size_t)az.u[c] * Nfy + ay.u[a]) * Nfx + ax.u[b]];
+        const double wm = az.w[c] * ay.w[a] * ax.w[b] *
+                          m_fine[((size_t)az.u[c] * Nfy + ay.u[a]) * Nfx + ax.u[b]];
+        if (bfx) {
+          const double beta = bfx[ax.u[b]] + bfy[ay.u[a]] + (bfz ? bfz[az.u[c]] : 0.0);
+          acc = acc + wm * sponge_s(beta);
+        } else {
+          acc.re += wm;
+        }
       }
     }
   }
-  k2c[((size_t)cz * ncy + cy) * ncx + cx] = omega2 * acc;
+  const size_t o = ((size_t)cz * ncy + cy) * ncx + cx;
+  k2c[o] = omega2 * acc.re;
+  if (k2ci) k2ci[o] = omega2 * acc.im;
+}
+
+// The cell's complex k^2 and the real wavenumber Re sqrt(k^2) used for G
+// (in a sponge k^2 (1 + i beta)^2 -> k; the damping does not change the
+// Table 9 coefficients).
+__device__ __forceinline__ c128 cell_k2(const double* k2c, const double* k2ci, size_t o,
+                                        double* kreal) {
+  const double re = k2c[o], im = k2ci ? k2ci[o] : 0.0;
+  const double mod = sqrt(re * re + im * im);
+  *kreal = sqrt(fmax(0.0, 0.5 * (mod + re)));
+  return mk(re, im);
 }
 
 __device__ __forceinline__ void table9_2d(double inv_G, double c[3]) {
@@ -162,6 +185,7 @@ struct FeMesh {
   int lo, hi, wl;             // column of cell cx in k2c: clamp(cx - wl + lo, lo, hi + 1)
   double H, omega;            // reference spacing for G
   size_t sq, sk, sx;          // output index = q*sq + k*sk + x*sx, q = (dy+1)*3 + (dx+1)
+  const double* k2ci;         // imaginary part of the cell k^2 (sponge) or null
 };
 
 // Assemble the 9-point FE stencil of every unknown of the mesh.
@@ -179,14 +203,15 @@ __global__ void fe_assemble_kernel(FeMesh ms, cplx<R>* out) {
       const int cx = x + cxo;
       const int ax_ = cxo == 0 ? 1 : 0;
       const int gcx = min(max(cx - ms.wl + ms.lo, ms.lo), ms.hi + 1);
-      const double k2 = ms.k2c[(size_t)cy * ms.k2_ld + gcx];
+      double kr;
+      const c128 k2 = cell_k2(ms.k2c, ms.k2ci, (size_t)cy * ms.k2_ld + gcx, &kr);
       const double hx = ms.hx[cx], hy = ms.hy[cy];
       const c128 alx = ms.ax[cx], aly = ms.ay[cy];
       double c[3];
-      table9_2d(ms.H * sqrt(k2) / (2.0 * M_PI), c);
+      table9_2d(ms.H * kr / (2.0 * M_PI), c);
       const double I[3] = {c[0] / 4, c[1] / 8, (1 - c[0] - c[1]) / 4};
       const double Jc[2] = {c[2] / 2, (1 - c[2]) / 2};
-      const c128 mass = (hx * hy * k2) * cinv(alx * aly);
+      const c128 mass = (hx * hy) * (k2 * cinv(alx * aly));
       const c128 sx_ = (hy / hx) * (alx * cinv(aly));    // (alpha_x/h_x)(h_y/alpha_y)
       const c128 sy_ = (hx / hy) * (aly * cinv(alx));    // (alpha_y/h_y)(h_x/alpha_x)
       for (int by = 0; by < 2; ++by) {
@@ -224,6 +249,7 @@ struct FeMesh3 {
   int lo, hi, wl;
   double H, omega;
   size_t sq, sz, sy, sx;
+  const double* k2ci;         // imaginary part of the cell k^2 (sponge) or null
 };
 
 template <typename R>
@@ -243,7 +269,9 @@ __global__ void fe3_assemble_kernel(FeMesh3 ms, cplx<R>* out) {
       corner[l] = o == 0 ? 1 : 0;           // the node's corner index in that cell
     }
     const int gcx = min(max(cell[0] - ms.wl + ms.lo, ms.lo), ms.hi + 1);
-    const double k2 = ms.k2c[((size_t)cell[2] * ms.k2_ny1 + cell[1]) * ms.k2_ld + gcx];
+    double kr;
+    const c128 k2 =
+        cell_k2(ms.k2c, ms.k2ci, ((size_t)cell[2] * ms.k2_ny1 + cell[1]) * ms.k2_ld + gcx, &kr);
     double hl[3];
     c128 al[3];
     for (int l = 0; l < 3; ++l) {
@@ -251,7 +279,7 @@ __global__ void fe3_assemble_kernel(FeMesh3 ms, cplx<R>* out) {
       al[l] = ms.a[l][cell[l]];
     }
     double c[5];
-    table9_3d(ms.H * sqrt(k2) / (2.0 * M_PI), c);
+    table9_3d(ms.H * kr / (2.0 * M_PI), c);
     const double I[4] = {c[0] / 8, c[1] / 24, c[2] / 24, (1 - c[0] - c[1] - c[2]) / 8};
     const double Jc[3] = {c[3] / 4, c[4] / 8, (1 - c[3] - c[4]) / 4};
     const c128 pa = al[0] * al[1] * al[2];
@@ -410,6 +438,15 @@ void build_level_fe(hz_handle* h, Level& L, const Level& fine, const int* n_int,
                     double hh, cudaStream_t s) {
   const int d = fine.dim3d ? 3 : 2;
   L.dim3d = fine.dim3d;
+  // sponge: standard coarsening (Section 4.1), every fine cell merged in
+  // pairs, no kept layers and no PML on the coarse grid
+  const bool sponge = h->p.boundary == HZ_BOUNDARY_SPONGE;
+  int n_in[3] = {n_int[0], n_int[1], d == 3 ? n_int[2] : 0};
+  if (sponge) {
+    for (int l = 0; l < d; ++l) n_in[l] += 2 * w_out;
+    w_out = 0;
+  }
+  n_int = n_in;
   int n_c[3] = {1, 1, 1};
   for (int l = 0; l < d; ++l) n_c[l] = 2 * w_out + n_int[l] / 2;
   L.nx = n_c[0] - 1;
@@ -436,24 +473,27 @@ void build_level_fe(hz_handle* h, Level& L, const Level& fine, const int* n_int,
                                                               L.q0[l], L.q1[l]);
   }
   const int ncz = d == 3 ? n_c[2] : 1;
-  L.k2c = (double*)dmalloc(sizeof(double) * (size_t)n_c[0] * n_c[1] * ncz);
+  const size_t ncells = (size_t)n_c[0] * n_c[1] * ncz;
+  L.k2c = (double*)dmalloc(sizeof(double) * ncells);
+  if (sponge) L.k2ci = (double*)dmalloc(sizeof(double) * ncells);
   coarse_k2_kernel<<<dim3(cdiv(n_c[0], 128), n_c[1], ncz), 128, 0, s>>>(
       n_c[0], n_c[1], ncz, Nf[0], Nf[1], Nf[2], L.ifp[0], L.refined[0], L.ifp[1], L.refined[1],
-      L.ifp[2], L.refined[2], fine.m, h->p.omega * h->p.omega, L.k2c);
+      L.ifp[2], L.refined[2], fine.m, h->p.omega * h->p.omega, L.k2c, fine.ax.beta,
+      fine.ay.beta, d == 3 ? fine.az.beta : nullptr, L.k2ci);
   const size_t plane = L.size();
   const int nq = L.planes();
   L.st128 = (c128*)dmalloc(sizeof(c128) * nq * plane);
   L.st64 = (c64*)dmalloc(sizeof(c64) * nq * plane);
   if (d == 2) {
     FeMesh ms{L.nx, L.ny, L.ax.h_cell, L.ax.a_cell, L.ay.h_cell, L.ay.a_cell, L.k2c, n_c[0],
-              0, L.nx - 1, 0, L.h, h->p.omega, plane, (size_t)L.nx, 1};
+              0, L.nx - 1, 0, L.h, h->p.omega, plane, (size_t)L.nx, 1, L.k2ci};
     dim3 grid(cdiv(L.nx, 128), L.ny);
     fe_assemble_kernel<double><<<grid, 128, 0, s>>>(ms, L.st128);
     fe_assemble_kernel<float><<<grid, 128, 0, s>>>(ms, L.st64);
   } else {
     FeMesh3 ms{L.nx, L.ny, L.nz, {L.ax.h_cell, L.ay.h_cell, L.az.h_cell},
                {L.ax.a_cell, L.ay.a_cell, L.az.a_cell}, L.k2c, n_c[0], n_c[1], 0, L.nx - 1, 0,
-               L.h, h->p.omega, plane, (size_t)L.nx * L.ny, (size_t)L.nx, 1};
+               L.h, h->p.omega, plane, (size_t)L.nx * L.ny, (size_t)L.nx, 1, L.k2ci};
     dim3 grid(cdiv(L.nx, 64), L.ny, L.nz);
     fe3_assemble_kernel<double><<<grid, 64, 0, s>>>(ms, L.st128);
     fe3_assemble_kernel<float><<<grid, 64, 0, s>>>(ms, L.st64);
@@ -469,14 +509,14 @@ template <typename R>
 void slab_stencil_fe(hz_handle* h, const Level& L, const Slab& S, cudaStream_t s) {
   if (!L.dim3d) {
     FeMesh ms{S.W, L.ny, S.ax.h_cell, S.ax.a_cell, L.ay.h_cell, L.ay.a_cell, L.k2c, L.nx + 1,
-              S.lo, S.hi, S.wl, L.h, h->p.omega, (size_t)S.wp, (size_t)9 * S.wp, 1};
+              S.lo, S.hi, S.wl, L.h, h->p.omega, (size_t)S.wp, (size_t)9 * S.wp, 1, L.k2ci};
     dim3 grid(cdiv(S.W, 128), L.ny);
     fe_assemble_kernel<R><<<grid, 128, 0, s>>>(ms, (cplx<R>*)S.st);
   } else {
     const size_t B = (size_t)L.ny * S.W;
     FeMesh3 ms{S.W, L.ny, L.nz, {S.ax.h_cell, L.ay.h_cell, L.az.h_cell},
                {S.ax.a_cell, L.ay.a_cell, L.az.a_cell}, L.k2c, L.nx + 1, L.ny + 1, S.lo, S.hi,
-               S.wl, L.h, h->p.omega, B, 27 * B, (size_t)S.W, 1};
+               S.wl, L.h, h->p.omega, B, 27 * B, (size_t)S.W, 1, L.k2ci};
     dim3 grid(cdiv(S.W, 64), L.ny, L.nz);
     fe3_assemble_kernel<R><<<grid, 64, 0, s>>>(ms, (cplx<R>*)S.st3);
   }

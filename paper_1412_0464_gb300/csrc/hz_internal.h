@@ -91,8 +91,18 @@ struct AxisTables {
   c64* ia_node32 = nullptr;
   // unknowns in_lo..in_hi have alpha = 1 exactly at the node and both
   // adjacent cells (the PML-free interior; fine level only, empty if none)
+  // and no sponge damping
   int in_lo = 1, in_hi = 0;
+  double* beta = nullptr;    // [N] sponge profile at the unknowns (fine level; null: PML)
+  float* beta32 = nullptr;
 };
+
+// Sponge factor (1 + i beta)^2 of the mass term, beta the sum of the axes'
+// profiles (Section 2.1: k -> k (1 + i beta)).
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> sponge_s(R beta) {
+  return mk<R>((R)1 - beta * beta, (R)2 * beta);
+}
 
 // Slab j: core columns lo..hi, wl/wr added PML columns, W = width.
 struct Slab {
@@ -139,6 +149,7 @@ struct Level {
   c128* st128 = nullptr;     // FE level: 9 / 27 coefficient planes [q][nz][ny][nx]
   c64* st64 = nullptr;
   double* k2c = nullptr;     // FE level: cell k^2 [(nz+1)][(ny+1)][(nx+1)] ((ny+1)(nx+1) in 2-D)
+  double* k2ci = nullptr;    // FE level with a sponge: imaginary part of the cell k^2 (else null)
   int* ifp[3] = {};          // FE level, per axis x, y, z: coarse node -> fine node,
   int* refined[3] = {};      //   coarse cell refined flags,
   int* q0[3] = {};           //   prolongation sources per fine node

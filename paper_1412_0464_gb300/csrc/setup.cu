@@ -127,7 +127,8 @@ template <typename R>
 __global__ void slab_stencil_fd_kernel(int W, int wp, int ny, int lo, int hi, int wl, int nx,
                                        double h2w2, const double* m, const c128* sa_node,
                                        const c128* sa_cell, const c128* ay_node,
-                                       const c128* ay_cell, cplx<R>* st) {
+                                       const c128* ay_cell, const double* bx, const double* by,
+                                       cplx<R>* st) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
   if (e >= W || k >= ny) return;
@@ -137,7 +138,10 @@ __global__ void slab_stencil_fd_kernel(int W, int wp, int ny, int lo, int hi, in
   c128 inv_a1 = cinv(sa_node[e]);
   c128 a1l = sa_cell[e], a1r = sa_cell[e + 1];
   c128 a2d = ay_cell[k], a2u = ay_cell[k + 1];
-  c128 diag = inv_a2 * (a1l + a1r) + inv_a1 * (a2d + a2u) - (h2w2 * mm) * (inv_a1 * inv_a2);
+  // sponge: k^2 (1 + i beta)^2, frozen with k in the added columns (Eq. 10)
+  const c128 sp = bx ? sponge_s(bx[g] + by[k]) : mk(1.0, 0.0);
+  c128 diag = inv_a2 * (a1l + a1r) + inv_a1 * (a2d + a2u) -
+              (h2w2 * mm) * (sp * (inv_a1 * inv_a2));
   c128 z = mk(0.0, 0.0);
   c128 v[9];
   for (int q = 0; q < 9; ++q) v[q] = z;
@@ -241,6 +245,7 @@ static void alloc_axis(AxisTables& a, int N) {
 static void free_axis(AxisTables& a) {
   dfree(a.a_node); dfree(a.a_cell); dfree(a.h_cell); dfree(a.a_node32); dfree(a.a_cell32);
   dfree(a.ia_node); dfree(a.ia_node32);
+  dfree(a.beta); dfree(a.beta32);
   a = AxisTables{};
 }
 
@@ -297,7 +302,14 @@ void build_level_fd(hz_handle* h, Level& L, const int* n_int, int w_out, double 
   L.nz = dim3d ? n_int[2] + 2 * w_out - 1 : 1;
   L.h = hh;
   L.fe = false;
-  double C = (w_out > 0) ? h->p.s_pml_out * h->c_pml / std::pow(w_out * hh, 3) : 0.0;
+  const bool sponge = h->p.boundary == HZ_BOUNDARY_SPONGE;
+  // the outer layers: PML (Eq. 5), or a sponge (no PML; alpha = 1)
+  double C = (w_out > 0 && !sponge) ? h->p.s_pml_out * h->c_pml / std::pow(w_out * hh, 3) : 0.0;
+  // sponge: beta = beta_max (d / (w_out h))^2 per axis, beta_max from the
+  // one-way damping exp(-k beta_max w_out h / 3) at k = omega / c_pml
+  const double bmax = sponge ? 3.0 * std::log(1.0 / h->p.sponge_damping) /
+                                   (h->p.omega / h->c_pml * w_out * hh)
+                             : 0.0;
   AxisTables* axes[3] = {&L.ax, &L.ay, &L.az};
   for (int l = 0; l < (dim3d ? 3 : 2); ++l) {
     AxisTables* a = axes[l];
@@ -310,9 +322,25 @@ void build_level_fd(hz_handle* h, Level& L, const int* n_int, int w_out, double 
         N, n_cells, w_out, hh, C, h->p.omega, a->a_node, a->a_cell, a->h_cell, a->a_node32,
         a->a_cell32, a->ia_node, a->ia_node32);
     HZ_CU(cudaGetLastError());
-    // PML-free interior (the operator's coefficients are real there): the
-    // longest run of unknowns with 1/alpha = 1 at the node and alpha = 1 at
-    // both adjacent cells, read back from the tables just built
+    std::vector<double> beta(N, 0.0);
+    if (sponge) {
+      const double lo = w_out * hh, hi = (n_cells - w_out) * hh;
+      std::vector<float> b32(N);
+      for (int i = 0; i < N; ++i) {
+        const double x = (i + 1) * hh;
+        const double d = std::max(0.0, std::max(lo - x, x - hi)) / (w_out * hh);
+        beta[i] = bmax * d * d;
+        b32[i] = (float)beta[i];
+      }
+      a->beta = (double*)dmalloc(sizeof(double) * N);
+      a->beta32 = (float*)dmalloc(sizeof(float) * N);
+      HZ_CU(cudaMemcpyAsync(a->beta, beta.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+      HZ_CU(cudaMemcpyAsync(a->beta32, b32.data(), sizeof(float) * N, cudaMemcpyHostToDevice, s));
+    }
+    // PML- and sponge-free interior (the operator's coefficients are real
+    // there): the longest run of unknowns with 1/alpha = 1 at the node and
+    // alpha = 1 at both adjacent cells, read back from the tables just built,
+    // and beta = 0
     std::vector<c128> ia(N), ac(N + 1);
     HZ_CU(cudaMemcpyAsync(ia.data(), a->ia_node, sizeof(c128) * N, cudaMemcpyDeviceToHost, s));
     HZ_CU(cudaMemcpyAsync(ac.data(), a->a_cell, sizeof(c128) * (N + 1), cudaMemcpyDeviceToHost,
@@ -321,7 +349,7 @@ void build_level_fd(hz_handle* h, Level& L, const int* n_int, int w_out, double 
     auto one = [](const c128& v) { return v.re == 1.0 && v.im == 0.0; };
     int best_lo = 1, best_hi = 0, run = -1;
     for (int i = 0; i <= N; ++i) {
-      const bool ok = i < N && one(ia[i]) && one(ac[i]) && one(ac[i + 1]);
+      const bool ok = i < N && one(ia[i]) && one(ac[i]) && one(ac[i + 1]) && beta[i] == 0.0;
       if (ok && run < 0) run = i;
       if (!ok && run >= 0) {
         if (i - 1 - run > best_hi - best_lo) { best_lo = run; best_hi = i - 1; }
@@ -388,7 +416,8 @@ static void build_slabs_t(hz_handle* h, Level& L, cudaStream_t s) {
       double h2w2 = L.h * L.h * h->p.omega * h->p.omega;
       slab_stencil_fd_kernel<R><<<grid, 128, 0, s>>>(S.W, S.wp, L.ny, S.lo, S.hi, S.wl, L.nx, h2w2,
                                                      L.m, S.ax.a_node, S.ax.a_cell, L.ay.a_node,
-                                                     L.ay.a_cell, (cplx<R>*)S.st);
+                                                     L.ay.a_cell, L.ax.beta, L.ay.beta,
+                                                     (cplx<R>*)S.st);
       inj_fd_kernel<R><<<cdiv(L.ny, 128), 128, 0, s>>>(L.ny, beta, bt, L.ax.a_cell, L.ay.a_node,
                                                        (cplx<R>*)S.inj);
     } else {
@@ -479,7 +508,7 @@ void free_level(Level& L) {
   free_axis(L.ay);
   free_axis(L.az);
   dfree(L.m); dfree(L.m32); dfree(L.st128); dfree(L.st64); dfree(L.seg_dev);
-  dfree(L.k2c);
+  dfree(L.k2c); dfree(L.k2ci);
   for (int l = 0; l < 3; ++l) {
     dfree(L.ifp[l]); dfree(L.refined[l]); dfree(L.q0[l]); dfree(L.q1[l]);
   }

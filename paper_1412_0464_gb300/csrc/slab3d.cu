@@ -83,7 +83,9 @@ __global__ void slab3_stencil_fd_kernel(int W, int ny, int nz, int lo, int hi, i
                                         double hh, double h2w2, const double* m,
                                         const c128* sa_node, const c128* sa_cell,
                                         const c128* ay_node, const c128* ay_cell,
-                                        const c128* az_node, const c128* az_cell, cplx<R>* st) {
+                                        const c128* az_node, const c128* az_cell,
+                                        const double* bx, const double* by, const double* bz,
+                                        cplx<R>* st) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   if (e >= W) return;
@@ -97,8 +99,10 @@ __global__ void slab3_stencil_fd_kernel(int W, int ny, int nz, int lo, int hi, i
   const c128 zero = mk(0.0, 0.0);
   c128 v[27];
   for (int q = 0; q < 27; ++q) v[q] = zero;
+  // sponge: k^2 (1 + i beta)^2, frozen with k in the added columns (Eq. 10)
+  const c128 sp = bx ? sponge_s(bx[g] + by[y] + bz[z]) : mk(1.0, 0.0);
   v[qidx(0, 0, 0)] = hh * (s23 * (xl + xr) + s13 * (yl + yr) + s12 * (zl + zr)) -
-                     (hh * h2w2 * mm) * (s12 * i3);
+                     (hh * h2w2 * mm) * (sp * (s12 * i3));
   if (e > 0) v[qidx(0, 0, -1)] = -(hh * (s23 * xl));
   if (e < W - 1) v[qidx(0, 0, 1)] = -(hh * (s23 * xr));
   if (y > 0) v[qidx(0, -1, 0)] = -(hh * (s13 * yl));
@@ -177,7 +181,8 @@ void build_slabs3d(hz_handle* h, Level& L, cudaStream_t s) {
       const double h2w2 = L.h * L.h * h->p.omega * h->p.omega;
       slab3_stencil_fd_kernel<R><<<dim3(cdiv(S.W, 64), L.ny, L.nz), 64, 0, s>>>(
           S.W, L.ny, L.nz, S.lo, S.hi, S.wl, L.nx, L.h, h2w2, L.m, S.ax.a_node, S.ax.a_cell,
-          L.ay.a_node, L.ay.a_cell, L.az.a_node, L.az.a_cell, (cplx<R>*)S.st3);
+          L.ay.a_node, L.ay.a_cell, L.az.a_node, L.az.a_cell, L.ax.beta, L.ay.beta, L.az.beta,
+          (cplx<R>*)S.st3);
       inj3_kernel<R><<<dim3(cdiv(L.ny, 128), L.nz), 128, 0, s>>>(
           L.nx, L.ny, L.nz, beta, bt, L.h, L.ax.a_cell, L.ay.a_node, L.az.a_node, nullptr,
           (cplx<R>*)S.inj3);

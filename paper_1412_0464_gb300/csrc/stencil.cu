@@ -22,10 +22,12 @@ template <typename R> struct Tab;
 template <> struct Tab<double> {
   static const c128* inode(const AxisTables& a) { return a.ia_node; }
   static const c128* cell(const AxisTables& a) { return a.a_cell; }
+  static const double* beta(const AxisTables& a) { return a.beta; }
 };
 template <> struct Tab<float> {
   static const c64* inode(const AxisTables& a) { return a.ia_node32; }
   static const c64* cell(const AxisTables& a) { return a.a_cell32; }
+  static const float* beta(const AxisTables& a) { return a.beta32; }
 };
 template <typename R> struct Med;
 template <> struct Med<double> { static const double* m(const Level& L) { return L.m; } };
@@ -46,7 +48,9 @@ __device__ __forceinline__ cplx<R> fd_row(const cplx<R>* __restrict__ u, int nx,
                                           const cplx<R>* __restrict__ ia1n,
                                           const cplx<R>* __restrict__ a1c,
                                           const cplx<R>* __restrict__ ia2n,
-                                          const cplx<R>* __restrict__ a2c, cplx<R>* diag) {
+                                          const cplx<R>* __restrict__ a2c, cplx<R>* diag,
+                                          const R* __restrict__ bx = nullptr,
+                                          const R* __restrict__ by = nullptr) {
   const cplx<R> z = mk<R>(0, 0);
   cplx<R> uc = u[(size_t)k * nx + x];
   cplx<R> ul = (x > 0) ? u[(size_t)k * nx + x - 1] : z;
@@ -59,6 +63,7 @@ __device__ __forceinline__ cplx<R> fd_row(const cplx<R>* __restrict__ u, int nx,
   cplx<R> tx = (l + r) * uc - l * ul - r * ur;
   cplx<R> ty = (d + up) * uc - d * ud - up * uu;
   cplx<R> mass = (h2w2 * m[(size_t)k * nx + x]) * (ia1 * ia2);
+  if (bx) mass = mass * sponge_s<R>(bx[x] + by[k]);     // sponge: k^2 (1 + i beta)^2
   if (diag) *diag = ia2 * (l + r) + ia1 * (d + up) - mass;
   return ia2 * tx + ia1 * ty - mass * uc;
 }
@@ -117,7 +122,9 @@ __global__ void __launch_bounds__(256) op_kernel(int mode, int nx, int ny, R h2w
                                                  const cplx<R>* __restrict__ f,
                                                  const cplx<R>* __restrict__ u,
                                                  cplx<R>* __restrict__ y, R omega_jac,
-                                                 int xlo, int xhi, int ylo, int yhi) {
+                                                 int xlo, int xhi, int ylo, int yhi,
+                                                 const R* __restrict__ bx,
+                                                 const R* __restrict__ by) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
   int r = blockIdx.z;
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(256) op_kernel(int mode, int nx, int ny, R h2w
   cplx<R> dg;
   cplx<R> au = STORED ? st_row<R>(ur, nx, ny, k, x, st, mode == 2 ? &dg : nullptr)
                       : fd_row<R>(ur, nx, ny, k, x, h2w2, m, a1n, a1c, a2n, a2c,
-                                  mode == 2 ? &dg : nullptr);
+                                  mode == 2 ? &dg : nullptr, bx, by);
   if (mode == 0) {
     y[i] = au;
   } else if (mode == 1) {
@@ -163,7 +170,8 @@ __global__ void __launch_bounds__(256) op_pair_kernel_c64(
     int mode, int nx, int ny, float h2w2, const float* __restrict__ m,
     const c64* __restrict__ a1n, const c64* __restrict__ a1c, const c64* __restrict__ a2n,
     const c64* __restrict__ a2c, const c64* __restrict__ f, const c64* __restrict__ u,
-    c64* __restrict__ y, float omega_jac, int xlo, int xhi, int ylo, int yhi) {
+    c64* __restrict__ y, float omega_jac, int xlo, int xhi, int ylo, int yhi,
+    const float* __restrict__ bx, const float* __restrict__ by) {
   const size_t n = (size_t)nx * ny;
   const size_t e = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (e >= n) return;
@@ -214,7 +222,8 @@ __global__ void __launch_bounds__(256) op_pair_kernel_c64(
       au = fd_row_interior<float>(U, nx, ny, kk, xx, h2w2, m, &dr);
       dg = mk(dr, 0.f);
     } else {
-      au = fd_row<float>(U, nx, ny, kk, xx, h2w2, m, a1n, a1c, a2n, a2c, mode == 2 ? &dg : nullptr);
+      au = fd_row<float>(U, nx, ny, kk, xx, h2w2, m, a1n, a1c, a2n, a2c, mode == 2 ? &dg : nullptr,
+                         bx, by);
     }
     if (mode == 0) y[i] = au;
     else if (mode == 1) y[i] = f[i] - au;
@@ -243,7 +252,7 @@ static void launch_op(hz_handle* h, const Level& L, int mode, const cplx<R>* f,
     timed(h, tag, bytes, s, [&] {
       op_kernel<R, true><<<grid, block, 0, s>>>(mode, L.nx, L.ny, h2w2, nullptr, nullptr, nullptr,
                                                 nullptr, nullptr, Planes<R>::st(L), f, u, y,
-                                                (R)omega_jac, 1, 0, 1, 0);
+                                                (R)omega_jac, 1, 0, 1, 0, nullptr, nullptr);
     });
   else if constexpr (sizeof(R) == 4)
     timed(h, tag, bytes, s, [&] {
@@ -251,14 +260,14 @@ static void launch_op(hz_handle* h, const Level& L, int mode, const cplx<R>* f,
       op_pair_kernel_c64<<<dim3((unsigned)cdiv(pairs, 256), n_rhs), 256, 0, s>>>(
           mode, L.nx, L.ny, h2w2, Med<R>::m(L), Tab<R>::inode(L.ax), Tab<R>::cell(L.ax),
           Tab<R>::inode(L.ay), Tab<R>::cell(L.ay), f, u, y, (R)omega_jac, L.ax.in_lo, L.ax.in_hi,
-          L.ay.in_lo, L.ay.in_hi);
+          L.ay.in_lo, L.ay.in_hi, Tab<R>::beta(L.ax), Tab<R>::beta(L.ay));
     });
   else
     timed(h, tag, bytes, s, [&] {
       op_kernel<R, false><<<grid, block, 0, s>>>(
           mode, L.nx, L.ny, h2w2, Med<R>::m(L), Tab<R>::inode(L.ax), Tab<R>::cell(L.ax),
           Tab<R>::inode(L.ay), Tab<R>::cell(L.ay), nullptr, f, u, y, (R)omega_jac, L.ax.in_lo,
-          L.ax.in_hi, L.ay.in_lo, L.ay.in_hi);
+          L.ax.in_hi, L.ay.in_lo, L.ay.in_hi, Tab<R>::beta(L.ax), Tab<R>::beta(L.ay));
     });
   h->launches++;
   HZ_CU(cudaGetLastError());

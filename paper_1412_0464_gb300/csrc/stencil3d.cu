@@ -20,12 +20,14 @@ namespace {
 
 template <typename R> struct Tab3;
 template <> struct Tab3<double> {
+  static const double* beta(const AxisTables& a) { return a.beta; }
   static const c128* inode(const AxisTables& a) { return a.ia_node; }
   static const c128* cell(const AxisTables& a) { return a.a_cell; }
   static const double* m(const Level& L) { return L.m; }
   static const c128* st(const Level& L) { return L.st128; }
 };
 template <> struct Tab3<float> {
+  static const float* beta(const AxisTables& a) { return a.beta32; }
   static const c64* inode(const AxisTables& a) { return a.ia_node32; }
   static const c64* cell(const AxisTables& a) { return a.a_cell32; }
   static const float* m(const Level& L) { return L.m32; }
@@ -39,6 +41,7 @@ struct Op3Args {
   const R* m;
   const cplx<R>* ia[3];                // 1/alpha at unknowns, x y z
   const cplx<R>* ac[3];                // alpha at cell midpoints, x y z
+  const R* beta[3];                    // sponge profiles, x y z (null: PML)
   const cplx<R>* st;                   // stored 27-point planes or null
   int lo[3], hi[3];                    // real-coefficient interior box
   const cplx<R>* f;
@@ -101,7 +104,9 @@ __global__ void __launch_bounds__(128) op3d_kernel(Op3Args<R> a) {
       const cplx<R> ty = (yl + yr) * uc - yl * ud - yr * uu;
       const cplx<R> tz = (zl + zr) * uc - zl * ub - zr * ut;
       const cplx<R> s23 = i2 * i3, s13 = i1 * i3, s12 = i1 * i2;
-      const cplx<R> mass = mm * (s12 * i3);
+      cplx<R> mass = mm * (s12 * i3);
+      if (a.beta[0])                      // sponge: k^2 (1 + i beta)^2
+        mass = mass * sponge_s<R>(a.beta[0][x] + a.beta[1][yy] + a.beta[2][z]);
       au = a.hh * (s23 * tx + s13 * ty + s12 * tz - mass * uc);
       dg = a.hh * (s23 * (xl + xr) + s13 * (yl + yr) + s12 * (zl + zr) - mass);
     }
@@ -134,6 +139,7 @@ void launch_op3d(hz_handle* h, const Level& L, int mode, const cplx<R>* f, const
     if (!L.fe) {
       a.ia[l] = Tab3<R>::inode(*ax[l]);
       a.ac[l] = Tab3<R>::cell(*ax[l]);
+      a.beta[l] = Tab3<R>::beta(*ax[l]);
     }
   }
   if (!L.fe) a.m = Tab3<R>::m(L);

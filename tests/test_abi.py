@@ -41,7 +41,12 @@ def _params(**kw):
                                  dict(n=(40, 2, 40)), dict(dim=3, n=(40, 40, 3)), dict(max_rhs=0),
                                  dict(max_rhs=99), dict(tol=0.0), dict(w_dd=0), dict(J=60),
                                  dict(precision=7), dict(sweep=5), dict(h=-1.0),
-                                 dict(two_grid=1, n=(40, 41, 40))])
+                                 dict(two_grid=1, n=(40, 41, 40)), dict(boundary=2),
+                                 dict(boundary=1, sponge_damping=0.0),
+                                 dict(boundary=1, sponge_damping=1.5),
+                                 dict(boundary=1, sponge_damping=0.01, w_out=0),
+                                 dict(sweep=hz.HZ_SWEEP_NX, n_cell=0),
+                                 dict(sweep=hz.HZ_SWEEP_NX, n_cell=3)])
 def test_setup_rejects_bad_parameters(L, bad):
     h = ctypes.c_void_p()
     st = L.hz_setup(ctypes.byref(_params(**bad)), ctypes.c_void_p(1), ctypes.byref(h))
