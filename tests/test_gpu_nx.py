@@ -2,7 +2,7 @@
 
 One application element by element (FP64 1e-9, complex64 3e-4, as for the
 other sweeps), the one-cell case equal to the X-sweep, and the ordering of
-Table 4 (the partial sweeps need more GMRES iterations than the X-sweep).
+Table 7 (the partial sweeps need more GMRES iterations than the X-sweep).
 """
 
 import numpy as np
@@ -56,7 +56,7 @@ def test_nx_one_cell_is_the_x_sweep():
     assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
 
 
-def test_table4_ordering_on_gpu():
+def test_table7_ordering_on_gpu():
     """Constant medium (configuration 1 recipe), J = 16: the X-sweep needs fewer
     iterations than every partial sweep, NX(2) no more than NX(8)."""
     hz = _hz()

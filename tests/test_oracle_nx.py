@@ -10,7 +10,7 @@
   PML widens), while it is not a global inverse.  A wrong wiring of the
   cell boundaries (the final boundary solve without the left cell's layers)
   breaks the pin.
-* Table 4 of the paper (constant medium): the partial sweeps need more GMRES
+* Table 7 of the paper (constant medium): the partial sweeps need more GMRES
   iterations than the X-sweep, and more as the cell count grows.
 """
 
@@ -130,7 +130,7 @@ def test_planted_one_way_boundary_fails(monkeypatch):
     assert _errs_1d("cell", ws=(16,))[-1] > 1e-1
 
 
-def test_table4_partial_sweeps_need_more_iterations():
+def test_table7_partial_sweeps_need_more_iterations():
     cfg = synth.scaled_workload(1, 120, w_out=8, J=12)
     b = synth.sources(cfg)[0]
     its = {}
