@@ -73,6 +73,15 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 GEMM peak (burst) times the
+    nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
+    return 1900.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
+
+
 def _sm_max_mhz():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -401,7 +410,8 @@ def main():
             "slab_bwd", "slab_solve", "slab_factor", "slab_middle", "segment_product",
             "segment_prefix", "stencil_c64", "stencil_c128",
             "slab_factor3d_schur", "slab_factor3d_panel", "slab_factor3d_rowmod",
-            "slab_factor3d_update", "slab_factor3d_writeout", "slab3_gemv", "slab_solve3d"]
+            "slab_factor3d_update", "slab_factor3d_inner", "slab_factor3d_writeout", "slab3_gemv",
+            "slab_solve3d"]
     kt = {t: solver.kernel_timing(t) for t in tags}
     solver.enable_timing(False)
     ms_step, value = replica_throughput(total_ms / args.steps, cfg.ndof * cfg.n_src, ws, "cuda")
@@ -468,17 +478,25 @@ def main():
                     "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
         roofline["hbm_kernel"] = hbm_line(dom_hbm)
     elif dom == "slab_factor3d_update":
-        # the rank-32 complex GEMM update of the 3-D Gauss-Jordan inverse: its tag
-        # carries the algorithmic flop (8 B^2 32 per chain and panel)
+        # the rank-128 complex GEMM update (outer blocks) of the 3-D Gauss-Jordan
+        # inverse; its tag carries the algorithmic flop, 8 B (B - 128) 128 per
+        # chain and block.  complex64: tcgen05 kind::tf32 with three TF32 passes
+        # per real product, so the tensor pipe executes 3x the algorithmic flop;
+        # complex128: FP64 SIMT
         d = indiv[dom]
         ach = d["bytes"] / (d["ms"] / 1000.0) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak,
-                    "unit": "TFLOP/s", "frac": ach / alu_peak,
-                    "peak_source": (f"measured {'FP32' if fprec == 'mixed' else 'FP64'} FMA "
-                                    "throughput (hz_alu_peak)"),
-                    "traffic": None, "avg_launch_us": 1000 * d["ms"] / d["launches"],
-                    "algorithmic_flop_per_launch": d["bytes"] / d["launches"],
-                    "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
+        common = {"kernel": dom, "achieved": ach, "unit": "TFLOP/s", "traffic": _traffic(dom),
+                  "avg_launch_us": 1000 * d["ms"] / d["launches"],
+                  "algorithmic_flop_per_launch": d["bytes"] / d["launches"],
+                  "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
+        if fprec == "mixed":
+            tpk, tsrc = _tf32_peak()
+            roofline = {"bound": "tensor", "peak": tpk, "frac": ach / tpk, "peak_source": tsrc,
+                        "tensor_pipe_frac": 3.0 * ach / tpk,
+                        "note": "3xTF32 split: executed TF32 flop = 3 x algorithmic", **common}
+        else:
+            roofline = {"bound": "alu", "peak": alu_peak, "frac": ach / alu_peak,
+                        "peak_source": "measured FP64 FMA throughput (hz_alu_peak)", **common}
         roofline["hbm_kernel"] = hbm_line(dom_hbm)
     else:
         roofline = hbm_line(dom)

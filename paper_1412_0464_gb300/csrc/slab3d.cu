@@ -19,13 +19,18 @@
 // marked, not moved; G[p][piv[q]] = S[piv[p]][q] at the end).  One
 // elimination step with pivot row r for column p is the rank-1 update
 //   S -= c rho^T,  c = S[:, p] - e_r,  rho = S[r, :] / S[r][p] + e_p,
-// which turns column p into the inverse's column.  Panels of NB columns:
-// one CTA per chain eliminates the panel's columns on the panel only and
-// records the colmods c (C, B x NB), the pivot rows and 1 / S[r][p]; the
-// pivot rows' other columns follow from the short recurrence
-//   rho_t = (S[r_t, :] - sum_{s<t} C[r_t][s] rho_s) / S[r_t][p_t];
-// then S -= C R over the other columns is a dense complex GEMM of depth NB.
-// Every launch takes all chains of all slabs at the same step.
+// which turns column p into the inverse's column.  Two levels of blocking:
+// within an outer block of kOuter columns, panels of 16 (or NB) columns: one
+// CTA per chain eliminates the panel's columns on the panel only and records
+// the colmods c (C, B x kOuter), the pivot rows and 1 / S[r][p]; the pivot
+// rows' other columns follow from the short recurrence
+//   rho_t = (S[r_t, :] - sum_{s<t} C[r_t][s] rho_s) / S[r_t][p_t]
+// (for columns outside the outer block with all earlier steps of the block,
+// since those columns are not updated until the block ends); S -= C R then
+// updates the block's other columns (rank 16), and at the end of the block
+// all columns outside it (a dense complex GEMM of depth kOuter, on the tensor
+// cores in complex64).  Every launch takes all chains of all slabs at the
+// same step.
 //
 // Solve: forward y_t = G_t (f_t - L_t y_{t-1}) along both chains, meeting
 // x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1}), backward
@@ -33,6 +38,8 @@
 // dense GEMV with the stored inverse (a skinny GEMM over the right-hand
 // sides).
 #include "hz_internal.h"
+#include "ptx.cuh"
+#include "tc.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -63,6 +70,7 @@ void launch_pdl3(void (*k)(KArgs...), dim3 grid, unsigned block, cudaStream_t s,
 }
 
 constexpr int NB = 32;            // panel width of the blocked Gauss-Jordan inverse
+constexpr int kOuter = 128;       // outer block of panels (rank of the delayed update)
 constexpr int kPanelThreads = 512;
 constexpr int kMaxB = 8192;       // largest block (pivot flags live in shared memory)
 
@@ -216,12 +224,12 @@ struct FChain {
   cplx<R>* G;          // [nz][bstride]
   size_t bstride;
   cplx<R>* S;          // [B][B] Schur complement, inverted in place
-  cplx<R>* C;          // [NB][B] colmods of the current panel
-  cplx<R>* Rm;         // [NB][B] rowmods of the current panel
-  cplx<R>* pinfo;      // [NB] 1 / pivot of the panel's columns
+  cplx<R>* C;          // [kOuter][B] colmods of the current outer block (slot = column - P0)
+  cplx<R>* Rm;         // [kOuter][B] rowmods of the current outer block
+  cplx<R>* pinfo;      // [kOuter] 1 / pivot of the block's columns
   int* piv;            // [B] pivot row of column p
   int* pinv;           // [B] column whose pivot row is r (-1: not yet a pivot row)
-  int* prow;           // [NB] pivot rows of the panel
+  int* prow;           // [kOuter] pivot rows of the block's columns
 };
 
 // Entry (i, j) of the in-layer block D_k (9-point in (y, x), zero elsewhere).
@@ -316,7 +324,8 @@ __device__ __forceinline__ unsigned long long pivot_key(float a2, int row) {
 // scaled panel row, and applies the rank-1 update to the panel columns of
 // every row, recording the colmods (C) and the next column's pivot keys.
 template <typename R>
-__global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>* chains, int p0) {
+__global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>* chains, int p0,
+                                                                 int slot) {
   const FChain<R> c = chains[blockIdx.x];
   const int B = c.B;
   if (p0 >= B) return;
@@ -349,7 +358,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
       flag[r] = 1;
       c.piv[p0 + t] = r;
       c.pinv[r] = p0 + t;
-      c.prow[t] = r;
+      c.prow[slot + t] = r;
     }
     __syncthreads();
     const int r = sh_r;
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
       cplx<R> x = v * inv;
       if (lane == t) x = inv + mk<R>(1, 0);
       if (lane < NB) rm[lane] = x;
-      if (lane == 0) c.pinfo[t] = inv;
+      if (lane == 0) c.pinfo[slot + t] = inv;
     }
     __syncthreads();
     const cplx<R> rq = lane < nbp ? rm[lane] : mk<R>(0, 0);
@@ -372,7 +381,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
       if (i == r) ci.re -= (R)1;
       v = v - ci * rq;
       if (lane < nbp) row[lane] = v;
-      if (lane == 0) c.C[(size_t)t * B + i] = ci;
+      if (lane == 0) c.C[(size_t)(slot + t) * B + i] = ci;
       if (t + 1 < nbp) {
         const cplx<R> nv = mk<R>(__shfl_sync(0xffffffffu, v.re, t + 1),
                                  __shfl_sync(0xffffffffu, v.im, t + 1));
@@ -390,12 +399,13 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
 // small enough: B (PW + 1) elements): one thread per row (rows tid, tid +
 // 1024, ...), panel rows padded to PW + 1 elements; per step a block-wide
 // pivot-key maximum, the scaled pivot row, and each thread's rank-1 update of
-// its rows with the next column's keys.  The colmods go to C [NB][B].
+// its rows with the next column's keys.  The colmods go to C [kOuter][B] at
+// the panel's slots.
 constexpr int kSmemPanelThreads = 1024;
 
 template <typename R, int PW>
 __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const FChain<R>* chains,
-                                                                         int p0) {
+                                                                         int p0, int slot) {
   const FChain<R> c = chains[blockIdx.x];
   const int B = c.B;
   if (p0 >= B) return;
@@ -441,7 +451,7 @@ __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const 
         flag[r] = 1;
         c.piv[p0 + t] = r;
         c.pinv[r] = p0 + t;
-        c.prow[t] = r;
+        c.prow[slot + t] = r;
       }
     }
     __syncthreads();
@@ -451,7 +461,7 @@ __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const 
       cplx<R> x = P[r * LD + tid] * inv;
       if (tid == t) x = inv + mk<R>(1, 0);
       rm[tid] = tid < nbp ? x : mk<R>(0, 0);
-      if (tid == 0) c.pinfo[t] = inv;
+      if (tid == 0) c.pinfo[slot + t] = inv;
     }
     __syncthreads();
     best = 0;
@@ -459,7 +469,7 @@ __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const 
       cplx<R>* row = P + i * LD;
       cplx<R> ci = row[t];
       if (i == r) ci.re -= (R)1;
-      c.C[(size_t)t * B + i] = ci;
+      c.C[(size_t)(slot + t) * B + i] = ci;
 #pragma unroll
       for (int q = 0; q < PW; ++q) row[q] = row[q] - ci * rm[q];
       if (t + 1 < nbp && !flag[i]) {
@@ -480,85 +490,126 @@ size_t panel_smem_bytes(int B) {
   return (size_t)B * (PW + 1) * sizeof(cplx<R>) + 32 * 8 + PW * sizeof(cplx<R>) + 16 + B + 16;
 }
 
-// Pivot rows' other columns (one thread per column j outside the panel):
-//   rho_t[j] = (S[r_t][j] - sum_{s<t} C[r_t][s] rho_s[j]) / S[r_t][p0+t];
-// zero on the panel columns (the panel kernel has finished them).
+// Pivot rows' other columns for the panel [p0, p0 + nbp), slots slot ..
+// slot + nbp of the outer block [P0, P0 + kb) (one thread per column j
+// outside the panel).  Columns inside the outer block are kept current by the
+// inner updates:
+//   rho_t[j] = (S[r_t][j] - sum_{s<t} C[r_t][s] rho_s[j]) / S[r_t][p0+t]   (s, t in the panel);
+// columns outside it have not been updated since the block began, so the
+// earlier slots of the block enter as well (delayed update):
+//   rho_t[j] = (S[r_t][j] - sum_{s<slot} C[r_t][s] rho_s[j] - sum_{panel s<t} ...) / S[r_t][p0+t].
+// Zero on the panel columns (the panel kernel has finished them).  Dynamic
+// shared memory: Cp [NB][NB] (in-panel colmods at the pivot rows) and Cq
+// [NB][slot] (earlier slots).
 template <typename R>
-__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0, int nbw) {
+__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0, int nbw,
+                                                        int P0, int KBw) {
   const FChain<R> c = chains[blockIdx.y];
   const int B = c.B;
   if (p0 >= B) return;
-  const int nbp = min(nbw, B - p0);
-  __shared__ cplx<R> Cp[NB][NB];
+  const int nbp = min(nbw, B - p0), slot = p0 - P0, blk_hi = min(P0 + KBw, B);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* Cp = (cplx<R>*)smem_raw;              // [NB][NB]
+  cplx<R>* Cq = Cp + NB * NB;                    // [NB][slot]
   __shared__ cplx<R> inv[NB];
   __shared__ int pr[NB];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int t = e / NB, s = e - t * NB;
-    Cp[t][s] = (t < nbp && s < t) ? c.C[(size_t)s * B + c.prow[t]] : mk<R>(0, 0);
-  }
   for (int t = threadIdx.x; t < NB; t += blockDim.x) {
-    inv[t] = t < nbp ? c.pinfo[t] : mk<R>(0, 0);
-    pr[t] = t < nbp ? c.prow[t] : 0;
+    inv[t] = t < nbp ? c.pinfo[slot + t] : mk<R>(0, 0);
+    pr[t] = t < nbp ? c.prow[slot + t] : 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int t = e / NB, q = e - t * NB;
+    Cp[e] = (t < nbp && q < t) ? c.C[(size_t)(slot + q) * B + pr[t]] : mk<R>(0, 0);
+  }
+  for (int e = threadIdx.x; e < NB * slot; e += blockDim.x) {
+    const int t = e / slot, q = e - t * slot;
+    Cq[e] = t < nbp ? c.C[(size_t)q * B + pr[t]] : mk<R>(0, 0);
   }
   __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B) return;
   if (j >= p0 && j < p0 + nbp) {
-    for (int t = 0; t < NB; ++t) c.Rm[(size_t)t * B + j] = mk<R>(0, 0);
+    for (int t = 0; t < nbp; ++t) c.Rm[(size_t)(slot + t) * B + j] = mk<R>(0, 0);
     return;
   }
-  cplx<R> rv[NB];
+  cplx<R> a[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) a[t] = t < nbp ? c.S[(size_t)pr[t] * B + j] : mk<R>(0, 0);
+  if (j < P0 || j >= blk_hi) {
+    for (int q = 0; q < slot; ++q) {
+      const cplx<R> x = c.Rm[(size_t)q * B + j];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) a[t] = a[t] - Cq[t * slot + q] * x;
+    }
+  }
 #pragma unroll
   for (int t = 0; t < NB; ++t) {
-    cplx<R> a = mk<R>(0, 0);
     if (t < nbp) {
-      a = c.S[(size_t)pr[t] * B + j];
 #pragma unroll
-      for (int s = 0; s < t; ++s) a = a - Cp[t][s] * rv[s];
-      a = a * inv[t];
+      for (int q = 0; q < t; ++q) a[t] = a[t] - Cp[t * NB + q] * a[q];
+      a[t] = a[t] * inv[t];
+      c.Rm[(size_t)(slot + t) * B + j] = a[t];
     }
-    rv[t] = a;
-    c.Rm[(size_t)t * B + j] = a;
   }
 }
 
-// S -= C Rm over a 64 x 64 tile per CTA (256 threads, 4 x 4 outputs each:
-// rows ty + 16 a, columns tx + 16 b), depth NB through shared memory.
 template <typename R>
-__global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains, int p0, int nbw) {
+size_t rowmod_smem(int slot) { return (size_t)NB * (NB + slot) * sizeof(cplx<R>); }
+
+// S[i][j] -= sum_{t < depth} C[slot + t][i] Rm[slot + t][j], 64 x 64 tile per
+// CTA (256 threads, 4 x 4 outputs each: rows ty + 16 a, columns tx + 16 b),
+// depth in chunks of NB through shared memory.  inner: the panel [base,
+// base + depth) of the outer block [P0, P0 + KBw) updates the block's other
+// columns (slots from base - P0); else the outer block's colmods and rowmods
+// (slots 0 .. depth) update every column outside the block.
+template <typename R>
+__global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains, int base,
+                                                        int width, int P0, int KBw, int inner) {
   const FChain<R> c = chains[blockIdx.z];
   const int B = c.B;
-  if (p0 >= B) return;
-  const int nbp = min(nbw, B - p0);
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  if (i0 >= B || j0 >= B) return;
-  if (j0 >= p0 && j0 + 64 <= p0 + nbp) return;   // panel columns only: nothing to do
+  if (base >= B) return;
+  const int depth = min(width, B - base), slot = base - P0;
+  int wlo, whi, xlo, xhi;
+  if (inner) {
+    wlo = P0; whi = min(P0 + KBw, B); xlo = base; xhi = base + depth;
+  } else {
+    wlo = 0; whi = B; xlo = P0; xhi = min(P0 + KBw, B);
+  }
+  const int i0 = blockIdx.y * 64, j0 = wlo + blockIdx.x * 64;
+  if (i0 >= B || j0 >= whi) return;
+  if (j0 >= xlo && j0 + 64 <= xhi) return;       // excluded columns only: nothing to do
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* Cs = (cplx<R>*)smem_raw;              // [64][NB + 1]
   cplx<R>* Rs = Cs + 64 * (NB + 1);              // [NB][64]
-  for (int e = threadIdx.x; e < 64 * NB; e += 256) {
-    const int t = e / 64, q = e - t * 64;        // colmods [NB][B], rowmods [NB][B]
-    Cs[q * (NB + 1) + t] = (i0 + q < B && t < nbp) ? c.C[(size_t)t * B + i0 + q] : mk<R>(0, 0);
-    Rs[t * 64 + q] = (j0 + q < B && t < nbp) ? c.Rm[(size_t)t * B + j0 + q] : mk<R>(0, 0);
-  }
-  __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   cplx<R> acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = mk<R>(0, 0);
+  for (int k0 = 0; k0 < depth; k0 += NB) {
+    for (int e = threadIdx.x; e < 64 * NB; e += 256) {
+      const int t = e / 64, q = e - t * 64;      // colmods [slot][B], rowmods [slot][B]
+      const bool ok = k0 + t < depth;
+      const size_t row = (size_t)(slot + k0 + t) * B;
+      Cs[q * (NB + 1) + t] = (ok && i0 + q < B) ? c.C[row + i0 + q] : mk<R>(0, 0);
+      Rs[t * 64 + q] = (ok && j0 + q < whi) ? c.Rm[row + j0 + q] : mk<R>(0, 0);
+    }
+    __syncthreads();
 #pragma unroll 4
-  for (int t = 0; t < NB; ++t) {
-    cplx<R> cv[4], rv[4];
+    for (int t = 0; t < NB; ++t) {
+      cplx<R> cv[4], rv[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) cv[a] = Cs[(ty + 16 * a) * (NB + 1) + t];
+      for (int a = 0; a < 4; ++a) cv[a] = Cs[(ty + 16 * a) * (NB + 1) + t];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) rv[b] = Rs[t * 64 + tx + 16 * b];
+      for (int b = 0; b < 4; ++b) rv[b] = Rs[t * 64 + tx + 16 * b];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) cfma(acc[a][b], cv[a], rv[b]);
+        for (int b = 0; b < 4; ++b) cfma(acc[a][b], cv[a], rv[b]);
+    }
+    __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -567,7 +618,7 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains,
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int j = j0 + tx + 16 * b;
-      if (j >= B || (j >= p0 && j < p0 + nbp)) continue;
+      if (j >= whi || (j >= xlo && j < xhi)) continue;
       cplx<R>* p = c.S + (size_t)i * B + j;
       *p = *p - acc[a][b];
     }
@@ -585,6 +636,153 @@ __global__ void __launch_bounds__(256) gj_writeout_kernel(const FChain<R>* chain
 }
 
 size_t update_smem(size_t el) { return (64 * (NB + 1) + NB * 64) * el; }
+
+// The outer-block update of the complex64 factorisation on the tensor cores
+// (tcgen05, kind::tf32, FP32 accumulation in tensor memory): one CTA per
+// 128 x 128 tile of S, 128 threads,
+//   S[i][j] -= sum_{t < kb} C[t][i] Rm[t][j]   (j outside [P0, P0 + kb)).
+// Complex products as real ones, Dr = Cr Rr - Ci Ri and Di = Cr Ri + Ci Rr,
+// each real product in three TF32 passes (x = hi + lo: hi hi + hi lo + lo hi)
+// so that the result keeps about FP32 accuracy.  The depth runs in stages of
+// kTcK: all threads split and store one stage's operands (eight K-major
+// 128 x kTcK TF32 tiles: Cr, Ci, Rr, Ri, hi and lo) while the MMAs of the
+// previous stage run; thread 0 issues the stage's 24 MMAs (128 x 128 x 8) and
+// commits them to the stage's mbarrier, which frees its buffer.  Dr and Di
+// occupy tensor-memory columns [0, 128) and [128, 256); the epilogue moves
+// them through shared memory (rows XOR-swizzled) and subtracts them from S in
+// coalesced rows.  Every wait is bounded (device flag on timeout).
+constexpr int kTcM = 128;          // tile rows (MMA M) and columns (MMA N)
+constexpr int kTcK = 16;           // complex depth per stage
+constexpr uint32_t kTcTile = kTcM * kTcK * 4;    // one TF32 operand tile: 8 KB
+constexpr uint32_t kTcStage = 8 * kTcTile;       // Cr hi/lo, Ci hi/lo, Rr hi/lo, Ri hi/lo
+constexpr size_t kTcSmem = 2 * (size_t)kTcStage + 64;
+
+__global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float>* chains, int P0,
+                                                              int KBw, int* flag) {
+  const FChain<float> c = chains[blockIdx.z];
+  const int B = c.B;
+  if (P0 >= B) return;
+  const int kb = min(KBw, B - P0), xlo = P0, xhi = P0 + kb;
+  const int i0 = blockIdx.y * kTcM, j0 = blockIdx.x * kTcM;
+  if (i0 >= B || j0 >= B) return;
+  if (j0 >= xlo && j0 + kTcM <= xhi) return;     // excluded columns only
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* bar = (uint64_t*)(sm + 2 * kTcStage);                 // [0], [1]: stage buffers
+  uint32_t* tptr = (uint32_t*)(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tptr, 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tptr;
+  const int nst = (kb + kTcK - 1) / kTcK;
+  bool ok = true;
+  const int r = tid;                              // the operand row this thread stages
+  for (int st = 0; st < nst; ++st) {
+    const int buf = st & 1;
+    unsigned char* base = sm + buf * kTcStage;
+    if (st >= 2 && ok) ok = mbar_wait(&bar[buf], ((st - 2) >> 1) & 1, flag);
+#pragma unroll
+    for (int kg = 0; kg < kTcK; kg += 4) {
+      float4 v[8];
+      float* f = (float*)v;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int kk = st * kTcK + kg + q;
+        c64 a = mk<float>(0, 0), b = mk<float>(0, 0);
+        if (kk < kb) {
+          if (i0 + r < B) a = c.C[(size_t)kk * B + i0 + r];
+          const int j = j0 + r;
+          if (j < B && (j < xlo || j >= xhi)) b = c.Rm[(size_t)kk * B + j];
+        }
+        tc::split_tf32(a.re, f[0 * 4 + q], f[1 * 4 + q]);
+        tc::split_tf32(a.im, f[2 * 4 + q], f[3 * 4 + q]);
+        tc::split_tf32(b.re, f[4 * 4 + q], f[5 * 4 + q]);
+        tc::split_tf32(b.im, f[6 * 4 + q], f[7 * 4 + q]);
+      }
+      const uint32_t off = tc::kmajor_off(r, kg, kTcK / 4);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) *(float4*)(base + t * kTcTile + off) = v[t];
+    }
+    fence_proxy_async_smem();
+    ok = __syncthreads_and(ok);                   // uniform: a timed-out wait stops every thread
+    if (!ok) break;
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t sb = smem_u32(base);
+      constexpr uint32_t lbo = 128, sbo = (kTcK / 4) * 128;
+      constexpr uint32_t id = tc::idesc_tf32(kTcM, kTcM, false);
+      constexpr uint32_t idn = tc::idesc_tf32(kTcM, kTcM, true);
+#pragma unroll
+      for (int ks = 0; ks < kTcK / 8; ++ks) {
+        const uint32_t ko = ks * 256;             // two core matrices along K per MMA
+        auto d = [&](int t) { return tc::smem_desc(sb + t * kTcTile + ko, lbo, sbo); };
+        const bool acc = st > 0 || ks > 0;
+        // tiles: 0 Cr hi, 1 Cr lo, 2 Ci hi, 3 Ci lo, 4 Rr hi, 5 Rr lo, 6 Ri hi, 7 Ri lo
+        tc::mma_tf32(tmem, d(0), d(4), id, acc);          // Dr += Cr Rr
+        tc::mma_tf32(tmem, d(0), d(5), id, true);
+        tc::mma_tf32(tmem, d(1), d(4), id, true);
+        tc::mma_tf32(tmem, d(2), d(6), idn, true);        // Dr -= Ci Ri
+        tc::mma_tf32(tmem, d(2), d(7), idn, true);
+        tc::mma_tf32(tmem, d(3), d(6), idn, true);
+        tc::mma_tf32(tmem + 128, d(0), d(6), id, acc);    // Di += Cr Ri
+        tc::mma_tf32(tmem + 128, d(0), d(7), id, true);
+        tc::mma_tf32(tmem + 128, d(1), d(6), id, true);
+        tc::mma_tf32(tmem + 128, d(2), d(4), id, true);   // Di += Ci Rr
+        tc::mma_tf32(tmem + 128, d(2), d(5), id, true);
+        tc::mma_tf32(tmem + 128, d(3), d(4), id, true);
+      }
+      tc::commit(&bar[buf]);
+    }
+  }
+  // the last stage's commit covers every MMA issued before it
+  if (ok) ok = mbar_wait(&bar[(nst - 1) & 1], ((nst - 1) >> 1) & 1, flag);
+  ok = __syncthreads_and(ok);
+  tc::fence_after_sync();
+  c64* D = (c64*)sm;                              // [128][128], column XOR-swizzled by row
+  const int row = warp * 32 + (tid & 31);
+  if (ok) {
+#pragma unroll 1
+    for (int cc = 0; cc < kTcM; cc += 32) {
+      float vr[32], vi[32];
+      tc::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + cc, vr);
+      tc::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + 128 + cc, vi);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) D[row * kTcM + ((cc + q) ^ (row & 31))] = mk<float>(vr[q], vi[q]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (ok) {
+    const int j = j0 + tid;
+    const bool col_ok = j < B && (j < xlo || j >= xhi);
+    for (int rr = 0; rr < kTcM; ++rr) {
+      const int i = i0 + rr;
+      if (i >= B) break;
+      if (col_ok) {
+        float2* p = (float2*)(c.S + (size_t)i * B + j);
+        const c64 v = D[rr * kTcM + (tid ^ (rr & 31))];
+        float2 x = *p;
+        x.x -= v.re;
+        x.y -= v.im;
+        *p = x;
+      }
+    }
+  }
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 256);
+  }
+}
+
 
 // ------------------------------------------------------------------- solves
 // Right-hand side of a 3-D slab solve (SubdomSolve, Table 2) into the layer
@@ -826,12 +1024,12 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
   int Bmax = 0;
   for (int j = 1; j <= J; ++j) Bmax = std::max(Bmax, L.slabs[j].B);
   const int nch = 2 * J;
-  const size_t sS = (size_t)Bmax * Bmax, sC = (size_t)Bmax * NB;
+  const size_t sS = (size_t)Bmax * Bmax, sC = (size_t)Bmax * kOuter;
   if (!L.f3_S) {   // work buffers and descriptors: built by the first factorisation, kept
     L.f3_S = dmalloc(el * sS * nch);
     L.f3_C = dmalloc(el * sC * nch);
-    L.f3_R = dmalloc(el * sC * nch + el * NB * nch);
-    L.f3_piv = (int*)dmalloc(sizeof(int) * ((size_t)2 * Bmax + NB) * nch);
+    L.f3_R = dmalloc(el * sC * nch + el * kOuter * nch);
+    L.f3_piv = (int*)dmalloc(sizeof(int) * ((size_t)2 * Bmax + kOuter) * nch);
     std::vector<FChain<R>> all;
     auto chain = [&](int j, int c) {
       const Slab& S = L.slabs[j];
@@ -843,8 +1041,8 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       f.S = (cplx<R>*)L.f3_S + sS * c;
       f.C = (cplx<R>*)L.f3_C + sC * c;
       f.Rm = (cplx<R>*)L.f3_R + sC * c;
-      f.pinfo = (cplx<R>*)L.f3_R + sC * nch + (size_t)NB * c;
-      int* ip = L.f3_piv + ((size_t)2 * Bmax + NB) * c;
+      f.pinfo = (cplx<R>*)L.f3_R + sC * nch + (size_t)kOuter * c;
+      int* ip = L.f3_piv + ((size_t)2 * Bmax + kOuter) * c;
       f.piv = ip; f.pinv = ip + Bmax; f.prow = ip + 2 * Bmax;
       return f;
     };
@@ -875,9 +1073,16 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s));
     HZ_CU(cudaFuncSetAttribute(gj_update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)update_smem(el)));
+    HZ_CU(cudaFuncSetAttribute(gj_rowmod_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rowmod_smem<R>(kOuter)));
+    HZ_CU(cudaFuncSetAttribute(gj_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTcSmem));
   }
   const FChain<R>* desc = (const FChain<R>*)L.f3_desc;
   const int fe = L.fe ? 1 : 0;
+  // complex64 outer updates on the tensor cores (HZ_TEST_NO_TC=1: the FP32
+  // SIMT kernel instead, for comparison)
+  const bool use_tc = sizeof(R) == 4 && test_hook("HZ_TEST_NO_TC") <= 0;
   // panels of 16 columns held in shared memory when a block's panel fits,
   // else panels of NB columns eliminated in place in global memory
   const size_t psm = panel_smem_bytes<R, 16>(Bmax);
@@ -900,23 +1105,44 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       }
     });
     h->launches += fe ? 1 + 2 * nterm : 1;
-    for (int p0 = 0; p0 < Bmax; p0 += nbw) {
-      timed(h, "slab_factor3d_panel", 0.0, s, [&] {
-        if (smem_panel)
-          gj_panel_smem_kernel<R, 16><<<cnt, kSmemPanelThreads, psm, s>>>(d, p0);
-        else
-          gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0);
-      });
-      timed(h, "slab_factor3d_rowmod", 0.0, s, [&] {
-        gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 128), cnt), 128, 0, s>>>(d, p0, nbw);
-      });
-      // algorithmic flop of the update: 8 B^2 nb per chain (complex MACs x 8)
-      const double fl = 8.0 * (double)Bmax * Bmax * std::min(nbw, Bmax - p0) * cnt;
-      timed(h, "slab_factor3d_update", fl, s, [&] {
-        gj_update_kernel<R><<<dim3(cdiv(Bmax, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el), s>>>(
-            d, p0, nbw);
-      });
-      h->launches += 3;
+    // outer blocks of kOuter columns: inner panels of nbw columns update the
+    // block's own columns (rank nbw); the block's colmods and rowmods then
+    // update every other column at once (rank kOuter; tensor cores in complex64)
+    for (int P0 = 0; P0 < Bmax; P0 += kOuter) {
+      const int bw = std::min(kOuter, Bmax - P0);
+      for (int p0 = P0; p0 < P0 + bw; p0 += nbw) {
+        const int slot = p0 - P0;
+        timed(h, "slab_factor3d_panel", 0.0, s, [&] {
+          if (smem_panel)
+            gj_panel_smem_kernel<R, 16><<<cnt, kSmemPanelThreads, psm, s>>>(d, p0, slot);
+          else
+            gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0, slot);
+        });
+        timed(h, "slab_factor3d_rowmod", 0.0, s, [&] {
+          gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 128), cnt), 128, rowmod_smem<R>(slot), s>>>(
+              d, p0, nbw, P0, kOuter);
+        });
+        const int nbp = std::min(nbw, Bmax - p0);
+        const double fli = 8.0 * (double)Bmax * std::max(0, bw - nbp) * nbp * cnt;
+        timed(h, "slab_factor3d_inner", fli, s, [&] {
+          gj_update_kernel<R><<<dim3(cdiv(bw, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el), s>>>(
+              d, p0, nbw, P0, kOuter, 1);
+        });
+        h->launches += 3;
+      }
+      // algorithmic flop of the outer update: 8 B (B - kb) kb per chain (complex MACs x 8)
+      const double fl = 8.0 * (double)Bmax * (Bmax - bw) * bw * cnt;
+      if (Bmax > bw) {
+        timed(h, "slab_factor3d_update", fl, s, [&] {
+          if (use_tc)
+            gj_update_tc_kernel<<<dim3(cdiv(Bmax, kTcM), cdiv(Bmax, kTcM), cnt), 128, kTcSmem, s>>>(
+                (const FChain<float>*)d, P0, kOuter, h->dev_flag);
+          else
+            gj_update_kernel<R><<<dim3(cdiv(Bmax, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el),
+                                  s>>>(d, P0, kOuter, P0, kOuter, 0);
+        });
+        h->launches += 1;
+      }
     }
     timed(h, "slab_factor3d_writeout", 0.0, s,
           [&] { gj_writeout_kernel<R><<<dim3(cdiv(Bmax, 256), Bmax, cnt), 256, 0, s>>>(d); });
@@ -931,6 +1157,7 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
   }
   layer(desc + off, J, 2);
   HZ_CU(cudaStreamSynchronize(s));
+  check_dev_flag(h, s);          // a bounded tensor-core wait that gave up
 }
 
 namespace {
