@@ -93,6 +93,11 @@ typedef struct {
                          * coarsens every cell: n[l] + 2 w_out even, Section 4.1) */
   double sponge_damping;/* sponge: one-way amplitude damping exp(-k beta_max w_out h / 3)
                          * of the layer at k = omega / c_pml, in (0, 1) */
+  int    block_3d;      /* 3-D slab factorisation: outer block width of the two-level
+                         * blocked Gauss-Jordan inverse (the rank of its delayed update,
+                         * on the tensor cores in complex64): 64, 128 or 256 (0: 128).
+                         * A tuning parameter; the result does not depend on it beyond
+                         * rounding */
 } hz_params;
 
 enum { HZ_BOUNDARY_PML = 0, HZ_BOUNDARY_SPONGE = 1 };

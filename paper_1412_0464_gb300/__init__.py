@@ -34,7 +34,7 @@ class hz_params(ctypes.Structure):
         ("precision", ctypes.c_int), ("gmres_m", ctypes.c_int), ("max_iter", ctypes.c_int),
         ("tol", ctypes.c_double), ("max_rhs", ctypes.c_int), ("segments", ctypes.c_int),
         ("c_pml", ctypes.c_double), ("n_cell", ctypes.c_int), ("boundary", ctypes.c_int),
-        ("sponge_damping", ctypes.c_double),
+        ("sponge_damping", ctypes.c_double), ("block_3d", ctypes.c_int),
     ]
 
 
@@ -167,7 +167,7 @@ class Solver:
     def __init__(self, m, *, n, w_out, omega, J, w_dd, s_dd, s_out=20.0, sweep="X",
                  precision="mixed", gmres_m=30, max_iter=500, tol=1e-6, max_rhs=1,
                  two_grid=False, nu=3, omega_jac=0.8, segments=0, c_pml=0.0, dim=2, dims=None,
-                 h=0.0, n_cell=2, boundary="pml", sponge_damping=1e-2):
+                 h=0.0, n_cell=2, boundary="pml", sponge_damping=1e-2, block_3d=0):
         import torch
         dims = tuple(dims) if dims is not None else (n,) * dim
         assert len(dims) == dim and dims[-1] == n
@@ -199,6 +199,7 @@ class Solver:
         p.c_pml = c_pml
         p.boundary = {"pml": HZ_BOUNDARY_PML, "sponge": HZ_BOUNDARY_SPONGE}[boundary]
         p.sponge_damping = sponge_damping
+        p.block_3d = block_3d
         self.params = p
         md = torch.as_tensor(m, dtype=torch.float64).to("cuda").contiguous()
         assert md.shape == self.shape

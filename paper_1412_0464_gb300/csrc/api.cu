@@ -105,6 +105,8 @@ void validate(const hz_params* p) {
   if (!(p->c_pml >= 0)) bad("c_pml must be >= 0 (0: mean wave speed)");
   if (p->max_rhs < 1 || p->max_rhs > 64) bad("max_rhs must be in 1..64");
   if (p->two_grid && (p->nu < 0 || !(p->omega_jac > 0))) bad("bad smoother parameters");
+  if (p->block_3d != 0 && p->block_3d != 64 && p->block_3d != 128 && p->block_3d != 256)
+    bad("block_3d must be 0, 64, 128 or 256");
   if (p->boundary != HZ_BOUNDARY_PML && p->boundary != HZ_BOUNDARY_SPONGE)
     bad("boundary must be HZ_BOUNDARY_PML or HZ_BOUNDARY_SPONGE");
   if (p->boundary == HZ_BOUNDARY_SPONGE) {
@@ -214,6 +216,7 @@ hz_status hz_set_medium(hz_handle* h, const double* m_dev) {
     // rebuild the level from scratch for the new medium (same grid)
     double t0 = now_s();
     const hz_params p = h->p;
+    clear_graphs(h);
     free_level(h->fine);
     free_level(h->coarse);
     h->c_pml = p.c_pml > 0 ? p.c_pml : mean_velocity(m_dev, n_dof(p), h->s2);
@@ -485,6 +488,7 @@ hz_status hz_kernel_timing(hz_handle* h, const char* tag, double* ms, long long*
 void hz_destroy(hz_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  clear_graphs(h);
   free_level(h->fine);
   free_level(h->coarse);
   release_work(h);

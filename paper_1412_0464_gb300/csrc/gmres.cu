@@ -306,7 +306,7 @@ void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
     for (int j = 0; j < m; ++j) {
       c128* Vj = h->V + (size_t)j * vs;
       c128* Zj = h->Z + (size_t)j * vs;
-      precond_apply(h, Vj, Zj, nr, s);
+      precond_graphed(h, Vj, Zj, nr, s);
       h->stats.precond_applies++;
       apply_fine64(h, Zj, h->W, nr, s);
       gm.dots(h->V, vs, j + 1, h->W, hc, hs);                       // h1 = V^H w
@@ -360,6 +360,63 @@ void gmres_solve(hz_handle* h, const c128* f, c128* u, int nr, cudaStream_t s) {
     conv = conv && relres[r] <= tol;
   }
   if (!conv) throw Failure(HZ_ENOTCONV, "GMRES did not reach the tolerance within max_iter");
+}
+
+// The preconditioner application is a fixed sequence of a few hundred
+// launches (sweeps over J slabs, each a chain of substitution kernels, plus
+// the two-grid transfers), identical for every GMRES iteration with the same
+// buffers.  It is captured once per (input, output, n_rhs) as a CUDA graph
+// and replayed, which removes the per-launch host cost; the X-sweep's second
+// stream joins the capture through its fork / join events.  The first
+// application for an n_rhs runs uncaptured (it makes the lazy allocations),
+// and timing (per-kernel events) or HZ_TEST_NO_GRAPH=1 bypass the graphs.
+void precond_graphed(hz_handle* h, const c128* in, c128* out, int nr, cudaStream_t s) {
+  const bool warm = std::find(h->pwarm.begin(), h->pwarm.end(), nr) != h->pwarm.end();
+  if (h->timing.on || !warm || test_hook("HZ_TEST_NO_GRAPH") > 0) {
+    precond_apply(h, in, out, nr, s);
+    if (!warm) h->pwarm.push_back(nr);
+    return;
+  }
+  hz_handle::PrecGraph* g = nullptr;
+  for (auto& e : h->pgraphs)
+    if (e.in == in && e.out == out && e.nr == nr) g = &e;
+  if (!g) {
+    // capture; if the capture or the instantiation fails, this (in, out, n_rhs)
+    // keeps running uncaptured (an entry without a graph)
+    const long long l0 = h->launches;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool captured = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (captured) {
+      try {
+        precond_apply(h, in, out, nr, s);
+      } catch (...) {
+        captured = false;
+      }
+      const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+      captured = captured && ec == cudaSuccess && graph != nullptr;
+      if (captured) captured = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();                          // a failed capture leaves no sticky error
+    const long long nl = h->launches - l0;
+    h->launches = l0;
+    h->pgraphs.push_back({in, out, nr, captured ? exec : nullptr, nl});
+    g = &h->pgraphs.back();
+  }
+  if (!g->exec) {
+    precond_apply(h, in, out, nr, s);
+    return;
+  }
+  HZ_CU(cudaGraphLaunch(g->exec, s));
+  h->launches += g->launches;
+}
+
+void clear_graphs(hz_handle* h) {
+  for (auto& e : h->pgraphs)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  h->pgraphs.clear();
+  h->pwarm.clear();
 }
 
 }  // namespace hz

@@ -135,6 +135,7 @@ struct Slab {
   void* st3 = nullptr;
   void* inj3 = nullptr;
   void* V = nullptr;
+  void* gpart = nullptr;     // 3-D: split-K partial sums of the layer GEMM [2][8][max_rhs][B]
 };
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.
@@ -179,6 +180,7 @@ struct Level {
   void* f3_C = nullptr;
   void* f3_R = nullptr;
   int* f3_piv = nullptr;
+  float* f3_pack = nullptr;  //   packed tensor-core operands (complex64)
   void* f3_desc = nullptr;
 };
 
@@ -253,6 +255,17 @@ struct hz_handle {
   hz::c128* gr_mu = nullptr;    //   adjoint fields
   double* gr_phi = nullptr;     //   per right-hand-side misfit [max_rhs]
   void* gm_state = nullptr;     // GMRES Arnoldi state (Hessenberg, rotations, ...) [max_rhs]
+  // CUDA graphs of the preconditioner application inside GMRES, one per
+  // (input, output, n_rhs); valid while the levels' buffers stay allocated
+  struct PrecGraph {
+    const void* in;
+    void* out;
+    int nr;
+    cudaGraphExec_t exec;
+    long long launches;         // kernels in the graph
+  };
+  std::vector<PrecGraph> pgraphs;
+  std::vector<int> pwarm;       // n_rhs values whose preconditioner has run once uncaptured
 };
 
 namespace hz {
@@ -352,6 +365,9 @@ template <typename R>
 void sweep_apply(hz_handle* h, Level& L, const cplx<R>* f, cplx<R>* u, int n_rhs,
                  cudaStream_t s);  // u = P f (P_X or P_UD)
 void precond_apply(hz_handle* h, const c128* r, c128* z, int n_rhs, cudaStream_t s);
+// The same through a captured CUDA graph (GMRES); clear_graphs drops them.
+void precond_graphed(hz_handle* h, const c128* r, c128* z, int n_rhs, cudaStream_t s);
+void clear_graphs(hz_handle* h);
 
 // gmres.cu
 void gmres_solve(hz_handle* h, const c128* f, c128* u, int n_rhs, cudaStream_t s);

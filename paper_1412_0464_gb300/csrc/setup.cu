@@ -501,7 +501,7 @@ void free_level(Level& L) {
     dfree(S.PhiP); dfree(S.PsiP);
     dfree(S.inj); dfree(S.Y);
     dfree(S.carry_f); dfree(S.carry_b);
-    dfree(S.st3); dfree(S.inj3); dfree(S.V);
+    dfree(S.st3); dfree(S.inj3); dfree(S.V); dfree(S.gpart);
   }
   L.slabs.clear();
   free_axis(L.ax);
@@ -513,7 +513,7 @@ void free_level(Level& L) {
     dfree(L.ifp[l]); dfree(L.refined[l]); dfree(L.q0[l]); dfree(L.q1[l]);
   }
   dfree(L.fac_desc); dfree(L.fac_sync);
-  dfree(L.f3_S); dfree(L.f3_C); dfree(L.f3_R); dfree(L.f3_piv); dfree(L.f3_desc);
+  dfree(L.f3_S); dfree(L.f3_C); dfree(L.f3_R); dfree(L.f3_piv); dfree(L.f3_pack); dfree(L.f3_desc);
   L = Level{};
 }
 

@@ -20,15 +20,15 @@
 // elimination step with pivot row r for column p is the rank-1 update
 //   S -= c rho^T,  c = S[:, p] - e_r,  rho = S[r, :] / S[r][p] + e_p,
 // which turns column p into the inverse's column.  Two levels of blocking:
-// within an outer block of kOuter columns, panels of 16 (or NB) columns: one
+// within an outer block of KO columns (hz_params.block_3d), panels of 16 (or NB) columns: one
 // CTA per chain eliminates the panel's columns on the panel only and records
-// the colmods c (C, B x kOuter), the pivot rows and 1 / S[r][p]; the pivot
+// the colmods c (C, B x KO), the pivot rows and 1 / S[r][p]; the pivot
 // rows' other columns follow from the short recurrence
 //   rho_t = (S[r_t, :] - sum_{s<t} C[r_t][s] rho_s) / S[r_t][p_t]
 // (for columns outside the outer block with all earlier steps of the block,
 // since those columns are not updated until the block ends); S -= C R then
 // updates the block's other columns (rank 16), and at the end of the block
-// all columns outside it (a dense complex GEMM of depth kOuter, on the tensor
+// all columns outside it (a dense complex GEMM of depth KO, on the tensor
 // cores in complex64).  Every launch takes all chains of all slabs at the
 // same step.
 //
@@ -70,7 +70,8 @@ void launch_pdl3(void (*k)(KArgs...), dim3 grid, unsigned block, cudaStream_t s,
 }
 
 constexpr int NB = 32;            // panel width of the blocked Gauss-Jordan inverse
-constexpr int kOuter = 128;       // outer block of panels (rank of the delayed update)
+constexpr int kOuterDefault = 128;  // outer block of panels (rank of the delayed update);
+constexpr int kOuterMax = 256;      //   hz_params.block_3d: 64, 128 or 256
 constexpr int kPanelThreads = 512;
 constexpr int kMaxB = 8192;       // largest block (pivot flags live in shared memory)
 
@@ -203,6 +204,7 @@ void build_slabs3d(hz_handle* h, Level& L, cudaStream_t s) {
     S.G = dmalloc(el * S.bstride * L.nz);
     S.Y = dmalloc(el * (size_t)L.nz * R_ * B);
     S.V = dmalloc(el * 2 * (size_t)R_ * B);
+    if (R_ > 4) S.gpart = dmalloc(el * 2 * 8 * (size_t)R_ * B);
   }
   L.mid = (L.nz - 1) / 2;
   HZ_CU(cudaStreamSynchronize(s));
@@ -224,12 +226,14 @@ struct FChain {
   cplx<R>* G;          // [nz][bstride]
   size_t bstride;
   cplx<R>* S;          // [B][B] Schur complement, inverted in place
-  cplx<R>* C;          // [kOuter][B] colmods of the current outer block (slot = column - P0)
-  cplx<R>* Rm;         // [kOuter][B] rowmods of the current outer block
-  cplx<R>* pinfo;      // [kOuter] 1 / pivot of the block's columns
+  cplx<R>* C;          // [KO][B] colmods of the current outer block (slot = column - P0)
+  cplx<R>* Rm;         // [KO][B] rowmods of the current outer block
+  cplx<R>* pinfo;      // [KO] 1 / pivot of the block's columns
   int* piv;            // [B] pivot row of column p
   int* pinv;           // [B] column whose pivot row is r (-1: not yet a pivot row)
-  int* prow;           // [kOuter] pivot rows of the block's columns
+  int* prow;           // [KO] pivot rows of the block's columns
+  float* Ap;           // complex64 tensor-core path: packed colmods (tc_pack_kernel)
+  float* Bp;           //   and rowmods of the current outer block
 };
 
 // Entry (i, j) of the in-layer block D_k (9-point in (y, x), zero elsewhere).
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
 // small enough: B (PW + 1) elements): one thread per row (rows tid, tid +
 // 1024, ...), panel rows padded to PW + 1 elements; per step a block-wide
 // pivot-key maximum, the scaled pivot row, and each thread's rank-1 update of
-// its rows with the next column's keys.  The colmods go to C [kOuter][B] at
+// its rows with the next column's keys.  The colmods go to C [KO][B] at
 // the panel's slots.
 constexpr int kSmemPanelThreads = 1024;
 
@@ -502,7 +506,7 @@ size_t panel_smem_bytes(int B) {
 // shared memory: Cp [NB][NB] (in-panel colmods at the pivot rows) and Cq
 // [NB][slot] (earlier slots).
 template <typename R>
-__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0, int nbw,
+__global__ void __launch_bounds__(64) gj_rowmod_kernel(const FChain<R>* chains, int p0, int nbw,
                                                         int P0, int KBw) {
   const FChain<R> c = chains[blockIdx.y];
   const int B = c.B;
@@ -537,6 +541,7 @@ __global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains,
 #pragma unroll
   for (int t = 0; t < NB; ++t) a[t] = t < nbp ? c.S[(size_t)pr[t] * B + j] : mk<R>(0, 0);
   if (j < P0 || j >= blk_hi) {
+#pragma unroll 4
     for (int q = 0; q < slot; ++q) {
       const cplx<R> x = c.Rm[(size_t)q * B + j];
 #pragma unroll
@@ -611,6 +616,18 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains,
     }
     __syncthreads();
   }
+  // all sixteen loads before the stores (in flight together)
+  cplx<R> sv[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx + 16 * b;
+      const bool ok = i < B && j < whi && (j < xlo || j >= xhi);
+      sv[a][b] = ok ? c.S[(size_t)i * B + j] : mk<R>(0, 0);
+    }
+  }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int i = i0 + ty + 16 * a;
@@ -619,8 +636,7 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains,
     for (int b = 0; b < 4; ++b) {
       const int j = j0 + tx + 16 * b;
       if (j >= whi || (j >= xlo && j < xhi)) continue;
-      cplx<R>* p = c.S + (size_t)i * B + j;
-      *p = *p - acc[a][b];
+      c.S[(size_t)i * B + j] = sv[a][b] - acc[a][b];
     }
   }
 }
@@ -638,24 +654,65 @@ __global__ void __launch_bounds__(256) gj_writeout_kernel(const FChain<R>* chain
 size_t update_smem(size_t el) { return (64 * (NB + 1) + NB * 64) * el; }
 
 // The outer-block update of the complex64 factorisation on the tensor cores
-// (tcgen05, kind::tf32, FP32 accumulation in tensor memory): one CTA per
-// 128 x 128 tile of S, 128 threads,
+// (tcgen05, kind::tf32, FP32 accumulation in tensor memory):
 //   S[i][j] -= sum_{t < kb} C[t][i] Rm[t][j]   (j outside [P0, P0 + kb)).
 // Complex products as real ones, Dr = Cr Rr - Ci Ri and Di = Cr Ri + Ci Rr,
 // each real product in three TF32 passes (x = hi + lo: hi hi + hi lo + lo hi)
-// so that the result keeps about FP32 accuracy.  The depth runs in stages of
-// kTcK: all threads split and store one stage's operands (eight K-major
-// 128 x kTcK TF32 tiles: Cr, Ci, Rr, Ri, hi and lo) while the MMAs of the
-// previous stage run; thread 0 issues the stage's 24 MMAs (128 x 128 x 8) and
-// commits them to the stage's mbarrier, which frees its buffer.  Dr and Di
-// occupy tensor-memory columns [0, 128) and [128, 256); the epilogue moves
-// them through shared memory (rows XOR-swizzled) and subtracts them from S in
-// coalesced rows.  Every wait is bounded (device flag on timeout).
+// so that the result keeps about FP32 accuracy.
+//
+// tc_pack_kernel splits the block's colmods and rowmods once into TF32 hi /
+// lo planes laid out as the MMA operands: per 128-row tile (rows of S for C,
+// columns of S for Rm) and per stage of kTcK depth, four K-major 128 x kTcK
+// tiles (re hi, re lo, im hi, im lo), 32 KB contiguous; rowmods of the
+// block's own columns and depths >= kb are zero.  gj_update_tc_kernel then
+// takes one 128 x 128 tile of S per CTA: warp 0 streams the stages (one 32 KB
+// bulk copy of each operand per stage, kTcBuf buffers), warp 1 issues the
+// stage's 24 MMAs (128 x 128 x 8) once its copies have landed and commits
+// them to the buffer's release barrier; Dr and Di accumulate in tensor-memory
+// columns [0, 128) and [128, 256).  The epilogue moves them through shared
+// memory (rows XOR-swizzled) and subtracts them from S in coalesced rows.
+// Every wait is bounded (device flag on timeout).
 constexpr int kTcM = 128;          // tile rows (MMA M) and columns (MMA N)
 constexpr int kTcK = 16;           // complex depth per stage
+constexpr int kTcBuf = 3;          // stage buffers
 constexpr uint32_t kTcTile = kTcM * kTcK * 4;    // one TF32 operand tile: 8 KB
-constexpr uint32_t kTcStage = 8 * kTcTile;       // Cr hi/lo, Ci hi/lo, Rr hi/lo, Ri hi/lo
-constexpr size_t kTcSmem = 2 * (size_t)kTcStage + 64;
+constexpr uint32_t kTcHalf = 4 * kTcTile;        // one operand's stage: re hi/lo, im hi/lo
+constexpr uint32_t kTcStage = 2 * kTcHalf;       // C half then Rm half: 64 KB
+constexpr size_t kTcSmem = kTcBuf * (size_t)kTcStage + 128;
+// packed operand floats per chain and operand: row tiles x stages (KO / kTcK) x 32 KB
+size_t tc_pack_floats(int Bmax, int KO) {
+  return (size_t)((Bmax + kTcM - 1) / kTcM) * (KO / kTcK) * (kTcHalf / 4);
+}
+
+// grid (row tiles, stages, 2 x chains): z even packs C (rows i), odd Rm
+// (columns j); thread r takes row r of the tile, four depths per 16-byte store.
+__global__ void __launch_bounds__(128) tc_pack_kernel(const FChain<float>* chains, int P0, int KBw) {
+  const FChain<float> c = chains[blockIdx.z >> 1];
+  const bool isC = (blockIdx.z & 1) == 0;
+  const int B = c.B;
+  if (P0 >= B) return;
+  const int kb = min(KBw, B - P0), xhi = P0 + kb;
+  const int tile = blockIdx.x, st = blockIdx.y, r = threadIdx.x;
+  const int q = tile * kTcM + r;                  // row i of S (C) or column j (Rm)
+  float* out = (isC ? c.Ap : c.Bp) + ((size_t)tile * (KBw / kTcK) + st) * (kTcHalf / 4);
+  const c64* src = isC ? c.C : c.Rm;
+  const bool live = q < B && (isC || q < P0 || q >= xhi);
+#pragma unroll
+  for (int kg = 0; kg < kTcK; kg += 4) {
+    float4 v[4];
+    float* f = (float*)v;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = st * kTcK + kg + u;
+      const c64 x = (live && kk < kb) ? src[(size_t)kk * B + q] : mk<float>(0, 0);
+      tc::split_tf32(x.re, f[0 * 4 + u], f[1 * 4 + u]);
+      tc::split_tf32(x.im, f[2 * 4 + u], f[3 * 4 + u]);
+    }
+    const uint32_t off = tc::kmajor_off(r, kg, kTcK / 4) / 4;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) *(float4*)(out + t * (kTcTile / 4) + off) = v[t];
+  }
+}
 
 __global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float>* chains, int P0,
                                                               int KBw, int* flag) {
@@ -667,12 +724,17 @@ __global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float
   if (i0 >= B || j0 >= B) return;
   if (j0 >= xlo && j0 + kTcM <= xhi) return;     // excluded columns only
   extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t* bar = (uint64_t*)(sm + 2 * kTcStage);                 // [0], [1]: stage buffers
-  uint32_t* tptr = (uint32_t*)(bar + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t* full = (uint64_t*)(sm + kTcBuf * kTcStage);   // [kTcBuf] operands landed
+  uint64_t* empty = full + kTcBuf;                          // [kTcBuf] buffer released
+  uint64_t* done = empty + kTcBuf;                          // all MMAs complete
+  uint32_t* tptr = (uint32_t*)(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < kTcBuf; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], 1);
+    }
+    mbar_init(done, 1);
     mbar_fence_init();
   }
   if (warp == 0) {
@@ -685,42 +747,28 @@ __global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float
   const uint32_t tmem = *tptr;
   const int nst = (kb + kTcK - 1) / kTcK;
   bool ok = true;
-  const int r = tid;                              // the operand row this thread stages
-  for (int st = 0; st < nst; ++st) {
-    const int buf = st & 1;
-    unsigned char* base = sm + buf * kTcStage;
-    if (st >= 2 && ok) ok = mbar_wait(&bar[buf], ((st - 2) >> 1) & 1, flag);
-#pragma unroll
-    for (int kg = 0; kg < kTcK; kg += 4) {
-      float4 v[8];
-      float* f = (float*)v;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int kk = st * kTcK + kg + q;
-        c64 a = mk<float>(0, 0), b = mk<float>(0, 0);
-        if (kk < kb) {
-          if (i0 + r < B) a = c.C[(size_t)kk * B + i0 + r];
-          const int j = j0 + r;
-          if (j < B && (j < xlo || j >= xhi)) b = c.Rm[(size_t)kk * B + j];
-        }
-        tc::split_tf32(a.re, f[0 * 4 + q], f[1 * 4 + q]);
-        tc::split_tf32(a.im, f[2 * 4 + q], f[3 * 4 + q]);
-        tc::split_tf32(b.re, f[4 * 4 + q], f[5 * 4 + q]);
-        tc::split_tf32(b.im, f[6 * 4 + q], f[7 * 4 + q]);
-      }
-      const uint32_t off = tc::kmajor_off(r, kg, kTcK / 4);
-#pragma unroll
-      for (int t = 0; t < 8; ++t) *(float4*)(base + t * kTcTile + off) = v[t];
+  if (warp == 0 && lane == 0) {                   // producer: bulk copies of the packed operands
+    const float* Ap = c.Ap + (size_t)blockIdx.y * (KBw / kTcK) * (kTcHalf / 4);
+    const float* Bp = c.Bp + (size_t)blockIdx.x * (KBw / kTcK) * (kTcHalf / 4);
+    for (int st = 0; st < nst && ok; ++st) {
+      const int buf = st % kTcBuf;
+      if (st >= kTcBuf) ok = mbar_wait(&empty[buf], ((st - kTcBuf) / kTcBuf) & 1, flag);
+      if (!ok) break;
+      unsigned char* dst = sm + buf * kTcStage;
+      mbar_expect_tx(&full[buf], kTcStage);
+      tma_load_1d(dst, Ap + (size_t)st * (kTcHalf / 4), kTcHalf, &full[buf]);
+      tma_load_1d(dst + kTcHalf, Bp + (size_t)st * (kTcHalf / 4), kTcHalf, &full[buf]);
     }
-    fence_proxy_async_smem();
-    ok = __syncthreads_and(ok);                   // uniform: a timed-out wait stops every thread
-    if (!ok) break;
-    if (tid == 0) {
+  } else if (warp == 1 && lane == 0) {            // MMA issuer
+    constexpr uint32_t lbo = 128, sbo = (kTcK / 4) * 128;
+    constexpr uint32_t id = tc::idesc_tf32(kTcM, kTcM, false);
+    constexpr uint32_t idn = tc::idesc_tf32(kTcM, kTcM, true);
+    for (int st = 0; st < nst && ok; ++st) {
+      const int buf = st % kTcBuf;
+      ok = mbar_wait(&full[buf], (st / kTcBuf) & 1, flag);
+      if (!ok) break;
       tc::fence_after_sync();
-      const uint32_t sb = smem_u32(base);
-      constexpr uint32_t lbo = 128, sbo = (kTcK / 4) * 128;
-      constexpr uint32_t id = tc::idesc_tf32(kTcM, kTcM, false);
-      constexpr uint32_t idn = tc::idesc_tf32(kTcM, kTcM, true);
+      const uint32_t sb = smem_u32(sm + buf * kTcStage);
 #pragma unroll
       for (int ks = 0; ks < kTcK / 8; ++ks) {
         const uint32_t ko = ks * 256;             // two core matrices along K per MMA
@@ -740,15 +788,16 @@ __global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float
         tc::mma_tf32(tmem + 128, d(2), d(5), id, true);
         tc::mma_tf32(tmem + 128, d(3), d(4), id, true);
       }
-      tc::commit(&bar[buf]);
+      tc::commit(&empty[buf]);
     }
+    if (ok) tc::commit(done);                     // covers every MMA issued before it
   }
-  // the last stage's commit covers every MMA issued before it
-  if (ok) ok = mbar_wait(&bar[(nst - 1) & 1], ((nst - 1) >> 1) & 1, flag);
+  __syncwarp();
+  ok = mbar_wait(done, 0, flag);
   ok = __syncthreads_and(ok);
   tc::fence_after_sync();
   c64* D = (c64*)sm;                              // [128][128], column XOR-swizzled by row
-  const int row = warp * 32 + (tid & 31);
+  const int row = warp * 32 + lane;
   if (ok) {
 #pragma unroll 1
     for (int cc = 0; cc < kTcM; cc += 32) {
@@ -762,18 +811,36 @@ __global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float
   tc::fence_before_sync();
   __syncthreads();
   if (ok) {
-    const int j = j0 + tid;
-    const bool col_ok = j < B && (j < xlo || j >= xhi);
-    for (int rr = 0; rr < kTcM; ++rr) {
-      const int i = i0 + rr;
-      if (i >= B) break;
-      if (col_ok) {
+    // thread: columns j0 + cp, j0 + cp + 1 of the rows 2 u + rs; sixteen rows'
+    // loads are issued before any store, so that they are in flight together
+    const int cp = (tid & 63) * 2, rs = tid >> 6;
+    const int j = j0 + cp;
+    const bool c0 = j < B && (j < xlo || j >= xhi);
+    const bool c1 = j + 1 < B && (j + 1 < xlo || j + 1 >= xhi);
+#pragma unroll 1
+    for (int rb = 0; rb < kTcM; rb += 32) {
+      float2 x0[16], x1[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int i = i0 + rb + 2 * u + rs;
+        const float2* p = (const float2*)(c.S + (size_t)i * B + j);
+        x0[u] = (i < B && c0) ? p[0] : make_float2(0.f, 0.f);
+        x1[u] = (i < B && c1) ? p[1] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int rr = rb + 2 * u + rs, i = i0 + rr;
+        if (i >= B) continue;
         float2* p = (float2*)(c.S + (size_t)i * B + j);
-        const c64 v = D[rr * kTcM + (tid ^ (rr & 31))];
-        float2 x = *p;
-        x.x -= v.re;
-        x.y -= v.im;
-        *p = x;
+        const int sw = rr & 31;
+        if (c0) {
+          const c64 v = D[rr * kTcM + (cp ^ sw)];
+          p[0] = make_float2(x0[u].x - v.re, x0[u].y - v.im);
+        }
+        if (c1) {
+          const c64 v = D[rr * kTcM + ((cp + 1) ^ sw)];
+          p[1] = make_float2(x1[u].x - v.re, x1[u].y - v.im);
+        }
       }
     }
   }
@@ -782,7 +849,6 @@ __global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float
     tc::tmem_dealloc(tmem, 256);
   }
 }
-
 
 // ------------------------------------------------------------------- solves
 // Right-hand side of a 3-D slab solve (SubdomSolve, Table 2) into the layer
@@ -971,6 +1037,87 @@ __global__ void __launch_bounds__(256) slab3_gemv_kernel(Gemv3<R> a) {
   }
 }
 
+// The layer product for many right-hand sides as a register-tiled complex
+// GEMM, Y (B x nr) = G (B x B) V (B x nr): a CTA takes 64 rows x 32
+// right-hand sides over one of `nsplit` column ranges (split K, so that
+// about two CTAs run per SM), streams G and V through shared memory in
+// depth chunks of GK, and each thread accumulates 2 rows x 4 right-hand
+// sides.  The partial sums go to part [np][nsplit][nr][B]; the reduce kernel
+// adds them in a fixed order (deterministic) into y.
+constexpr int kG3Rows = 64, kG3Rhs = 32;
+template <typename R> struct G3K { static constexpr int v = 32; };
+template <> struct G3K<double> { static constexpr int v = 16; };
+
+template <typename R>
+__global__ void __launch_bounds__(256) slab3_gemm_kernel(Gemv3<R> a, int nsplit, cplx<R>* part) {
+  pdl_wait3();
+  constexpr int GK = G3K<R>::v;
+  const GemvPiece<R> P = blockIdx.z == 0 ? a.p[0] : a.p[1];
+  const int B = a.B, tid = threadIdx.x;
+  const int i0 = blockIdx.x * kG3Rows, sp = blockIdx.y;
+  const int kper = (B + nsplit - 1) / nsplit;
+  const int klo = sp * kper, khi = min(B, klo + kper);
+  __shared__ cplx<R> Gs[kG3Rows][GK + 1];
+  __shared__ cplx<R> Vs[kG3Rhs][GK + 1];
+  const int tx = tid & 7, ty = tid >> 3;          // rhs 4 tx .. 4 tx + 3, rows 2 ty, 2 ty + 1
+  cplx<R>* pout = part + ((size_t)blockIdx.z * nsplit + sp) * a.nr * B;
+  for (int r0 = 0; r0 < a.nr; r0 += kG3Rhs) {
+    cplx<R> acc[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[q][u] = mk<R>(0, 0);
+    for (int k0 = klo; k0 < khi; k0 += GK) {
+      for (int e = tid; e < kG3Rows * GK; e += 256) {
+        const int rr = e / GK, k = e - rr * GK;
+        const int i = i0 + rr, kk = k0 + k;
+        Gs[rr][k] = (i < B && kk < khi) ? P.G[(size_t)i * B + kk] : mk<R>(0, 0);
+      }
+      for (int e = tid; e < kG3Rhs * GK; e += 256) {
+        const int r = e / GK, k = e - r * GK;
+        const int kk = k0 + k;
+        Vs[r][k] = (r0 + r < a.nr && kk < khi) ? P.v[(size_t)(r0 + r) * B + kk] : mk<R>(0, 0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < GK; ++k) {
+        const cplx<R> g0 = Gs[2 * ty][k], g1 = Gs[2 * ty + 1][k];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const cplx<R> v = Vs[4 * tx + u][k];
+          cfma(acc[0][u], g0, v);
+          cfma(acc[1][u], g1, v);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = i0 + 2 * ty + q;
+      if (i >= B) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 4 * tx + u;
+        if (r < a.nr) pout[(size_t)r * B + i] = acc[q][u];
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void slab3_gemm_reduce_kernel(Gemv3<R> a, int nsplit, const cplx<R>* part) {
+  pdl_wait3();
+  const GemvPiece<R> P = blockIdx.z == 0 ? a.p[0] : a.p[1];
+  const int B = a.B;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (i >= B || r >= a.nr) return;
+  const cplx<R>* pp = part + (size_t)blockIdx.z * nsplit * a.nr * B + (size_t)r * B + i;
+  cplx<R> s = mk<R>(0, 0);
+  for (int sp = 0; sp < nsplit; ++sp) s = s + pp[(size_t)sp * a.nr * B];
+  cplx<R>* out = P.y + (size_t)r * B + i;
+  *out = a.mode == 0 ? s : *out - s;
+}
+
 // Epilogue of a 3-D slab solve (Table 2): the slab solution's core columns
 // (ua, ub] into the global field, the layers at e2, e2+1 (B2) and e4, e4+1
 // (B4) for the transmission, or the whole slab field (raw).
@@ -1024,12 +1171,16 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
   int Bmax = 0;
   for (int j = 1; j <= J; ++j) Bmax = std::max(Bmax, L.slabs[j].B);
   const int nch = 2 * J;
-  const size_t sS = (size_t)Bmax * Bmax, sC = (size_t)Bmax * kOuter;
+  // outer block width (a multiple of both panel widths)
+  const int KO = h->p.block_3d > 0 ? h->p.block_3d : kOuterDefault;
+  const size_t sS = (size_t)Bmax * Bmax, sC = (size_t)Bmax * KO;
   if (!L.f3_S) {   // work buffers and descriptors: built by the first factorisation, kept
     L.f3_S = dmalloc(el * sS * nch);
     L.f3_C = dmalloc(el * sC * nch);
-    L.f3_R = dmalloc(el * sC * nch + el * kOuter * nch);
-    L.f3_piv = (int*)dmalloc(sizeof(int) * ((size_t)2 * Bmax + kOuter) * nch);
+    L.f3_R = dmalloc(el * sC * nch + el * KO * nch);
+    L.f3_piv = (int*)dmalloc(sizeof(int) * ((size_t)2 * Bmax + KO) * nch);
+    const size_t npk = tc_pack_floats(Bmax, KO);
+    if (sizeof(R) == 4) L.f3_pack = (float*)dmalloc(sizeof(float) * npk * 2 * nch);
     std::vector<FChain<R>> all;
     auto chain = [&](int j, int c) {
       const Slab& S = L.slabs[j];
@@ -1041,9 +1192,13 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       f.S = (cplx<R>*)L.f3_S + sS * c;
       f.C = (cplx<R>*)L.f3_C + sC * c;
       f.Rm = (cplx<R>*)L.f3_R + sC * c;
-      f.pinfo = (cplx<R>*)L.f3_R + sC * nch + (size_t)kOuter * c;
-      int* ip = L.f3_piv + ((size_t)2 * Bmax + kOuter) * c;
+      f.pinfo = (cplx<R>*)L.f3_R + sC * nch + (size_t)KO * c;
+      int* ip = L.f3_piv + ((size_t)2 * Bmax + KO) * c;
       f.piv = ip; f.pinv = ip + Bmax; f.prow = ip + 2 * Bmax;
+      if (L.f3_pack) {
+        f.Ap = L.f3_pack + npk * 2 * c;
+        f.Bp = f.Ap + npk;
+      }
       return f;
     };
     for (int t = 0; t < T; ++t)
@@ -1074,7 +1229,7 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
     HZ_CU(cudaFuncSetAttribute(gj_update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)update_smem(el)));
     HZ_CU(cudaFuncSetAttribute(gj_rowmod_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)rowmod_smem<R>(kOuter)));
+                               (int)rowmod_smem<R>(kOuterMax)));
     HZ_CU(cudaFuncSetAttribute(gj_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTcSmem));
   }
@@ -1105,11 +1260,11 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       }
     });
     h->launches += fe ? 1 + 2 * nterm : 1;
-    // outer blocks of kOuter columns: inner panels of nbw columns update the
+    // outer blocks of KO columns: inner panels of nbw columns update the
     // block's own columns (rank nbw); the block's colmods and rowmods then
-    // update every other column at once (rank kOuter; tensor cores in complex64)
-    for (int P0 = 0; P0 < Bmax; P0 += kOuter) {
-      const int bw = std::min(kOuter, Bmax - P0);
+    // update every other column at once (rank KO; tensor cores in complex64)
+    for (int P0 = 0; P0 < Bmax; P0 += KO) {
+      const int bw = std::min(KO, Bmax - P0);
       for (int p0 = P0; p0 < P0 + bw; p0 += nbw) {
         const int slot = p0 - P0;
         timed(h, "slab_factor3d_panel", 0.0, s, [&] {
@@ -1119,14 +1274,14 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
             gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0, slot);
         });
         timed(h, "slab_factor3d_rowmod", 0.0, s, [&] {
-          gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 128), cnt), 128, rowmod_smem<R>(slot), s>>>(
-              d, p0, nbw, P0, kOuter);
+          gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 64), cnt), 64, rowmod_smem<R>(slot), s>>>(
+              d, p0, nbw, P0, KO);
         });
         const int nbp = std::min(nbw, Bmax - p0);
         const double fli = 8.0 * (double)Bmax * std::max(0, bw - nbp) * nbp * cnt;
         timed(h, "slab_factor3d_inner", fli, s, [&] {
           gj_update_kernel<R><<<dim3(cdiv(bw, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el), s>>>(
-              d, p0, nbw, P0, kOuter, 1);
+              d, p0, nbw, P0, KO, 1);
         });
         h->launches += 3;
       }
@@ -1134,14 +1289,17 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       const double fl = 8.0 * (double)Bmax * (Bmax - bw) * bw * cnt;
       if (Bmax > bw) {
         timed(h, "slab_factor3d_update", fl, s, [&] {
-          if (use_tc)
+          if (use_tc) {
+            tc_pack_kernel<<<dim3(cdiv(Bmax, kTcM), KO / kTcK, 2 * cnt), 128, 0, s>>>(
+                (const FChain<float>*)d, P0, KO);
             gj_update_tc_kernel<<<dim3(cdiv(Bmax, kTcM), cdiv(Bmax, kTcM), cnt), 128, kTcSmem, s>>>(
-                (const FChain<float>*)d, P0, kOuter, h->dev_flag);
+                (const FChain<float>*)d, P0, KO, h->dev_flag);
+          }
           else
             gj_update_kernel<R><<<dim3(cdiv(Bmax, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el),
-                                  s>>>(d, P0, kOuter, P0, kOuter, 0);
+                                  s>>>(d, P0, KO, P0, KO, 0);
         });
-        h->launches += 1;
+        h->launches += use_tc ? 2 : 1;
       }
     }
     timed(h, "slab_factor3d_writeout", 0.0, s,
@@ -1188,11 +1346,25 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
     pa.np = np;
     launch_pdl3(slab3_prep_kernel<R>, dim3(cdiv(B, 128), nr, np), 128, s, pa);
   };
+  // many right-hand sides: the split-K register-tiled GEMM and its reduction
+  // (partial sums in the slab's GEMM scratch); few: the GEMV kernel
+  const bool tiled = nr > 4 && S.gpart != nullptr;
+  const int nI = cdiv(B, kG3Rows);
+  const int nsplit = std::max(1, std::min(8, cdiv(2 * h->sms, 2 * nI)));
   auto gemv = [&](int np, int mode) {
     ga.np = np;
     ga.mode = mode;
-    timed(h, "slab3_gemv", np * (gbytes + 2.0 * nr * B * el), s,
-          [&] { launch_pdl3(slab3_gemv_kernel<R, NR>, dim3(gblocks, np), 256, s, ga); });
+    timed(h, "slab3_gemv", np * (gbytes + 2.0 * nr * B * el), s, [&] {
+      if (tiled) {
+        cplx<R>* part = (cplx<R>*)S.gpart;
+        launch_pdl3(slab3_gemm_kernel<R>, dim3(nI, nsplit, np), 256, s, ga, nsplit, part);
+        launch_pdl3(slab3_gemm_reduce_kernel<R>, dim3(cdiv(B, 128), nr, np), 128, s, ga, nsplit,
+                    (const cplx<R>*)part);
+        h->launches++;
+      } else {
+        launch_pdl3(slab3_gemv_kernel<R, NR>, dim3(gblocks, np), 256, s, ga);
+      }
+    });
   };
   // forward: y_t = G_t (f_t - L_t y_{t-1}), both chains per launch
   for (int t = 0; t < T; ++t) {

@@ -46,7 +46,8 @@ def _params(**kw):
                                  dict(boundary=1, sponge_damping=1.5),
                                  dict(boundary=1, sponge_damping=0.01, w_out=0),
                                  dict(sweep=hz.HZ_SWEEP_NX, n_cell=0),
-                                 dict(sweep=hz.HZ_SWEEP_NX, n_cell=3)])
+                                 dict(sweep=hz.HZ_SWEEP_NX, n_cell=3), dict(block_3d=96),
+                                 dict(block_3d=-1)])
 def test_setup_rejects_bad_parameters(L, bad):
     h = ctypes.c_void_p()
     st = L.hz_setup(ctypes.byref(_params(**bad)), ctypes.c_void_p(1), ctypes.byref(h))
