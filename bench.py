@@ -55,6 +55,10 @@ def _args():
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the workload's recipe at this interior size (not a bench line)")
     ap.add_argument("--J", type=int, default=0, help="profiling only: slab count with --n")
+    ap.add_argument("--write-traffic", nargs=3, metavar=("CSV", "COMMAND", "WORKLOAD"),
+                    help="write profiles/traffic.json from an ncu DRAM-bytes capture and exit")
+    ap.add_argument("--summarize-launches", metavar="CSV",
+                    help="print the per-kernel table of an ncu launch list and exit")
     return ap.parse_args()
 
 
@@ -142,23 +146,108 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _slab_hash():
+# kernels whose DRAM traffic profiles/traffic.json records: bench tag -> (kernel
+# name patterns summed per launch, the sources that define them).  An entry is
+# used only while the hash of those sources matches the one stored with it.
+TRAFFIC_KERNELS = {
+    "slab_factor": (["slab_factor_fused_kernel"],
+                    ["slab.cuh", "slab_c64.cu", "slab_c128.cu", "ptx.cuh", "hz_internal.h"]),
+    "stencil_c64": (["op_pair_kernel_c64"], ["stencil.cu", "hz_internal.h"]),
+    "stencil_c128": (["op_kernel<double"], ["stencil.cu", "hz_internal.h"]),
+    "slab_factor3d_update": (["tc_pack_kernel", "gj_update_tc_kernel"],
+                             ["slab3d.cu", "tc.cuh", "ptx.cuh", "hz_internal.h"]),
+    "slab3_gemv": (["slab3_gemm_kernel", "slab3_gemm_reduce_kernel"],
+                   ["slab3d.cu", "hz_internal.h"]),
+}
+
+
+def _src_hash(files):
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1412_0464_gb300", "csrc"))):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1412_0464_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _traffic(tag):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    """DRAM bytes per launch from the committed ncu summary, if its kernel's
+    sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or tag not in TRAFFIC_KERNELS:
         return None
-    d = json.load(open(p))
-    if d.get("source_hash") != _slab_hash():
+    e = json.load(open(p)).get("kernels", {}).get(tag)
+    if e is None or e.get("source_hash") != _src_hash(TRAFFIC_KERNELS[tag][1]):
         return None
-    e = d.get("kernels", {}).get(tag)
-    return None if e is None else e.get("dram_bytes_per_launch_full_size")
+    return e.get("dram_bytes_per_launch")
+
+
+def _ncu_rows(path):
+    """(kernel name, metric, value) rows of an `ncu --csv` log."""
+    import csv
+    rows = []
+    with open(path) as f:
+        lines = [l for l in f if l.startswith('"')]
+    for r in csv.DictReader(lines):
+        try:
+            v = float(r["Metric Value"].replace(",", ""))
+        except (KeyError, ValueError):
+            continue
+        rows.append((r["ID"], r["Kernel Name"], r["Metric Name"], v))
+    return rows
+
+
+def write_traffic(csv_path, command, workload):
+    """profiles/traffic.json from an ncu capture of dram__bytes_read.sum and
+    dram__bytes_write.sum (one pass, no replay)."""
+    rows = _ncu_rows(csv_path)
+    per = {}
+    for lid, name, metric, v in rows:
+        if metric in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            per.setdefault((lid, name), 0.0)
+            per[(lid, name)] += v
+    out = {"command": command, "workload": workload,
+           "note": "DRAM bytes (read + write) per launch, mean over the captured launches; "
+                   "a tag that sums two kernels (pack + update, GEMM + reduce) adds their means",
+           "kernels": {}}
+    for tag, (pats, files) in TRAFFIC_KERNELS.items():
+        total, ok = 0.0, True
+        counts = []
+        for pat in pats:
+            vals = [v for (lid, name), v in per.items() if pat in name.split("(")[0]]
+            if not vals:
+                ok = False
+                break
+            total += sum(vals) / len(vals)
+            counts.append(len(vals))
+        if ok:
+            out["kernels"][tag] = {"dram_bytes_per_launch": total, "launches_captured": counts,
+                                   "source_hash": _src_hash(files)}
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    old = json.load(open(p)).get("kernels", {}) if os.path.exists(p) else {}
+    for tag, e in old.items():              # keep entries of kernels this capture did not see
+        if tag not in out["kernels"] and tag in TRAFFIC_KERNELS:
+            out["kernels"][tag] = e
+    with open(p, "w") as f:
+        json.dump(out, f, indent=1)
+    return out
+
+
+def summarize_launches(csv_path):
+    """Markdown table of an ncu launch list (gpu__time_duration.sum): launches,
+    total time and share per kernel."""
+    rows = _ncu_rows(csv_path)
+    agg = {}
+    for lid, name, metric, v in rows:
+        if metric != "gpu__time_duration.sum":
+            continue
+        k = name.split("(")[0].replace("void ", "").replace("hz::", "").replace("(anonymous namespace)::", "")
+        a = agg.setdefault(k, [0, 0.0])
+        a[0] += 1
+        a[1] += v
+    tot = sum(v[1] for v in agg.values())
+    lines = ["| kernel | launches | total (ms) | share |", "|---|---|---|---|"]
+    for k, (n, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        lines.append(f"| `{k}` | {n} | {t / 1e6:.3f} | {t / tot:.3f} |")
+    return "\n".join(lines)
 
 
 def adjoint_leg(hz, synth, stream, flush, n=512, reps=3, cfg=None):
@@ -326,6 +415,13 @@ def reference_arm(args):
 
 def main():
     args = _args()
+    if args.write_traffic:
+        out = write_traffic(*args.write_traffic)
+        print(json.dumps({t: e["dram_bytes_per_launch"] for t, e in out["kernels"].items()}))
+        return
+    if args.summarize_launches:
+        print(summarize_launches(args.summarize_launches))
+        return
     if args.impl == "reference":
         return reference_arm(args)
     import numpy as np

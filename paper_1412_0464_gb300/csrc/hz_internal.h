@@ -135,7 +135,7 @@ struct Slab {
   void* st3 = nullptr;
   void* inj3 = nullptr;
   void* V = nullptr;
-  void* gpart = nullptr;     // 3-D: split-K partial sums of the layer GEMM [2][8][max_rhs][B]
+  void* gpart = nullptr;     // 3-D: split-K partial sums of the layer GEMM [2][16][max_rhs][B]
 };
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.

@@ -74,6 +74,7 @@ constexpr int kOuterDefault = 128;  // outer block of panels (rank of the delaye
 constexpr int kOuterMax = 256;      //   hz_params.block_3d: 64, 128 or 256
 constexpr int kPanelThreads = 512;
 constexpr int kMaxB = 8192;       // largest block (pivot flags live in shared memory)
+constexpr int kG3MaxSplit = 16;   // split-K ranges of the layer GEMM (many right-hand sides)
 
 template <typename R>
 __device__ __forceinline__ cplx<R> ldg(const cplx<R>* p) { return *p; }
@@ -204,7 +205,7 @@ void build_slabs3d(hz_handle* h, Level& L, cudaStream_t s) {
     S.G = dmalloc(el * S.bstride * L.nz);
     S.Y = dmalloc(el * (size_t)L.nz * R_ * B);
     S.V = dmalloc(el * 2 * (size_t)R_ * B);
-    if (R_ > 4) S.gpart = dmalloc(el * 2 * 8 * (size_t)R_ * B);
+    if (R_ > 4) S.gpart = dmalloc(el * 2 * kG3MaxSplit * (size_t)R_ * B);
   }
   L.mid = (L.nz - 1) / 2;
   HZ_CU(cudaStreamSynchronize(s));
@@ -1038,13 +1039,13 @@ __global__ void __launch_bounds__(256) slab3_gemv_kernel(Gemv3<R> a) {
 }
 
 // The layer product for many right-hand sides as a register-tiled complex
-// GEMM, Y (B x nr) = G (B x B) V (B x nr): a CTA takes 64 rows x 32
+// GEMM, Y (B x nr) = G (B x B) V (B x nr): a CTA takes 128 rows x 32
 // right-hand sides over one of `nsplit` column ranges (split K, so that
-// about two CTAs run per SM), streams G and V through shared memory in
-// depth chunks of GK, and each thread accumulates 2 rows x 4 right-hand
-// sides.  The partial sums go to part [np][nsplit][nr][B]; the reduce kernel
-// adds them in a fixed order (deterministic) into y.
-constexpr int kG3Rows = 64, kG3Rhs = 32;
+// about four CTAs run per SM), streams G and V through shared memory in
+// depth chunks of GK, and each thread accumulates 4 rows (ty + 32 q) x 4
+// right-hand sides.  The partial sums go to part [np][nsplit][nr][B]; the
+// reduce kernel adds them in a fixed order (deterministic) into y.
+constexpr int kG3Rows = 128, kG3Rhs = 32;
 template <typename R> struct G3K { static constexpr int v = 32; };
 template <> struct G3K<double> { static constexpr int v = 16; };
 
@@ -1059,12 +1060,12 @@ __global__ void __launch_bounds__(256) slab3_gemm_kernel(Gemv3<R> a, int nsplit,
   const int klo = sp * kper, khi = min(B, klo + kper);
   __shared__ cplx<R> Gs[kG3Rows][GK + 1];
   __shared__ cplx<R> Vs[kG3Rhs][GK + 1];
-  const int tx = tid & 7, ty = tid >> 3;          // rhs 4 tx .. 4 tx + 3, rows 2 ty, 2 ty + 1
+  const int tx = tid & 7, ty = tid >> 3;          // rhs 4 tx .. 4 tx + 3, rows ty + 32 q
   cplx<R>* pout = part + ((size_t)blockIdx.z * nsplit + sp) * a.nr * B;
   for (int r0 = 0; r0 < a.nr; r0 += kG3Rhs) {
-    cplx<R> acc[2][4];
+    cplx<R> acc[4][4];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[q][u] = mk<R>(0, 0);
     for (int k0 = klo; k0 < khi; k0 += GK) {
@@ -1079,21 +1080,23 @@ __global__ void __launch_bounds__(256) slab3_gemm_kernel(Gemv3<R> a, int nsplit,
         Vs[r][k] = (r0 + r < a.nr && kk < khi) ? P.v[(size_t)(r0 + r) * B + kk] : mk<R>(0, 0);
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int k = 0; k < GK; ++k) {
-        const cplx<R> g0 = Gs[2 * ty][k], g1 = Gs[2 * ty + 1][k];
+        cplx<R> g[4], v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const cplx<R> v = Vs[4 * tx + u][k];
-          cfma(acc[0][u], g0, v);
-          cfma(acc[1][u], g1, v);
-        }
+        for (int q = 0; q < 4; ++q) g[q] = Gs[ty + 32 * q][k];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = Vs[4 * tx + u][k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cfma(acc[q][u], g[q], v[u]);
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = i0 + 2 * ty + q;
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + ty + 32 * q;
       if (i >= B) continue;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -1350,7 +1353,8 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
   // (partial sums in the slab's GEMM scratch); few: the GEMV kernel
   const bool tiled = nr > 4 && S.gpart != nullptr;
   const int nI = cdiv(B, kG3Rows);
-  const int nsplit = std::max(1, std::min(8, cdiv(2 * h->sms, 2 * nI)));
+  // at least ~4 CTAs per SM (two pieces), so that the last wave is short
+  const int nsplit = std::max(1, std::min(kG3MaxSplit, cdiv(4 * h->sms, 2 * nI)));
   auto gemv = [&](int np, int mode) {
     ga.np = np;
     ga.mode = mode;
