@@ -506,54 +506,74 @@ size_t panel_smem_bytes(int B) {
 // Zero on the panel columns (the panel kernel has finished them).  Dynamic
 // shared memory: Cp [NB][NB] (in-panel colmods at the pivot rows) and Cq
 // [NB][slot] (earlier slots).
-template <typename R>
-__global__ void __launch_bounds__(64) gj_rowmod_kernel(const FChain<R>* chains, int p0, int nbw,
-                                                        int P0, int KBw) {
+template <typename R, int PW>
+__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0, int P0,
+                                                         int KBw) {
+  // 32 columns per CTA; warp w takes a quarter of the earlier slots of the
+  // delayed sum, warp 0 adds the quarters and runs the in-panel recurrence
   const FChain<R> c = chains[blockIdx.y];
   const int B = c.B;
   if (p0 >= B) return;
-  const int nbp = min(nbw, B - p0), slot = p0 - P0, blk_hi = min(P0 + KBw, B);
+  const int nbp = min(PW, B - p0), slot = p0 - P0, blk_hi = min(P0 + KBw, B);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* Cp = (cplx<R>*)smem_raw;              // [NB][NB]
-  cplx<R>* Cq = Cp + NB * NB;                    // [NB][slot]
-  __shared__ cplx<R> inv[NB];
-  __shared__ int pr[NB];
-  for (int t = threadIdx.x; t < NB; t += blockDim.x) {
+  cplx<R>* Cp = (cplx<R>*)smem_raw;              // [PW][PW]
+  cplx<R>* Cq = Cp + PW * PW;                    // [PW][slot]
+  cplx<R>* part = Cq + PW * slot;                // [3][PW][32]
+  __shared__ cplx<R> inv[PW];
+  __shared__ int pr[PW];
+  for (int t = threadIdx.x; t < PW; t += blockDim.x) {
     inv[t] = t < nbp ? c.pinfo[slot + t] : mk<R>(0, 0);
     pr[t] = t < nbp ? c.prow[slot + t] : 0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int t = e / NB, q = e - t * NB;
+  for (int e = threadIdx.x; e < PW * PW; e += blockDim.x) {
+    const int t = e / PW, q = e - t * PW;
     Cp[e] = (t < nbp && q < t) ? c.C[(size_t)(slot + q) * B + pr[t]] : mk<R>(0, 0);
   }
-  for (int e = threadIdx.x; e < NB * slot; e += blockDim.x) {
+  for (int e = threadIdx.x; e < PW * slot; e += blockDim.x) {
     const int t = e / slot, q = e - t * slot;
     Cq[e] = t < nbp ? c.C[(size_t)q * B + pr[t]] : mk<R>(0, 0);
   }
   __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= B) return;
-  if (j >= p0 && j < p0 + nbp) {
+  const int j = blockIdx.x * 32 + lane;
+  const bool live = j < B && (j < p0 || j >= p0 + nbp);
+  const bool outside = j < P0 || j >= blk_hi;
+  cplx<R> a[PW];
+#pragma unroll
+  for (int t = 0; t < PW; ++t) a[t] = mk<R>(0, 0);
+  if (live && outside) {                          // this warp's quarter of the delayed sum
+    const int qn = (slot + 3) / 4, q0 = warp * qn, q1 = min(slot, q0 + qn);
+#pragma unroll 4
+    for (int q = q0; q < q1; ++q) {
+      const cplx<R> x = c.Rm[(size_t)q * B + j];
+#pragma unroll
+      for (int t = 0; t < PW; ++t) a[t] = a[t] - Cq[t * slot + q] * x;
+    }
+  }
+  if (warp > 0) {
+#pragma unroll
+    for (int t = 0; t < PW; ++t) part[((warp - 1) * PW + t) * 32 + lane] = a[t];
+  }
+  __syncthreads();
+  if (warp > 0 || j >= B) return;
+  if (!live) {                                    // panel column: the panel kernel finished it
     for (int t = 0; t < nbp; ++t) c.Rm[(size_t)(slot + t) * B + j] = mk<R>(0, 0);
     return;
   }
-  cplx<R> a[NB];
 #pragma unroll
-  for (int t = 0; t < NB; ++t) a[t] = t < nbp ? c.S[(size_t)pr[t] * B + j] : mk<R>(0, 0);
-  if (j < P0 || j >= blk_hi) {
-#pragma unroll 4
-    for (int q = 0; q < slot; ++q) {
-      const cplx<R> x = c.Rm[(size_t)q * B + j];
-#pragma unroll
-      for (int t = 0; t < NB; ++t) a[t] = a[t] - Cq[t * slot + q] * x;
-    }
+  for (int t = 0; t < PW; ++t) {
+    cplx<R> v = t < nbp ? c.S[(size_t)pr[t] * B + j] : mk<R>(0, 0);
+    if (outside)
+      v = v + a[t] + part[(0 * PW + t) * 32 + lane] + part[(1 * PW + t) * 32 + lane] +
+          part[(2 * PW + t) * 32 + lane];
+    a[t] = v;
   }
 #pragma unroll
-  for (int t = 0; t < NB; ++t) {
+  for (int t = 0; t < PW; ++t) {
     if (t < nbp) {
 #pragma unroll
-      for (int q = 0; q < t; ++q) a[t] = a[t] - Cp[t * NB + q] * a[q];
+      for (int q = 0; q < t; ++q) a[t] = a[t] - Cp[t * PW + q] * a[q];
       a[t] = a[t] * inv[t];
       c.Rm[(size_t)(slot + t) * B + j] = a[t];
     }
@@ -561,7 +581,9 @@ __global__ void __launch_bounds__(64) gj_rowmod_kernel(const FChain<R>* chains, 
 }
 
 template <typename R>
-size_t rowmod_smem(int slot) { return (size_t)NB * (NB + slot) * sizeof(cplx<R>); }
+size_t rowmod_smem(int pw, int slot) {
+  return (size_t)pw * (pw + slot + 3 * 32) * sizeof(cplx<R>);
+}
 
 // S[i][j] -= sum_{t < depth} C[slot + t][i] Rm[slot + t][j], 64 x 64 tile per
 // CTA (256 threads, 4 x 4 outputs each: rows ty + 16 a, columns tx + 16 b),
@@ -1231,8 +1253,10 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s));
     HZ_CU(cudaFuncSetAttribute(gj_update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)update_smem(el)));
-    HZ_CU(cudaFuncSetAttribute(gj_rowmod_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)rowmod_smem<R>(kOuterMax)));
+    HZ_CU(cudaFuncSetAttribute(gj_rowmod_kernel<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rowmod_smem<R>(16, kOuterMax)));
+    HZ_CU(cudaFuncSetAttribute(gj_rowmod_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rowmod_smem<R>(NB, kOuterMax)));
     HZ_CU(cudaFuncSetAttribute(gj_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kTcSmem));
   }
@@ -1277,8 +1301,12 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
             gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0, slot);
         });
         timed(h, "slab_factor3d_rowmod", 0.0, s, [&] {
-          gj_rowmod_kernel<R><<<dim3(cdiv(Bmax, 64), cnt), 64, rowmod_smem<R>(slot), s>>>(
-              d, p0, nbw, P0, KO);
+          if (nbw == 16)
+            gj_rowmod_kernel<R, 16><<<dim3(cdiv(Bmax, 32), cnt), 128, rowmod_smem<R>(16, slot), s>>>(
+                d, p0, P0, KO);
+          else
+            gj_rowmod_kernel<R, NB><<<dim3(cdiv(Bmax, 32), cnt), 128, rowmod_smem<R>(NB, slot), s>>>(
+                d, p0, P0, KO);
         });
         const int nbp = std::min(nbw, Bmax - p0);
         const double fli = 8.0 * (double)Bmax * std::max(0, bw - nbp) * nbp * cnt;
