@@ -136,6 +136,10 @@ struct Slab {
   void* inj3 = nullptr;
   void* V = nullptr;
   void* gpart = nullptr;     // 3-D: split-K partial sums of the layer GEMM [2][16][max_rhs][B]
+  float* Gp = nullptr;       // 3-D complex64, many right-hand sides: G of every layer split
+                             //   into TF32 hi / lo planes as tensor-core operand tiles
+  float* Vp = nullptr;       //   and the packed right-hand-side blocks of the two chains
+  size_t gp_layer = 0;       //   floats per layer of Gp
 };
 
 // A grid level on which the sweeping preconditioner (and possibly GMRES) runs.

@@ -501,7 +501,7 @@ void free_level(Level& L) {
     dfree(S.PhiP); dfree(S.PsiP);
     dfree(S.inj); dfree(S.Y);
     dfree(S.carry_f); dfree(S.carry_b);
-    dfree(S.st3); dfree(S.inj3); dfree(S.V); dfree(S.gpart);
+    dfree(S.st3); dfree(S.inj3); dfree(S.V); dfree(S.gpart); dfree(S.Gp); dfree(S.Vp);
   }
   L.slabs.clear();
   free_axis(L.ax);

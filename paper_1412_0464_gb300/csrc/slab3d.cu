@@ -42,6 +42,7 @@
 #include "tc.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 namespace hz {
@@ -53,6 +54,22 @@ namespace {
 // overlap its predecessor; every such kernel waits for the predecessor's
 // results (griddepcontrol.wait) before touching any data.
 __device__ __forceinline__ void pdl_wait3() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_pdl3s(void (*k)(KArgs...), dim3 grid, unsigned block, size_t smem, cudaStream_t s,
+                  Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  HZ_CU(cudaLaunchKernelEx(&cfg, k, args...));
+}
 
 template <typename... KArgs, typename... Args>
 void launch_pdl3(void (*k)(KArgs...), dim3 grid, unsigned block, cudaStream_t s, Args... args) {
@@ -206,6 +223,14 @@ void build_slabs3d(hz_handle* h, Level& L, cudaStream_t s) {
     S.Y = dmalloc(el * (size_t)L.nz * R_ * B);
     S.V = dmalloc(el * 2 * (size_t)R_ * B);
     if (R_ > 4) S.gpart = dmalloc(el * 2 * kG3MaxSplit * (size_t)R_ * B);
+    if (R_ > 4 && sizeof(R) == 4) {
+      // packed inverses for the tensor-core layer products (zero padding kept)
+      const size_t nrt = cdiv(B, 128), nkc = cdiv(B, 16);
+      S.gp_layer = nrt * nkc * 8192;
+      S.Gp = (float*)dmalloc(sizeof(float) * S.gp_layer * L.nz);
+      HZ_CU(cudaMemsetAsync(S.Gp, 0, sizeof(float) * S.gp_layer * L.nz, s));
+      S.Vp = (float*)dmalloc(sizeof(float) * 2 * nkc * 2048);
+    }
   }
   L.mid = (L.nz - 1) / 2;
   HZ_CU(cudaStreamSynchronize(s));
@@ -235,6 +260,8 @@ struct FChain {
   int* prow;           // [KO] pivot rows of the block's columns
   float* Ap;           // complex64 tensor-core path: packed colmods (tc_pack_kernel)
   float* Bp;           //   and rowmods of the current outer block
+  float* Gp;           // packed inverses of the slab's layers (layer stride gp_layer) or null
+  size_t gp_layer;
 };
 
 // Entry (i, j) of the in-layer block D_k (9-point in (y, x), zero elsewhere).
@@ -670,8 +697,20 @@ __global__ void __launch_bounds__(256) gj_writeout_kernel(const FChain<R>* chain
   const FChain<R> c = chains[blockIdx.z];
   const int col = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
   if (col >= c.B || p >= c.B) return;
-  c.G[(size_t)c.k * c.bstride + (size_t)p * c.B + col] =
-      c.S[(size_t)c.piv[p] * c.B + c.pinv[col]];
+  const cplx<R> v = c.S[(size_t)c.piv[p] * c.B + c.pinv[col]];
+  c.G[(size_t)c.k * c.bstride + (size_t)p * c.B + col] = v;
+  if (c.Gp) {   // the same entry as tensor-core operand: row tile p / 128, depth chunk col / 16
+    const int nkc = (c.B + 15) / 16;
+    float* t = c.Gp + (size_t)c.k * c.gp_layer + ((size_t)(p >> 7) * nkc + (col >> 4)) * 8192 +
+               tc::kmajor_off(p & 127, col & 15, 4) / 4;
+    float hi, lo;
+    tc::split_tf32((float)v.re, hi, lo);
+    t[0] = hi;
+    t[2048] = lo;
+    tc::split_tf32((float)v.im, hi, lo);
+    t[4096] = hi;
+    t[6144] = lo;
+  }
 }
 
 size_t update_smem(size_t el) { return (64 * (NB + 1) + NB * 64) * el; }
@@ -1143,6 +1182,161 @@ __global__ void slab3_gemm_reduce_kernel(Gemv3<R> a, int nsplit, const cplx<R>* 
   *out = a.mode == 0 ? s : *out - s;
 }
 
+// The layer product on the tensor cores (complex64, more than four right-
+// hand sides): Y (B x nr) = G V with G packed at write-out (row tiles of
+// 128, depth chunks of 16, four TF32 planes re hi / lo, im hi / lo) and V
+// packed per call by tc_vpack_kernel (N = 32 right-hand-side rows per chunk).
+// One CTA per row tile and K range (split K): warp 0 streams the chunks (a
+// 32 KB and an 8 KB bulk copy per stage), warp 1 issues the chunk's 24 MMAs
+// (M = 128, N = 32, K = 8; three TF32 passes per real product) into Dr / Di
+// (tensor-memory columns [0, 32) and [32, 64)), and the four warps write
+// the row tile's partial sums to part [np][nsplit][nr][B] (reduced by
+// slab3_gemm_reduce_kernel).  Right-hand sides in chunks of 32 (one pass of
+// the K range per chunk).  Every wait is bounded.
+constexpr int kTgN = 32;                                // right-hand sides per MMA (N)
+constexpr uint32_t kTgA = 4 * 8192;                     // G chunk: 4 planes x 128 x 16 TF32
+constexpr uint32_t kTgB = 4 * 2048;                     // V chunk: 4 planes x 32 x 16 TF32
+constexpr uint32_t kTgStage = kTgA + kTgB;              // 40 KB
+constexpr int kTgBuf = 4;
+constexpr size_t kTgSmem = kTgBuf * (size_t)kTgStage + 128;
+
+// V [nr][B] (rows r0 .. r0 + 31) -> Vp [nkc][4 planes][32 x 16] K-major (2 KB per
+// plane); one thread per (rhs row, depth chunk), four depths per 16-byte store
+__global__ void __launch_bounds__(128) tc_vpack_kernel(Gemv3<float> a, int r0, float* vp_all) {
+  pdl_wait3();
+  const GemvPiece<float> P = blockIdx.z == 0 ? a.p[0] : a.p[1];
+  const int B = a.B, nkc = (B + 15) / 16;
+  float* vp = vp_all + (size_t)blockIdx.z * nkc * 2048;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = e & 31, kc = e >> 5;
+  if (kc >= nkc) return;
+  const int rr = r0 + r;
+#pragma unroll
+  for (int kg = 0; kg < 16; kg += 4) {
+    float4 v[4];
+    float* f = (float*)v;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = kc * 16 + kg + u;
+      const c64 x = (rr < a.nr && j < B) ? P.v[(size_t)rr * B + j] : mk<float>(0, 0);
+      tc::split_tf32(x.re, f[0 * 4 + u], f[1 * 4 + u]);
+      tc::split_tf32(x.im, f[2 * 4 + u], f[3 * 4 + u]);
+    }
+    float* out = vp + (size_t)kc * 2048 + tc::kmajor_off(r, kg, 4) / 4;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) *(float4*)(out + t * 512) = v[t];
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) slab3_gemm_tc_kernel(Gemv3<float> a, const float* gp0,
+                                                               const float* gp1, int nsplit,
+                                                               const float* vp_all, int r0,
+                                                               c64* part, int* flag) {
+  pdl_wait3();
+  const int B = a.B, nkc = (B + 15) / 16, rt = blockIdx.x, sp = blockIdx.y, pc = blockIdx.z;
+  const int kper = (nkc + nsplit - 1) / nsplit;
+  const int kc0 = sp * kper, kc1 = min(nkc, kc0 + kper);
+  const int nst = kc1 - kc0;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* full = (uint64_t*)(sm + kTgBuf * kTgStage);
+  uint64_t* empty = full + kTgBuf;
+  uint64_t* done = empty + kTgBuf;
+  uint32_t* tptr = (uint32_t*)(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int b = 0; b < kTgBuf; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], 1);
+    }
+    mbar_init(done, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tptr, 64);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tptr;
+  bool ok = true;
+  if (nst > 0) {
+    if (warp == 0 && lane == 0) {               // producer
+      const float* G = (pc == 0 ? gp0 : gp1) + (size_t)rt * nkc * 8192;
+      const float* V = vp_all + (size_t)pc * nkc * 2048;
+      for (int st = 0; st < nst && ok; ++st) {
+        const int buf = st % kTgBuf;
+        if (st >= kTgBuf) ok = mbar_wait(&empty[buf], ((st - kTgBuf) / kTgBuf) & 1, flag);
+        if (!ok) break;
+        unsigned char* dst = sm + buf * kTgStage;
+        mbar_expect_tx(&full[buf], kTgStage);
+        tma_load_1d(dst, G + (size_t)(kc0 + st) * 8192, kTgA, &full[buf]);
+        tma_load_1d(dst + kTgA, V + (size_t)(kc0 + st) * 2048, kTgB, &full[buf]);
+      }
+    } else if (warp == 1 && lane == 0) {        // MMA issuer
+      constexpr uint32_t lbo = 128, sbo = 4 * 128;
+      constexpr uint32_t id = tc::idesc_tf32(128, kTgN, false);
+      constexpr uint32_t idn = tc::idesc_tf32(128, kTgN, true);
+      for (int st = 0; st < nst && ok; ++st) {
+        const int buf = st % kTgBuf;
+        ok = mbar_wait(&full[buf], (st / kTgBuf) & 1, flag);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t sa = smem_u32(sm + buf * kTgStage), sbb = sa + kTgA;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint32_t ko = ks * 256;
+          auto A = [&](int t) { return tc::smem_desc(sa + t * 8192 + ko, lbo, sbo); };
+          auto Bd = [&](int t) { return tc::smem_desc(sbb + t * 2048 + ko, lbo, sbo); };
+          const bool acc = st > 0 || ks > 0;
+          // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo (G: A, V: B)
+          tc::mma_tf32(tmem, A(0), Bd(0), id, acc);          // Dr += Gr Vr
+          tc::mma_tf32(tmem, A(0), Bd(1), id, true);
+          tc::mma_tf32(tmem, A(1), Bd(0), id, true);
+          tc::mma_tf32(tmem, A(2), Bd(2), idn, true);        // Dr -= Gi Vi
+          tc::mma_tf32(tmem, A(2), Bd(3), idn, true);
+          tc::mma_tf32(tmem, A(3), Bd(2), idn, true);
+          tc::mma_tf32(tmem + 32, A(0), Bd(2), id, acc);     // Di += Gr Vi
+          tc::mma_tf32(tmem + 32, A(0), Bd(3), id, true);
+          tc::mma_tf32(tmem + 32, A(1), Bd(2), id, true);
+          tc::mma_tf32(tmem + 32, A(2), Bd(0), id, true);    // Di += Gi Vr
+          tc::mma_tf32(tmem + 32, A(2), Bd(1), id, true);
+          tc::mma_tf32(tmem + 32, A(3), Bd(0), id, true);
+        }
+        tc::commit(&empty[buf]);
+      }
+      if (ok) tc::commit(done);
+    }
+    __syncwarp();
+    ok = mbar_wait(done, 0, flag);
+  }
+  ok = __syncthreads_and(ok);
+  tc::fence_after_sync();
+  const int i = rt * 128 + warp * 32 + lane;
+  if (ok) {
+    float vr[32], vi[32];
+    if (nst > 0) {
+      tc::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16), vr);
+      tc::ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + 32, vi);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) vr[q] = vi[q] = 0.f;
+    }
+    if (i < B) {
+      c64* po = part + ((size_t)pc * nsplit + sp) * a.nr * B;
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (r0 + q < a.nr) po[(size_t)(r0 + q) * B + i] = mk<float>(vr[q], vi[q]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 64);
+  }
+}
+
 // Epilogue of a 3-D slab solve (Table 2): the slab solution's core columns
 // (ua, ub] into the global field, the layers at e2, e2+1 (B2) and e4, e4+1
 // (B4) for the transmission, or the whole slab field (raw).
@@ -1214,6 +1408,8 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       f.st = (const cplx<R>*)S.st3;
       f.G = (cplx<R>*)S.G;
       f.bstride = S.bstride;
+      f.Gp = S.Gp;
+      f.gp_layer = S.gp_layer;
       f.S = (cplx<R>*)L.f3_S + sS * c;
       f.C = (cplx<R>*)L.f3_C + sC * c;
       f.Rm = (cplx<R>*)L.f3_R + sC * c;
@@ -1380,6 +1576,20 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
   // many right-hand sides: the split-K register-tiled GEMM and its reduction
   // (partial sums in the slab's GEMM scratch); few: the GEMV kernel
   const bool tiled = nr > 4 && S.gpart != nullptr;
+  // complex64: the tensor-core product with the packed inverses
+  const bool tcg = tiled && S.Gp != nullptr && test_hook("HZ_TEST_NO_TC") <= 0;
+  static bool tg_attr = false;
+  if (tcg && !tg_attr) {
+    HZ_CU(cudaFuncSetAttribute(slab3_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTgSmem));
+    tg_attr = true;
+  }
+  const int nkc = cdiv(B, 16), nrt = cdiv(B, 128);
+  const int nsplit_tc = std::max(1, std::min(kG3MaxSplit, cdiv(2 * h->sms, 2 * nrt)));
+  auto gp_of = [&](const cplx<R>* Gl) {   // packed inverse of the layer whose G is Gl
+    const size_t layer = (size_t)(Gl - G) / S.bstride;
+    return S.Gp + layer * S.gp_layer;
+  };
   const int nI = cdiv(B, kG3Rows);
   // at least ~4 CTAs per SM (two pieces), so that the last wave is short
   const int nsplit = std::max(1, std::min(kG3MaxSplit, cdiv(4 * h->sms, 2 * nI)));
@@ -1387,7 +1597,21 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
     ga.np = np;
     ga.mode = mode;
     timed(h, "slab3_gemv", np * (gbytes + 2.0 * nr * B * el), s, [&] {
-      if (tiled) {
+      if (tcg) {
+        if constexpr (std::is_same<R, float>::value) {
+          c64* part = (c64*)S.gpart;
+          const float* g0 = gp_of(ga.p[0].G);
+          const float* g1 = np > 1 ? gp_of(ga.p[1].G) : g0;
+          for (int r0 = 0; r0 < nr; r0 += kTgN) {
+            launch_pdl3(tc_vpack_kernel, dim3(cdiv(32 * nkc, 128), 1, np), 128, s, ga, r0, S.Vp);
+            launch_pdl3s(slab3_gemm_tc_kernel, dim3(nrt, nsplit_tc, np), 128, kTgSmem, s, ga, g0,
+                         g1, nsplit_tc, (const float*)S.Vp, r0, part, h->dev_flag);
+            h->launches += 2;
+          }
+          launch_pdl3(slab3_gemm_reduce_kernel<float>, dim3(cdiv(B, 128), nr, np), 128, s, ga,
+                      nsplit_tc, (const c64*)part);
+        }
+      } else if (tiled) {
         cplx<R>* part = (cplx<R>*)S.gpart;
         launch_pdl3(slab3_gemm_kernel<R>, dim3(nI, nsplit, np), 256, s, ga, nsplit, part);
         launch_pdl3(slab3_gemm_reduce_kernel<R>, dim3(cdiv(B, 128), nr, np), 128, s, ga, nsplit,

@@ -195,21 +195,21 @@ def test_gradient_3d_matches_oracle():
 @pytest.mark.parametrize("idx,n,w_out,J", [(4, 24, 4, 2), (5, 40, 4, 2)])
 def test_tensor_core_update_matches_simt_and_oracle(idx, n, w_out, J, monkeypatch):
     """The complex64 3-D factorisation updates S outside each outer block of
-    128 columns on the tensor cores (three TF32 passes per real product).
-    Blocks of B = 31 x 19 = 589 (finite differences) and 27 x 17 = 459
-    (two-grid coarse level) unknowns span several outer blocks and a ragged
-    last one; the
-    slab solves agree with the FP32 SIMT update (HZ_TEST_NO_TC=1) and with
-    the oracle's exact slab solves."""
+    128 columns on the tensor cores (three TF32 passes per real product), and
+    slab solves with 8 right-hand sides multiply by the stored inverses on the
+    tensor cores too.  Blocks of B = 31 x 19 = 589 (finite differences) and
+    27 x 17 = 459 (two-grid coarse level) unknowns span several outer blocks
+    and a ragged last one; the slab solves agree with the FP32 SIMT kernels
+    (HZ_TEST_NO_TC=1) and with the oracle's exact slab solves."""
     hz = _hz()
-    cfg = synth.scaled_workload(idx, n, w_out=w_out, J=J, n_src=2)
+    cfg = synth.scaled_workload(idx, n, w_out=w_out, J=J, n_src=8)
     p = Problem(cfg)
     s = hz.Solver.from_workload(cfg, precision="mixed")
     fds = {}
     for j in range(1, J + 1):
         sl = p.dd.slabs[j]
         nt = sl.A.shape[0] // sl.W
-        fds[j] = _rand((2, nt, sl.W), 40 + j)
+        fds[j] = _rand((8, nt, sl.W), 40 + j)
     out = {}
     for mode in ("tc", "simt"):
         if mode == "simt":
@@ -220,7 +220,7 @@ def test_tensor_core_update_matches_simt_and_oracle(idx, n, w_out, J, monkeypatc
     for j, fd in fds.items():
         sl = p.dd.slabs[j]
         nt = sl.A.shape[0] // sl.W
-        for r in range(2):
+        for r in range(8):
             ref = sl.lu.solve(fd[r].ravel()).reshape(nt, sl.W)
             assert _close(out["tc"][j][r], ref, TOL["mixed"]), (j, r, _rel(out["tc"][j][r], ref))
             assert _close(out["tc"][j][r], out["simt"][j][r], TOL["mixed"])
