@@ -514,13 +514,14 @@ def main():
 
     # end to end through the C ABI with host buffers (pinned), copies included
     f_host = torch.from_numpy(b).pin_memory()
+    u_host = torch.empty_like(f_host).pin_memory()          # the result lands in pinned memory
     e2e_ms = []
     for i in range(max(2, min(args.steps, 3)) + 1):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         solver.factor()
-        u_host, _ = solver.solve_host(f_host)
+        solver.solve_host(f_host, out=u_host)
         e2e_ms.append(1000 * (time.perf_counter() - t0))
     e2e_ms = statistics.mean(e2e_ms[1:])
     nbytes = cfg.ndof * cfg.n_src * 16

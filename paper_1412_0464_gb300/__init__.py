@@ -263,11 +263,19 @@ class Solver:
             self._check(code)
         return (u[0] if single else u), st.as_dict()
 
-    def solve_host(self, f_host, stream=None):
-        """Same with host (CPU) tensors; the copies are part of the call."""
+    def solve_host(self, f_host, stream=None, out=None):
+        """Same with host (CPU) tensors; the copies are part of the call.  ``out``
+        (complex128 host tensor of f's batch shape, pinned for full copy speed)
+        receives the solution; otherwise a pageable tensor is allocated."""
         import torch
         fb, single = self._field(f_host, cuda=False)
-        u = torch.empty_like(fb)
+        if out is None:
+            u = torch.empty_like(fb)
+        else:
+            u = out.reshape(fb.shape) if out.dim() == fb.dim() - 1 else out
+            if u.dtype != torch.complex128 or u.is_cuda or tuple(u.shape) != tuple(fb.shape) \
+                    or not u.is_contiguous():
+                raise ValueError("out must be a contiguous complex128 host tensor shaped like f")
         st = hz_stats()
         self._check(lib().hz_solve_host(self.h, _ptr(fb), _ptr(u), fb.shape[0], _stream(stream),
                                         ctypes.byref(st)))

@@ -279,6 +279,7 @@ __device__ __forceinline__ cplx<R> d_entry(const FChain<R>& c, int i, int j) {
 // the G slot of layer k (free until its inverse is written).
 template <typename R>
 __global__ void __launch_bounds__(128) schur_T_kernel(const FChain<R>* chains, int term) {
+  pdl_wait3();
   const FChain<R> c = chains[blockIdx.z];
   const int j = blockIdx.x * blockDim.x + threadIdx.x, a = blockIdx.y;
   if (j >= c.B || a >= c.B) return;
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(128) schur_T_kernel(const FChain<R>* chains, i
 template <typename R>
 __global__ void __launch_bounds__(128) schur_S_kernel(const FChain<R>* chains, int term, int init,
                                                       int fe) {
+  pdl_wait3();
   const FChain<R> c = chains[blockIdx.z];
   const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
   if (j >= c.B || i >= c.B) return;
@@ -358,6 +360,7 @@ __device__ __forceinline__ unsigned long long pivot_key(float a2, int row) {
 template <typename R>
 __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>* chains, int p0,
                                                                  int slot) {
+  pdl_wait3();
   const FChain<R> c = chains[blockIdx.x];
   const int B = c.B;
   if (p0 >= B) return;
@@ -428,16 +431,18 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
 }
 
 // The same panel elimination with the panel held in shared memory (blocks
-// small enough: B (PW + 1) elements): one thread per row (rows tid, tid +
-// 1024, ...), panel rows padded to PW + 1 elements; per step a block-wide
-// pivot-key maximum, the scaled pivot row, and each thread's rank-1 update of
-// its rows with the next column's keys.  The colmods go to C [KO][B] at
+// small enough: B (PW + 1) elements): rows tid, tid + 1024, ... per thread,
+// panel rows padded to PW + 1 elements; per step a block-wide pivot-key
+// maximum (warp 0 then also forms the scaled pivot row: two block barriers
+// per pivot), and each thread's rank-1 update of its rows with the next
+// column's keys.  The colmods go to C [KO][B] at
 // the panel's slots.
 constexpr int kSmemPanelThreads = 1024;
 
 template <typename R, int PW>
 __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const FChain<R>* chains,
                                                                          int p0, int slot) {
+  pdl_wait3();
   const FChain<R> c = chains[blockIdx.x];
   const int B = c.B;
   if (p0 >= B) return;
@@ -470,32 +475,31 @@ __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const 
     }
     if (lane == 0) wkey[warp] = best;
     __syncthreads();
-    if (warp == 0) {
-      unsigned long long b = wkey[lane];
+    if (warp == 0) {   // pivot row of column t and its scaled panel row, in one warp
+      unsigned long long b = lane < kSmemPanelThreads / 32 ? wkey[lane] : 0ull;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
         b = v > b ? v : b;
       }
+      const int r = (int)(0xffffffffu - (unsigned)(b & 0xffffffffu));
       if (lane == 0) {
-        const int r = (int)(0xffffffffu - (unsigned)(b & 0xffffffffu));
         shr[0] = r;
         flag[r] = 1;
         c.piv[p0 + t] = r;
         c.pinv[r] = p0 + t;
         c.prow[slot + t] = r;
       }
+      if (lane < PW) {
+        const cplx<R> inv = cinv(P[r * LD + t]);
+        cplx<R> x = P[r * LD + lane] * inv;
+        if (lane == t) x = inv + mk<R>(1, 0);
+        rm[lane] = lane < nbp ? x : mk<R>(0, 0);
+        if (lane == 0) c.pinfo[slot + t] = inv;
+      }
     }
     __syncthreads();
     const int r = shr[0];
-    if (tid < PW) {
-      const cplx<R> inv = cinv(P[r * LD + t]);
-      cplx<R> x = P[r * LD + tid] * inv;
-      if (tid == t) x = inv + mk<R>(1, 0);
-      rm[tid] = tid < nbp ? x : mk<R>(0, 0);
-      if (tid == 0) c.pinfo[slot + t] = inv;
-    }
-    __syncthreads();
     best = 0;
     for (int i = tid; i < B; i += kSmemPanelThreads) {
       cplx<R>* row = P + i * LD;
@@ -536,6 +540,7 @@ size_t panel_smem_bytes(int B) {
 template <typename R, int PW>
 __global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0, int P0,
                                                          int KBw) {
+  pdl_wait3();
   // 32 columns per CTA; warp w takes a quarter of the earlier slots of the
   // delayed sum, warp 0 adds the quarters and runs the in-panel recurrence
   const FChain<R> c = chains[blockIdx.y];
@@ -621,6 +626,7 @@ size_t rowmod_smem(int pw, int slot) {
 template <typename R>
 __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains, int base,
                                                         int width, int P0, int KBw, int inner) {
+  pdl_wait3();
   const FChain<R> c = chains[blockIdx.z];
   const int B = c.B;
   if (base >= B) return;
@@ -652,8 +658,9 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains,
       Rs[t * 64 + q] = (ok && j0 + q < whi) ? c.Rm[row + j0 + q] : mk<R>(0, 0);
     }
     __syncthreads();
+    const int tmax = min(NB, depth - k0);         // a 16-column panel fills half a chunk
 #pragma unroll 4
-    for (int t = 0; t < NB; ++t) {
+    for (int t = 0; t < tmax; ++t) {
       cplx<R> cv[4], rv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) cv[a] = Cs[(ty + 16 * a) * (NB + 1) + t];
@@ -694,6 +701,7 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains,
 // G_k[p][col] = S[piv[p]][pinv[col]] (undo the implicit pivoting).
 template <typename R>
 __global__ void __launch_bounds__(256) gj_writeout_kernel(const FChain<R>* chains) {
+  pdl_wait3();
   const FChain<R> c = chains[blockIdx.z];
   const int col = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
   if (col >= c.B || p >= c.B) return;
@@ -749,6 +757,7 @@ size_t tc_pack_floats(int Bmax, int KO) {
 // grid (row tiles, stages, 2 x chains): z even packs C (rows i), odd Rm
 // (columns j); thread r takes row r of the tile, four depths per 16-byte store.
 __global__ void __launch_bounds__(128) tc_pack_kernel(const FChain<float>* chains, int P0, int KBw) {
+  pdl_wait3();
   const FChain<float> c = chains[blockIdx.z >> 1];
   const bool isC = (blockIdx.z & 1) == 0;
   const int B = c.B;
@@ -778,6 +787,7 @@ __global__ void __launch_bounds__(128) tc_pack_kernel(const FChain<float>* chain
 
 __global__ void __launch_bounds__(128, 1) gj_update_tc_kernel(const FChain<float>* chains, int P0,
                                                               int KBw, int* flag) {
+  pdl_wait3();
   const FChain<float> c = chains[blockIdx.z];
   const int B = c.B;
   if (P0 >= B) return;
@@ -1473,12 +1483,12 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
     const dim3 gs(cdiv(Bmax, 128), Bmax, cnt);
     timed(h, "slab_factor3d_schur", 0.0, s, [&] {
       if (!fe) {
-        schur_S_kernel<R><<<gs, 128, 0, s>>>(d, -1, 1, 0);
+        launch_pdl3(schur_S_kernel<R>, gs, 128, s, d, -1, 1, 0);
       } else {
-        schur_S_kernel<R><<<gs, 128, 0, s>>>(d, -1, 1, 1);
+        launch_pdl3(schur_S_kernel<R>, gs, 128, s, d, -1, 1, 1);
         for (int t = 0; t < nterm; ++t) {
-          schur_T_kernel<R><<<gs, 128, 0, s>>>(d, t);
-          schur_S_kernel<R><<<gs, 128, 0, s>>>(d, t, 0, 1);
+          launch_pdl3(schur_T_kernel<R>, gs, 128, s, d, t);
+          launch_pdl3(schur_S_kernel<R>, gs, 128, s, d, t, 0, 1);
         }
       }
     });
@@ -1492,23 +1502,23 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
         const int slot = p0 - P0;
         timed(h, "slab_factor3d_panel", 0.0, s, [&] {
           if (smem_panel)
-            gj_panel_smem_kernel<R, 16><<<cnt, kSmemPanelThreads, psm, s>>>(d, p0, slot);
+            launch_pdl3s(gj_panel_smem_kernel<R, 16>, dim3(cnt), kSmemPanelThreads, psm, s, d, p0, slot);
           else
-            gj_panel_kernel<R><<<cnt, kPanelThreads, 0, s>>>(d, p0, slot);
+            launch_pdl3(gj_panel_kernel<R>, dim3(cnt), kPanelThreads, s, d, p0, slot);
         });
         timed(h, "slab_factor3d_rowmod", 0.0, s, [&] {
           if (nbw == 16)
-            gj_rowmod_kernel<R, 16><<<dim3(cdiv(Bmax, 32), cnt), 128, rowmod_smem<R>(16, slot), s>>>(
-                d, p0, P0, KO);
+            launch_pdl3s(gj_rowmod_kernel<R, 16>, dim3(cdiv(Bmax, 32), cnt), 128,
+                         rowmod_smem<R>(16, slot), s, d, p0, P0, KO);
           else
-            gj_rowmod_kernel<R, NB><<<dim3(cdiv(Bmax, 32), cnt), 128, rowmod_smem<R>(NB, slot), s>>>(
-                d, p0, P0, KO);
+            launch_pdl3s(gj_rowmod_kernel<R, NB>, dim3(cdiv(Bmax, 32), cnt), 128,
+                         rowmod_smem<R>(NB, slot), s, d, p0, P0, KO);
         });
         const int nbp = std::min(nbw, Bmax - p0);
         const double fli = 8.0 * (double)Bmax * std::max(0, bw - nbp) * nbp * cnt;
         timed(h, "slab_factor3d_inner", fli, s, [&] {
-          gj_update_kernel<R><<<dim3(cdiv(bw, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el), s>>>(
-              d, p0, nbw, P0, KO, 1);
+          launch_pdl3s(gj_update_kernel<R>, dim3(cdiv(bw, 64), cdiv(Bmax, 64), cnt), 256,
+                       update_smem(el), s, d, p0, nbw, P0, KO, 1);
         });
         h->launches += 3;
       }
@@ -1517,20 +1527,20 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
       if (Bmax > bw) {
         timed(h, "slab_factor3d_update", fl, s, [&] {
           if (use_tc) {
-            tc_pack_kernel<<<dim3(cdiv(Bmax, kTcM), KO / kTcK, 2 * cnt), 128, 0, s>>>(
-                (const FChain<float>*)d, P0, KO);
-            gj_update_tc_kernel<<<dim3(cdiv(Bmax, kTcM), cdiv(Bmax, kTcM), cnt), 128, kTcSmem, s>>>(
-                (const FChain<float>*)d, P0, KO, h->dev_flag);
+            launch_pdl3(tc_pack_kernel, dim3(cdiv(Bmax, kTcM), KO / kTcK, 2 * cnt), 128, s,
+                        (const FChain<float>*)d, P0, KO);
+            launch_pdl3s(gj_update_tc_kernel, dim3(cdiv(Bmax, kTcM), cdiv(Bmax, kTcM), cnt), 128,
+                         kTcSmem, s, (const FChain<float>*)d, P0, KO, h->dev_flag);
           }
           else
-            gj_update_kernel<R><<<dim3(cdiv(Bmax, 64), cdiv(Bmax, 64), cnt), 256, update_smem(el),
-                                  s>>>(d, P0, KO, P0, KO, 0);
+            launch_pdl3s(gj_update_kernel<R>, dim3(cdiv(Bmax, 64), cdiv(Bmax, 64), cnt), 256,
+                         update_smem(el), s, d, P0, KO, P0, KO, 0);
         });
         h->launches += use_tc ? 2 : 1;
       }
     }
     timed(h, "slab_factor3d_writeout", 0.0, s,
-          [&] { gj_writeout_kernel<R><<<dim3(cdiv(Bmax, 256), Bmax, cnt), 256, 0, s>>>(d); });
+          [&] { launch_pdl3(gj_writeout_kernel<R>, dim3(cdiv(Bmax, 256), Bmax, cnt), 256, s, d); });
     h->launches += 1;
     HZ_CU(cudaGetLastError());
   };

@@ -225,3 +225,20 @@ def test_two_grid_solve_matches_oracle(precision):
     assert _rel(u, exact) <= 1e-5
     if precision == "fp64":
         assert abs(st["iters_max"] - info["iters"]) <= 1
+
+
+def test_solve_host_into_pinned_output_matches_device_solve():
+    """hz_solve_host (host buffers, copies inside the call) writes into a
+    caller's pinned output and gives the device solve's result bit for bit."""
+    hz = _hz()
+    cfg = synth.scaled_workload(2, 90, w_out=8, J=4, n_src=2)
+    b = torch.from_numpy(synth.sources(cfg)[:2])
+    s = hz.Solver.from_workload(cfg, max_rhs=2)
+    s.factor()
+    u_dev, _ = s.solve(b.cuda())
+    out = torch.empty_like(b).pin_memory()
+    u_host, st = s.solve_host(b.pin_memory(), out=out)
+    assert u_host.data_ptr() == out.data_ptr()
+    assert torch.equal(u_host, u_dev.cpu()) and st["relres_max"] <= cfg.tol
+    with pytest.raises(ValueError):
+        s.solve_host(b, out=torch.empty(3, dtype=torch.complex128))
