@@ -156,8 +156,8 @@ TRAFFIC_KERNELS = {
     "stencil_c128": (["op_kernel<double"], ["stencil.cu", "hz_internal.h"]),
     "slab_factor3d_update": (["tc_pack_kernel", "gj_update_tc_kernel"],
                              ["slab3d.cu", "tc.cuh", "ptx.cuh", "hz_internal.h"]),
-    "slab3_gemv": (["slab3_gemm_kernel", "slab3_gemm_reduce_kernel"],
-                   ["slab3d.cu", "hz_internal.h"]),
+    "slab3_gemv": (["tc_vpack_kernel", "slab3_gemm_tc_kernel", "slab3_gemm_reduce_kernel"],
+                   ["slab3d.cu", "tc.cuh", "ptx.cuh", "hz_internal.h"]),
 }
 
 
