@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the workload's recipe at this interior size (not a bench line)")
     ap.add_argument("--J", type=int, default=0, help="profiling only: slab count with --n")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="run with the automatic parameters instead of the autotuner's choice")
     ap.add_argument("--write-traffic", nargs=3, metavar=("CSV", "COMMAND", "WORKLOAD"),
                     help="write profiles/traffic.json from an ncu DRAM-bytes capture and exit")
     ap.add_argument("--summarize-launches", metavar="CSV",
@@ -444,7 +446,14 @@ def main():
         cfg = synth.scaled_workload(args.workload, args.n3d, J=args.J or None)
     m = synth.medium(cfg)
     b = synth.sources(cfg)
-    solver = hz.Solver.from_workload(cfg, m=m)
+    # run-time tuning parameters (segment count / 3-D outer block) from the
+    # autotuner: timed once per device and workload shape, outside the timed steps
+    tuned = {}
+    if not args.no_autotune:
+        from paper_1412_0464_gb300 import autotune
+        tuned_entry = autotune.tune(cfg, m=m)
+        tuned = tuned_entry["params"]
+    solver = hz.Solver.from_workload(cfg, m=m, **tuned)
     f_dev = torch.from_numpy(b).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -614,6 +623,8 @@ def main():
             "data": "synthetic (seeded random-field + layer medium, point source)",
             "config": {"workload": workload_string(cfg),
                        "n_rhs": cfg.n_src, "step": "hz_factor + hz_solve",
+                       "autotune": ({"params": tuned, "candidates_ms": tuned_entry["ms"]}
+                                    if not args.no_autotune else "off"),
                        "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "time_to_solution_s": ms_step / 1000.0, "solve_only_s": statistics.mean(solve_s),
