@@ -58,7 +58,8 @@ def _args():
     ap.add_argument("--no-autotune", action="store_true",
                     help="run with the automatic parameters instead of the autotuner's choice")
     ap.add_argument("--write-traffic", nargs=3, metavar=("CSV", "COMMAND", "WORKLOAD"),
-                    help="write profiles/traffic.json from an ncu DRAM-bytes capture and exit")
+                    help="write profiles/traffic.json from an ncu DRAM-bytes capture of the "
+                         "bench's mixed run on WORKLOAD (its config.workload string) and exit")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print the per-kernel table of an ncu launch list and exit")
     return ap.parse_args()
@@ -170,13 +171,18 @@ def _src_hash(files):
     return h.hexdigest()[:16]
 
 
-def _traffic(tag):
-    """DRAM bytes per launch from the committed ncu summary, if its kernel's
-    sources are unchanged since the capture."""
+def _traffic(tag, workload=None, precision=None):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    this workload and precision and its kernel's sources are unchanged since."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p) or tag not in TRAFFIC_KERNELS:
         return None
-    e = json.load(open(p)).get("kernels", {}).get(tag)
+    d = json.load(open(p))
+    if workload is not None and d.get("bench_workload") != workload:
+        return None
+    if precision is not None and d.get("precision") != precision:
+        return None
+    e = d.get("kernels", {}).get(tag)
     if e is None or e.get("source_hash") != _src_hash(TRAFFIC_KERNELS[tag][1]):
         return None
     return e.get("dram_bytes_per_launch")
@@ -206,7 +212,7 @@ def write_traffic(csv_path, command, workload):
         if metric in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             per.setdefault((lid, name), 0.0)
             per[(lid, name)] += v
-    out = {"command": command, "workload": workload,
+    out = {"command": command, "workload": workload, "bench_workload": workload, "precision": "mixed",
            "note": "DRAM bytes (read + write) per launch, mean over the captured launches; "
                    "a tag that sums two kernels (pack + update, GEMM + reduce) adds their means",
            "kernels": {}}
@@ -234,21 +240,41 @@ def write_traffic(csv_path, command, workload):
 
 
 def summarize_launches(csv_path):
-    """Markdown table of an ncu launch list (gpu__time_duration.sum): launches,
-    total time and share per kernel."""
+    """Markdown table of an ncu launch list: launches, total time and share per
+    kernel, and, when the capture has them, the mean DRAM rate and the mean
+    utilisations (DRAM, SM, FMA / FP64 / tensor pipes) over the kernel's launches."""
     rows = _ncu_rows(csv_path)
-    agg = {}
+    per = {}
     for lid, name, metric, v in rows:
-        if metric != "gpu__time_duration.sum":
-            continue
         k = name.split("(")[0].replace("void ", "").replace("hz::", "").replace("(anonymous namespace)::", "")
-        a = agg.setdefault(k, [0, 0.0])
-        a[0] += 1
-        a[1] += v
-    tot = sum(v[1] for v in agg.values())
-    lines = ["| kernel | launches | total (ms) | share |", "|---|---|---|---|"]
-    for k, (n, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
-        lines.append(f"| `{k}` | {n} | {t / 1e6:.3f} | {t / tot:.3f} |")
+        per.setdefault((lid, k), {})[metric] = v
+    agg = {}
+    for (lid, k), m in per.items():
+        a = agg.setdefault(k, {"n": 0, "t": 0.0, "bytes": 0.0, "u": {}})
+        a["n"] += 1
+        a["t"] += m.get("gpu__time_duration.sum", 0.0)
+        a["bytes"] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+        for key, v in m.items():
+            if key.endswith("pct_of_peak_sustained_elapsed") or key.endswith("pct_of_peak_sustained_active"):
+                a["u"].setdefault(key, []).append(v)
+    tot = sum(v["t"] for v in agg.values()) or 1.0
+    short = [("gpu__dram_throughput", "DRAM %"), ("sm__throughput", "SM %"),
+             ("sm__pipe_fma_cycles", "FMA pipe %"), ("sm__pipe_fp64_cycles", "FP64 pipe %"),
+             ("sm__pipe_tensor_cycles", "tensor pipe %")]
+    have = [(p, h) for p, h in short if any(any(k.startswith(p) for k in a["u"]) for a in agg.values())]
+    hdr = "| kernel | launches | total (ms) | share |"
+    if any(a["bytes"] > 0 for a in agg.values()):
+        hdr += " DRAM GB/s |"
+    hdr += "".join(f" {h} |" for _, h in have)
+    lines = [hdr, "|" + "---|" * (hdr.count("|") - 1)]
+    for k, a in sorted(agg.items(), key=lambda kv: -kv[1]["t"]):
+        row = f"| `{k}` | {a['n']} | {a['t'] / 1e6:.3f} | {a['t'] / tot:.3f} |"
+        if "DRAM GB/s" in hdr:
+            row += f" {a['bytes'] / a['t'] if a['t'] else 0:.0f} |"
+        for p, _ in have:
+            vals = [x for key, v in a["u"].items() if key.startswith(p) for x in v]
+            row += f" {sum(vals) / len(vals):.1f} |" if vals else " — |"
+        lines.append(row)
     return "\n".join(lines)
 
 
@@ -566,7 +592,7 @@ def main():
         d = indiv[tag]
         ach = d["bytes"] / (d["ms"] / 1000.0) / 1e9
         return {"bound": "hbm", "kernel": tag, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": peak_kind, "traffic": _traffic(tag),
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": _traffic(tag, workload_string(cfg), cfg.precision),
                 "avg_launch_us": 1000 * d["ms"] / d["launches"],
                 "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
@@ -579,7 +605,7 @@ def main():
                     "peak_source": (f"measured {'FP32' if fprec == 'mixed' else 'FP64'} FMA "
                                     "throughput (hz_alu_peak)"),
                     "peak_fp32_derived": alu_derived,
-                    "traffic": _traffic(dom), "avg_launch_us": 1000 * d["ms"] / d["launches"],
+                    "traffic": _traffic(dom, workload_string(cfg), cfg.precision), "avg_launch_us": 1000 * d["ms"] / d["launches"],
                     "algorithmic_flop_per_launch": factor_flop,
                     "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
         roofline["hbm_kernel"] = hbm_line(dom_hbm)
@@ -591,7 +617,7 @@ def main():
         # complex128: FP64 SIMT
         d = indiv[dom]
         ach = d["bytes"] / (d["ms"] / 1000.0) / 1e12
-        common = {"kernel": dom, "achieved": ach, "unit": "TFLOP/s", "traffic": _traffic(dom),
+        common = {"kernel": dom, "achieved": ach, "unit": "TFLOP/s", "traffic": _traffic(dom, workload_string(cfg), cfg.precision),
                   "avg_launch_us": 1000 * d["ms"] / d["launches"],
                   "algorithmic_flop_per_launch": d["bytes"] / d["launches"],
                   "share_of_device_time": d["ms"] / sum(v["ms"] for v in indiv.values())}
