@@ -224,3 +224,22 @@ def test_tensor_core_update_matches_simt_and_oracle(idx, n, w_out, J, monkeypatc
             ref = sl.lu.solve(fd[r].ravel()).reshape(nt, sl.W)
             assert _close(out["tc"][j][r], ref, TOL["mixed"]), (j, r, _rel(out["tc"][j][r], ref))
             assert _close(out["tc"][j][r], out["simt"][j][r], TOL["mixed"])
+
+
+def test_slab_solve_3d_40_rhs_two_tensor_core_chunks():
+    """40 right-hand sides: the tensor-core layer products run in two chunks
+    of 32 (the second one partly filled) and one reduction; every solution
+    matches the oracle's exact slab solve."""
+    hz = _hz()
+    cfg = synth.scaled_workload(4, 16, w_out=4, J=2, n_src=40)
+    p = Problem(cfg)
+    s = hz.Solver.from_workload(cfg, precision="mixed")
+    s.factor()
+    for j in (1, 2):
+        sl = p.dd.slabs[j]
+        nt = sl.A.shape[0] // sl.W
+        fd = _rand((40, nt, sl.W), 70 + j)
+        ud = s.slab_solve(j, torch.from_numpy(fd).cuda()).cpu().numpy()
+        for r in (0, 17, 31, 32, 39):
+            ref = sl.lu.solve(fd[r].ravel()).reshape(nt, sl.W)
+            assert _close(ud[r], ref, TOL["mixed"]), (j, r, _rel(ud[r], ref))
