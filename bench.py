@@ -239,6 +239,13 @@ def write_traffic(csv_path, command, workload):
     return out
 
 
+def _short_kernel_name(name):
+    """Kernel name without the namespaces, the return type and the argument list."""
+    for pre in ("(anonymous namespace)::", "<unnamed>::", "unnamed>::", "void ", "hz::"):
+        name = name.replace(pre, "")
+    return name.split("(")[0].strip()
+
+
 def summarize_launches(csv_path):
     """Markdown table of an ncu launch list: launches, total time and share per
     kernel, and, when the capture has them, the mean DRAM rate and the mean
@@ -246,7 +253,7 @@ def summarize_launches(csv_path):
     rows = _ncu_rows(csv_path)
     per = {}
     for lid, name, metric, v in rows:
-        k = name.split("(")[0].replace("void ", "").replace("hz::", "").replace("(anonymous namespace)::", "")
+        k = _short_kernel_name(name)
         per.setdefault((lid, k), {})[metric] = v
     agg = {}
     for (lid, k), m in per.items():
