@@ -1595,7 +1595,11 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
     tg_attr = true;
   }
   const int nkc = cdiv(B, 16), nrt = cdiv(B, 128);
-  const int nsplit_tc = std::max(1, std::min(kG3MaxSplit, cdiv(2 * h->sms, 2 * nrt)));
+  // K splits of the tensor-core products: one wave of CTAs (one per SM), so
+  // that no second, nearly empty wave follows
+  auto nsplit_of = [&](int np) {
+    return std::max(1, std::min(kG3MaxSplit, h->sms / (np * nrt)));
+  };
   auto gp_of = [&](const cplx<R>* Gl) {   // packed inverse of the layer whose G is Gl
     const size_t layer = (size_t)(Gl - G) / S.bstride;
     return S.Gp + layer * S.gp_layer;
@@ -1612,6 +1616,7 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
           c64* part = (c64*)S.gpart;
           const float* g0 = gp_of(ga.p[0].G);
           const float* g1 = np > 1 ? gp_of(ga.p[1].G) : g0;
+          const int nsplit_tc = nsplit_of(np);
           for (int r0 = 0; r0 < nr; r0 += kTgN) {
             launch_pdl3(tc_vpack_kernel, dim3(cdiv(32 * nkc, 128), 1, np), 128, s, ga, r0, S.Vp);
             launch_pdl3s(slab3_gemm_tc_kernel, dim3(nrt, nsplit_tc, np), 128, kTgSmem, s, ga, g0,
