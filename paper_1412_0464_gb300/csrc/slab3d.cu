@@ -431,15 +431,70 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const FChain<R>
 }
 
 // The same panel elimination with the panel held in shared memory (blocks
-// small enough: B (PW + 1) elements): rows tid, tid + 1024, ... per thread,
-// panel rows padded to PW + 1 elements; per step a block-wide pivot-key
-// maximum (warp 0 then also forms the scaled pivot row: two block barriers
-// per pivot), and each thread's rank-1 update of its rows with the next
-// column's keys.  The colmods go to C [KO][B] at
-// the panel's slots.
+// small enough: B x LD elements, B < 2047; complex128, and complex64 blocks
+// too large for the register form below): rows tid, tid + 1024, ... per
+// thread, panel rows padded to LD = PW + 1 elements (an odd stride).  Two
+// block barriers per pivot:
+//  * each warp reduces its 32-bit pivot keys (redux.sync) into its key slot;
+//    after the first barrier every warp reduces the 32 slots itself, so that
+//    all threads know the pivot row r, and the first warp writes the scaled
+//    pivot row rho = S[r, :] / S[r][t] + e_t to shared memory;
+//  * after the second barrier every thread applies the rank-1 step
+//    row -= c_i rho to its rows (c_i = row[t], minus 1 on row r) and forms
+//    their keys for column t + 1.
+// The panel is loaded with cp.async (all of a thread's copies in flight at
+// once); the colmods go to C [KO][B] at the panel's slots.
 constexpr int kSmemPanelThreads = 1024;
+static_assert(kSmemPanelThreads == 32 * 32, "one key slot per warp, each warp reduces all slots");
 
-template <typename R, int PW>
+// 32-bit pivot key: the top 21 bits of |a|^2 (its exponent and leading 13
+// mantissa bits) above the reversed row index (11 bits, rows < 2047), so that
+// an unsigned maximum takes the largest magnitude, near-ties (within 2^-13)
+// going to the lowest row; every candidate's key is nonzero.
+__device__ __forceinline__ unsigned pivot_key32(float a2, int row) {
+  return ((__float_as_uint(a2) & 0x7fffffffu) >> 10 << 11) | (2047u - (unsigned)row);
+}
+
+template <typename R>
+__device__ __forceinline__ void cp_async_el3(cplx<R>* dst, const cplx<R>* src) {
+  if constexpr (sizeof(cplx<R>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// row[q] -= s pr[q], q < PW, for one padded panel row (4 FMAs per element);
+// pr is a separate buffer, so that the loads of both can run ahead of the
+// stores
+template <typename R, int PW, int LD>
+__device__ __forceinline__ void panel_row_update(cplx<R>* __restrict__ row,
+                                                 const cplx<R>* __restrict__ pr, cplx<R> s) {
+  if constexpr (sizeof(R) == 4 && LD % 2 == 0) {
+    float4* rv = reinterpret_cast<float4*>(row);
+    const float4* pv = reinterpret_cast<const float4*>(pr);
+#pragma unroll
+    for (int h = 0; h < PW / 2; ++h) {
+      float4 a = rv[h];
+      const float4 b = pv[h];
+      a.x = fmaf(-s.re, b.x, fmaf(s.im, b.y, a.x));
+      a.y = fmaf(-s.re, b.y, fmaf(-s.im, b.x, a.y));
+      a.z = fmaf(-s.re, b.z, fmaf(s.im, b.w, a.z));
+      a.w = fmaf(-s.re, b.w, fmaf(-s.im, b.z, a.w));
+      rv[h] = a;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+      cplx<R> a = row[q];
+      const cplx<R> b = pr[q];
+      a.re = fma(-s.re, b.re, fma(s.im, b.im, a.re));
+      a.im = fma(-s.re, b.im, fma(-s.im, b.re, a.im));
+      row[q] = a;
+    }
+  }
+}
+
+template <typename R, int PW, int LD>
 __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const FChain<R>* chains,
                                                                          int p0, int slot) {
   pdl_wait3();
@@ -448,70 +503,54 @@ __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const 
   if (p0 >= B) return;
   const int nbp = min(PW, B - p0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int LD = PW + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* P = (cplx<R>*)smem_raw;                                  // [B][LD]
-  unsigned long long* wkey = (unsigned long long*)(P + (size_t)B * LD);   // [32]
-  cplx<R>* rm = (cplx<R>*)(wkey + 32);                              // [PW]
-  int* shr = (int*)(rm + PW);                                       // [4]
-  unsigned char* flag = (unsigned char*)(shr + 4);                  // [B]
+  cplx<R>* P = (cplx<R>*)smem_raw;                          // [B][LD]
+  cplx<R>* rho = P + (size_t)B * LD;                        // [LD] scaled pivot row
+  unsigned* wkey = (unsigned*)(rho + LD);                   // [32]
+  unsigned char* flag = (unsigned char*)(wkey + 32);        // [B]
   for (int e = tid; e < B * PW; e += kSmemPanelThreads) {
     const int i = e / PW, q = e - i * PW;
-    P[i * LD + q] = q < nbp ? c.S[(size_t)i * B + p0 + q] : mk<R>(0, 0);
+    if (q < nbp)
+      cp_async_el3(P + i * LD + q, c.S + (size_t)i * B + p0 + q);
+    else
+      P[i * LD + q] = mk<R>(0, 0);
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   for (int i = tid; i < B; i += kSmemPanelThreads) flag[i] = c.pinv[i] >= 0;
   __syncthreads();
-  unsigned long long best = 0;
+  unsigned best = 0;
   for (int i = tid; i < B; i += kSmemPanelThreads)
-    if (!flag[i]) {
-      const unsigned long long k = pivot_key((float)cabs2(P[i * LD]), i);
-      best = k > best ? k : best;
-    }
+    if (!flag[i]) best = max(best, pivot_key32((float)cabs2(P[i * LD]), i));
   for (int t = 0; t < nbp; ++t) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
-      best = v > best ? v : best;
-    }
+    best = __reduce_max_sync(0xffffffffu, best);
     if (lane == 0) wkey[warp] = best;
     __syncthreads();
-    if (warp == 0) {   // pivot row of column t and its scaled panel row, in one warp
-      unsigned long long b = lane < kSmemPanelThreads / 32 ? wkey[lane] : 0ull;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
-        b = v > b ? v : b;
-      }
-      const int r = (int)(0xffffffffu - (unsigned)(b & 0xffffffffu));
+    const unsigned kb = __reduce_max_sync(0xffffffffu, wkey[lane]);
+    const int r = min(2047 - (int)(kb & 2047u), B - 1);
+    if (warp == 0 && lane < PW) {   // the scaled pivot row, one element per lane
+      const cplx<R>* pr = P + r * LD;
+      const cplx<R> inv = cinv(pr[t]);
+      rho[lane] = lane == t ? inv + mk<R>(1, 0) : pr[lane] * inv;
       if (lane == 0) {
-        shr[0] = r;
         flag[r] = 1;
         c.piv[p0 + t] = r;
         c.pinv[r] = p0 + t;
         c.prow[slot + t] = r;
-      }
-      if (lane < PW) {
-        const cplx<R> inv = cinv(P[r * LD + t]);
-        cplx<R> x = P[r * LD + lane] * inv;
-        if (lane == t) x = inv + mk<R>(1, 0);
-        rm[lane] = lane < nbp ? x : mk<R>(0, 0);
-        if (lane == 0) c.pinfo[slot + t] = inv;
+        c.pinfo[slot + t] = inv;
       }
     }
     __syncthreads();
-    const int r = shr[0];
     best = 0;
     for (int i = tid; i < B; i += kSmemPanelThreads) {
       cplx<R>* row = P + i * LD;
       cplx<R> ci = row[t];
       if (i == r) ci.re -= (R)1;
       c.C[(size_t)(slot + t) * B + i] = ci;
-#pragma unroll
-      for (int q = 0; q < PW; ++q) row[q] = row[q] - ci * rm[q];
-      if (t + 1 < nbp && !flag[i]) {
-        const unsigned long long k = pivot_key((float)cabs2(row[t + 1]), i);
-        best = k > best ? k : best;
-      }
+      panel_row_update<R, PW, LD>(row, rho, ci);
+      // the vector stores above and the element load below touch the same
+      // words: keep the compiler from reordering them
+      asm volatile("" ::: "memory");
+      if (t + 1 < nbp && !flag[i]) best = max(best, pivot_key32((float)cabs2(row[t + 1]), i));
     }
   }
   __syncthreads();
@@ -521,9 +560,180 @@ __global__ void __launch_bounds__(kSmemPanelThreads) gj_panel_smem_kernel(const 
   }
 }
 
-template <typename R, int PW>
+template <typename R, int PW, int LD>
 size_t panel_smem_bytes(int B) {
-  return (size_t)B * (PW + 1) * sizeof(cplx<R>) + 32 * 8 + PW * sizeof(cplx<R>) + 16 + B + 16;
+  return (size_t)(B + 1) * LD * sizeof(cplx<R>) + 32 * sizeof(unsigned) + B + 16;
+}
+
+template <int PW>
+size_t panel_reg_smem_bytes(int B) {
+  return (size_t)(B + 1) * (PW + 2) * sizeof(c64) + 32 * sizeof(unsigned) +
+         PW * (sizeof(c64) + sizeof(int)) + B + 16;
+}
+
+// complex64 panel elimination with rows held in registers.  The
+// shared-memory form above re-reads and re-writes the whole B x PW panel in
+// shared memory at every pivot, which its shared-memory bandwidth bounds;
+// here rows tid and tid + 512 of each of the 512 threads stay in registers
+// for all PW steps, and only rows from 1024 on (B > 1024) are updated in
+// shared memory.  The step loop is not unrolled (one copy of its body stays
+// in the instruction cache); the register rows' column t + 1, which gives
+// the next pivot key and the next colmod, is picked out during the update by
+// selects.  Two barriers per pivot as above: the warps reduce the pivot keys,
+// the thread holding row r writes rho = S[r, :] / S[r][t] + e_t to shared
+// memory, and every thread applies row -= c_i rho to its rows.  Shared
+// memory stages the panel in and out (coalesced), holds the rows beyond 1024
+// (padded to PW + 2 elements: 144-byte rows put eight consecutive rows'
+// 16-byte accesses on disjoint banks), and the pivot bookkeeping is written
+// out at the end.
+constexpr int kRegPanelThreads = 512;
+
+template <int PW>
+__global__ void __launch_bounds__(kRegPanelThreads) gj_panel_reg_kernel(const FChain<float>* chains,
+                                                                       int p0, int slot) {
+  constexpr int LD = PW + 2, T = kRegPanelThreads, NW = T / 32;
+  static_assert(PW % 2 == 0 && NW <= 32, "float4 pairs; one key slot per warp");
+  pdl_wait3();
+  const FChain<float> c = chains[blockIdx.x];
+  const int B = c.B;
+  if (p0 >= B) return;
+  const int nbp = min(PW, B - p0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c64* P = (c64*)smem_raw;                                  // [B][LD]
+  c64* rho = P + (size_t)B * LD;                            // [LD]
+  unsigned* wkey = (unsigned*)(rho + LD);                   // [32]
+  c64* sinv = (c64*)(wkey + 32);                            // [PW] 1 / pivot
+  int* spiv = (int*)(sinv + PW);                            // [PW] pivot rows
+  unsigned char* flag = (unsigned char*)(spiv + PW);        // [B] rows from 2 T on
+  for (int e = tid; e < B * PW; e += T) {
+    const int i = e / PW, q = e - i * PW;
+    if (q < nbp)
+      cp_async_el3(P + i * LD + q, c.S + (size_t)i * B + p0 + q);
+    else
+      P[i * LD + q] = mk<float>(0, 0);
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  const int i0 = tid, i1 = tid + T;
+  const bool has0 = i0 < B, has1 = i1 < B;
+  bool fl0 = !has0 || c.pinv[i0] >= 0;   // not (or no longer) a pivot candidate
+  bool fl1 = !has1 || c.pinv[i1] >= 0;
+  for (int i = tid + 2 * T; i < B; i += T) flag[i] = c.pinv[i] >= 0;
+  __syncthreads();
+  float4 a0[PW / 2], a1[PW / 2];   // rows i0, i1: (re, im) of columns 2h and 2h + 1
+  {
+    const float4* s0 = reinterpret_cast<const float4*>(P + (size_t)(has0 ? i0 : 0) * LD);
+    const float4* s1 = reinterpret_cast<const float4*>(P + (size_t)(has1 ? i1 : 0) * LD);
+#pragma unroll
+    for (int h = 0; h < PW / 2; ++h) {
+      a0[h] = s0[h];
+      a1[h] = s1[h];
+    }
+  }
+  c64 n0 = mk<float>(a0[0].x, a0[0].y), n1 = mk<float>(a1[0].x, a1[0].y);   // column t
+  unsigned best = 0;
+  if (!fl0) best = pivot_key32(cabs2(n0), i0);
+  if (!fl1) best = max(best, pivot_key32(cabs2(n1), i1));
+  for (int i = tid + 2 * T; i < B; i += T)
+    if (!flag[i]) best = max(best, pivot_key32(cabs2(P[i * LD]), i));
+  c64* Ccol = c.C + (size_t)slot * B;   // colmods of the panel's slots
+#pragma unroll 1
+  for (int t = 0; t < nbp; ++t) {
+    best = __reduce_max_sync(0xffffffffu, best);
+    if (lane == 0) wkey[warp] = best;
+    __syncthreads();
+    const unsigned kb = __reduce_max_sync(0xffffffffu, lane < NW ? wkey[lane] : 0u);
+    const int r = min(2047 - (int)(kb & 2047u), B - 1);
+    if ((r & (T - 1)) == tid) {   // this thread holds the pivot row
+      const int k = r / T;
+      float4* pr = reinterpret_cast<float4*>(P + (size_t)r * LD);
+      if (k == 0) {
+#pragma unroll
+        for (int h = 0; h < PW / 2; ++h) pr[h] = a0[h];
+        fl0 = true;
+      } else if (k == 1) {
+#pragma unroll
+        for (int h = 0; h < PW / 2; ++h) pr[h] = a1[h];
+        fl1 = true;
+      } else {
+        flag[r] = 1;
+      }
+      const c64 inv = cinv(P[(size_t)r * LD + t]);
+      float4* rv = reinterpret_cast<float4*>(rho);
+#pragma unroll 1
+      for (int h = 0; h < PW / 2; ++h) {
+        const float4 x = pr[h];
+        const c64 x0 = 2 * h == t ? inv + mk<float>(1, 0) : mk<float>(x.x, x.y) * inv;
+        const c64 x1 = 2 * h + 1 == t ? inv + mk<float>(1, 0) : mk<float>(x.z, x.w) * inv;
+        rv[h] = make_float4(x0.re, x0.im, x1.re, x1.im);
+      }
+      spiv[t] = r;
+      sinv[t] = inv;
+    }
+    __syncthreads();
+    const float4* rv = reinterpret_cast<const float4*>(rho);
+    c64 ci0 = n0, ci1 = n1;
+    if (i0 == r) ci0.re -= 1.f;
+    if (i1 == r) ci1.re -= 1.f;
+    if (has0) Ccol[(size_t)t * B + i0] = ci0;
+    if (has1) Ccol[(size_t)t * B + i1] = ci1;
+    const int hn = (t + 1) >> 1;
+    const bool odd = (t + 1) & 1;
+#pragma unroll
+    for (int h = 0; h < PW / 2; ++h) {   // both register rows; rho read once
+      const float4 b = rv[h];
+      a0[h].x = fmaf(-ci0.re, b.x, fmaf(ci0.im, b.y, a0[h].x));
+      a0[h].y = fmaf(-ci0.re, b.y, fmaf(-ci0.im, b.x, a0[h].y));
+      a0[h].z = fmaf(-ci0.re, b.z, fmaf(ci0.im, b.w, a0[h].z));
+      a0[h].w = fmaf(-ci0.re, b.w, fmaf(-ci0.im, b.z, a0[h].w));
+      a1[h].x = fmaf(-ci1.re, b.x, fmaf(ci1.im, b.y, a1[h].x));
+      a1[h].y = fmaf(-ci1.re, b.y, fmaf(-ci1.im, b.x, a1[h].y));
+      a1[h].z = fmaf(-ci1.re, b.z, fmaf(ci1.im, b.w, a1[h].z));
+      a1[h].w = fmaf(-ci1.re, b.w, fmaf(-ci1.im, b.z, a1[h].w));
+      if (h == hn) {
+        n0 = odd ? mk<float>(a0[h].z, a0[h].w) : mk<float>(a0[h].x, a0[h].y);
+        n1 = odd ? mk<float>(a1[h].z, a1[h].w) : mk<float>(a1[h].x, a1[h].y);
+      }
+    }
+    best = 0;
+    if (t + 1 < nbp) {
+      if (!fl0) best = pivot_key32(cabs2(n0), i0);
+      if (!fl1) best = max(best, pivot_key32(cabs2(n1), i1));
+    }
+    for (int i = tid + 2 * T; i < B; i += T) {
+      c64* row = P + (size_t)i * LD;
+      c64 ci = row[t];
+      if (i == r) ci.re -= 1.f;
+      Ccol[(size_t)t * B + i] = ci;
+      panel_row_update<float, PW, LD>(row, rho, ci);
+      // the vector stores above and the element load below touch the same
+      // words: keep the compiler from reordering them
+      asm volatile("" ::: "memory");
+      if (t + 1 < nbp && !flag[i]) best = max(best, pivot_key32(cabs2(row[t + 1]), i));
+    }
+  }
+  if (has0) {
+    float4* d0 = reinterpret_cast<float4*>(P + (size_t)i0 * LD);
+#pragma unroll
+    for (int h = 0; h < PW / 2; ++h) d0[h] = a0[h];
+  }
+  if (has1) {
+    float4* d1 = reinterpret_cast<float4*>(P + (size_t)i1 * LD);
+#pragma unroll
+    for (int h = 0; h < PW / 2; ++h) d1[h] = a1[h];
+  }
+  __syncthreads();
+  if (tid < nbp) {
+    const int r = spiv[tid];
+    c.piv[p0 + tid] = r;
+    c.pinv[r] = p0 + tid;
+    c.prow[slot + tid] = r;
+    c.pinfo[slot + tid] = sinv[tid];
+  }
+  for (int e = tid; e < B * PW; e += T) {
+    const int i = e / PW, q = e - i * PW;
+    if (q < nbp) c.S[(size_t)i * B + p0 + q] = P[i * LD + q];
+  }
 }
 
 // Pivot rows' other columns for the panel [p0, p0 + nbp), slots slot ..
@@ -1471,14 +1681,28 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
   // complex64 outer updates on the tensor cores (HZ_TEST_NO_TC=1: the FP32
   // SIMT kernel instead, for comparison)
   const bool use_tc = sizeof(R) == 4 && test_hook("HZ_TEST_NO_TC") <= 0;
-  // panels of 16 columns held in shared memory when a block's panel fits,
-  // else panels of NB columns eliminated in place in global memory
-  const size_t psm = panel_smem_bytes<R, 16>(Bmax);
-  const bool smem_panel = psm <= (size_t)225 * 1024;
+  // panels of 16 columns held in shared memory when a block's panel fits
+  // (complex64 rows padded to 18 elements for vector access where those fit,
+  // else to 17), else panels of NB columns eliminated in place in global memory
+  // (complex64 with 18-element rows: the register-resident form)
+  constexpr bool c64_path = std::is_same<R, float>::value;
+  const size_t psm_v = c64_path ? panel_reg_smem_bytes<16>(Bmax) : panel_smem_bytes<R, 16, 17>(Bmax);
+  const size_t psm_o = panel_smem_bytes<R, 16, 17>(Bmax);
+  const size_t smem_cap = (size_t)225 * 1024;
+  const bool smem_panel = Bmax < 2047 && psm_o <= smem_cap;   // 11-bit row field of the pivot keys
+  const bool vec_panel = smem_panel && psm_v <= smem_cap;
+  const size_t psm = vec_panel ? psm_v : psm_o;
+  void (*panel_fn)(const FChain<R>*, int, int) = gj_panel_smem_kernel<R, 16, 17>;
+  int panel_threads = kSmemPanelThreads;
+  if constexpr (c64_path) {
+    if (vec_panel) {
+      panel_fn = gj_panel_reg_kernel<16>;
+      panel_threads = kRegPanelThreads;
+    }
+  }
   const int nbw = smem_panel ? 16 : NB;
   if (smem_panel)
-    HZ_CU(cudaFuncSetAttribute(gj_panel_smem_kernel<R, 16>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+    HZ_CU(cudaFuncSetAttribute(panel_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
   auto layer = [&](const FChain<R>* d, int cnt, int nterm) {
     const dim3 gs(cdiv(Bmax, 128), Bmax, cnt);
     timed(h, "slab_factor3d_schur", 0.0, s, [&] {
@@ -1502,7 +1726,7 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
         const int slot = p0 - P0;
         timed(h, "slab_factor3d_panel", 0.0, s, [&] {
           if (smem_panel)
-            launch_pdl3s(gj_panel_smem_kernel<R, 16>, dim3(cnt), kSmemPanelThreads, psm, s, d, p0, slot);
+            launch_pdl3s(panel_fn, dim3(cnt), panel_threads, psm, s, d, p0, slot);
           else
             launch_pdl3(gj_panel_kernel<R>, dim3(cnt), kPanelThreads, s, d, p0, slot);
         });
