@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(kRegPanelThreads) gj_panel_reg_kernel(const FC
 // shared memory: Cp [NB][NB] (in-panel colmods at the pivot rows) and Cq
 // [NB][slot] (earlier slots).
 template <typename R, int PW>
-__global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains, int p0, int P0,
+__global__ void __launch_bounds__(128, sizeof(R) * PW <= 64 ? 7 : 1) gj_rowmod_kernel(const FChain<R>* chains, int p0, int P0,
                                                          int KBw) {
   pdl_wait3();
   // 32 columns per CTA; warp w takes a quarter of the earlier slots of the
@@ -769,14 +769,23 @@ __global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains,
     pr[t] = t < nbp ? c.prow[slot + t] : 0;
   }
   __syncthreads();
+  // the colmods at the pivot rows: scattered single elements, all of a
+  // thread's copies in flight at once (cp.async)
   for (int e = threadIdx.x; e < PW * PW; e += blockDim.x) {
     const int t = e / PW, q = e - t * PW;
-    Cp[e] = (t < nbp && q < t) ? c.C[(size_t)(slot + q) * B + pr[t]] : mk<R>(0, 0);
+    if (t < nbp && q < t)
+      cp_async_el3(Cp + e, c.C + (size_t)(slot + q) * B + pr[t]);
+    else
+      Cp[e] = mk<R>(0, 0);
   }
   for (int e = threadIdx.x; e < PW * slot; e += blockDim.x) {
     const int t = e / slot, q = e - t * slot;
-    Cq[e] = t < nbp ? c.C[(size_t)q * B + pr[t]] : mk<R>(0, 0);
+    if (t < nbp)
+      cp_async_el3(Cq + e, c.C + (size_t)q * B + pr[t]);
+    else
+      Cq[e] = mk<R>(0, 0);
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   const int j = blockIdx.x * 32 + lane;
   const bool live = j < B && (j < p0 || j >= p0 + nbp);
@@ -786,7 +795,8 @@ __global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains,
   for (int t = 0; t < PW; ++t) a[t] = mk<R>(0, 0);
   if (live && outside) {                          // this warp's quarter of the delayed sum
     const int qn = (slot + 3) / 4, q0 = warp * qn, q1 = min(slot, q0 + qn);
-#pragma unroll 4
+    constexpr int kUnroll = sizeof(cplx<R>) * PW <= 128 ? 8 : 4;   // loads in flight, within registers
+#pragma unroll kUnroll
     for (int q = q0; q < q1; ++q) {
       const cplx<R> x = c.Rm[(size_t)q * B + j];
 #pragma unroll
@@ -814,9 +824,15 @@ __global__ void __launch_bounds__(128) gj_rowmod_kernel(const FChain<R>* chains,
 #pragma unroll
   for (int t = 0; t < PW; ++t) {
     if (t < nbp) {
+      // two partial sums: half the dependent FMA chain of the recurrence
+      cplx<R> s0 = a[t], s1 = mk<R>(0, 0);
 #pragma unroll
-      for (int q = 0; q < t; ++q) a[t] = a[t] - Cp[t * PW + q] * a[q];
-      a[t] = a[t] * inv[t];
+      for (int q = 0; q + 1 < t; q += 2) {
+        s0 = s0 - Cp[t * PW + q] * a[q];
+        s1 = s1 - Cp[t * PW + q + 1] * a[q + 1];
+      }
+      if (t & 1) s0 = s0 - Cp[t * PW + t - 1] * a[t - 1];
+      a[t] = (s0 + s1) * inv[t];
       c.Rm[(size_t)(slot + t) * B + j] = a[t];
     }
   }
@@ -834,7 +850,7 @@ size_t rowmod_smem(int pw, int slot) {
 // columns (slots from base - P0); else the outer block's colmods and rowmods
 // (slots 0 .. depth) update every column outside the block.
 template <typename R>
-__global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains, int base,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) gj_update_kernel(const FChain<R>* chains, int base,
                                                         int width, int P0, int KBw, int inner) {
   pdl_wait3();
   const FChain<R> c = chains[blockIdx.z];
@@ -860,15 +876,23 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const FChain<R>* chains,
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = mk<R>(0, 0);
   for (int k0 = 0; k0 < depth; k0 += NB) {
-    for (int e = threadIdx.x; e < 64 * NB; e += 256) {
-      const int t = e / 64, q = e - t * 64;      // colmods [slot][B], rowmods [slot][B]
-      const bool ok = k0 + t < depth;
-      const size_t row = (size_t)(slot + k0 + t) * B;
-      Cs[q * (NB + 1) + t] = (ok && i0 + q < B) ? c.C[row + i0 + q] : mk<R>(0, 0);
-      Rs[t * 64 + q] = (ok && j0 + q < whi) ? c.Rm[row + j0 + q] : mk<R>(0, 0);
-    }
-    __syncthreads();
     const int tmax = min(NB, depth - k0);         // a 16-column panel fills half a chunk
+    // colmods [slot][B], rowmods [slot][B]: the chunk's tmax rows, all of a
+    // thread's copies in flight at once (cp.async)
+    for (int e = threadIdx.x; e < 64 * tmax; e += 256) {
+      const int t = e / 64, q = e - t * 64;
+      const size_t row = (size_t)(slot + k0 + t) * B;
+      if (i0 + q < B)
+        cp_async_el3(Cs + q * (NB + 1) + t, c.C + row + i0 + q);
+      else
+        Cs[q * (NB + 1) + t] = mk<R>(0, 0);
+      if (j0 + q < whi)
+        cp_async_el3(Rs + t * 64 + q, c.Rm + row + j0 + q);
+      else
+        Rs[t * 64 + q] = mk<R>(0, 0);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
 #pragma unroll 4
     for (int t = 0; t < tmax; ++t) {
       cplx<R> cv[4], rv[4];
