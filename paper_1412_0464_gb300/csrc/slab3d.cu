@@ -230,6 +230,9 @@ void build_slabs3d(hz_handle* h, Level& L, cudaStream_t s) {
       S.Gp = (float*)dmalloc(sizeof(float) * S.gp_layer * L.nz);
       HZ_CU(cudaMemsetAsync(S.Gp, 0, sizeof(float) * S.gp_layer * L.nz, s));
       S.Vp = (float*)dmalloc(sizeof(float) * 2 * nkc * 2048);
+      // zero padding (rows beyond B of the last chunk): the products with
+      // at most 32 right-hand sides write only the live entries
+      HZ_CU(cudaMemsetAsync(S.Vp, 0, sizeof(float) * 2 * nkc * 2048, s));
     }
   }
   L.mid = (L.nz - 1) / 2;
@@ -1229,6 +1232,11 @@ struct Prep3 {
   const cplx<R>* st;
   int np;
   Piece3<R> p[2];
+  // complex64 tensor-core products with at most 32 right-hand sides: out is
+  // written straight into the packed operand (TF32 hi/lo planes, the layout
+  // tc_vpack_kernel writes) instead, nkc chunks per piece; null otherwise
+  float* vp;
+  int nkc;
 };
 
 template <typename R>
@@ -1262,6 +1270,19 @@ __global__ void slab3_prep_kernel(Prep3<R> a) {
   cplx<R> v = P.base ? P.base[o] : mk<R>(0, 0);
   v.re += a.sgn * acc.re;
   v.im += a.sgn * acc.im;
+  if constexpr (std::is_same<R, float>::value) {
+    if (a.vp) {   // planes re hi, re lo, im hi, im lo of chunk b / 16, row r, k = b mod 16
+      float* q = a.vp + ((size_t)blockIdx.z * a.nkc + (b >> 4)) * 2048 + tc::kmajor_off(r, b & 15, 4) / 4;
+      float hi, lo;
+      tc::split_tf32(v.re, hi, lo);
+      q[0] = hi;
+      q[512] = lo;
+      tc::split_tf32(v.im, hi, lo);
+      q[1024] = hi;
+      q[1536] = lo;
+      return;
+    }
+  }
   P.out[o] = v;
 }
 
@@ -1843,6 +1864,13 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
     tg_attr = true;
   }
   const int nkc = cdiv(B, 16), nrt = cdiv(B, 128);
+  // one chunk of right-hand sides: the coupling kernel packs the operand
+  // itself (no tc_vpack_kernel launch per layer)
+  const bool fuse_pack = tcg && nr <= kTgN;
+  if (fuse_pack) {
+    pa.vp = S.Vp;
+    pa.nkc = nkc;
+  }
   // K splits of the tensor-core products: one wave of CTAs (one per SM), so
   // that no second, nearly empty wave follows
   auto nsplit_of = [&](int np) {
@@ -1866,10 +1894,13 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
           const float* g1 = np > 1 ? gp_of(ga.p[1].G) : g0;
           const int nsplit_tc = nsplit_of(np);
           for (int r0 = 0; r0 < nr; r0 += kTgN) {
-            launch_pdl3(tc_vpack_kernel, dim3(cdiv(32 * nkc, 128), 1, np), 128, s, ga, r0, S.Vp);
+            if (!fuse_pack) {
+              launch_pdl3(tc_vpack_kernel, dim3(cdiv(32 * nkc, 128), 1, np), 128, s, ga, r0, S.Vp);
+              h->launches++;
+            }
             launch_pdl3s(slab3_gemm_tc_kernel, dim3(nrt, nsplit_tc, np), 128, kTgSmem, s, ga, g0,
                          g1, nsplit_tc, (const float*)S.Vp, r0, part, h->dev_flag);
-            h->launches += 2;
+            h->launches++;
           }
           launch_pdl3(slab3_gemm_reduce_kernel<float>, dim3(cdiv(B, 128), nr, np), 128, s, ga,
                       nsplit_tc, (const c64*)part);
