@@ -1290,6 +1290,24 @@ __global__ void slab3_prep_kernel(Prep3<R> a) {
 // chains): y[r][i] = G[i][:] v[r][:] (mode 0) or y[r][i] - G[i][:] v[r][:]
 // (mode 1), r < NR.
 constexpr int kGemvRows = 4;
+// The coupling term of a chain's next layer step, computed by the reduction
+// of the current step (diagonal couplings, complex64 tensor-core path, one
+// chunk of right-hand sides): V' = base' + sgn * st' x, with x the layer just
+// solved, written packed into piece slot z of the next step.
+template <typename R>
+struct NextPiece {
+  const cplx<R>* st;         // [B] the next layer's coupling plane, null: no next step
+  const cplx<R>* base;       // [nr][B] or null
+  int z;
+};
+template <typename R>
+struct NextCpl {
+  float* vp;                 // packed operand of the next step, null: not fused
+  int nkc;
+  R sgn;
+  NextPiece<R> p[2];
+};
+
 template <typename R>
 struct GemvPiece {
   const cplx<R>* G;          // [B][B]
@@ -1434,7 +1452,8 @@ __global__ void __launch_bounds__(256) slab3_gemm_kernel(Gemv3<R> a, int nsplit,
 }
 
 template <typename R>
-__global__ void slab3_gemm_reduce_kernel(Gemv3<R> a, int nsplit, const cplx<R>* part) {
+__global__ void slab3_gemm_reduce_kernel(Gemv3<R> a, int nsplit, const cplx<R>* part,
+                                         NextCpl<R> nx) {
   pdl_wait3();
   const GemvPiece<R> P = blockIdx.z == 0 ? a.p[0] : a.p[1];
   const int B = a.B;
@@ -1444,7 +1463,28 @@ __global__ void slab3_gemm_reduce_kernel(Gemv3<R> a, int nsplit, const cplx<R>* 
   cplx<R> s = mk<R>(0, 0);
   for (int sp = 0; sp < nsplit; ++sp) s = s + pp[(size_t)sp * a.nr * B];
   cplx<R>* out = P.y + (size_t)r * B + i;
-  *out = a.mode == 0 ? s : *out - s;
+  const cplx<R> x = a.mode == 0 ? s : *out - s;
+  *out = x;
+  if constexpr (std::is_same<R, float>::value) {
+    // the next layer's right-hand side of this chain, written packed: the
+    // same arithmetic as slab3_prep_kernel with one diagonal coupling
+    const NextPiece<R> N = blockIdx.z == 0 ? nx.p[0] : nx.p[1];   // static parameter offsets
+    if (nx.vp && N.st) {
+      cplx<R> acc = mk<R>(0, 0);
+      cfma(acc, N.st[i], x);
+      cplx<R> v = N.base ? N.base[(size_t)r * B + i] : mk<R>(0, 0);
+      v.re += nx.sgn * acc.re;
+      v.im += nx.sgn * acc.im;
+      float* q = nx.vp + ((size_t)N.z * nx.nkc + (i >> 4)) * 2048 + tc::kmajor_off(r, i & 15, 4) / 4;
+      float hi, lo;
+      tc::split_tf32(v.re, hi, lo);
+      q[0] = hi;
+      q[512] = lo;
+      tc::split_tf32(v.im, hi, lo);
+      q[1024] = hi;
+      q[1536] = lo;
+    }
+  }
 }
 
 // The layer product on the tensor cores (complex64, more than four right-
@@ -1851,6 +1891,7 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
   auto prep = [&](int np) {
     pa.np = np;
     launch_pdl3(slab3_prep_kernel<R>, dim3(cdiv(B, 128), nr, np), 128, s, pa);
+    h->launches++;
   };
   // many right-hand sides: the split-K register-tiled GEMM and its reduction
   // (partial sums in the slab's GEMM scratch); few: the GEMV kernel
@@ -1883,7 +1924,33 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
   const int nI = cdiv(B, kG3Rows);
   // at least ~4 CTAs per SM (two pieces), so that the last wave is short
   const int nsplit = std::max(1, std::min(kG3MaxSplit, cdiv(4 * h->sms, 2 * nI)));
-  auto gemv = [&](int np, int mode) {
+  // complex64 tensor-core path with diagonal couplings: the reduction of a
+  // layer step also forms the next step's packed right-hand side, so that
+  // slab3_prep_kernel runs only for the first step of each sweep and the
+  // meeting layer.  next_of(t, fwd): the next step's coupling per piece.
+  const bool fuse_next = fuse_pack && pa.diag;
+  auto next_of = [&](int t, bool fwd) {
+    NextCpl<R> nx{};
+    if (!fuse_next || t + 1 >= T) return nx;
+    nx.vp = S.Vp;
+    nx.nkc = nkc;
+    nx.sgn = fwd ? (R)-1 : (R)1;
+    int z = 0, zn = 0;
+    for (int side = 0; side < 2; ++side) {
+      const int len = side == 0 ? ntop : nbot;
+      if (t >= len) continue;                 // this side has no step t
+      NextPiece<R>& N = nx.p[z++];
+      if (t + 1 >= len) continue;             // nor a step t + 1 (N.st stays null)
+      const int k = fwd ? (side == 0 ? t : nz - 1 - t) : (side == 0 ? m - 1 - t : m + 1 + t);
+      const int kn = side == 0 ? (fwd ? k + 1 : k - 1) : (fwd ? k - 1 : k + 1);
+      const int dz = (side == 0) == fwd ? -1 : +1;
+      N.st = pa.st + ((size_t)kn * 27 + qidx(dz, 0, 0)) * B;
+      N.base = fwd ? Yk(kn) : nullptr;
+      N.z = zn++;
+    }
+    return nx;
+  };
+  auto gemv = [&](int np, int mode, const NextCpl<R>& nx) {
     ga.np = np;
     ga.mode = mode;
     timed(h, "slab3_gemv", np * (gbytes + 2.0 * nr * B * el), s, [&] {
@@ -1903,13 +1970,13 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
             h->launches++;
           }
           launch_pdl3(slab3_gemm_reduce_kernel<float>, dim3(cdiv(B, 128), nr, np), 128, s, ga,
-                      nsplit_tc, (const c64*)part);
+                      nsplit_tc, (const c64*)part, nx);
         }
       } else if (tiled) {
         cplx<R>* part = (cplx<R>*)S.gpart;
         launch_pdl3(slab3_gemm_kernel<R>, dim3(nI, nsplit, np), 256, s, ga, nsplit, part);
         launch_pdl3(slab3_gemm_reduce_kernel<R>, dim3(cdiv(B, 128), nr, np), 128, s, ga, nsplit,
-                    (const cplx<R>*)part);
+                    (const cplx<R>*)part, NextCpl<R>{});
         h->launches++;
       } else {
         launch_pdl3(slab3_gemv_kernel<R, NR>, dim3(gblocks, np), 256, s, ga);
@@ -1917,6 +1984,7 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
     });
   };
   // forward: y_t = G_t (f_t - L_t y_{t-1}), both chains per launch
+  bool packed = false;   // this step's packed right-hand side written by the last reduction
   for (int t = 0; t < T; ++t) {
     int np = 0;
     for (int side = 0; side < 2; ++side) {
@@ -1932,8 +2000,10 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
       ++np;
     }
     pa.sgn = (R)-1;
-    prep(np);
-    gemv(np, 0);
+    if (!packed) prep(np);
+    const NextCpl<R> nx = next_of(t, true);
+    gemv(np, 0, nx);
+    packed = nx.vp != nullptr;
   }
   // meeting: x_m = G_m (f_m - C_m y_{m-1} - B_m y_{m+1})
   pa.p[0].base = Yk(m);
@@ -1944,7 +2014,8 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
   pa.sgn = (R)-1;
   prep(1);
   ga.p[0] = GemvPiece<R>{Gk(m), V, Yk(m)};
-  gemv(1, 0);
+  gemv(1, 0, NextCpl<R>{});
+  packed = false;
   // backward: x_t = y_t - G_t R_t x_{t+1}, outwards from the meeting layer
   for (int t = 0; t < T; ++t) {
     int np = 0;
@@ -1961,11 +2032,13 @@ void run_solve3d(hz_handle* h, Level& L, Slab& S, Rhs3<R> q, Out3<R> o, int nr, 
       ++np;
     }
     pa.sgn = (R)1;
-    prep(np);
-    gemv(np, 1);
+    if (!packed) prep(np);
+    const NextCpl<R> nx = next_of(t, false);
+    gemv(np, 1, nx);
+    packed = nx.vp != nullptr;
   }
   slab3_out_kernel<R><<<dim3(cdiv(B, 128), nz, nr), 128, 0, s>>>(o, S.W, L.ny, nz, Y, ldl);
-  h->launches += 2 + 2 * (2 * T + 1);
+  h->launches += 2 + (2 * T + 1);   // rhs and out kernels, one reduction or GEMV per step
   HZ_CU(cudaGetLastError());
 }
 
