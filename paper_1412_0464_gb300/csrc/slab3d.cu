@@ -287,8 +287,11 @@ __global__ void __launch_bounds__(128) schur_T_kernel(const FChain<R>* chains, i
   const int j = blockIdx.x * blockDim.x + threadIdx.x, a = blockIdx.y;
   if (j >= c.B || a >= c.B) return;
   const int W = c.W, yj = j / W, ej = j - yj * W;
-  const cplx<R>* Gp = c.G + (size_t)c.kp[term] * c.bstride + (size_t)a * c.B;
-  const cplx<R>* stp = c.st + (size_t)c.kp[term] * 27 * c.B;
+  // static indices into the descriptor's two-term arrays (a runtime index
+  // would copy the descriptor to local memory in every thread)
+  const int kp = term == 0 ? c.kp[0] : c.kp[1], dzR = term == 0 ? c.dzR[0] : c.dzR[1];
+  const cplx<R>* Gp = c.G + (size_t)kp * c.bstride + (size_t)a * c.B;
+  const cplx<R>* stp = c.st + (size_t)kp * 27 * c.B;
   cplx<R> acc = mk<R>(0, 0);
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(128) schur_T_kernel(const FChain<R>* chains, i
       const int eb = ej - dx;
       if (eb < 0 || eb >= W) continue;
       const int b = yb * W + eb;
-      cfma(acc, Gp[b], stp[(size_t)qidx(c.dzR[term], dy, dx) * c.B + b]);
+      cfma(acc, Gp[b], stp[(size_t)qidx(dzR, dy, dx) * c.B + b]);
     }
   }
   c.G[(size_t)c.k * c.bstride + (size_t)a * c.B + j] = acc;
@@ -322,7 +325,9 @@ __global__ void __launch_bounds__(128) schur_S_kernel(const FChain<R>* chains, i
   cplx<R> v = init ? d_entry(c, i, j) : *Sij;
   const cplx<R>* stk = c.st + (size_t)c.k * 27 * c.B;
   if (!fe) {
-    for (int t = 0; t < c.nterm; ++t) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {   // static indices into the two-term arrays
+      if (t >= c.nterm) break;
       const cplx<R> l = stk[(size_t)qidx(c.dzL[t], 0, 0) * c.B + i];
       const cplx<R> r = c.st[((size_t)c.kp[t] * 27 + qidx(c.dzR[t], 0, 0)) * c.B + j];
       const cplx<R> g = c.G[(size_t)c.kp[t] * c.bstride + (size_t)i * c.B + j];
@@ -330,6 +335,7 @@ __global__ void __launch_bounds__(128) schur_S_kernel(const FChain<R>* chains, i
     }
   } else if (term >= 0) {
     const int W = c.W, yi = i / W, ei = i - yi * W;
+    const int dzL = term == 0 ? c.dzL[0] : c.dzL[1];
     const cplx<R>* T = c.G + (size_t)c.k * c.bstride;
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(128) schur_S_kernel(const FChain<R>* chains, i
       for (int dx = -1; dx <= 1; ++dx) {
         const int ea = ei + dx;
         if (ea < 0 || ea >= W) continue;
-        const cplx<R> l = stk[(size_t)qidx(c.dzL[term], dy, dx) * c.B + i];
+        const cplx<R> l = stk[(size_t)qidx(dzL, dy, dx) * c.B + i];
         v = v - l * T[(size_t)(ya * W + ea) * c.B + j];
       }
     }
@@ -1327,7 +1333,7 @@ struct Gemv3 {
 template <typename R, int NR>
 __global__ void __launch_bounds__(256) slab3_gemv_kernel(Gemv3<R> a) {
   pdl_wait3();
-  const GemvPiece<R>& P = a.p[blockIdx.y];
+  const GemvPiece<R> P = blockIdx.y == 0 ? a.p[0] : a.p[1];   // static parameter offsets
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B = a.B;
   const int i0 = blockIdx.x * kGemvRows;
