@@ -213,9 +213,8 @@ hz_status hz_slab_solve(hz_handle* h, int j, const hz_c128* f_dev, hz_c128* u_de
  * mixed precision, n_rhs * N_t * W in FP64, plus segment carries) returns
  * HZ_EINVAL before any GPU work.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current
- * and keeps it; make that first call before any stream capture, and do not
- * call this entry point after cudaDeviceReset (the kept address would be
- * stale).  All calls share the one array and it keeps the last call's
+ * and keeps it; do not call this entry point after cudaDeviceReset (the kept
+ * address would be stale).  All calls share the one array and it keeps the last call's
  * contents: calls whose GPU work overlaps (two streams, two host threads)
  * race and give wrong results.  The call synchronises `stream` before
  * returning.  Requires hz_factor. */
