@@ -243,3 +243,31 @@ def test_slab_solve_3d_40_rhs_two_tensor_core_chunks():
         for r in (0, 17, 31, 32, 39):
             ref = sl.lu.solve(fd[r].ravel()).reshape(nt, sl.W)
             assert _close(ud[r], ref, TOL["mixed"]), (j, r, _rel(ud[r], ref))
+
+
+@pytest.mark.gpu
+def test_slab_solve_3d_blocks_beyond_1024_rows_mixed_matches_fp64():
+    """Dense blocks of more than 1024 unknowns (43 x 25 and 43 x 26): the
+    complex64 panels keep rows 1024 and up in shared memory beside the two
+    register rows of each thread, and the complex128 blocks are too large for
+    the shared-memory panel and take the global-memory one.  8 right-hand
+    sides run the tensor-core layer products, with the packed right-hand sides
+    formed by the coupling kernel and by the reductions.  At this size the
+    oracle's sparse LU of a slab takes too long, so the mixed solve is checked
+    against the FP64 solve (itself matched to the oracle at the sizes above)
+    within the complex64 tolerance."""
+    hz = _hz()
+    cfg = synth.scaled_workload(4, 36, w_out=4, J=2, n_src=8)
+    s64 = hz.Solver.from_workload(cfg, precision="fp64")
+    s64.factor()
+    s32 = hz.Solver.from_workload(cfg, precision="mixed")
+    s32.factor()
+    nt = cfg.shape[1] * cfg.shape[2]
+    for j in (1, 2):
+        W = s32.slab_info(j)["W"]
+        assert cfg.shape[1] * W > 1024
+        fd = torch.from_numpy(_rand((8, nt, W), 90 + j)).cuda()
+        u64 = s64.slab_solve(j, fd).cpu().numpy()
+        u32 = s32.slab_solve(j, fd).cpu().numpy()
+        for r in range(8):
+            assert _close(u32[r], u64[r], TOL["mixed"]), (j, r, _rel(u32[r], u64[r]))
