@@ -583,25 +583,24 @@ size_t panel_reg_smem_bytes(int B) {
 // complex64 panel elimination with rows held in registers.  The
 // shared-memory form above re-reads and re-writes the whole B x PW panel in
 // shared memory at every pivot, which its shared-memory bandwidth bounds;
-// here rows tid and tid + 512 of each of the 512 threads stay in registers
-// for all PW steps, and only rows from 1024 on (B > 1024) are updated in
+// here rows tid, tid + T, ..., tid + (NR - 1) T of each of the T threads stay
+// in registers for all PW steps (T = 512 with two rows, or 448 with three
+// for blocks of up to 1344 rows), and only rows from NR T on are updated in
 // shared memory.  The step loop is not unrolled (one copy of its body stays
 // in the instruction cache); the register rows' column t + 1, which gives
 // the next pivot key and the next colmod, is picked out during the update by
 // selects.  Two barriers per pivot as above: the warps reduce the pivot keys,
 // the thread holding row r writes rho = S[r, :] / S[r][t] + e_t to shared
 // memory, and every thread applies row -= c_i rho to its rows.  Shared
-// memory stages the panel in and out (coalesced), holds the rows beyond 1024
+// memory stages the panel in and out (coalesced), holds the rows beyond NR T
 // (padded to PW + 2 elements: 144-byte rows put eight consecutive rows'
 // 16-byte accesses on disjoint banks), and the pivot bookkeeping is written
 // out at the end.
-constexpr int kRegPanelThreads = 512;
-
-template <int PW>
-__global__ void __launch_bounds__(kRegPanelThreads) gj_panel_reg_kernel(const FChain<float>* chains,
-                                                                       int p0, int slot) {
-  constexpr int LD = PW + 2, T = kRegPanelThreads, NW = T / 32;
-  static_assert(PW % 2 == 0 && NW <= 32, "float4 pairs; one key slot per warp");
+template <int PW, int T, int NR>
+__global__ void __launch_bounds__(T) gj_panel_reg_kernel(const FChain<float>* chains, int p0,
+                                                         int slot) {
+  constexpr int LD = PW + 2, NW = T / 32;
+  static_assert(PW % 2 == 0 && T % 32 == 0 && NW <= 32, "float4 pairs; one key slot per warp");
   pdl_wait3();
   const FChain<float> c = chains[blockIdx.x];
   const int B = c.B;
@@ -614,7 +613,7 @@ __global__ void __launch_bounds__(kRegPanelThreads) gj_panel_reg_kernel(const FC
   unsigned* wkey = (unsigned*)(rho + LD);                   // [32]
   c64* sinv = (c64*)(wkey + 32);                            // [PW] 1 / pivot
   int* spiv = (int*)(sinv + PW);                            // [PW] pivot rows
-  unsigned char* flag = (unsigned char*)(spiv + PW);        // [B] rows from 2 T on
+  unsigned char* flag = (unsigned char*)(spiv + PW);        // [B] rows from NR T on
   for (int e = tid; e < B * PW; e += T) {
     const int i = e / PW, q = e - i * PW;
     if (q < nbp)
@@ -623,27 +622,26 @@ __global__ void __launch_bounds__(kRegPanelThreads) gj_panel_reg_kernel(const FC
       P[i * LD + q] = mk<float>(0, 0);
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
-  const int i0 = tid, i1 = tid + T;
-  const bool has0 = i0 < B, has1 = i1 < B;
-  bool fl0 = !has0 || c.pinv[i0] >= 0;   // not (or no longer) a pivot candidate
-  bool fl1 = !has1 || c.pinv[i1] >= 0;
-  for (int i = tid + 2 * T; i < B; i += T) flag[i] = c.pinv[i] >= 0;
-  __syncthreads();
-  float4 a0[PW / 2], a1[PW / 2];   // rows i0, i1: (re, im) of columns 2h and 2h + 1
-  {
-    const float4* s0 = reinterpret_cast<const float4*>(P + (size_t)(has0 ? i0 : 0) * LD);
-    const float4* s1 = reinterpret_cast<const float4*>(P + (size_t)(has1 ? i1 : 0) * LD);
+  bool fl[NR];                           // not (or no longer) a pivot candidate
 #pragma unroll
-    for (int h = 0; h < PW / 2; ++h) {
-      a0[h] = s0[h];
-      a1[h] = s1[h];
-    }
+  for (int k = 0; k < NR; ++k) fl[k] = tid + k * T >= B || c.pinv[tid + k * T] >= 0;
+  for (int i = tid + NR * T; i < B; i += T) flag[i] = c.pinv[i] >= 0;
+  __syncthreads();
+  float4 a[NR][PW / 2];   // rows tid + k T: (re, im) of columns 2h and 2h + 1
+  c64 n[NR];              // their column t
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    const int i = tid + k * T;
+    const float4* src = reinterpret_cast<const float4*>(P + (size_t)(i < B ? i : 0) * LD);
+#pragma unroll
+    for (int h = 0; h < PW / 2; ++h) a[k][h] = src[h];
+    n[k] = mk<float>(a[k][0].x, a[k][0].y);
   }
-  c64 n0 = mk<float>(a0[0].x, a0[0].y), n1 = mk<float>(a1[0].x, a1[0].y);   // column t
   unsigned best = 0;
-  if (!fl0) best = pivot_key32(cabs2(n0), i0);
-  if (!fl1) best = max(best, pivot_key32(cabs2(n1), i1));
-  for (int i = tid + 2 * T; i < B; i += T)
+#pragma unroll
+  for (int k = 0; k < NR; ++k)
+    if (!fl[k]) best = max(best, pivot_key32(cabs2(n[k]), tid + k * T));
+  for (int i = tid + NR * T; i < B; i += T)
     if (!flag[i]) best = max(best, pivot_key32(cabs2(P[i * LD]), i));
   c64* Ccol = c.C + (size_t)slot * B;   // colmods of the panel's slots
 #pragma unroll 1
@@ -653,20 +651,17 @@ __global__ void __launch_bounds__(kRegPanelThreads) gj_panel_reg_kernel(const FC
     __syncthreads();
     const unsigned kb = __reduce_max_sync(0xffffffffu, lane < NW ? wkey[lane] : 0u);
     const int r = min(2047 - (int)(kb & 2047u), B - 1);
-    if ((r & (T - 1)) == tid) {   // this thread holds the pivot row
-      const int k = r / T;
+    if (r % T == tid) {   // this thread holds the pivot row
+      const int kr = r / T;
       float4* pr = reinterpret_cast<float4*>(P + (size_t)r * LD);
-      if (k == 0) {
 #pragma unroll
-        for (int h = 0; h < PW / 2; ++h) pr[h] = a0[h];
-        fl0 = true;
-      } else if (k == 1) {
+      for (int k = 0; k < NR; ++k)
+        if (kr == k) {
 #pragma unroll
-        for (int h = 0; h < PW / 2; ++h) pr[h] = a1[h];
-        fl1 = true;
-      } else {
-        flag[r] = 1;
-      }
+          for (int h = 0; h < PW / 2; ++h) pr[h] = a[k][h];
+          fl[k] = true;
+        }
+      if (kr >= NR) flag[r] = 1;
       const c64 inv = cinv(P[(size_t)r * LD + t]);
       float4* rv = reinterpret_cast<float4*>(rho);
 #pragma unroll 1
@@ -681,55 +676,54 @@ __global__ void __launch_bounds__(kRegPanelThreads) gj_panel_reg_kernel(const FC
     }
     __syncthreads();
     const float4* rv = reinterpret_cast<const float4*>(rho);
-    c64 ci0 = n0, ci1 = n1;
-    if (i0 == r) ci0.re -= 1.f;
-    if (i1 == r) ci1.re -= 1.f;
-    if (has0) Ccol[(size_t)t * B + i0] = ci0;
-    if (has1) Ccol[(size_t)t * B + i1] = ci1;
+    c64 ci[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int i = tid + k * T;
+      ci[k] = n[k];
+      if (i == r) ci[k].re -= 1.f;
+      if (i < B) Ccol[(size_t)t * B + i] = ci[k];
+    }
     const int hn = (t + 1) >> 1;
     const bool odd = (t + 1) & 1;
 #pragma unroll
-    for (int h = 0; h < PW / 2; ++h) {   // both register rows; rho read once
+    for (int h = 0; h < PW / 2; ++h) {   // all register rows; rho read once
       const float4 b = rv[h];
-      a0[h].x = fmaf(-ci0.re, b.x, fmaf(ci0.im, b.y, a0[h].x));
-      a0[h].y = fmaf(-ci0.re, b.y, fmaf(-ci0.im, b.x, a0[h].y));
-      a0[h].z = fmaf(-ci0.re, b.z, fmaf(ci0.im, b.w, a0[h].z));
-      a0[h].w = fmaf(-ci0.re, b.w, fmaf(-ci0.im, b.z, a0[h].w));
-      a1[h].x = fmaf(-ci1.re, b.x, fmaf(ci1.im, b.y, a1[h].x));
-      a1[h].y = fmaf(-ci1.re, b.y, fmaf(-ci1.im, b.x, a1[h].y));
-      a1[h].z = fmaf(-ci1.re, b.z, fmaf(ci1.im, b.w, a1[h].z));
-      a1[h].w = fmaf(-ci1.re, b.w, fmaf(-ci1.im, b.z, a1[h].w));
-      if (h == hn) {
-        n0 = odd ? mk<float>(a0[h].z, a0[h].w) : mk<float>(a0[h].x, a0[h].y);
-        n1 = odd ? mk<float>(a1[h].z, a1[h].w) : mk<float>(a1[h].x, a1[h].y);
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        a[k][h].x = fmaf(-ci[k].re, b.x, fmaf(ci[k].im, b.y, a[k][h].x));
+        a[k][h].y = fmaf(-ci[k].re, b.y, fmaf(-ci[k].im, b.x, a[k][h].y));
+        a[k][h].z = fmaf(-ci[k].re, b.z, fmaf(ci[k].im, b.w, a[k][h].z));
+        a[k][h].w = fmaf(-ci[k].re, b.w, fmaf(-ci[k].im, b.z, a[k][h].w));
+        if (h == hn) n[k] = odd ? mk<float>(a[k][h].z, a[k][h].w) : mk<float>(a[k][h].x, a[k][h].y);
       }
     }
     best = 0;
     if (t + 1 < nbp) {
-      if (!fl0) best = pivot_key32(cabs2(n0), i0);
-      if (!fl1) best = max(best, pivot_key32(cabs2(n1), i1));
+#pragma unroll
+      for (int k = 0; k < NR; ++k)
+        if (!fl[k]) best = max(best, pivot_key32(cabs2(n[k]), tid + k * T));
     }
-    for (int i = tid + 2 * T; i < B; i += T) {
+    for (int i = tid + NR * T; i < B; i += T) {
       c64* row = P + (size_t)i * LD;
-      c64 ci = row[t];
-      if (i == r) ci.re -= 1.f;
-      Ccol[(size_t)t * B + i] = ci;
-      panel_row_update<float, PW, LD>(row, rho, ci);
+      c64 cs = row[t];
+      if (i == r) cs.re -= 1.f;
+      Ccol[(size_t)t * B + i] = cs;
+      panel_row_update<float, PW, LD>(row, rho, cs);
       // the vector stores above and the element load below touch the same
       // words: keep the compiler from reordering them
       asm volatile("" ::: "memory");
       if (t + 1 < nbp && !flag[i]) best = max(best, pivot_key32(cabs2(row[t + 1]), i));
     }
   }
-  if (has0) {
-    float4* d0 = reinterpret_cast<float4*>(P + (size_t)i0 * LD);
 #pragma unroll
-    for (int h = 0; h < PW / 2; ++h) d0[h] = a0[h];
-  }
-  if (has1) {
-    float4* d1 = reinterpret_cast<float4*>(P + (size_t)i1 * LD);
+  for (int k = 0; k < NR; ++k) {
+    const int i = tid + k * T;
+    if (i < B) {
+      float4* d = reinterpret_cast<float4*>(P + (size_t)i * LD);
 #pragma unroll
-    for (int h = 0; h < PW / 2; ++h) d1[h] = a1[h];
+      for (int h = 0; h < PW / 2; ++h) d[h] = a[k][h];
+    }
   }
   __syncthreads();
   if (tid < nbp) {
@@ -1786,9 +1780,10 @@ void factor_level3d(hz_handle* h, Level& L, cudaStream_t s) {
   void (*panel_fn)(const FChain<R>*, int, int) = gj_panel_smem_kernel<R, 16, 17>;
   int panel_threads = kSmemPanelThreads;
   if constexpr (c64_path) {
-    if (vec_panel) {
-      panel_fn = gj_panel_reg_kernel<16>;
-      panel_threads = kRegPanelThreads;
+    if (vec_panel) {   // all rows in registers up to 1344 (448 threads x 3), else 1024 of them
+      const bool three = Bmax > 1024 && Bmax <= 448 * 3;
+      panel_fn = three ? gj_panel_reg_kernel<16, 448, 3> : gj_panel_reg_kernel<16, 512, 2>;
+      panel_threads = three ? 448 : 512;
     }
   }
   const int nbw = smem_panel ? 16 : NB;

@@ -246,18 +246,20 @@ def test_slab_solve_3d_40_rhs_two_tensor_core_chunks():
 
 
 @pytest.mark.gpu
-def test_slab_solve_3d_blocks_beyond_1024_rows_mixed_matches_fp64():
-    """Dense blocks of more than 1024 unknowns (43 x 25 and 43 x 26): the
-    complex64 panels keep rows 1024 and up in shared memory beside the two
-    register rows of each thread, and the complex128 blocks are too large for
-    the shared-memory panel and take the global-memory one.  8 right-hand
-    sides run the tensor-core layer products, with the packed right-hand sides
-    formed by the coupling kernel and by the reductions.  At this size the
-    oracle's sparse LU of a slab takes too long, so the mixed solve is checked
-    against the FP64 solve (itself matched to the oracle at the sizes above)
-    within the complex64 tolerance."""
+@pytest.mark.parametrize("n", [36, 44])
+def test_slab_solve_3d_blocks_beyond_1024_rows_mixed_matches_fp64(n):
+    """Dense blocks of more than 1024 unknowns: 43 x 25 and 43 x 26 (n = 36),
+    51 x 29 and 51 x 30 (n = 44).  The complex64 panels hold three rows per
+    thread in registers up to 1344 rows, and beyond that two, with rows 1024
+    and up in shared memory.  The complex128 blocks are too large for the
+    shared-memory panel and take the global-memory one.  8 right-hand sides run
+    the tensor-core layer products, with the packed right-hand sides formed by
+    the coupling kernel and by the reductions.  At this size the oracle's
+    sparse LU of a slab takes too long, so the mixed solve is checked against
+    the FP64 solve (itself matched to the oracle at the sizes above) within
+    the complex64 tolerance."""
     hz = _hz()
-    cfg = synth.scaled_workload(4, 36, w_out=4, J=2, n_src=8)
+    cfg = synth.scaled_workload(4, n, w_out=4, J=2, n_src=8)
     s64 = hz.Solver.from_workload(cfg, precision="fp64")
     s64.factor()
     s32 = hz.Solver.from_workload(cfg, precision="mixed")
