@@ -249,9 +249,10 @@ def _short_kernel_name(name):
 
 
 def summarize_launches(csv_path):
-    """Markdown table of an ncu launch list: launches, total time and share per
-    kernel, and, when the capture has them, the mean DRAM rate and the mean
-    utilisations (DRAM, SM, FMA / FP64 / tensor pipes) over the kernel's launches."""
+    """Markdown table of an ncu launch list: launches, total time, share and mean
+    time per launch per kernel, and, when the capture has them, the mean DRAM
+    rate and the mean utilisations (DRAM, SM, FMA / FP64 / tensor pipes) over
+    the kernel's launches."""
     rows = _ncu_rows(csv_path)
     per = {}
     for lid, name, metric, v in rows:
@@ -271,13 +272,13 @@ def summarize_launches(csv_path):
              ("sm__pipe_fma_cycles", "FMA pipe %"), ("sm__pipe_fp64_cycles", "FP64 pipe %"),
              ("sm__pipe_tensor_cycles", "tensor pipe %")]
     have = [(p, h) for p, h in short if any(any(k.startswith(p) for k in a["u"]) for a in agg.values())]
-    hdr = "| kernel | launches | total (ms) | share |"
+    hdr = "| kernel | launches | total (ms) | share | per launch (us) |"
     if any(a["bytes"] > 0 for a in agg.values()):
         hdr += " DRAM GB/s |"
     hdr += "".join(f" {h} |" for _, h in have)
     lines = [hdr, "|" + "---|" * (hdr.count("|") - 1)]
     for k, a in sorted(agg.items(), key=lambda kv: -kv[1]["t"]):
-        row = f"| `{k}` | {a['n']} | {a['t'] / 1e6:.3f} | {a['t'] / tot:.3f} |"
+        row = f"| `{k}` | {a['n']} | {a['t'] / 1e6:.3f} | {a['t'] / tot:.3f} | {a['t'] / 1e3 / a['n']:.1f} |"
         if "DRAM GB/s" in hdr:
             row += f" {a['bytes'] / a['t'] if a['t'] else 0:.0f} |"
         for p, _ in have:

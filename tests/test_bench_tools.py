@@ -40,11 +40,11 @@ def test_summarize_launches_shares_rates_and_pipes(tmp_path):
     assert "DRAM GB/s" in t[0] and "FMA pipe %" in t[0]
     first = [c.strip() for c in t[2].split("|")]
     assert first[1] == "`slab_factor_fused_kernel<float, 6, 3, 5, 3>`"
-    assert first[2:5] == ["1", "3.000", "0.600"]           # 3 of 5 ms
+    assert first[2:6] == ["1", "3.000", "0.600", "3000.0"]   # 3 of 5 ms, one launch
     second = [c.strip() for c in t[3].split("|")]
-    assert second[2:5] == ["2", "2.000", "0.400"]
-    assert second[5] == "3"                                # 6 MB in 2 ms = 3 GB/s
-    assert second[6] == "8.0"                              # mean of 7 and 9
+    assert second[2:6] == ["2", "2.000", "0.400", "1000.0"]
+    assert second[6] == "3"                                # 6 MB in 2 ms = 3 GB/s
+    assert second[7] == "8.0"                              # mean of 7 and 9
 
 
 def test_traffic_record_applies_only_to_its_workload_and_sources(tmp_path, monkeypatch):
